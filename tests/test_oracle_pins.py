@@ -1,0 +1,256 @@
+"""Pins of the FP64 oracle against closed forms, invariants, special cases and brute force.
+
+Each test fixes a part of the oracle by something other than the oracle itself,
+chosen so that a dropped term, a wrong sign or index, or a transposed operand
+in that part fails it.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+import wpccc_inputs as wi
+from oracle import wpccc_oracle as O
+import brute_force as BF
+
+
+def _centre(Z, nl, grid, eps=None):
+    f = [wi.hydrogenic_radial(n, l, Z, grid.r) for n, l in nl]
+    e = np.zeros(len(nl)) if eps is None else np.asarray(eps, float)
+    return wi.centre_from_functions(Z, [l for n, l in nl], [n for n, l in nl], f, e)
+
+
+@pytest.fixture(scope="module")
+def grid():
+    return wi.radial_grid(2000)
+
+
+@pytest.fixture(scope="module")
+def tiny2c(grid):
+    T = _centre(1.0, [(1, 0), (2, 0), (2, 1)], grid)
+    P = _centre(2.0, [(1, 0), (2, 1)], grid)
+    return wi.Basis(grid=grid, T=T, P=P, quad=wi.make_quadrature(48, 48, 0.5), Z_T=1.0, Z_P=2.0)
+
+
+# ---------------------------------------------------------------- angular algebra
+def test_clebsch_gordan_known_values_and_orthogonality():
+    CG = O.clebsch_gordan
+    assert CG(1, 0, 1, 0, 0, 0) == pytest.approx(-1 / math.sqrt(3), abs=1e-15)
+    assert CG(1, 1, 1, -1, 0, 0) == pytest.approx(1 / math.sqrt(3), abs=1e-15)
+    assert CG(1, 0, 1, 0, 2, 0) == pytest.approx(math.sqrt(2 / 3), abs=1e-15)
+    assert CG(1, 1, 1, 0, 1, 1) == pytest.approx(1 / math.sqrt(2), abs=1e-15)
+    assert CG(2, 0, 1, 0, 1, 0) == pytest.approx(-math.sqrt(2 / 5), abs=1e-15)
+    assert CG(1, 0, 1, 0, 1, 0) == 0.0
+    # sum_{m1 m2} <j1 m1 j2 m2|J M><j1 m1 j2 m2|J' M'> = delta
+    for j1, j2 in [(2, 3), (1, 4), (3, 3)]:
+        for J in range(abs(j1 - j2), j1 + j2 + 1):
+            for Jp in range(abs(j1 - j2), j1 + j2 + 1):
+                for M in range(-min(J, Jp), min(J, Jp) + 1):
+                    s = sum(CG(j1, m1, j2, M - m1, J, M) * CG(j1, m1, j2, M - m1, Jp, M)
+                            for m1 in range(-j1, j1 + 1) if abs(M - m1) <= j2)
+                    assert s == pytest.approx(1.0 if J == Jp else 0.0, abs=1e-13)
+
+
+def test_wigner_d_closed_form_identity_and_group_law():
+    b = 0.73
+    c, s = math.cos(b), math.sin(b)
+    d1 = {(1, 1): (1 + c) / 2, (1, 0): -s / math.sqrt(2), (1, -1): (1 - c) / 2,
+          (0, 1): s / math.sqrt(2), (0, 0): c, (0, -1): -s / math.sqrt(2),
+          (-1, 1): (1 - c) / 2, (-1, 0): s / math.sqrt(2), (-1, -1): (1 + c) / 2}
+    for (mp, m), val in d1.items():
+        assert O.wigner_d(1, mp, m, b) == pytest.approx(val, abs=1e-15)
+    for l in range(5):
+        ms = range(-l, l + 1)
+        assert np.allclose([[O.wigner_d(l, a, c_, 0.0) for c_ in ms] for a in ms], np.eye(2 * l + 1), atol=1e-15)
+        A = np.array([[O.wigner_d(l, a, c_, 0.4) for c_ in ms] for a in ms])
+        B = np.array([[O.wigner_d(l, a, c_, 0.9) for c_ in ms] for a in ms])
+        C = np.array([[O.wigner_d(l, a, c_, 1.3) for c_ in ms] for a in ms])
+        assert np.allclose(A @ B, C, atol=1e-13)
+        assert np.allclose(A @ A.T, np.eye(2 * l + 1), atol=1e-13)
+
+
+def test_legendre_closed_forms_and_phase():
+    x = np.linspace(-0.95, 0.95, 7)
+    sq = np.sqrt(1 - x * x)
+    assert np.allclose(O.assoc_legendre(1, 1, x), -sq, atol=1e-15)
+    assert np.allclose(O.assoc_legendre(2, 1, x), -3 * x * sq, atol=1e-14)
+    assert np.allclose(O.assoc_legendre(2, 2, x), 3 * (1 - x * x), atol=1e-14)
+    assert np.allclose(O.assoc_legendre(2, -1, x), 0.5 * x * sq, atol=1e-14)
+    # normalisation: int Theta_lq^2 dx = 1
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    for l in range(5):
+        for q in range(-l, l + 1):
+            assert np.sum(wg * O.norm_legendre(l, q, xg) ** 2) == pytest.approx(1.0, abs=1e-13)
+
+
+# ---------------------------------------------------------------- interpolation and Eq. 7
+def test_interp5_exact_on_quartics_and_zero_outside(grid):
+    r = grid.r
+    poly = 0.3 - 1.1 * r + 0.07 * r ** 2 - 2e-3 * r ** 3 + 1e-5 * r ** 4
+    x = np.array([r[0] * 0.5, r[0], 0.0371, 1.234567, 17.0, 63.2, r[-3] + 1e-3, r[-1]])
+    want = 0.3 - 1.1 * x + 0.07 * x ** 2 - 2e-3 * x ** 3 + 1e-5 * x ** 4
+    got = O.interp5(r, poly[None, :], x)[0]
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-12)
+    assert O.interp5(r, poly[None, :], np.array([r[-1] * 1.0001]))[0, 0] == 0.0
+
+
+def test_radial_integral_1s1s_closed_form_converges():
+    # F_0(R) for 1s-1s = 1/R - (1 + 1/R) e^{-2R}; the grid rule is O(h^2) accurate
+    errs = []
+    for Nr in (1000, 2000, 4000):
+        g = wi.radial_grid(Nr)
+        f = wi.hydrogenic_radial(1, 0, 1.0, g.r)[None, :]
+        e = []
+        for R in (0.3, 1.04, 3.7, 12.0):
+            ex = 1 / R - (1 + 1 / R) * math.exp(-2 * R)
+            e.append(abs(O.radial_F(g, f, f, 0, R)[0] - ex))
+        errs.append(max(e))
+    assert errs[1] < 5e-5
+    assert 3.0 < errs[1] / errs[2] < 5.0          # second-order convergence
+
+
+def test_direct_1s1s_matches_closed_form(grid):
+    c = _centre(1.0, [(1, 0)], grid)
+    for b, z in [(0.5, 0.0), (1.0, -2.0), (3.0, 4.0)]:
+        R = math.hypot(b, z)
+        D = O.direct_block(grid, c, 1.0, R, z / R, other_at_minus_R=False)
+        assert D[0, 0] == pytest.approx(-(1 / R - (1 + 1 / R) * math.exp(-2 * R)), abs=5e-5)
+
+
+# ---------------------------------------------------------------- Eq. 6 structure
+def test_direct_hermitian_and_m_reflection(grid):
+    c = _centre(1.0, [(1, 0), (2, 1), (3, 2)], grid)
+    D = O.direct_block(grid, c, 1.0, 2.3, 0.4, other_at_minus_R=False)
+    assert np.allclose(D, D.T, atol=1e-14)
+    for i in range(c.N):
+        for j in range(c.N):
+            ii = [k for k in range(c.N) if c.st_rad[k] == c.st_rad[i] and c.st_m[k] == -c.st_m[i]][0]
+            jj = [k for k in range(c.N) if c.st_rad[k] == c.st_rad[j] and c.st_m[k] == -c.st_m[j]][0]
+            assert D[ii, jj] == pytest.approx((-1) ** int(c.st_m[i] - c.st_m[j]) * D[i, j], abs=1e-14)
+
+
+def test_direct_elements_brute_force(tiny2c):
+    T, P = tiny2c.T, tiny2c.P
+    for b, z in [(1.3, -0.7), (0.6, 2.2)]:
+        S, H = O.assemble(tiny2c, b, 1.0, z)
+        Ts = [(int(T.rad_n[T.st_rad[i]]), int(T.st_l[i]), int(T.st_m[i]), 1.0) for i in range(T.N)]
+        Ps = [(int(P.rad_n[P.st_rad[i]]), int(P.st_l[i]), int(P.st_m[i]), 2.0) for i in range(P.N)]
+        DT = BF.direct_elements(Ts, 2.0, b, z)
+        DP = BF.direct_elements(Ps, 1.0, b, z, centre_is_projectile=True)
+        assert np.abs(H[:T.N, :T.N] - DT).max() < 2e-5
+        assert np.abs(H[T.N:, T.N:] - DP).max() < 2e-5
+
+
+# ---------------------------------------------------------------- Eq. 8/9
+def test_two_centre_closed_forms_at_rest(grid):
+    # v = 0, 1s on both hydrogen centres: overlap e^{-R}(1+R+R^2/3), <1s_A|-1/r_A|1s_B> = -e^{-R}(1+R)
+    T = _centre(1.0, [(1, 0)], grid)
+    P = _centre(1.0, [(1, 0)], grid)
+    basis = wi.Basis(grid=grid, T=T, P=P, quad=wi.make_quadrature(48, 48, 0.5), Z_T=1.0, Z_P=1.0)
+    for b, z in [(0.4, 0.0), (1.5, 1.0), (2.0, -5.0)]:
+        R = math.hypot(b, z)
+        S, H = O.assemble(basis, b, 1e-300, z)  # v -> 0: phases are 1 (zero energies), ETF off
+        Smol, Qmol, Qtmol = O.molecular_integrals(basis, b, 0.0, z)
+        assert Smol[0, 0].real == pytest.approx(math.exp(-R) * (1 + R + R * R / 3), abs=1e-7)
+        assert Qmol[0, 0].real == pytest.approx(-math.exp(-R) * (1 + R), abs=1e-7)
+        assert Qtmol[0, 0].real == pytest.approx(-math.exp(-R) * (1 + R), abs=1e-7)
+        assert abs(Smol[0, 0].imag) < 1e-15
+
+
+@pytest.mark.parametrize("b,z,v", [(1.3, -0.7, 0.9), (0.5, 1.8, 2.0), (2.5, 0.3, 1.5)])
+def test_two_centre_brute_force(tiny2c, b, z, v):
+    T, P = tiny2c.T, tiny2c.P
+    S, H = O.assemble(tiny2c, b, v, z)
+    Ts = [(int(T.rad_n[T.st_rad[i]]), int(T.st_l[i]), int(T.st_m[i]), 1.0) for i in range(T.N)]
+    Ps = [(int(P.rad_n[P.st_rad[i]]), int(P.st_l[i]), int(P.st_m[i]), 2.0) for i in range(P.N)]
+    Sb, Qb, Qtb = BF.two_centre_elements(Ts, Ps, 1.0, 2.0, b, z, v)
+    NT = T.N
+    assert np.abs(S[:NT, NT:] - Sb).max() < 1e-8
+    assert np.abs(H[:NT, NT:] - Qb).max() < 1e-8
+    assert np.abs(H[NT:, :NT] - Qtb).max() < 1e-8
+    assert np.allclose(S[NT:, :NT], S[:NT, NT:].conj().T, atol=0)
+
+
+def test_far_limit_S_to_identity(tiny2c):
+    # radial functions vanish beyond r_max = 100: for R > 2 r_max every two-centre element is exactly 0
+    S, H = O.assemble(tiny2c, 1.0, 1.0, 250.0)
+    NT = tiny2c.T.N
+    assert np.array_equal(S, np.eye(tiny2c.N))
+    assert np.all(H[:NT, NT:] == 0) and np.all(H[NT:, :NT] == 0)
+    # and they decay like the slowest orbital (2p on Z=1: e^{-r/2}): small at R = 40, negligible at R = 80
+    S2, _ = O.assemble(tiny2c, 1.0, 1.0, 40.0)
+    S3, _ = O.assemble(tiny2c, 1.0, 1.0, 80.0)
+    assert np.abs(S2 - np.eye(tiny2c.N)).max() < 1e-6
+    assert np.abs(S3 - np.eye(tiny2c.N)).max() < 1e-13
+
+
+def test_energy_phases(grid):
+    T = _centre(1.0, [(1, 0), (2, 1)], grid, eps=[-0.5, -0.125])
+    basis = wi.Basis(grid=grid, T=T, P=None, quad=None, Z_T=1.0, Z_P=1.0)
+    T0 = _centre(1.0, [(1, 0), (2, 1)], grid)
+    b0 = wi.Basis(grid=grid, T=T0, P=None, quad=None, Z_T=1.0, Z_P=1.0)
+    z, v = 1.7, 0.8
+    _, H = O.assemble(basis, 1.0, v, z)
+    _, H0 = O.assemble(b0, 1.0, v, z)
+    # element (1s, 2p m) carries exp(i (eps_1s - eps_2p) z / v)
+    assert H[0, 2] == pytest.approx(H0[0, 2] * np.exp(1j * (-0.5 + 0.125) * z / v), abs=1e-15)
+
+
+# ---------------------------------------------------------------- solve and Algorithm 1
+def test_solve_residual(tiny2c):
+    S, H = O.assemble(tiny2c, 0.5, 1.2, 0.1)
+    X = O.solve(S, H)
+    assert np.abs(S @ X - H).max() < 1e-13 * max(1.0, np.abs(H).max())
+
+
+def test_rk4_one_step_is_taylor_polynomial():
+    rng = np.random.default_rng(0)
+    M = (rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6))) * 0.3
+    c0 = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    h = 0.37
+    got = O.rk4_path(lambda z: M, np.array([0.0, h]), c0)
+    want = sum(np.linalg.matrix_power(h * M, k) @ c0 / math.factorial(k) for k in range(5))
+    assert np.abs(got - want).max() < 1e-14
+
+
+def test_rk4_converges_to_matrix_exponential_propagation(tiny2c):
+    # tiny two-centre basis; reference: product of exp(h' M(z_mid)) with h' = h/64 (scipy expm)
+    b, v = 1.0, 1.5
+    Mf = lambda z: O.coupling_M(tiny2c, b, v, z)
+    z0, z1 = -3.0, 3.0
+    c0 = O.initial_state(tiny2c)
+    zf = np.linspace(z0, z1, 12 * 64 + 1)
+    ref = c0.copy()
+    for a, bb in zip(zf[:-1], zf[1:]):
+        ref = expm((bb - a) * Mf(0.5 * (a + bb))) @ ref
+    e = []
+    for n in (12, 24, 48):
+        c = O.rk4_path(Mf, np.linspace(z0, z1, n + 1), c0)
+        e.append(np.abs(c - ref).max())
+    # exp-midpoint reference itself carries an O(h'^2) error: compare the RK4 sequence's convergence
+    assert e[2] < 1e-4
+    assert e[0] > e[1] > e[2]
+
+
+def test_one_centre_unitarity():
+    # S = I and D Hermitian: |c|^2 is conserved up to RK4's (h w)^6/72 per step
+    g = wi.radial_grid(1000)
+    T = _centre(1.0, [(1, 0), (2, 0), (2, 1)], g, eps=[-0.5, -0.125, -0.125])
+    basis = wi.Basis(grid=g, T=T, P=None, quad=None, Z_T=1.0, Z_P=1.0)
+    zg = wi.uniform_zgrid(-6.0, 6.0, 0.01)
+    c = O.propagate(basis, 0.8, 1.0, zg)
+    assert abs(np.vdot(c, c).real - 1.0) < 1e-10
+    P = O.probabilities(c)
+    # m <-> -m reflection: P(2p, m=+1) == P(2p, m=-1)
+    assert P[2] == pytest.approx(P[4], abs=1e-14)
+    assert P[1] > 1e-6 and P[3] > 1e-6  # the collision does excite
+
+
+def test_two_centre_m_reflection_of_probabilities(tiny2c):
+    c = O.propagate(tiny2c, 1.0, 1.5, wi.uniform_zgrid(-4.0, 4.0, 0.2))
+    P = O.probabilities(c)
+    T, Pc = tiny2c.T, tiny2c.P
+    idx = lambda cen, off, rad, m: off + [k for k in range(cen.N) if cen.st_rad[k] == rad and cen.st_m[k] == m][0]
+    assert P[idx(T, 0, 2, 1)] == pytest.approx(P[idx(T, 0, 2, -1)], rel=1e-10, abs=1e-15)
+    assert P[idx(Pc, T.N, 1, 1)] == pytest.approx(P[idx(Pc, T.N, 1, -1)], rel=1e-10, abs=1e-15)

@@ -1,0 +1,349 @@
+"""Seeded / deterministic input generators shared by the oracle and the CUDA path.
+
+This module builds the *inputs* of the close-coupling calculation and nothing
+of the method itself: the radial grid with its integration weights, the
+radial basis functions tabulated on that grid (hydrogenic bound states and
+Coulomb wave-packet pseudostates), their energies, the state list, the
+Gauss-Laguerre / Gauss-Legendre quadrature rules used in the two-centre
+integrals, and the straight-line paths (impact parameters, velocity, z-grid).
+
+None of the method's arithmetic (Eq. 6-9 matrix elements, Eq. 4 solve,
+Algorithm 1 propagation) lives here; the oracle and the CUDA library each
+implement that on their own and only consume what is built here.
+
+The basis functions themselves are defined in the WP-CCC literature the paper
+cites (its Sec. II refers to earlier work for the formalism); the reading used
+here is: bound states are the closed-form hydrogenic radial functions, and a
+wave-packet pseudostate of angular momentum l on the k-bin [k_i, k_{i+1}] is
+(k_{i+1}-k_i)^(-1/2) * integral over the bin of the delta(k-k')-normalised
+regular Coulomb function u_kl(r)/r, with energy (k_i^2 + k_i k_{i+1} +
+k_{i+1}^2)/6.  Pseudostates are then orthonormalised on the grid against the
+bound states of the same l (Gram-Schmidt), so the tabulated basis is
+orthonormal under the grid's own quadrature.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy import special
+from scipy.interpolate import CubicSpline
+
+__all__ = [
+    "RadialGrid", "Centre", "Basis", "Quadrature", "Paths",
+    "radial_grid", "hydrogenic_radial", "coulomb_bins", "make_centre",
+    "make_basis", "make_quadrature", "uniform_zgrid", "geometric_zgrid",
+    "make_paths", "CONFIGS", "config_inputs",
+]
+
+
+# --------------------------------------------------------------------------
+# radial grid (Sec. II: r-grid from 0 to ~100 a.u., denser near the origin)
+# --------------------------------------------------------------------------
+@dataclass
+class RadialGrid:
+    r: np.ndarray        # [Nr] strictly increasing, r[0] > 0, r[-1] = rmax
+    w: np.ndarray        # [Nr] integration weights: sum_i w_i g(r_i) ~ int_0^rmax g dr
+    rmax: float
+    alpha: float
+
+
+def radial_grid(Nr: int = 2000, rmax: float = 100.0, alpha: float = 3.5) -> RadialGrid:
+    """sinh-mapped grid r_i = rmax sinh(alpha i/Nr)/sinh(alpha), i = 1..Nr.
+
+    Weights are the trapezoid rule in the mapped variable x = i/Nr times the
+    Jacobian dr/dx (the x = 0 end point, r = 0, is dropped: every integrand the
+    method forms carries a factor r^2 there).  The trapezoid rule is used
+    because its weights stay a valid rule for any split of the range at a grid
+    node, which the min(r,R)/max(r,R) kernel of Eq. 7 requires.
+    """
+    i = np.arange(1, Nr + 1, dtype=np.float64)
+    x = i / Nr
+    r = rmax * np.sinh(alpha * x) / math.sinh(alpha)
+    jac = rmax * alpha * np.cosh(alpha * x) / math.sinh(alpha)
+    w = jac / Nr
+    w[-1] *= 0.5
+    r[-1] = rmax
+    return RadialGrid(r=r, w=w, rmax=float(rmax), alpha=float(alpha))
+
+
+# --------------------------------------------------------------------------
+# radial functions
+# --------------------------------------------------------------------------
+def hydrogenic_radial(n: int, l: int, Z: float, r: np.ndarray) -> np.ndarray:
+    """Closed-form hydrogenic R_nl(r), normalised so int r^2 R^2 dr = 1."""
+    rho = 2.0 * Z * r / n
+    norm = math.sqrt((2.0 * Z / n) ** 3 * math.factorial(n - l - 1)
+                     / (2.0 * n * math.factorial(n + l)))
+    return norm * np.exp(-rho / 2.0) * rho ** l * special.eval_genlaguerre(n - l - 1, 2 * l + 1, rho)
+
+
+def _coulomb_regular(Z: float, l: int, ks: np.ndarray, rmatch: float, dr: float):
+    """delta(k-k')-normalised regular Coulomb functions u_kl(r) on a uniform grid.
+
+    Outward Numerov for u'' = (l(l+1)/r^2 - 2Z/r - k^2) u from a power-series
+    start, normalised to the local WKB amplitude sqrt(2k/(pi*kappa(r))) over the
+    last few wavelengths before rmatch.
+    """
+    n = int(math.ceil(rmatch / dr))
+    ru = dr * np.arange(n + 1)
+    k2 = ks[None, :] ** 2
+    u = np.zeros((n + 1, ks.size))
+    # series u = r^{l+1} (1 + a1 r + a2 r^2 + a3 r^3)
+    a1 = -Z / (l + 1)
+    a2 = (-2.0 * Z * a1 - k2) / (2.0 * (2 * l + 3))
+    a3 = (-2.0 * Z * a2 - k2 * a1) / (3.0 * (2 * l + 4))
+    for i in (1, 2):
+        x = ru[i]
+        u[i] = x ** (l + 1) * (1.0 + a1 * x + a2 * x * x + a3 * x ** 3)
+    h2 = dr * dr / 12.0
+
+    def g(i):
+        x = ru[i]
+        return l * (l + 1) / (x * x) - 2.0 * Z / x - k2[0]
+
+    gm, g0 = g(1), g(2)
+    for i in range(2, n):
+        gp = g(i + 1)
+        u[i + 1] = (2.0 * (1.0 + 5.0 * h2 * g0) * u[i] - (1.0 - h2 * gm) * u[i - 1]) / (1.0 - h2 * gp)
+        gm, g0 = g0, gp
+    # amplitude match over the tail
+    tail = slice(int(0.8 * n), n)
+    rt = ru[tail]
+    du = (u[2:] - u[:-2])[tail.start - 1:tail.stop - 1] / (2.0 * dr)
+    kap = np.sqrt(k2 + 2.0 * Z / rt[:, None] - l * (l + 1) / rt[:, None] ** 2)
+    amp2 = u[tail] ** 2 + (du / kap) ** 2
+    want = 2.0 * ks[None, :] / (np.pi * kap)
+    scale = np.sqrt(np.mean(want, axis=0) / np.mean(amp2, axis=0))
+    return ru, u * scale[None, :]
+
+
+def coulomb_bins(Z: float, l: int, kmax: float, nbins: int, r: np.ndarray,
+                 nk: int = 16, rmatch: float = 200.0, dr: float = 0.01):
+    """Wave-packet pseudostates on uniform k-bins of (0, kmax]; returns (f[nbins, Nr], eps[nbins])."""
+    edges = np.linspace(0.0, kmax, nbins + 1)
+    xg, wg = np.polynomial.legendre.leggauss(nk)
+    ks, wk, owner = [], [], []
+    for i in range(nbins):
+        a, b = edges[i], edges[i + 1]
+        ks.append(0.5 * (b - a) * xg + 0.5 * (a + b))
+        wk.append(0.5 * (b - a) * wg)
+        owner.append(np.full(nk, i))
+    ks, wk, owner = np.concatenate(ks), np.concatenate(wk), np.concatenate(owner)
+    ru, u = _coulomb_regular(Z, l, ks, max(rmatch, r[-1] + 10.0), dr)
+    spl = CubicSpline(ru, u, axis=0)
+    ur = spl(r)                                    # [Nr, nk*nbins]
+    f = np.zeros((nbins, r.size))
+    for i in range(nbins):
+        sel = owner == i
+        dk = edges[i + 1] - edges[i]
+        f[i] = (ur[:, sel] * wk[sel][None, :]).sum(axis=1) / r / math.sqrt(dk)
+    eps = (edges[:-1] ** 2 + edges[:-1] * edges[1:] + edges[1:] ** 2) / 6.0
+    return f, eps
+
+
+# --------------------------------------------------------------------------
+# one centre's basis and the two-centre basis
+# --------------------------------------------------------------------------
+@dataclass
+class Centre:
+    Z: float                 # nuclear charge of this centre
+    rad_l: np.ndarray        # [n_rad] int, angular momentum of each radial function
+    rad_n: np.ndarray        # [n_rad] int, principal number (bound) or 100+bin index (pseudostate)
+    f: np.ndarray            # [n_rad, Nr] radial functions on the grid
+    rad_eps: np.ndarray      # [n_rad] energies
+    st_rad: np.ndarray       # [N] radial index of each state
+    st_l: np.ndarray         # [N]
+    st_m: np.ndarray         # [N]
+    st_eps: np.ndarray       # [N]
+
+    @property
+    def n_rad(self) -> int:
+        return int(self.rad_l.size)
+
+    @property
+    def N(self) -> int:
+        return int(self.st_rad.size)
+
+
+def _orthonormalise(funcs: list, grid: RadialGrid, fixed: int) -> list:
+    """Gram-Schmidt under the grid inner product; the first `fixed` functions are kept as they are."""
+    wr2 = grid.w * grid.r ** 2
+    out = list(funcs[:fixed])
+    for f in funcs[fixed:]:
+        g = f.copy()
+        for _ in range(2):
+            for q in out:
+                g -= (np.sum(wr2 * q * g) / np.sum(wr2 * q * q)) * q
+        g /= math.sqrt(np.sum(wr2 * g * g))
+        out.append(g)
+    return out
+
+
+def make_centre(Z: float, nmax: int, lmax: int, nbins: int, kmax: float,
+                grid: RadialGrid, all_m: bool = True) -> Centre:
+    """Bound hydrogenic n<=nmax and `nbins` Coulomb pseudostates per l<=lmax, on a centre of charge Z.
+
+    Radial functions are ordered by l, then bound states by n, then bins by k.
+    States are ordered by radial function, then m = -l..l (all_m) or 0..l.
+    """
+    rad_l, rad_n, f, eps = [], [], [], []
+    for l in range(lmax + 1):
+        fl, el, nl = [], [], []
+        for n in range(l + 1, nmax + 1):
+            fl.append(hydrogenic_radial(n, l, Z, grid.r))
+            el.append(-Z * Z / (2.0 * n * n))
+            nl.append(n)
+        nbound = len(fl)
+        if nbins > 0:
+            fb, eb = coulomb_bins(Z, l, kmax, nbins, grid.r)
+            fl.extend(list(fb))
+            el.extend(list(eb))
+            nl.extend([100 + i for i in range(nbins)])
+        fl = _orthonormalise(fl, grid, nbound)
+        rad_l += [l] * len(fl)
+        rad_n += nl
+        f += fl
+        eps += el
+    rad_l = np.array(rad_l, dtype=np.int32)
+    st_rad, st_l, st_m = [], [], []
+    for i, l in enumerate(rad_l):
+        for m in (range(-l, l + 1) if all_m else range(0, l + 1)):
+            st_rad.append(i)
+            st_l.append(int(l))
+            st_m.append(m)
+    eps = np.array(eps, dtype=np.float64)
+    st_rad = np.array(st_rad, dtype=np.int32)
+    return Centre(Z=float(Z), rad_l=rad_l, rad_n=np.array(rad_n, dtype=np.int32),
+                  f=np.ascontiguousarray(np.array(f, dtype=np.float64)), rad_eps=eps,
+                  st_rad=st_rad, st_l=np.array(st_l, dtype=np.int32),
+                  st_m=np.array(st_m, dtype=np.int32), st_eps=eps[st_rad].copy())
+
+
+def centre_from_functions(Z: float, rad_l, rad_n, f, eps, all_m: bool = True) -> Centre:
+    """A centre from explicitly given radial functions (used for tiny test bases)."""
+    rad_l = np.asarray(rad_l, dtype=np.int32)
+    eps = np.asarray(eps, dtype=np.float64)
+    st_rad, st_l, st_m = [], [], []
+    for i, l in enumerate(rad_l):
+        for m in (range(-l, l + 1) if all_m else range(0, l + 1)):
+            st_rad.append(i)
+            st_l.append(int(l))
+            st_m.append(m)
+    st_rad = np.array(st_rad, dtype=np.int32)
+    return Centre(Z=float(Z), rad_l=rad_l, rad_n=np.asarray(rad_n, dtype=np.int32),
+                  f=np.ascontiguousarray(np.asarray(f, dtype=np.float64)), rad_eps=eps,
+                  st_rad=st_rad, st_l=np.array(st_l, dtype=np.int32),
+                  st_m=np.array(st_m, dtype=np.int32), st_eps=eps[st_rad].copy())
+
+
+@dataclass
+class Quadrature:
+    """Gauss-Laguerre in s (eta = 1 + s/(gamma R)) and Gauss-Legendre in tau (Eq. 9)."""
+    s: np.ndarray           # [Geta] Laguerre nodes
+    ws: np.ndarray          # [Geta] Laguerre weights times e^{s} (computed in log space)
+    tau: np.ndarray         # [Gtau]
+    wtau: np.ndarray        # [Gtau]
+    gamma: float            # eta scale
+
+    @property
+    def G(self) -> int:
+        return int(self.s.size * self.tau.size)
+
+
+def make_quadrature(Geta: int = 48, Gtau: int = 48, gamma: float = 0.5) -> Quadrature:
+    s, w = special.roots_laguerre(Geta)
+    ws = np.exp(np.log(w) + s)
+    tau, wtau = np.polynomial.legendre.leggauss(Gtau)
+    return Quadrature(s=s.astype(np.float64), ws=ws, tau=tau, wtau=wtau, gamma=float(gamma))
+
+
+@dataclass
+class Basis:
+    grid: RadialGrid
+    T: Centre
+    P: Centre | None              # None in one-centre mode
+    quad: Quadrature | None
+    Z_T: float                    # charge of the target nucleus
+    Z_P: float                    # charge of the projectile nucleus
+
+    @property
+    def n_centres(self) -> int:
+        return 1 if self.P is None else 2
+
+    @property
+    def N(self) -> int:
+        return self.T.N + (0 if self.P is None else self.P.N)
+
+
+def make_basis(Z_T: float, Z_P: float, nmax, lmax, nbins, kmax, two_centre: bool,
+               Nr: int = 2000, rmax: float = 100.0, alpha: float = 3.5,
+               Geta: int = 48, Gtau: int = 48, gamma: float = 0.5, all_m: bool = True) -> Basis:
+    """nmax/lmax/nbins/kmax may be scalars (same on both centres) or (target, projectile) pairs."""
+    def pair(x):
+        return (x, x) if np.isscalar(x) else tuple(x)
+    nmax, lmax, nbins, kmax = pair(nmax), pair(lmax), pair(nbins), pair(kmax)
+    grid = radial_grid(Nr, rmax, alpha)
+    T = make_centre(Z_T, nmax[0], lmax[0], nbins[0], kmax[0], grid, all_m)
+    P = make_centre(Z_P, nmax[1], lmax[1], nbins[1], kmax[1], grid, all_m) if two_centre else None
+    quad = make_quadrature(Geta, Gtau, gamma) if two_centre else None
+    return Basis(grid=grid, T=T, P=P, quad=quad, Z_T=float(Z_T), Z_P=float(Z_P))
+
+
+# --------------------------------------------------------------------------
+# paths
+# --------------------------------------------------------------------------
+def uniform_zgrid(z0: float, z1: float, h: float) -> np.ndarray:
+    n = int(round((z1 - z0) / h))
+    return z0 + h * np.arange(n + 1, dtype=np.float64)
+
+
+def geometric_zgrid(zmin: float = 1e-3, zmax: float = 100.0, nz: int = 500) -> np.ndarray:
+    """Sec. II z-grid: zgrid[i] = zmin (zmax/zmin)^(i/nz), zgrid[0] = 0, zgrid[-i] = -zgrid[i]."""
+    i = np.arange(1, nz + 1, dtype=np.float64)
+    pos = zmin * (zmax / zmin) ** (i / nz)
+    return np.concatenate([-pos[::-1], [0.0], pos])
+
+
+@dataclass
+class Paths:
+    b: np.ndarray                     # [n_paths]
+    v: np.ndarray                     # [n_paths]
+    z: list = field(default_factory=list)   # n_paths arrays of z nodes (ascending)
+
+    @property
+    def n_paths(self) -> int:
+        return int(self.b.size)
+
+
+def make_paths(bs, v, zgrid) -> Paths:
+    bs = np.asarray(bs, dtype=np.float64)
+    vs = np.broadcast_to(np.asarray(v, dtype=np.float64), bs.shape).copy()
+    return Paths(b=bs, v=vs, z=[np.asarray(zgrid, dtype=np.float64).copy() for _ in bs])
+
+
+# --------------------------------------------------------------------------
+# the workloads (synthetic stand-ins for the paper's p + H calculations)
+# --------------------------------------------------------------------------
+CONFIGS = {
+    # one-centre p + H, direct elements only
+    "p_H_1c_n3l2": dict(Z_T=1.0, Z_P=1.0, nmax=3, lmax=2, nbins=5, kmax=2.0, two_centre=False,
+                        v=1.0, b=(0.5, 8.0, 8), z=(-40.0, 40.0, 0.1)),
+    # two-centre p + H with electron capture
+    "p_H_2c_n4l3": dict(Z_T=1.0, Z_P=1.0, nmax=4, lmax=3, nbins=10, kmax=3.0, two_centre=True,
+                        v=1.5, b=(0.2, 12.0, 32), z=(-50.0, 50.0, 0.1)),
+}
+
+
+def config_inputs(name: str, **over):
+    """(basis, paths) of a named workload; keyword overrides shrink it for tests."""
+    c = dict(CONFIGS[name])
+    c.update(over)
+    basis = make_basis(c["Z_T"], c["Z_P"], c["nmax"], c["lmax"], c["nbins"], c["kmax"],
+                       c["two_centre"], Nr=c.get("Nr", 2000), rmax=c.get("rmax", 100.0),
+                       Geta=c.get("Geta", 48), Gtau=c.get("Gtau", 48), gamma=c.get("gamma", 0.5))
+    b0, b1, nb = c["b"]
+    z0, z1, h = c["z"]
+    paths = make_paths(np.linspace(b0, b1, nb), c["v"], uniform_zgrid(z0, z1, h))
+    return basis, paths
