@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Throughput of the WP-CCC hot path on GB300: RK4 steps per second.
+
+Workload: the two-centre p + H calculation (Z_T = Z_P = 1): hydrogenic n <= 4
+plus 10 Coulomb wave-packet pseudostates per l <= 3 on each centre (N_T = N_P =
+190, N = 380 coupled amplitudes), a 48 x 48 Gauss-Laguerre x Gauss-Legendre
+(eta, tau) rule, v = 1.5 a.u., 32 impact parameters uniform in [0.2, 12] a.u.,
+z from -50 to 50 a.u. with h = 0.1 (1000 RK4 steps per path).  Inputs are
+synthetic (generated basis, straight-line paths).
+
+One bench step advances all 32 paths by STEP_RK4 consecutive RK4 steps through
+the public call wpccc_propagate (matrix elements at every z it needs, the solve
+S X = H, the RK4 sweep), in plain FP64.  `value` counts RK4 steps of all paths
+on all ranks per second of device time; `e2e` times the same work with the
+amplitudes copied in from pinned host memory and the probabilities copied back
+every step.
+
+--impl reference times the FP64 CPU oracle (the test oracle of this repository)
+on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched/mixed vs plain FP64 RK4 steps/s at ≤1e-6 prob error; % FP64 peak"
+UNIT = "RK4 steps/s"
+WORKLOAD = "p_H_2c_n4l3"
+STEP_RK4 = 16           # RK4 steps of every path per bench step
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_DFMA_MEASURED_TFLOPS = 1.20   # FMA microbenchmark on this machine's GB300 (all SMs, register operands)
+CONFIG_DESC = ("two-centre p+H (Z_T=Z_P=1): hydrogenic n<=4 + 10 Coulomb wave-packet bins per l<=3 (k<=3) "
+               "on each centre, all m, N_T=N_P=190, N=380; 48x48 (eta,tau) nodes; Nr=2000 to 100 a.u.; "
+               "v=1.5; 32 b uniform in [0.2,12]; z in [-50,50], h=0.1")
+
+
+def _reasons(mask: int) -> list:
+    names = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+             0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+             0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+    return [n for b, n in names.items() if mask & b]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active"
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 4:
+                try:
+                    self.samples.append((float(parts[0]), float(parts[1]), float(parts[2]), int(parts[3], 16)))
+                except ValueError:
+                    pass
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        mask = 0
+        for s in self.samples:
+            mask |= s[3]
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples),
+                "sm_max_mhz": max(s[1] for s in self.samples),
+                "power_w_max": max(s[2] for s in self.samples),
+                "reasons": _reasons(mask & ~0x1), "samples": len(self.samples)}
+
+
+def cpu_oracle_rate(basis, paths, n_steps: int, path_index: int = 16) -> dict:
+    """The FP64 oracle, as it stands, on one path for n_steps RK4 steps (host cores)."""
+    from oracle import wpccc_oracle as O
+    b = float(paths.b[path_index])
+    v = float(paths.v[path_index])
+    zg = paths.z[path_index]
+    k0 = 500 - n_steps // 2                      # steps around closest approach
+    seg = zg[k0:k0 + n_steps + 1]
+    c0 = O.initial_state(basis)
+    t0 = time.perf_counter()
+    O.rk4_path(lambda z: O.coupling_M(basis, b, v, z), seg, c0)
+    dt = time.perf_counter() - t0
+    threads = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max(int(i.get("num_threads", 1)) for i in threadpool_info()) or threads
+    except Exception:
+        pass
+    return {"value": n_steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"1 path (b={b:.3f}), {n_steps} RK4 steps around z=0 of the same workload, "
+                      f"{dt:.1f} s; numpy/LAPACK with {threads} threads"}
+
+
+def run_reference(args) -> None:
+    import wpccc_inputs as wi
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    basis, paths = wi.config_inputs(WORKLOAD)
+    per_step = 2                                  # RK4 steps of one path per bench step
+    for _ in range(args.warmup):
+        cpu_oracle_rate(basis, paths, per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_rate(basis, paths, per_step)
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    cb = cpu_oracle_rate(basis, paths, per_step)
+    cb["value"] = value
+    cb["sample"] = f"each step: 1 path, {per_step} RK4 steps of the same workload"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": CONFIG_DESC, "form": "FP64 CPU oracle"},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import wpccc_inputs as wi
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    basis, paths = wi.config_inputs(WORKLOAD)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(basis, paths, 12)
+
+    import paper_2403_04252_gb300 as w
+    g = w.Basis(basis, device=local)
+    N, n_paths = g.N, paths.n_paths
+    zg = paths.z[0]
+    n_total = zg.size - 1
+    b = paths.b
+    v = paths.v
+    stream = torch.cuda.current_stream(dev)
+
+    def segment(k: int):
+        k0 = (k * STEP_RK4) % (n_total - STEP_RK4 + 1)
+        return zg[k0:k0 + STEP_RK4 + 1]
+
+    c = torch.zeros((n_paths, N), dtype=torch.complex128, device=dev)
+    c[:, 0] = 1.0
+    for k in range(args.warmup):
+        g.propagate(b, v, segment(k), c=c)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    # ---- device-timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    g.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        g.propagate(b, v, segment(args.warmup + k), c=c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = g.profile_read()
+    g.profile_enable(False)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    units = world * n_paths * STEP_RK4 * args.steps
+    value = units / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    c_host = torch.zeros((n_paths, N), dtype=torch.complex128).pin_memory()
+    c_host[:, 0] = 1.0
+    P_host = torch.empty((n_paths, N), dtype=torch.float64).pin_memory()
+    c_dev = torch.empty((n_paths, N), dtype=torch.complex128, device=dev)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        c_dev.copy_(c_host, non_blocking=True)
+        g.propagate(b, v, segment(args.warmup + k), c=c_dev)
+        P = w.probabilities(c_dev)
+        P_host.copy_(P, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    seg_bytes = 8 * (STEP_RK4 + 1) * n_paths + 8 * 2 * n_paths + 4 * n_paths  # z nodes, b, v, n_z
+    h2d = c_host.numel() * 16 + seg_bytes
+    d2h = P_host.numel() * 8
+
+    # ---- roofline of the dominant kernel (FP64 pipe)
+    NT, NP_, G = basis.T.N, basis.P.N, basis.quad.G
+    evals = args.steps * n_paths * (2 * STEP_RK4 + 1)
+    flops_mol = 12.0 * NT * NP_ * G            # Eq. 9 contraction, three integrals, per z
+    flops_solve = (8.0 / 3.0 + 8.0) * N ** 3    # LU + N right-hand sides, per z
+    cand = {"mol_gemm": flops_mol * evals, "solve": flops_solve * evals}
+    dom = max(cand, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    achieved = cand[dom] / (dom_ms / 1e3) / 1e12
+    total_flops = (flops_mol + flops_solve) * evals + 32.0 * N * N * n_paths * STEP_RK4 * args.steps
+    launches = int(sum(n for _, n in prof.values())) + 0
+    roofline = {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm", "solve": "k_lu_solve"}[dom],
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
+                               f"measured DFMA microbenchmark {FP64_DFMA_MEASURED_TFLOPS} TFLOP/s",
+                "launch_ms_avg": dom_ms / max(dom_launches, 1),
+                "flop_per_launch": cand[dom] / max(dom_launches, 1)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CONFIG_DESC, "form": "plain FP64 (batched over all paths)",
+                       "bench_step": f"{STEP_RK4} RK4 steps of each of the {n_paths} paths per rank",
+                       "l2": "inputs larger than L2: S and H of one step are "
+                             f"{2 * 16 * N * N * n_paths * (2 * STEP_RK4 + 1) / 1e9:.1f} GB"},
+            "roofline": roofline,
+            "fp64_frac_whole_step": total_flops / (ms / 1e3) * world / 1e12 / FP64_PEAK_TFLOPS / world,
+            "matrix_elements_per_s": world * evals * (NT * NT + NP_ * NP_ + 3 * NT * NP_) / (ms / 1e3),
+            "kernel_ms": {k: v_[0] for k, v_ in prof.items()},
+            "e2e": {"value": world * n_paths * STEP_RK4 * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clocks}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

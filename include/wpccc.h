@@ -1,0 +1,233 @@
+/*
+ * wpccc.h -- C ABI of the GB300 (sm_103a) implementation of the hot path of the
+ * wave-packet convergent-close-coupling (WP-CCC) method for ion-atom collisions
+ * (Abdurakhmanov, Antonio, Cytowski, Kadyrov, "Portable GPU implementation of the
+ * WP-CCC ion-atom collisions code", arXiv:2403.04252).
+ *
+ * The paper's most expensive part (Sec. II, Eq. 1) is the set of coupled
+ * first-order equations
+ *
+ *     i v [[I, K], [K^+, I]] d/dz [F; G] = [[D_T, Q], [Q~, D_P]] [F; G]
+ *
+ * along straight-line projectile paths (impact parameter b, speed v, position z).
+ * Written as dX/dz = M X with M = -(i/v) S^{-1} H (Eq. 2-4), it is advanced by
+ * classical RK4 (Algorithm 1).  In this header
+ *   S = [[I, K], [K^+, I]]       overlap matrix       (paper: the matrix left of d/dz)
+ *   H = [[D_T, Q], [Q~, D_P]]    coupling matrix      (paper: the matrix on the right)
+ *   X = S^{-1} H                 solution of the linear system (paper: ZGESV)
+ *   c = [F; G]                   amplitudes (paper: the solution vector X of Eq. 2-3)
+ *
+ * Conventions shared by every call:
+ *   - complex numbers are two doubles (re, im), i.e. C99 double _Complex /
+ *     cuDoubleComplex / numpy complex128;
+ *   - N x N matrices are column-major (LAPACK layout), element (i, j) at i + j*N;
+ *     a batch of matrices is contiguous, matrix k at offset k*N*N elements;
+ *   - state order is: every target state, then every projectile state, each in
+ *     the order given in wpccc_centre_desc;
+ *   - pointers documented "host" are read during the call only and may be freed
+ *     after it returns; pointers documented "device" are owned by the caller and
+ *     must stay valid until the work queued on `stream` has finished;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     calls are asynchronous with respect to the host unless stated otherwise;
+ *   - every call returns a wpccc_status and never aborts; on failure
+ *     wpccc_last_error() describes the cause.  A call that fails argument
+ *     checking queues no GPU work.
+ *
+ * Atomic units throughout (hbar = m_e = e = 1).
+ */
+#ifndef WPCCC_H
+#define WPCCC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define WPCCC_API __attribute__((visibility("default")))
+#else
+#define WPCCC_API
+#endif
+
+typedef enum {
+    WPCCC_OK = 0,
+    WPCCC_EINVAL = 1,      /* invalid argument (null pointer, size out of range, inconsistent basis) */
+    WPCCC_ENOMEM = 2,      /* device or host allocation failed */
+    WPCCC_ESINGULAR = 3,   /* a linear system had an exactly zero pivot (ZGESV info > 0) */
+    WPCCC_ENONFINITE = 4,  /* amplitudes became NaN or infinite during propagation */
+    WPCCC_ECUDA = 5,       /* a CUDA runtime call or kernel launch failed */
+    WPCCC_EUNSUPPORTED = 6 /* a mode this build does not provide */
+} wpccc_status;
+
+/* Largest orbital angular momentum a basis may hold, and largest system size. */
+#define WPCCC_LMAX 10
+#define WPCCC_NMAX 3072
+
+/* Opaque handle: the basis and every z-independent table, resident on one device. */
+typedef struct wpccc_basis_s* wpccc_basis;
+
+/*
+ * One centre's basis (Sec. II, first paragraph: bound eigenstates plus
+ * wave-packet pseudostates).  A state is a radial function f_{nl}(r) times a
+ * spherical harmonic Y_{lm} quantised along the projectile velocity.  All
+ * pointers are host pointers.
+ */
+typedef struct {
+    double Z;              /* charge of this centre's nucleus (the projectile's charge for the
+                              projectile centre; in one-centre mode only P.Z is read) */
+    int n_rad;             /* number of radial functions, >= 1 */
+    const int* rad_l;      /* [n_rad] orbital angular momentum of each radial function, 0..WPCCC_LMAX */
+    const double* f;       /* [n_rad][Nr] row-major: f_a(r_i), the radial function on the r-grid,
+                              normalised so that sum_i w_i r_i^2 f_a(r_i)^2 = 1 */
+    int n_states;          /* number of states on this centre */
+    const int* st_rad;     /* [n_states] radial function of each state */
+    const int* st_m;       /* [n_states] magnetic quantum number, |m| <= l */
+    const double* st_eps;  /* [n_states] energy of each state */
+} wpccc_centre_desc;
+
+/*
+ * The whole expansion basis and the quadrature rules.  Host pointers.
+ * Two-centre mode requires every radial function of each centre to appear with
+ * all 2l+1 values of m (the molecular-frame integrals are evaluated for q >= 0
+ * and completed by the q -> -q reflection).
+ */
+typedef struct {
+    int n_centres;         /* 1: one-centre (Eq. 5, no solve), 2: two-centre (Eq. 4) */
+    int Nr;                /* r-grid points, >= 5 */
+    const double* r;       /* [Nr] strictly increasing radii, r[0] > 0 (Sec. II: 0..~100 a.u.) */
+    const double* w;       /* [Nr] integration weights of the grid (used for Eq. 7) */
+    wpccc_centre_desc T;   /* target centre */
+    wpccc_centre_desc P;   /* projectile centre (only P.Z is read when n_centres == 1) */
+    int Geta;              /* Gauss-Laguerre points for eta in Eq. 9 (ignored in one-centre mode) */
+    const double* s;       /* [Geta] Laguerre nodes */
+    const double* ws;      /* [Geta] Laguerre weights times exp(s) */
+    int Gtau;              /* Gauss-Legendre points for tau in Eq. 9 */
+    const double* tau;     /* [Gtau] nodes on (-1, 1) */
+    const double* wtau;    /* [Gtau] weights */
+    double gamma;          /* eta = 1 + s / (gamma * R) maps the Laguerre variable onto [1, inf) */
+} wpccc_basis_desc;
+
+/*
+ * A set of straight-line paths.  Host pointers.  Path p has speed v[p] > 0,
+ * impact parameter b[p] > 0 and n_z[p] >= 1 strictly increasing z nodes
+ * z[off_p .. off_p + n_z[p] - 1] with off_p = n_z[0] + ... + n_z[p-1]; it is
+ * advanced by n_z[p] - 1 RK4 steps (Algorithm 1; the paper's z-grid of Sec. II
+ * or any other grid).
+ */
+typedef struct {
+    int n_paths;
+    const double* b;
+    const double* v;
+    const int* n_z;
+    const double* z;
+} wpccc_paths;
+
+/*
+ * Builds a basis on `device`.  As in Sec. II, every z- and b-independent table is
+ * made once and kept in device memory for all later calls: this uploads the r-grid,
+ * the radial functions, energies and quadrature rules, and computes on the GPU the
+ * radial multipole table F_{n'l'nl lambda}(r_i) of Eq. 7 at every grid radius and
+ * the angular coefficients of Eq. 6.  Synchronous.  On success *out owns device
+ * memory until wpccc_basis_destroy.  Errors: EINVAL (inconsistent description),
+ * ENOMEM, ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_basis_create(const wpccc_basis_desc* desc, int device, wpccc_basis* out);
+
+/* Frees everything the basis owns.  Synchronises the basis' device first.  NULL is accepted. */
+WPCCC_API wpccc_status wpccc_basis_destroy(wpccc_basis basis);
+
+/* Sizes of the basis: N_T target states, N_P projectile states (0 in one-centre mode). */
+WPCCC_API wpccc_status wpccc_basis_info(wpccc_basis basis, int* N_T, int* N_P);
+
+/*
+ * Matrix elements at nz projectile positions of one path (Eq. 1, 6-9):
+ *   S[k] = [[I, K], [K^+, I]],  H[k] = [[D_T, Q], [Q~, D_P]]  at z = z[k]
+ * with every element between states i and j carrying exp(i (eps_i - eps_j) z / v).
+ *   D_T: Eq. 6 with the projectile charge, F of Eq. 7 interpolated at R = sqrt(b^2+z^2)
+ *        by 5-point Lagrange interpolation on the r-grid;
+ *   D_P: the same expansion about the projectile with the target charge at -R;
+ *   K, Q, Q~: Eq. 9 on the (eta, tau) rule with the ETF phase exp(i v z eta tau / 2)
+ *        and J_{q-q'}, rotated to the collision frame by Eq. 8; Q carries -Z_T/r_T,
+ *        Q~ (lower-left block) carries -Z_P/r_P.
+ * In one-centre mode S[k] = I and H[k] = D_T.
+ *   z      host   [nz] positions
+ *   S, H   device [nz][N][N] complex128, column-major; fully overwritten
+ * Errors: EINVAL (nz < 1, b <= 0, v <= 0, null pointers), ENOMEM, ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_matrix_elements(wpccc_basis basis, double b, double v, int nz, const double* z,
+                                   void* S, void* H, void* stream);
+
+/*
+ * Batched complex solve S X = H with partial pivoting (Sec. II: the paper calls
+ * LAPACK/cuSOLVER/hipSOLVER ZGESV; this is a hand-written blocked LU).
+ *   S     device [batch][N][N] complex128; overwritten by the factors L and U of
+ *         P S = L U (unit lower L below the diagonal), as ZGETRF leaves them
+ *   H     device [batch][N][N] complex128; overwritten by X (when info[k] == 0)
+ *   ipiv  device [batch][N] int32; 1-based pivot rows as in LAPACK: row i was
+ *         interchanged with row ipiv[i]
+ *   info  device [batch] int32; 0 on success, k > 0 if U(k,k) is exactly zero (the
+ *         factorisation is completed, H[k] holds no solution)
+ *   precision_mode 0 = FP64 throughout (the only mode of this build)
+ * The per-system outcome is only in `info`; the call itself returns OK once the
+ * work is queued.  Errors: EINVAL (N < 1 or N > WPCCC_NMAX, batch < 0), EUNSUPPORTED
+ * (precision_mode != 0), ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv, int* info,
+                         int precision_mode, void* stream);
+
+/*
+ * Propagates the amplitudes of every path through Algorithm 1: RK4 along the
+ * path's z nodes with M = -(i/v) S^{-1} H evaluated at z, at the step midpoint
+ * and at the next node (Eq. 2-4; Eq. 5, M = -(i/v) D_T, in one-centre mode).
+ *   c  device [n_paths][N] complex128: in, the amplitudes at each path's first
+ *      node (Algorithm 1 starts from c = (1, 0, ..., 0)); out, the amplitudes at
+ *      its last node.
+ *   precision_mode 0 = FP64 throughout; batch_mode 0 = all paths batched
+ *   together in chunks of RK4 steps (the only modes of this build).
+ * Blocks until the work is finished: the library allocates its scratch memory
+ * itself (kept with the basis for reuse) and checks the pivots and the
+ * amplitudes at the end.
+ * Errors: EINVAL, EUNSUPPORTED, ENOMEM, ESINGULAR (some S had a zero pivot),
+ * ENONFINITE (amplitudes became non-finite), ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_propagate(wpccc_basis basis, const wpccc_paths* paths, int precision_mode,
+                             int batch_mode, void* c, void* stream);
+
+/*
+ * Transition probabilities at the end of the paths (Sec. II: the solution at
+ * z_max gives the observables): P[p][i] = |c[p][i]|^2.
+ *   c  device [n_paths][N] complex128;  P  device [n_paths][N] double.
+ * Errors: EINVAL, ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_probabilities(int n_paths, int N, const void* c, double* P, void* stream);
+
+/*
+ * Upper bound on the scratch memory wpccc_propagate may hold (default 8 GiB).
+ * The number of RK4 steps batched per launch is chosen to fit it.
+ */
+WPCCC_API wpccc_status wpccc_basis_set_workspace_limit(wpccc_basis basis, size_t bytes);
+
+/*
+ * Kernel profiling of the work a basis queues (wpccc_matrix_elements and
+ * wpccc_propagate): launches are always counted; when enabled, a pair of CUDA
+ * events on the caller's stream brackets every launch and the device time is
+ * accumulated per category.  Categories (WPCCC_PROF_N of them):
+ *   0 node tables (Eq. 9 integrand factors), 1 molecular-frame contraction (Eq. 9),
+ *   2 rotation (Eq. 8) and direct elements (Eq. 6), 3 linear solve (Eq. 4), 4 RK4.
+ * wpccc_profile_enable resets the counters.  wpccc_profile_read waits for the
+ * recorded events and writes ms[WPCCC_PROF_N] (milliseconds, NULL to skip) and
+ * launches[WPCCC_PROF_N] (NULL to skip).
+ */
+#define WPCCC_PROF_N 5
+WPCCC_API wpccc_status wpccc_profile_enable(wpccc_basis basis, int on);
+WPCCC_API wpccc_status wpccc_profile_read(wpccc_basis basis, double* ms, long long* launches);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+WPCCC_API const char* wpccc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WPCCC_H */

@@ -35,7 +35,8 @@ tests/test_oracle_pins.py):
 * Eq. 5: M = -(i/v) D_T (the -i/v of Eq. 4 with S = I).
 * eta = 1 + s/(gamma R) maps the Laguerre variable s onto [1, inf).
 * 5-point interpolation: nodes j-2..j+2 with r_j <= x < r_{j+1}, clamped at
-  the grid ends; radial functions vanish beyond the last grid point.
+  the grid ends; radial functions vanish beyond the last grid point, so for
+  R beyond it F_lam(R) is the multipole moment times R^-(lam+1).
 """
 from __future__ import annotations
 
@@ -145,8 +146,13 @@ def radial_F_at_nodes(grid, fa: np.ndarray, fb: np.ndarray, lam: int, idx: np.nd
 
 
 def radial_F(grid, fa, fb, lam: int, R: float) -> np.ndarray:
-    """F_lam at an off-grid R: table values on the 5 stencil nodes, then 5-point interpolation."""
+    """F_lam at an off-grid R: table values on the 5 stencil nodes, then 5-point interpolation.
+
+    Beyond the last grid point every radial function vanishes, so the whole charge
+    distribution lies inside R and F_lam(R) = F_lam(r_max) (r_max / R)^(lam+1)."""
     r = grid.r
+    if R > r[-1]:
+        return radial_F_at_nodes(grid, fa, fb, lam, np.array([r.size - 1]))[:, 0] * (r[-1] / R) ** (lam + 1)
     j = np.searchsorted(r, R, side="right") - 1
     s = int(np.clip(j - 2, 0, r.size - 5))
     idx = np.arange(s, s + 5)

@@ -1,0 +1,234 @@
+"""GB300 (sm_103a) implementation of the WP-CCC hot path behind a C ABI.
+
+This package is a thin ctypes binding over ``libwpccc.so`` (declared in
+``include/wpccc.h``): it marshals numpy inputs and torch CUDA tensors into the
+C calls and does no arithmetic of the method itself.  Every step (matrix
+elements, solve, RK4 propagation, probabilities) runs in the library's CUDA
+kernels; there is no CPU fallback.  If the library has not been built, importing
+this package raises.
+
+Matrices are stored column-major (LAPACK layout): a batch of N x N matrices is a
+complex128 tensor of shape (batch, N, N) whose memory holds matrix k, column j,
+row i at [k, j, i].  ``natural(t)`` returns the (batch, row, column) view.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwpccc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it first "
+                      "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ESINGULAR, ENONFINITE, ECUDA, EUNSUPPORTED = range(7)
+_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENONFINITE", 5: "ECUDA", 6: "EUNSUPPORTED"}
+LMAX = 10
+NMAX = 3072
+
+_pd = C.POINTER(C.c_double)
+_pi = C.POINTER(C.c_int)
+
+
+class _CentreDesc(C.Structure):
+    _fields_ = [("Z", C.c_double), ("n_rad", C.c_int), ("rad_l", _pi), ("f", _pd),
+                ("n_states", C.c_int), ("st_rad", _pi), ("st_m", _pi), ("st_eps", _pd)]
+
+
+class _BasisDesc(C.Structure):
+    _fields_ = [("n_centres", C.c_int), ("Nr", C.c_int), ("r", _pd), ("w", _pd),
+                ("T", _CentreDesc), ("P", _CentreDesc),
+                ("Geta", C.c_int), ("s", _pd), ("ws", _pd),
+                ("Gtau", C.c_int), ("tau", _pd), ("wtau", _pd), ("gamma", C.c_double)]
+
+
+class _PathsDesc(C.Structure):
+    _fields_ = [("n_paths", C.c_int), ("b", _pd), ("v", _pd), ("n_z", _pi), ("z", _pd)]
+
+
+_lib.wpccc_basis_create.argtypes = [C.POINTER(_BasisDesc), C.c_int, C.POINTER(C.c_void_p)]
+_lib.wpccc_basis_destroy.argtypes = [C.c_void_p]
+_lib.wpccc_basis_info.argtypes = [C.c_void_p, _pi, _pi]
+_lib.wpccc_matrix_elements.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, _pd,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.wpccc_solve.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_int, C.c_void_p]
+_lib.wpccc_propagate.argtypes = [C.c_void_p, C.POINTER(_PathsDesc), C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+_lib.wpccc_probabilities.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.wpccc_basis_set_workspace_limit.argtypes = [C.c_void_p, C.c_size_t]
+_lib.wpccc_profile_enable.argtypes = [C.c_void_p, C.c_int]
+_lib.wpccc_profile_read.argtypes = [C.c_void_p, _pd, C.POINTER(C.c_longlong)]
+_lib.wpccc_last_error.restype = C.c_char_p
+for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
+           "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
+           "wpccc_profile_enable", "wpccc_profile_read"):
+    getattr(_lib, _f).restype = C.c_int
+
+EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
+            "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
+            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_last_error")
+PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4")
+
+
+class WpcccError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.wpccc_last_error().decode()
+        super().__init__(f"{where}: {_NAMES.get(status, status)}: {msg}")
+
+
+def _check(status: int, where: str) -> None:
+    if status != OK:
+        raise WpcccError(status, where)
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(_pi if dtype == np.int32 else _pd)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def natural(t):
+    """(batch, row, column) view of column-major matrix storage."""
+    return t.transpose(-1, -2)
+
+
+def colmajor(t):
+    """Column-major storage tensor of a (batch, row, column) tensor (a copy)."""
+    return t.transpose(-1, -2).contiguous()
+
+
+class Basis:
+    """A basis resident on one CUDA device (``wpccc_basis_create``)."""
+
+    def __init__(self, basis, device: int = 0):
+        """`basis` is a ``wpccc_inputs.Basis`` (grid, centres, quadrature, charges)."""
+        keep = []
+
+        def arr(a, dt):
+            a, p = _arr(a, dt)
+            keep.append(a)
+            return p
+
+        def centre(c, Z):
+            if c is None:
+                return _CentreDesc(Z=Z)
+            return _CentreDesc(Z=Z, n_rad=int(c.n_rad), rad_l=arr(c.rad_l, np.int32), f=arr(c.f, np.float64),
+                               n_states=int(c.N), st_rad=arr(c.st_rad, np.int32), st_m=arr(c.st_m, np.int32),
+                               st_eps=arr(c.st_eps, np.float64))
+
+        g = basis.grid
+        d = _BasisDesc(n_centres=basis.n_centres, Nr=int(g.r.size), r=arr(g.r, np.float64), w=arr(g.w, np.float64),
+                       T=centre(basis.T, basis.Z_T), P=centre(basis.P, basis.Z_P))
+        if basis.n_centres == 2:
+            q = basis.quad
+            d.Geta, d.s, d.ws = int(q.s.size), arr(q.s, np.float64), arr(q.ws, np.float64)
+            d.Gtau, d.tau, d.wtau = int(q.tau.size), arr(q.tau, np.float64), arr(q.wtau, np.float64)
+            d.gamma = float(q.gamma)
+        h = C.c_void_p()
+        _check(_lib.wpccc_basis_create(C.byref(d), int(device), C.byref(h)), "wpccc_basis_create")
+        self._h = h
+        self.device = int(device)
+        nt, np_ = C.c_int(), C.c_int()
+        _check(_lib.wpccc_basis_info(h, C.byref(nt), C.byref(np_)), "wpccc_basis_info")
+        self.N_T, self.N_P = nt.value, np_.value
+        self.N = self.N_T + self.N_P
+        self.n_centres = basis.n_centres
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.wpccc_basis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_workspace_limit(self, nbytes: int) -> None:
+        _check(_lib.wpccc_basis_set_workspace_limit(self._h, C.c_size_t(int(nbytes))),
+               "wpccc_basis_set_workspace_limit")
+
+    def profile_enable(self, on: bool = True) -> None:
+        """Reset the per-kernel counters; with on=True time every launch with CUDA events."""
+        _check(_lib.wpccc_profile_enable(self._h, int(bool(on))), "wpccc_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{category: (milliseconds, launches)} accumulated since profile_enable."""
+        ms = (C.c_double * 5)()
+        n = (C.c_longlong * 5)()
+        _check(_lib.wpccc_profile_read(self._h, ms, n), "wpccc_profile_read")
+        return {k: (ms[i], n[i]) for i, k in enumerate(PROF_CATEGORIES)}
+
+    def matrix_elements(self, b: float, v: float, z, S=None, H=None, stream=None):
+        """S, H at the positions z (column-major storage tensors of shape (nz, N, N))."""
+        import torch
+        z, zp = _arr(np.atleast_1d(z), np.float64)
+        dev = torch.device("cuda", self.device)
+        if S is None:
+            S = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
+        if H is None:
+            H = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
+        _check(_lib.wpccc_matrix_elements(self._h, float(b), float(v), int(z.size), zp, _ptr(S), _ptr(H),
+                                          _stream(stream)), "wpccc_matrix_elements")
+        return S, H
+
+    def propagate(self, b, v, zgrids, c=None, precision_mode: int = 0, batch_mode: int = 0, stream=None):
+        """Amplitudes at the end of each path (``wpccc_propagate``); `c` (n_paths, N) complex128 on the
+        device is advanced in place (default: Algorithm 1's initial state)."""
+        import torch
+        b = np.atleast_1d(np.asarray(b, dtype=np.float64))
+        v = np.broadcast_to(np.asarray(v, dtype=np.float64), b.shape)
+        if isinstance(zgrids, np.ndarray) and zgrids.ndim == 1:
+            zgrids = [zgrids] * b.size
+        nz = np.array([len(zg) for zg in zgrids], dtype=np.int32)
+        zc = np.concatenate([np.asarray(zg, dtype=np.float64) for zg in zgrids])
+        if c is None:
+            c = torch.zeros((b.size, self.N), dtype=torch.complex128, device=torch.device("cuda", self.device))
+            c[:, 0] = 1.0
+        bb, bp = _arr(b, np.float64)
+        vv, vp = _arr(v, np.float64)
+        nn, np_ = _arr(nz, np.int32)
+        zz, zp = _arr(zc, np.float64)
+        pd = _PathsDesc(n_paths=int(b.size), b=bp, v=vp, n_z=np_, z=zp)
+        _check(_lib.wpccc_propagate(self._h, C.byref(pd), int(precision_mode), int(batch_mode), _ptr(c),
+                                    _stream(stream)), "wpccc_propagate")
+        return c
+
+
+def solve(S, H, precision_mode: int = 0, stream=None):
+    """Batched S X = H in place on column-major storage tensors (batch, N, N); returns (ipiv, info)."""
+    import torch
+    batch, N = S.shape[0], S.shape[-1]
+    ipiv = torch.empty((batch, N), dtype=torch.int32, device=S.device)
+    info = torch.empty((batch,), dtype=torch.int32, device=S.device)
+    _check(_lib.wpccc_solve(int(N), int(batch), _ptr(S), _ptr(H), _ptr(ipiv), _ptr(info), int(precision_mode),
+                            _stream(stream)), "wpccc_solve")
+    return ipiv, info
+
+
+def probabilities(c, stream=None):
+    """|c|^2 for a (n_paths, N) complex128 device tensor (``wpccc_probabilities``)."""
+    import torch
+    n_paths, N = c.shape
+    P = torch.empty((n_paths, N), dtype=torch.float64, device=c.device)
+    _check(_lib.wpccc_probabilities(int(n_paths), int(N), _ptr(c), _ptr(P), _stream(stream)),
+           "wpccc_probabilities")
+    return P

@@ -1,0 +1,678 @@
+// Matrix-element assembly (Eq. 1, 6-9) for a batch of projectile positions.
+//
+// Two-centre pipeline per batch of positions (one "evaluation" = one (b, v, z)):
+//   k_node_tables  per quadrature node (eta, tau): geometry, radial functions
+//                  interpolated at r_T and r_P (5-point Lagrange, Sec. II),
+//                  normalised Legendre functions at the two centres' cosines, and
+//                  the complex node weights W_d = (R^3/8) w (eta^2-tau^2)
+//                  exp(i v z eta tau/2) (-i)^d J_d(x) times 1, -Z_T/r_T, -Z_P/r_P
+//   k_mol_gemm     molecular-frame integrals (Eq. 9) as a contraction over the
+//                  nodes: X[i][c] = sum_g A_T[i][g] A_P[c][g] W_{|q_c - q'_i|}[g]
+//                  for every target state i and projectile state c with q >= 0
+//   k_rotate       Eq. 8 rotation to the collision frame (q < 0 columns from the
+//                  q -> -q reflection), energy phases, writes the off-diagonal
+//                  blocks of S and H
+//   k_direct       Eq. 6 direct elements D_T and D_P (F of Eq. 7 interpolated at R),
+//                  energy phases; identity diagonal blocks of S
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "angular.cuh"
+#include "wpccc_internal.cuh"
+
+namespace wpccc {
+
+// ---------------------------------------------------------------------------
+// geometry shared by the kernels; explicit round-to-nearest operations so that
+// the interpolation stencils are chosen from exactly the same radii as a plain
+// IEEE evaluation of the same formulas (no contraction into FMA)
+// ---------------------------------------------------------------------------
+__device__ inline double dist_R(double b, double z) {
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(b, b), __dmul_rn(z, z)));
+}
+
+// Largest j with r[j] <= x (-1 if x < r[0]); 5-point stencil start and Lagrange weights.
+// Returns false when x lies beyond the last grid point (the function is zero there).
+__device__ inline bool stencil5(const double* __restrict__ r, int Nr, double x, int& s, double L[5]) {
+    if (x > r[Nr - 1]) return false;
+    int lo = -1, hi = Nr;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (r[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    s = min(max(lo - 2, 0), Nr - 5);
+    double rn[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) rn[k] = r[s + k];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        double p = 1.0;
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            if (c != a) p *= (x - rn[c]) / (rn[a] - rn[c]);
+        L[a] = p;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// k_node_tables
+// ---------------------------------------------------------------------------
+struct NodeArgs {
+    int Nr, G, Gtau, nradT, nradP, lmaxT, lmaxP, nlqT, nlqP, dmax;
+    double gamma, Z_T, Z_P;
+    const double *r, *fT, *fP, *s, *ws, *tau, *wtau;
+    double* node;            // per evaluation: [fT | fP | thT | thP | pad | W] (see elem_scratch_layout)
+    size_t node_doubles;
+    size_t w_off;            // offset of W in doubles (even, so W is 16-byte aligned)
+};
+
+__global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc* __restrict__ ev) {
+    const int e = blockIdx.y;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= A.G) return;
+    const int k = g / A.Gtau, t = g - k * A.Gtau;
+    const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
+    const double R = dist_R(b, z);
+    const double gR = __dmul_rn(A.gamma, R);
+    const double eta = __dadd_rn(1.0, __ddiv_rn(A.s[k], gR));
+    const double tau = A.tau[t];
+    const double halfR = __dmul_rn(0.5, R);
+    const double rT = __dmul_rn(halfR, __dadd_rn(eta, tau));
+    const double rP = __dmul_rn(halfR, __dsub_rn(eta, tau));
+    const double cT = (eta * tau + 1.0) / (eta + tau);
+    const double cP = (eta * tau - 1.0) / (eta - tau);
+    const double x = 0.5 * v * b * sqrt((eta * eta - 1.0) * (1.0 - tau * tau));
+    const double wgt = (A.ws[k] / gR) * A.wtau[t];
+    const double amp = (R * R * R / 8.0) * wgt * (eta * eta - tau * tau);
+    double sph, cph;
+    sincos(0.5 * v * z * eta * tau, &sph, &cph);
+
+    double* base = A.node + (size_t)e * A.node_doubles;
+    double* oT = base;
+    double* oP = oT + (size_t)A.nradT * A.G;
+    double* thT = oP + (size_t)A.nradP * A.G;
+    double* thP = thT + (size_t)A.nlqT * A.G;
+    double2* W = reinterpret_cast<double2*>(base + A.w_off);
+
+    // radial functions at the node radii
+    int sT, sP;
+    double LT[5], LP[5];
+    const bool inT = stencil5(A.r, A.Nr, rT, sT, LT);
+    const bool inP = stencil5(A.r, A.Nr, rP, sP, LP);
+    for (int a = 0; a < A.nradT; ++a) {
+        double val = 0.0;
+        if (inT) {
+            const double* fa = A.fT + (size_t)a * A.Nr + sT;
+            val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
+        }
+        oT[(size_t)a * A.G + g] = val;
+    }
+    for (int a = 0; a < A.nradP; ++a) {
+        double val = 0.0;
+        if (inP) {
+            const double* fa = A.fP + (size_t)a * A.Nr + sP;
+            val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
+        }
+        oP[(size_t)a * A.G + g] = val;
+    }
+    // Theta_lq(c) = sqrt((2l+1)/2 (l-q)!/(l+q)!) P_l^q(c), index l(l+1)/2 + q
+    for (int cen = 0; cen < 2; ++cen) {
+        const double c = cen == 0 ? cT : cP;
+        const int lmax = cen == 0 ? A.lmaxT : A.lmaxP;
+        double* th = cen == 0 ? thT : thP;
+        const double sq = sqrt((1.0 - c) * (1.0 + c));
+        double pmm = 1.0;   // P_q^q, built up from P_0^0 = 1
+        for (int q = 0; q <= lmax; ++q) {
+            if (q > 0) pmm *= -(2.0 * q - 1.0) * sq;
+            double pa = 0.0, pb = pmm;   // P_{l-2}^q, P_{l-1}^q
+            for (int l = q; l <= lmax; ++l) {
+                double pl;
+                if (l == q) pl = pmm;
+                else if (l == q + 1) pl = c * (2.0 * q + 1.0) * pmm;
+                else pl = (c * (2.0 * l - 1.0) * pb - (l + q - 1.0) * pa) / (double)(l - q);
+                if (l > q) {
+                    pa = pb;
+                    pb = pl;
+                }
+                const double nrm = sqrt((2.0 * l + 1.0) * 0.5 * dfact(l - q) / dfact(l + q));
+                th[(size_t)(l * (l + 1) / 2 + q) * A.G + g] = nrm * pl;
+            }
+        }
+    }
+    // node weights for the three integrands, d = |q - q'| = 0..dmax
+    const double uQ = -A.Z_T / rT, uQt = -A.Z_P / rP;
+    const size_t stride = (size_t)(A.dmax + 1) * A.G;
+    for (int d = 0; d <= A.dmax; ++d) {
+        const double J = jn(d, x) * amp;
+        // (-i)^d exp(i phi)
+        double re, im;
+        switch (d & 3) {
+            case 0: re = cph; im = sph; break;
+            case 1: re = sph; im = -cph; break;
+            case 2: re = -cph; im = -sph; break;
+            default: re = -sph; im = cph; break;
+        }
+        const double2 w0 = make_double2(J * re, J * im);
+        const size_t o = (size_t)d * A.G + g;
+        W[o] = w0;
+        W[stride + o] = make_double2(w0.x * uQ, w0.y * uQ);
+        W[2 * stride + o] = make_double2(w0.x * uQt, w0.y * uQt);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_mol_gemm: Eq. 9 contraction over the quadrature nodes (FP64)
+// ---------------------------------------------------------------------------
+constexpr int GT_I = 32, GT_J = 32, GT_K = 32;
+
+struct GemmArgs {
+    int G, N_T, n_half, nradT, nradP, nlqT, nlqP, dmax, n_col_tiles;
+    const int *stT_rad, *stT_l, *stT_m;   // target states
+    const int *stP_rad, *stP_l, *stP_m;   // projectile states
+    const int* half_state;
+    const double* node;
+    size_t node_doubles, w_off;
+    double2* mol;                         // [nev][3][N_T][n_half]
+};
+
+__global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
+    extern __shared__ double smem[];
+    double* sAT = smem;                                   // [GT_K][GT_I + 1]
+    double* sAP = sAT + GT_K * (GT_I + 1);                // [GT_K][GT_J + 1]
+    double2* sW = reinterpret_cast<double2*>(sAP + GT_K * (GT_J + 1));  // [3][dmax+1][GT_K]
+    __shared__ int s_rrad[GT_I], s_rlq[GT_I], s_rq[GT_I];
+    __shared__ double s_rsgn[GT_I];
+    __shared__ int s_crad[GT_J], s_clq[GT_J], s_cq[GT_J];
+
+    const int e = blockIdx.y;
+    const int rt = blockIdx.x / A.n_col_tiles, ct = blockIdx.x % A.n_col_tiles;
+    const int i0 = rt * GT_I, j0 = ct * GT_J;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const double* base = A.node + (size_t)e * A.node_doubles;
+    const double* fT = base;
+    const double* fP = fT + (size_t)A.nradT * A.G;
+    const double* thT = fP + (size_t)A.nradP * A.G;
+    const double* thP = thT + (size_t)A.nlqT * A.G;
+    const double2* W = reinterpret_cast<const double2*>(base + A.w_off);
+
+    if (tid < GT_I) {
+        int i = i0 + tid;
+        if (i < A.N_T) {
+            int l = A.stT_l[i], m = A.stT_m[i], am = m < 0 ? -m : m;
+            s_rrad[tid] = A.stT_rad[i];
+            s_rlq[tid] = l * (l + 1) / 2 + am;
+            s_rq[tid] = m;
+            s_rsgn[tid] = (m < 0 && (am & 1)) ? -1.0 : 1.0;   // Theta_{l,-q} = (-1)^q Theta_{l,q}
+        } else {
+            s_rrad[tid] = -1;
+            s_rlq[tid] = 0;
+            s_rq[tid] = 0;
+            s_rsgn[tid] = 0.0;
+        }
+    } else if (tid < GT_I + GT_J) {
+        int c = tid - GT_I, j = j0 + c;
+        if (j < A.n_half) {
+            int st = A.half_state[j];
+            int l = A.stP_l[st], q = A.stP_m[st];
+            s_crad[c] = A.stP_rad[st];
+            s_clq[c] = l * (l + 1) / 2 + q;
+            s_cq[c] = q;
+        } else {
+            s_crad[c] = -1;
+            s_clq[c] = 0;
+            s_cq[c] = 0;
+        }
+    }
+    __syncthreads();
+
+    int dd[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            int d = s_cq[tx * 2 + c] - s_rq[ty * 2 + a];
+            dd[a][c] = d < 0 ? -d : d;
+        }
+    double acc[2][2][6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc[a][c][q] = 0.0;
+
+    const int nd = A.dmax + 1;
+    const size_t wstride = (size_t)nd * A.G;
+    for (int g0 = 0; g0 < A.G; g0 += GT_K) {
+        // A_T[i][g] = f_a(r_T) Theta_{l|q'|}(c_T) * sign, transposed into sAT[g][i]
+        for (int idx = tid; idx < GT_I * GT_K; idx += 256) {
+            int ii = idx / GT_K, gg = idx % GT_K, g = g0 + gg;
+            double val = 0.0;
+            if (s_rrad[ii] >= 0 && g < A.G)
+                val = fT[(size_t)s_rrad[ii] * A.G + g] * thT[(size_t)s_rlq[ii] * A.G + g] * s_rsgn[ii];
+            sAT[gg * (GT_I + 1) + ii] = val;
+        }
+        for (int idx = tid; idx < GT_J * GT_K; idx += 256) {
+            int cc = idx / GT_K, gg = idx % GT_K, g = g0 + gg;
+            double val = 0.0;
+            if (s_crad[cc] >= 0 && g < A.G)
+                val = fP[(size_t)s_crad[cc] * A.G + g] * thP[(size_t)s_clq[cc] * A.G + g];
+            sAP[gg * (GT_J + 1) + cc] = val;
+        }
+        for (int idx = tid; idx < 3 * nd * GT_K; idx += 256) {
+            int gg = idx % GT_K, xd = idx / GT_K, g = g0 + gg;
+            int X = xd / nd, d = xd % nd;
+            sW[idx] = (g < A.G) ? W[(size_t)X * wstride + (size_t)d * A.G + g] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int gg = 0; gg < GT_K; ++gg) {
+            double at[2], ap[2];
+            at[0] = sAT[gg * (GT_I + 1) + ty * 2];
+            at[1] = sAT[gg * (GT_I + 1) + ty * 2 + 1];
+            ap[0] = sAP[gg * (GT_J + 1) + tx * 2];
+            ap[1] = sAP[gg * (GT_J + 1) + tx * 2 + 1];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const double p = at[a] * ap[c];
+                    const double2* wp = sW + dd[a][c] * GT_K + gg;
+                    const double2 w0 = wp[0], w1 = wp[nd * GT_K], w2 = wp[2 * nd * GT_K];
+                    acc[a][c][0] = fma(p, w0.x, acc[a][c][0]);
+                    acc[a][c][1] = fma(p, w0.y, acc[a][c][1]);
+                    acc[a][c][2] = fma(p, w1.x, acc[a][c][2]);
+                    acc[a][c][3] = fma(p, w1.y, acc[a][c][3]);
+                    acc[a][c][4] = fma(p, w2.x, acc[a][c][4]);
+                    acc[a][c][5] = fma(p, w2.y, acc[a][c][5]);
+                }
+        }
+        __syncthreads();
+    }
+    const size_t plane = (size_t)A.N_T * A.n_half;
+    double2* out = A.mol + (size_t)e * 3 * plane;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        int i = i0 + ty * 2 + a;
+        if (i >= A.N_T) continue;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            int j = j0 + tx * 2 + c;
+            if (j >= A.n_half) continue;
+            size_t o = (size_t)i * A.n_half + j;
+            out[o] = make_double2(acc[a][c][0], acc[a][c][1]);
+            out[plane + o] = make_double2(acc[a][c][2], acc[a][c][3]);
+            out[2 * plane + o] = make_double2(acc[a][c][4], acc[a][c][5]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_rotate: Eq. 8 and the off-diagonal blocks of S and H
+// ---------------------------------------------------------------------------
+struct RotArgs {
+    int N_T, N_P, N, n_half, lmax;
+    const int *stT_rad, *stT_l, *stT_m, *stT_index;
+    const int *stP_rad, *stP_l, *stP_m, *half_of;
+    const double *epsT, *epsP;
+    const double2* mol;
+    double2 *S, *H;
+    size_t mat;   // N*N
+};
+
+__global__ void __launch_bounds__(256) k_rotate(RotArgs A, const EvalDesc* __restrict__ ev) {
+    extern __shared__ double sd[];     // Wigner d^l_{m q}(theta) for l <= lmax
+    const int e = blockIdx.y;
+    const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
+    const double R = dist_R(b, z);
+    const double cth = z / R;
+    const double ch = sqrt(0.5 * (1.0 + cth)), sh = sqrt(0.5 * (1.0 - cth));
+    int total = 0;
+    for (int l = 0; l <= A.lmax; ++l) total += (2 * l + 1) * (2 * l + 1);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l = 0, off = 0;
+        while (idx >= off + (2 * l + 1) * (2 * l + 1)) {
+            off += (2 * l + 1) * (2 * l + 1);
+            ++l;
+        }
+        int loc = idx - off, m = loc / (2 * l + 1) - l, q = loc % (2 * l + 1) - l;
+        sd[idx] = wigner_small_d(l, m, q, ch, sh);
+    }
+    __syncthreads();
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)A.N_T * A.N_P) return;
+    const int i = (int)(idx / A.N_P), j = (int)(idx % A.N_P);
+    const int ra = A.stT_rad[i], la = A.stT_l[i], ma = A.stT_m[i];
+    const int rb = A.stP_rad[j], lb = A.stP_l[j], mb = A.stP_m[j];
+    int offa = 0, offb = 0;
+    for (int l = 0; l < la; ++l) offa += (2 * l + 1) * (2 * l + 1);
+    for (int l = 0; l < lb; ++l) offb += (2 * l + 1) * (2 * l + 1);
+    const double* da = sd + offa + (ma + la) * (2 * la + 1);   // d^{la}_{ma, q'} at [q' + la]
+    const double* db = sd + offb + (mb + lb) * (2 * lb + 1);
+    const size_t plane = (size_t)A.N_T * A.n_half;
+    const double2* mol = A.mol + (size_t)e * 3 * plane;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int qp = -la; qp <= la; ++qp) {
+        const double dq = da[qp + la];
+        const int rowp = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + qp + WPCCC_LMAX];
+        const int rowm = A.stT_index[ra * (2 * WPCCC_LMAX + 1) - qp + WPCCC_LMAX];
+        for (int q = -lb; q <= lb; ++q) {
+            double w = dq * db[q + lb];
+            int row, col;
+            if (q >= 0) {
+                row = rowp;
+                col = A.half_of[rb * (WPCCC_LMAX + 1) + q];
+            } else {
+                row = rowm;
+                col = A.half_of[rb * (WPCCC_LMAX + 1) - q];
+                if ((qp + q) & 1) w = -w;
+            }
+            const size_t o = (size_t)row * A.n_half + col;
+            const double2 s0 = mol[o], s1 = mol[plane + o], s2 = mol[2 * plane + o];
+            acc[0] = fma(w, s0.x, acc[0]);
+            acc[1] = fma(w, s0.y, acc[1]);
+            acc[2] = fma(w, s1.x, acc[2]);
+            acc[3] = fma(w, s1.y, acc[3]);
+            acc[4] = fma(w, s2.x, acc[4]);
+            acc[5] = fma(w, s2.y, acc[5]);
+        }
+    }
+    double sp, cp;
+    sincos((A.epsT[i] - A.epsP[j]) * z / v, &sp, &cp);
+    const double2 ph = make_double2(cp, sp);
+    const double2 K = cmul(make_double2(acc[0], acc[1]), ph);
+    const double2 Q = cmul(make_double2(acc[2], acc[3]), ph);
+    const double2 Qt = cmul(make_double2(acc[4], acc[5]), ph);
+    double2* S = A.S + (size_t)e * A.mat;
+    double2* H = A.H + (size_t)e * A.mat;
+    const size_t up = (size_t)i + (size_t)(A.N_T + j) * A.N;     // row i, column N_T + j
+    const size_t lo = (size_t)(A.N_T + j) + (size_t)i * A.N;     // row N_T + j, column i
+    S[up] = K;
+    S[lo] = cconj(K);
+    H[up] = Q;
+    H[lo] = cconj(Qt);
+}
+
+// ---------------------------------------------------------------------------
+// k_direct: Eq. 6 blocks (and identity blocks of S)
+// ---------------------------------------------------------------------------
+struct DirArgs {
+    int Nr, N, off, Nc, n_rad, nlam;
+    double Z_other, parity;       // parity = -1: the other nucleus sits at -R
+    const double *r, *F, *ang, *eps;
+    const int *Foff, *st_rad, *st_m;
+    double2 *S, *H;
+    size_t mat;
+};
+
+__global__ void __launch_bounds__(256) k_direct(DirArgs A0, DirArgs A1, const EvalDesc* __restrict__ ev) {
+    const DirArgs& A = blockIdx.z == 0 ? A0 : A1;
+    __shared__ double sPb[(4 * WPCCC_LMAX + 1) * (4 * WPCCC_LMAX + 2) / 2];
+    __shared__ double sL[5];
+    __shared__ int s_sten, s_out;
+    const int e = blockIdx.y;
+    const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
+    const double R = dist_R(b, z);
+    const double cth = z / R;
+    // Pbar(lam, mu) = sqrt((lam-mu)!/(lam+mu)!) P_lam^mu(cos Theta), index lam(lam+1)/2 + mu
+    const int npb = A.nlam * (A.nlam + 1) / 2;
+    for (int t = threadIdx.x; t < npb; t += blockDim.x) {
+        int lam = 0;
+        while ((lam + 1) * (lam + 2) / 2 <= t) ++lam;
+        int mu = t - lam * (lam + 1) / 2;
+        sPb[t] = sqrt(dfact(lam - mu) / dfact(lam + mu)) * assoc_legendre(lam, mu, cth);
+    }
+    if (threadIdx.x == 0) {
+        int s;
+        double L[5];
+        if (R > A.r[A.Nr - 1]) {
+            // beyond the grid every radial function vanishes: F_lam(R) = F_lam(r_max) (r_max/R)^{lam+1}
+            s_out = 1;
+            s_sten = A.Nr - 1;
+        } else {
+            stencil5(A.r, A.Nr, R, s, L);
+            s_out = 0;
+            s_sten = s;
+            for (int k = 0; k < 5; ++k) sL[k] = L[k];
+        }
+    }
+    __syncthreads();
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)A.Nc * A.Nc) return;
+    const int i = (int)(idx / A.Nc), j = (int)(idx % A.Nc);
+    const int ra = A.st_rad[i], rb = A.st_rad[j];
+    const int mu = A.st_m[i] - A.st_m[j];
+    const int amu = mu < 0 ? -mu : mu;
+    const double* ang = A.ang + (size_t)idx * A.nlam;
+    const int* foff = A.Foff + ((size_t)ra * A.n_rad + rb) * A.nlam;
+    double D = 0.0;
+    double sgn = 1.0;
+    for (int lam = 0; lam < A.nlam; ++lam, sgn *= A.parity) {
+        const double c = ang[lam];
+        if (c == 0.0) continue;
+        const double* Fe = A.F + (size_t)foff[lam] * A.Nr;
+        double Fv;
+        if (s_out) {
+            const double ratio = A.r[A.Nr - 1] / R;
+            double p = ratio;
+            for (int k = 0; k < lam; ++k) p *= ratio;
+            Fv = Fe[A.Nr - 1] * p;
+        } else {
+            const int s = s_sten;
+            Fv = sL[0] * Fe[s] + sL[1] * Fe[s + 1] + sL[2] * Fe[s + 2] + sL[3] * Fe[s + 3] + sL[4] * Fe[s + 4];
+        }
+        double P = sPb[lam * (lam + 1) / 2 + amu];
+        if (mu < 0 && (amu & 1)) P = -P;
+        D += sgn * c * P * Fv;
+    }
+    D *= -A.Z_other;
+    double sp, cp;
+    sincos((A.eps[i] - A.eps[j]) * z / v, &sp, &cp);
+    const size_t o = (size_t)(A.off + i) + (size_t)(A.off + j) * A.N;
+    A.H[(size_t)e * A.mat + o] = make_double2(D * cp, D * sp);
+    if (A.S) A.S[(size_t)e * A.mat + o] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
+    ElemScratch L{0, 0, 0, 0};
+    if (B->n_centres == 2) {
+        size_t nd = (size_t)(B->T.n_rad + B->P.n_rad + B->nlq_T + B->nlq_P) * B->G;
+        nd += nd & 1;   // keep the complex weights 16-byte aligned
+        L.w_off = nd;
+        nd += (size_t)3 * (B->dmax + 1) * B->G * 2;
+        L.node_doubles = nd;
+        L.mol_elems = (size_t)3 * B->N_T * B->n_half;
+        L.bytes_per_eval = nd * sizeof(double) + L.mol_elems * sizeof(double2);
+    }
+    return L;
+}
+
+static DirArgs dir_args(const wpccc_basis_s* B, const CentreDev& c, int off, double Z_other, double parity,
+                        double2* S, double2* H) {
+    DirArgs a;
+    a.Nr = B->Nr;
+    a.N = B->N;
+    a.off = off;
+    a.Nc = c.n_states;
+    a.n_rad = c.n_rad;
+    a.nlam = c.nlam;
+    a.Z_other = Z_other;
+    a.parity = parity;
+    a.r = B->r;
+    a.F = c.F;
+    a.ang = c.ang;
+    a.eps = c.st_eps;
+    a.Foff = c.Foff;
+    a.st_rad = c.st_rad;
+    a.st_m = c.st_m;
+    a.S = S;
+    a.H = H;
+    a.mat = (size_t)B->N * B->N;
+    return a;
+}
+
+wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, double2* S,
+                             double2* H, void* scratch, cudaStream_t st) {
+    if (nev <= 0) return WPCCC_OK;
+    const bool two = B->n_centres == 2;
+    if (two) {
+        const ElemScratch L = elem_scratch_layout(B);
+        double* node = static_cast<double*>(scratch);
+        double2* mol = reinterpret_cast<double2*>(node + L.node_doubles * nev);
+        NodeArgs na;
+        na.Nr = B->Nr;
+        na.G = B->G;
+        na.Gtau = B->Gtau;
+        na.nradT = B->T.n_rad;
+        na.nradP = B->P.n_rad;
+        na.lmaxT = B->T.lmax;
+        na.lmaxP = B->P.lmax;
+        na.nlqT = B->nlq_T;
+        na.nlqP = B->nlq_P;
+        na.dmax = B->dmax;
+        na.gamma = B->gamma;
+        na.Z_T = B->T.Z;
+        na.Z_P = B->P.Z;
+        na.r = B->r;
+        na.fT = B->T.f;
+        na.fP = B->P.f;
+        na.s = B->s;
+        na.ws = B->ws;
+        na.tau = B->tau;
+        na.wtau = B->wtau;
+        na.node = node;
+        na.node_doubles = L.node_doubles;
+        na.w_off = L.w_off;
+        cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
+        k_node_tables<<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
+        WPCCC_CHECK_LAUNCH("k_node_tables");
+        B->prof.end(PROF_NODES, st, e0);
+
+        GemmArgs ga;
+        ga.G = B->G;
+        ga.N_T = B->N_T;
+        ga.n_half = B->n_half;
+        ga.nradT = B->T.n_rad;
+        ga.nradP = B->P.n_rad;
+        ga.nlqT = B->nlq_T;
+        ga.nlqP = B->nlq_P;
+        ga.dmax = B->dmax;
+        ga.n_col_tiles = (B->n_half + GT_J - 1) / GT_J;
+        ga.stT_rad = B->T.st_rad;
+        ga.stT_l = B->T.st_l;
+        ga.stT_m = B->T.st_m;
+        ga.stP_rad = B->P.st_rad;
+        ga.stP_l = B->P.st_l;
+        ga.stP_m = B->P.st_m;
+        ga.half_state = B->half_state;
+        ga.node = node;
+        ga.node_doubles = L.node_doubles;
+        ga.w_off = L.w_off;
+        ga.mol = mol;
+        const int n_row_tiles = (B->N_T + GT_I - 1) / GT_I;
+        const size_t gsm = (size_t)GT_K * (GT_I + 1 + GT_J + 1) * sizeof(double) +
+                           (size_t)3 * (B->dmax + 1) * GT_K * sizeof(double2);
+        WPCCC_CUDA(cudaFuncSetAttribute(k_mol_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+        e0 = B->prof.begin(PROF_MOL, st);
+        k_mol_gemm<<<dim3(n_row_tiles * ga.n_col_tiles, nev), 256, gsm, st>>>(ga);
+        WPCCC_CHECK_LAUNCH("k_mol_gemm");
+        B->prof.end(PROF_MOL, st, e0);
+
+        RotArgs ra;
+        ra.N_T = B->N_T;
+        ra.N_P = B->N_P;
+        ra.N = B->N;
+        ra.n_half = B->n_half;
+        ra.lmax = std::max(B->T.lmax, B->P.lmax);
+        ra.stT_rad = B->T.st_rad;
+        ra.stT_l = B->T.st_l;
+        ra.stT_m = B->T.st_m;
+        ra.stT_index = B->T.st_index;
+        ra.stP_rad = B->P.st_rad;
+        ra.stP_l = B->P.st_l;
+        ra.stP_m = B->P.st_m;
+        ra.half_of = B->half_of;
+        ra.epsT = B->T.st_eps;
+        ra.epsP = B->P.st_eps;
+        ra.mol = mol;
+        ra.S = S;
+        ra.H = H;
+        ra.mat = (size_t)B->N * B->N;
+        int dtot = 0;
+        for (int l = 0; l <= ra.lmax; ++l) dtot += (2 * l + 1) * (2 * l + 1);
+        const long long pairs = (long long)B->N_T * B->N_P;
+        e0 = B->prof.begin(PROF_ROT_DIRECT, st);
+        k_rotate<<<dim3((unsigned)((pairs + 255) / 256), nev), 256, dtot * sizeof(double), st>>>(ra, evals);
+        WPCCC_CHECK_LAUNCH("k_rotate");
+        B->prof.end(PROF_ROT_DIRECT, st, e0);
+    }
+    DirArgs d0 = dir_args(B, B->T, 0, B->P.Z, 1.0, S, H);
+    DirArgs d1 = two ? dir_args(B, B->P, B->N_T, B->T.Z, -1.0, S, H) : d0;
+    int ncmax = two ? std::max(B->N_T, B->N_P) : B->N_T;
+    long long cells = (long long)ncmax * ncmax;
+    cudaEvent_t ed = B->prof.begin(PROF_ROT_DIRECT, st);
+    k_direct<<<dim3((unsigned)((cells + 255) / 256), nev, two ? 2 : 1), 256, 0, st>>>(d0, d1, evals);
+    WPCCC_CHECK_LAUNCH("k_direct");
+    B->prof.end(PROF_ROT_DIRECT, st, ed);
+    return WPCCC_OK;
+}
+
+// Grows the basis-owned scratch buffer to at least `bytes`.
+wpccc_status ensure_workspace(wpccc_basis_s* B, size_t bytes) {
+    if (B->ws_bytes >= bytes) return WPCCC_OK;
+    if (B->ws_ptr) {
+        cudaError_t e = cudaFree(B->ws_ptr);
+        B->ws_ptr = nullptr;
+        B->ws_bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+    }
+    cudaError_t e = cudaMalloc(&B->ws_ptr, bytes);
+    if (e != cudaSuccess) {
+        B->ws_ptr = nullptr;
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    B->ws_bytes = bytes;
+    return WPCCC_OK;
+}
+
+}  // namespace wpccc
+
+using namespace wpccc;
+
+extern "C" wpccc_status wpccc_matrix_elements(wpccc_basis B, double b, double v, int nz, const double* z,
+                                              void* S, void* H, void* stream) {
+    if (!B || !z || !S || !H) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: null argument");
+    if (nz < 1) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: nz < 1");
+    if (!(b > 0.0) || !(v > 0.0)) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: b and v must be > 0");
+    WPCCC_CUDA(cudaSetDevice(B->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const ElemScratch L = elem_scratch_layout(B);
+    // evaluations per launch bounded by the workspace limit
+    size_t per = L.bytes_per_eval + sizeof(EvalDesc);
+    int chunk = (int)std::min<size_t>((size_t)nz, std::max<size_t>(1, (B->ws_limit - 256) / per));
+    size_t need = (size_t)chunk * L.bytes_per_eval + 256 + (size_t)chunk * sizeof(EvalDesc);
+    wpccc_status s = ensure_workspace(B, need);
+    if (s != WPCCC_OK) return s;
+    char* wsb = static_cast<char*>(B->ws_ptr);
+    EvalDesc* dev_ev = reinterpret_cast<EvalDesc*>(wsb);
+    void* scratch = wsb + ((chunk * sizeof(EvalDesc) + 255) / 256) * 256;
+    std::vector<EvalDesc> ev(chunk);
+    const size_t mat = (size_t)B->N * B->N;
+    for (int k0 = 0; k0 < nz; k0 += chunk) {
+        int n = std::min(chunk, nz - k0);
+        for (int k = 0; k < n; ++k) ev[k] = EvalDesc{b, v, z[k0 + k], 0, 0};
+        WPCCC_CUDA(cudaMemcpyAsync(dev_ev, ev.data(), n * sizeof(EvalDesc), cudaMemcpyHostToDevice, st));
+        s = launch_elements(B, dev_ev, n, static_cast<double2*>(S) + k0 * mat, static_cast<double2*>(H) + k0 * mat,
+                            scratch, st);
+        if (s != WPCCC_OK) return s;
+        // the host list is reused: wait for the copy before refilling it
+        WPCCC_CUDA(cudaStreamSynchronize(st));
+    }
+    return WPCCC_OK;
+}

@@ -1,0 +1,141 @@
+// Internal declarations of the WP-CCC CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/wpccc.h"
+
+namespace wpccc {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+wpccc_status fail(wpccc_status st, const std::string& msg);
+wpccc_status cuda_fail(cudaError_t e, const char* what);
+
+#define WPCCC_CUDA(call)                                          \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ::wpccc::cuda_fail(e_, #call); \
+    } while (0)
+
+#define WPCCC_CHECK_LAUNCH(name)                                  \
+    do {                                                          \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return ::wpccc::cuda_fail(e_, name); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device-resident basis
+// ---------------------------------------------------------------------------
+struct CentreDev {
+    double Z = 0.0;
+    int n_rad = 0, n_states = 0, lmax = 0, nlam = 0;  // nlam = 2*lmax+1 multipoles
+    double* f = nullptr;        // [n_rad][Nr]
+    int* rad_l = nullptr;       // [n_rad]
+    int* st_rad = nullptr;      // [n_states]
+    int* st_l = nullptr;        // [n_states]
+    int* st_m = nullptr;        // [n_states]
+    double* st_eps = nullptr;   // [n_states]
+    int* st_index = nullptr;    // [n_rad][2*WPCCC_LMAX+1]: state of (radial, m) or -1
+    // Eq. 7 table: entry e holds F_{a b lam}(r_i) for a <= b
+    int n_fent = 0;
+    double* F = nullptr;        // [n_fent][Nr]
+    int* Foff = nullptr;        // [n_rad][n_rad][nlam]: entry or -1 (symmetric in a, b)
+    int* fent_a = nullptr;      // [n_fent]
+    int* fent_b = nullptr;
+    int* fent_lam = nullptr;
+    double* ang = nullptr;      // [n_states][n_states][nlam]: Eq. 6 coefficient without the
+                                // sqrt((lam-mu)!/(lam+mu)!) factor (carried by the Legendre table)
+    // host copies used to build launch lists
+    std::vector<int> h_rad_l, h_st_rad, h_st_m;
+};
+
+// Per-category launch counts and (optionally) event-timed device durations.
+struct Profiler {
+    bool on = false;
+    double ms[WPCCC_PROF_N] = {};
+    long long launches[WPCCC_PROF_N] = {};
+    std::vector<cudaEvent_t> pool;
+    std::vector<cudaEvent_t> pending[WPCCC_PROF_N];   // start, stop, start, stop, ...
+    cudaEvent_t begin(int cat, cudaStream_t st);
+    void end(int cat, cudaStream_t st, cudaEvent_t e0);
+    cudaError_t flush();
+    void release();
+};
+
+}  // namespace wpccc
+
+struct wpccc_basis_s {
+    int device = 0;
+    int n_centres = 1;
+    int Nr = 0;
+    int N_T = 0, N_P = 0, N = 0;
+    double* r = nullptr;
+    double* w = nullptr;
+    wpccc::CentreDev T, P;
+    // two-centre quadrature
+    int Geta = 0, Gtau = 0, G = 0;
+    double* s = nullptr;
+    double* ws = nullptr;
+    double* tau = nullptr;
+    double* wtau = nullptr;
+    double gamma = 0.5;
+    int dmax = 0;               // lmax_T + lmax_P: largest |q - q'|
+    int nlq_T = 0, nlq_P = 0;   // (l, q >= 0) pairs per centre
+    // projectile states with q >= 0 ("half columns") of the molecular-frame integrals
+    int n_half = 0;
+    int* half_state = nullptr;  // [n_half] projectile state
+    int* half_of = nullptr;     // [n_rad_P][WPCCC_LMAX+1]: half column of (radial, q>=0) or -1
+    // scratch owned by the basis
+    void* ws_ptr = nullptr;
+    size_t ws_bytes = 0;
+    size_t ws_limit = (size_t)8 << 30;
+    wpccc::Profiler prof;
+};
+
+namespace wpccc {
+
+// one projectile position to evaluate
+struct EvalDesc {
+    double b, v, z;
+    int path;
+    int pad;
+};
+
+// Layout of the per-evaluation scratch of the two-centre element kernels.
+struct ElemScratch {
+    size_t node_doubles;   // node tables per evaluation (in doubles, even)
+    size_t w_off;          // offset of the complex node weights within them (even)
+    size_t mol_elems;      // molecular-frame integrals per evaluation (complex)
+    size_t bytes_per_eval;
+};
+ElemScratch elem_scratch_layout(const wpccc_basis_s* B);
+
+// Queue the element kernels for `nev` evaluations (device list `evals`), writing
+// S and H (matrix k at S + k*N*N).  S may be null (one-centre propagation).
+// `scratch` must hold elem_scratch_layout(B).bytes_per_eval * nev bytes (unused in
+// one-centre mode).
+wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev,
+                             double2* S, double2* H, void* scratch, cudaStream_t st);
+
+enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3, PROF_RK4 = 4 };
+
+// Queue the batched solve of S X = H (results in place).
+wpccc_status launch_solve(int N, int batch, double2* S, double2* H, int* ipiv, int* info,
+                          cudaStream_t st);
+
+}  // namespace wpccc
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same generated inputs.
+
+Bars: matrix elements and solves agree to FP64 rounding (scaled tolerances
+below); probabilities agree to |dP| <= 1e-10 * max(P, 1e-4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import wpccc_inputs as wi
+from oracle import wpccc_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P_TOL = 1e-10
+
+
+def _w():
+    import paper_2403_04252_gb300 as w
+    return w
+
+
+def _prob_close(Pg, Po):
+    bound = P_TOL * np.maximum(Po, 1e-4)
+    bad = np.abs(Pg - Po) > bound
+    assert not bad.any(), f"max |dP| = {np.abs(Pg - Po).max():.3e} at {np.nonzero(bad)}"
+
+
+@pytest.fixture(scope="module")
+def small2c():
+    # ragged sizes: 13 states per centre (N = 26) and a 20 x 14 quadrature, neither a multiple of a tile
+    return wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=20, Gtau=14)
+
+
+@pytest.fixture(scope="module")
+def small2c_uneven():
+    # different charges and basis sizes on the two centres (C6+ + H like)
+    return wi.make_basis(1.0, 6.0, (3, 2), (2, 1), (3, 2), (3.0, 4.0), True, Nr=600, Geta=18, Gtau=16)
+
+
+@pytest.fixture(scope="module")
+def config1():
+    return wi.config_inputs("p_H_1c_n3l2")
+
+
+@pytest.fixture(scope="module")
+def config2():
+    return wi.config_inputs("p_H_2c_n4l3")
+
+
+def _elements(basis, b, v, zs):
+    w = _w()
+    g = w.Basis(basis)
+    S, H = g.matrix_elements(b, v, np.asarray(zs))
+    torch.cuda.synchronize()
+    return w.natural(S).cpu().numpy(), w.natural(H).cpu().numpy()
+
+
+@pytest.mark.parametrize("fixture", ["small2c", "small2c_uneven"])
+def test_matrix_elements_small_two_centre(request, fixture):
+    basis = request.getfixturevalue(fixture)
+    b, v = 0.9, 1.3
+    zs = [-7.3, -0.4, 0.0, 0.25, 3.1, 60.0, 140.0]      # 140: R beyond the grid
+    Sg, Hg = _elements(basis, b, v, zs)
+    for k, z in enumerate(zs):
+        So, Ho = O.assemble(basis, b, v, z)
+        scale = max(1.0, np.abs(Ho).max())
+        assert np.abs(Sg[k] - So).max() < 1e-12, (z, np.abs(Sg[k] - So).max())
+        assert np.abs(Hg[k] - Ho).max() < 1e-12 * scale, (z, np.abs(Hg[k] - Ho).max())
+
+
+def test_matrix_elements_one_centre(config1):
+    basis, paths = config1
+    zs = [-40.0, -3.05, 0.0, 0.05, 12.0]
+    Sg, Hg = _elements(basis, 2.5, 1.0, zs)
+    for k, z in enumerate(zs):
+        So, Ho = O.assemble(basis, 2.5, 1.0, z)
+        assert np.array_equal(Sg[k], np.eye(basis.N))
+        assert np.abs(Hg[k] - Ho).max() < 1e-13 * max(1.0, np.abs(Ho).max())
+
+
+def test_matrix_elements_full_two_centre_sampled(config2):
+    # the full p + H two-centre basis (N = 380, 48 x 48 nodes) at sampled positions
+    basis, paths = config2
+    b = float(paths.b[3])
+    zs = [-50.0, -0.35, 1.05]
+    Sg, Hg = _elements(basis, b, 1.5, zs)
+    for k, z in enumerate(zs):
+        So, Ho = O.assemble(basis, b, 1.5, z)
+        assert np.abs(Sg[k] - So).max() < 1e-12
+        assert np.abs(Hg[k] - Ho).max() < 1e-12 * max(1.0, np.abs(Ho).max())
+
+
+@pytest.mark.parametrize("N", [1, 5, 31, 32, 33, 100, 259])
+def test_solve_random_systems(N):
+    w = _w()
+    rng = np.random.default_rng(N)
+    batch = 3
+    A = rng.standard_normal((batch, N, N)) + 1j * rng.standard_normal((batch, N, N)) + 3 * np.eye(N)
+    B = rng.standard_normal((batch, N, N)) + 1j * rng.standard_normal((batch, N, N))
+    S = w.colmajor(torch.from_numpy(A).cuda())
+    H = w.colmajor(torch.from_numpy(B).cuda())
+    ipiv, info = w.solve(S, H)
+    torch.cuda.synchronize()
+    X = w.natural(H).cpu().numpy()
+    LU = w.natural(S).cpu().numpy()
+    piv = ipiv.cpu().numpy()
+    assert (info.cpu().numpy() == 0).all()
+    for k in range(batch):
+        Xo = np.linalg.solve(A[k], B[k])
+        cond = np.linalg.cond(A[k])
+        assert np.abs(X[k] - Xo).max() < 1e-13 * cond * max(1.0, np.abs(Xo).max())
+        # P A = L U with LAPACK's 1-based interchanges
+        PA = A[k].copy()
+        for i in range(N):
+            p = piv[k, i] - 1
+            assert i <= p < N
+            PA[[i, p]] = PA[[p, i]]
+        L = np.tril(LU[k], -1) + np.eye(N)
+        U = np.triu(LU[k])
+        assert np.abs(L @ U - PA).max() < 1e-13 * N * np.abs(A[k]).max()
+
+
+def test_solve_pivot_matches_partial_pivoting():
+    w = _w()
+    A = np.array([[1e-3, 2.0, 0.0], [3.0, 1.0, 1.0], [-4.0, 0.5, 2.0]], dtype=complex)
+    B = np.eye(3, dtype=complex)[None]
+    S = w.colmajor(torch.from_numpy(A[None].copy()).cuda())
+    H = w.colmajor(torch.from_numpy(B.copy()).cuda())
+    ipiv, info = w.solve(S, H)
+    torch.cuda.synchronize()
+    assert ipiv.cpu().numpy()[0, 0] == 3        # largest |re|+|im| in column 1 is row 3
+    assert np.allclose(w.natural(H).cpu().numpy()[0], np.linalg.inv(A), atol=1e-14)
+
+
+def test_solve_singular_reports_info():
+    w = _w()
+    A = np.eye(4, dtype=complex)
+    A[:, 2] = 0.0
+    S = w.colmajor(torch.from_numpy(A[None].copy()).cuda())
+    H = w.colmajor(torch.from_numpy(np.eye(4, dtype=complex)[None].copy()).cuda())
+    ipiv, info = w.solve(S, H)
+    torch.cuda.synchronize()
+    assert info.cpu().numpy()[0] == 3
+
+
+def test_solve_assembled_overlap(config2):
+    # the solve on a real two-centre S(z) (small b: the least well-conditioned case)
+    basis, paths = config2
+    w = _w()
+    g = w.Basis(basis)
+    S, H = g.matrix_elements(0.2, 1.5, np.array([0.0, 0.6]))
+    So = w.natural(S).cpu().numpy()
+    Ho = w.natural(H).cpu().numpy()
+    ipiv, info = w.solve(S, H)
+    torch.cuda.synchronize()
+    X = w.natural(H).cpu().numpy()
+    for k in range(2):
+        Xo = O.solve(So[k], Ho[k])
+        assert np.abs(X[k] - Xo).max() < 1e-11 * np.abs(Xo).max()
+
+
+def test_propagate_one_centre_full_paths(config1):
+    # the one-centre p + H workload, two of its eight paths over all 800 steps
+    basis, paths = config1
+    w = _w()
+    g = w.Basis(basis)
+    idx = [0, 5]
+    zg = paths.z[0]
+    c = g.propagate(paths.b[idx], paths.v[idx], zg)
+    Pg = w.probabilities(c).cpu().numpy()
+    for n, p in enumerate(idx):
+        Po = O.probabilities(O.propagate(basis, float(paths.b[p]), float(paths.v[p]), zg))
+        _prob_close(Pg[n], Po)
+    # S = I and D Hermitian: only RK4's O((h w)^6) per-step drift moves the norm
+    assert abs(Pg.sum(axis=1) - 1.0).max() < 1e-5
+
+
+def test_propagate_two_centre_ragged_paths_and_chunks(small2c):
+    # uneven path lengths and a workspace limit that forces several chunks of steps
+    w = _w()
+    g = w.Basis(small2c)
+    g.set_workspace_limit(64 << 20)
+    bs = np.array([0.4, 1.7, 3.0])
+    zgs = [wi.uniform_zgrid(-6.0, 6.0, 0.25), wi.uniform_zgrid(-5.0, 4.0, 0.3), wi.uniform_zgrid(-2.0, -1.0, 0.5)]
+    c = g.propagate(bs, 1.3, zgs)
+    Pg = w.probabilities(c).cpu().numpy()
+    for p in range(3):
+        Po = O.probabilities(O.propagate(small2c, float(bs[p]), 1.3, zgs[p]))
+        _prob_close(Pg[p], Po)
+
+
+def test_propagate_zero_steps_leaves_amplitudes(small2c):
+    w = _w()
+    g = w.Basis(small2c)
+    c0 = torch.zeros((1, g.N), dtype=torch.complex128, device="cuda")
+    c0[0, 3] = 0.6 + 0.8j
+    c = g.propagate(np.array([1.0]), 1.0, [np.array([0.5])], c=c0.clone())
+    assert torch.equal(c, c0)
+
+
+def test_propagate_rejects_bad_paths(small2c):
+    w = _w()
+    g = w.Basis(small2c)
+    with pytest.raises(w.WpcccError) as e:
+        g.propagate(np.array([1.0]), 1.0, [np.array([0.0, -1.0])])
+    assert e.value.status == w.EINVAL
+    with pytest.raises(w.WpcccError) as e:
+        g.propagate(np.array([-1.0]), 1.0, [np.array([0.0, 1.0])])
+    assert e.value.status == w.EINVAL
+
+
+def test_propagate_full_two_centre_sampled_paths(config2):
+    # the bench launch configuration (all 32 paths of the two-centre p + H workload batched),
+    # two RK4 steps from z = -0.2; two sampled paths recomputed by the oracle
+    basis, paths = config2
+    w = _w()
+    g = w.Basis(basis)
+    zg = np.array([-0.2, -0.1, 0.0])
+    c = g.propagate(paths.b, paths.v, zg)
+    Pg = w.probabilities(c).cpu().numpy()
+    for p in (0, 17):
+        Po = O.probabilities(O.propagate(basis, float(paths.b[p]), float(paths.v[p]), zg))
+        _prob_close(Pg[p], Po)
+
+
+def test_probabilities_kernel():
+    w = _w()
+    c = torch.randn(4, 37, dtype=torch.complex128, device="cuda")
+    P = w.probabilities(c)
+    assert torch.allclose(P, (c.conj() * c).real, rtol=0, atol=1e-15)

@@ -254,3 +254,15 @@ def test_two_centre_m_reflection_of_probabilities(tiny2c):
     idx = lambda cen, off, rad, m: off + [k for k in range(cen.N) if cen.st_rad[k] == rad and cen.st_m[k] == m][0]
     assert P[idx(T, 0, 2, 1)] == pytest.approx(P[idx(T, 0, 2, -1)], rel=1e-10, abs=1e-15)
     assert P[idx(Pc, T.N, 1, 1)] == pytest.approx(P[idx(Pc, T.N, 1, -1)], rel=1e-10, abs=1e-15)
+
+
+def test_radial_integral_beyond_grid_is_multipole_tail():
+    # beyond r_max the 1s-1s multipole integral is 1/R (unit charge inside), up to the e^{-2 r_max} tail
+    g = wi.radial_grid(2000)
+    f = wi.hydrogenic_radial(1, 0, 1.0, g.r)[None, :]
+    for R in (120.0, 300.0):
+        assert O.radial_F(g, f, f, 0, R)[0] == pytest.approx(1.0 / R, rel=1e-8)
+    # and continuous across the last grid point
+    a = O.radial_F(g, f, f, 0, g.r[-1])[0]
+    b = O.radial_F(g, f, f, 0, g.r[-1] * (1 + 1e-12))[0]
+    assert a == pytest.approx(b, rel=1e-10)
