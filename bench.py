@@ -162,6 +162,9 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all 32)")
+    ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
+    ap.add_argument("--solve-mode", default="stage", choices=["stage", "matrix"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -190,16 +193,19 @@ def main() -> None:
 
     import paper_2403_04252_gb300 as w
     g = w.Basis(basis, device=local)
-    N, n_paths = g.N, paths.n_paths
+    g.set_solve_mode(w.SOLVE_STAGE if args.solve_mode == "stage" else w.SOLVE_MATRIX)
+    n_paths = paths.n_paths if args.paths <= 0 else min(args.paths, paths.n_paths)
+    N = g.N
     zg = paths.z[0]
     n_total = zg.size - 1
-    b = paths.b
-    v = paths.v
+    b = paths.b[:n_paths]
+    v = paths.v[:n_paths]
+    STEP = args.rk4_per_step
     stream = torch.cuda.current_stream(dev)
 
     def segment(k: int):
-        k0 = (k * STEP_RK4) % (n_total - STEP_RK4 + 1)
-        return zg[k0:k0 + STEP_RK4 + 1]
+        k0 = (k * STEP) % (n_total - STEP + 1)
+        return zg[k0:k0 + STEP + 1]
 
     c = torch.zeros((n_paths, N), dtype=torch.complex128, device=dev)
     c[:, 0] = 1.0
@@ -230,7 +236,7 @@ def main() -> None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    units = world * n_paths * STEP_RK4 * args.steps
+    units = world * n_paths * STEP * args.steps
     value = units / (ms / 1e3)
 
     # ---- end to end through the public API with host buffers
@@ -253,20 +259,22 @@ def main() -> None:
         t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    seg_bytes = 8 * (STEP_RK4 + 1) * n_paths + 8 * 2 * n_paths + 4 * n_paths  # z nodes, b, v, n_z
+    seg_bytes = 8 * (STEP + 1) * n_paths + 8 * 2 * n_paths + 4 * n_paths  # z nodes, b, v, n_z
     h2d = c_host.numel() * 16 + seg_bytes
     d2h = P_host.numel() * 8
 
     # ---- roofline of the dominant kernel (FP64 pipe)
     NT, NP_, G = basis.T.N, basis.P.N, basis.quad.G
-    evals = args.steps * n_paths * (2 * STEP_RK4 + 1)
+    evals = args.steps * n_paths * (2 * STEP + 1)
     flops_mol = 12.0 * NT * NP_ * G            # Eq. 9 contraction, three integrals, per z
-    flops_solve = (8.0 / 3.0 + 8.0) * N ** 3    # LU + N right-hand sides, per z
+    # LU, plus N right-hand sides in the paper's form; the stage form's triangular solves run in the RK4 kernel
+    flops_solve = (8.0 / 3.0 + (8.0 if args.solve_mode == "matrix" else 0.0)) * N ** 3
     cand = {"mol_gemm": flops_mol * evals, "solve": flops_solve * evals}
     dom = max(cand, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
     achieved = cand[dom] / (dom_ms / 1e3) / 1e12
-    total_flops = (flops_mol + flops_solve) * evals + 32.0 * N * N * n_paths * STEP_RK4 * args.steps
+    rk4_flops = (32.0 if args.solve_mode == "matrix" else 64.0) * N * N   # per path-step (stage form: H y + 2 triangles)
+    total_flops = (flops_mol + flops_solve) * evals + rk4_flops * n_paths * STEP * args.steps
     launches = int(sum(n for _, n in prof.values())) + 0
     roofline = {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm", "solve": "k_lu_solve"}[dom],
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -278,15 +286,18 @@ def main() -> None:
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": CONFIG_DESC, "form": "plain FP64 (batched over all paths)",
-                       "bench_step": f"{STEP_RK4} RK4 steps of each of the {n_paths} paths per rank",
+            "config": {"workload": CONFIG_DESC, "paths": n_paths,
+                       "form": "plain FP64, all paths batched; S^-1 applied "
+                               + ("per RK4 stage from LU factors" if args.solve_mode == "stage"
+                                  else "as X = S^-1 H with N right-hand sides (the paper's ZGESV form)"),
+                       "bench_step": f"{STEP} RK4 steps of each of the {n_paths} paths per rank",
                        "l2": "inputs larger than L2: S and H of one step are "
-                             f"{2 * 16 * N * N * n_paths * (2 * STEP_RK4 + 1) / 1e9:.1f} GB"},
+                             f"{2 * 16 * N * N * n_paths * (2 * STEP + 1) / 1e9:.1f} GB"},
             "roofline": roofline,
             "fp64_frac_whole_step": total_flops / (ms / 1e3) * world / 1e12 / FP64_PEAK_TFLOPS / world,
             "matrix_elements_per_s": world * evals * (NT * NT + NP_ * NP_ + 3 * NT * NP_) / (ms / 1e3),
             "kernel_ms": {k: v_[0] for k, v_ in prof.items()},
-            "e2e": {"value": world * n_paths * STEP_RK4 * args.steps / e2e_s, "unit": UNIT,
+            "e2e": {"value": world * n_paths * STEP * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks}
     if cpu is not None:

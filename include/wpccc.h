@@ -62,7 +62,7 @@ typedef enum {
 
 /* Largest orbital angular momentum a basis may hold, and largest system size. */
 #define WPCCC_LMAX 10
-#define WPCCC_NMAX 3072
+#define WPCCC_NMAX 2900
 
 /* Opaque handle: the basis and every z-independent table, resident on one device. */
 typedef struct wpccc_basis_s* wpccc_basis;
@@ -201,6 +201,18 @@ WPCCC_API wpccc_status wpccc_propagate(wpccc_basis basis, const wpccc_paths* pat
  * Errors: EINVAL, ECUDA.
  */
 WPCCC_API wpccc_status wpccc_probabilities(int n_paths, int N, const void* c, double* P, void* stream);
+
+/*
+ * How wpccc_propagate applies S^{-1} (two-centre mode).  Both give M(z) c up to rounding.
+ *   WPCCC_SOLVE_STAGE  (default) LU-factorise S(z) once per position; at every RK4
+ *                      stage form H(z) y and solve S(z) k = H(z) y with the factors
+ *                      ((8/3) N^3 flops per position plus 16 N^2 per stage).
+ *   WPCCC_SOLVE_MATRIX the paper's form: X = S^{-1} H with N right-hand sides per
+ *                      position (ZGESV, (8/3 + 8) N^3 flops), then M c = -(i/v) X c.
+ */
+#define WPCCC_SOLVE_STAGE 0
+#define WPCCC_SOLVE_MATRIX 1
+WPCCC_API wpccc_status wpccc_basis_set_solve_mode(wpccc_basis basis, int mode);
 
 /*
  * Upper bound on the scratch memory wpccc_propagate may hold (default 8 GiB).

@@ -30,7 +30,7 @@ _lib = C.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ESINGULAR, ENONFINITE, ECUDA, EUNSUPPORTED = range(7)
 _NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENONFINITE", 5: "ECUDA", 6: "EUNSUPPORTED"}
 LMAX = 10
-NMAX = 3072
+NMAX = 2900
 
 _pd = C.POINTER(C.c_double)
 _pi = C.POINTER(C.c_int)
@@ -63,16 +63,18 @@ _lib.wpccc_propagate.argtypes = [C.c_void_p, C.POINTER(_PathsDesc), C.c_int, C.c
 _lib.wpccc_probabilities.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.wpccc_basis_set_workspace_limit.argtypes = [C.c_void_p, C.c_size_t]
 _lib.wpccc_profile_enable.argtypes = [C.c_void_p, C.c_int]
+_lib.wpccc_basis_set_solve_mode.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_profile_read.argtypes = [C.c_void_p, _pd, C.POINTER(C.c_longlong)]
 _lib.wpccc_last_error.restype = C.c_char_p
 for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
            "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
-           "wpccc_profile_enable", "wpccc_profile_read"):
+           "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
             "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
-            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_last_error")
+            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error")
+SOLVE_STAGE, SOLVE_MATRIX = 0, 1
 PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4")
 
 
@@ -165,6 +167,10 @@ class Basis:
     def set_workspace_limit(self, nbytes: int) -> None:
         _check(_lib.wpccc_basis_set_workspace_limit(self._h, C.c_size_t(int(nbytes))),
                "wpccc_basis_set_workspace_limit")
+
+    def set_solve_mode(self, mode: int) -> None:
+        """SOLVE_STAGE (factor S once per position, solve per RK4 stage) or SOLVE_MATRIX (X = S^-1 H)."""
+        _check(_lib.wpccc_basis_set_solve_mode(self._h, int(mode)), "wpccc_basis_set_solve_mode")
 
     def profile_enable(self, on: bool = True) -> None:
         """Reset the per-kernel counters; with on=True time every launch with CUDA events."""

@@ -402,6 +402,14 @@ extern "C" wpccc_status wpccc_profile_read(wpccc_basis B, double* ms, long long*
     return WPCCC_OK;
 }
 
+extern "C" wpccc_status wpccc_basis_set_solve_mode(wpccc_basis B, int mode) {
+    if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_solve_mode: null basis");
+    if (mode != WPCCC_SOLVE_STAGE && mode != WPCCC_SOLVE_MATRIX)
+        return fail(WPCCC_EINVAL, "wpccc_basis_set_solve_mode: unknown mode");
+    B->solve_mode = mode;
+    return WPCCC_OK;
+}
+
 extern "C" wpccc_status wpccc_basis_set_workspace_limit(wpccc_basis B, size_t bytes) {
     if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_workspace_limit: null basis");
     if (bytes < ((size_t)64 << 20)) return fail(WPCCC_EINVAL, "workspace limit below 64 MiB");

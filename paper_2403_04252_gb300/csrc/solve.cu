@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_solve(int N, double2* __restr
     const int sys = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t mat = (size_t)N * N;
     double2* A = Sall + (size_t)sys * mat;
-    double2* Bm = Hall + (size_t)sys * mat;
+    double2* Bm = Hall ? Hall + (size_t)sys * mat : nullptr;
     int* ipiv = ipiv_all + (size_t)sys * N;
     if (tid == 0) s_info = 0;
     __syncthreads();
@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_solve(int N, double2* __restr
         }
         // ---- 2. interchanges on every column outside the panel (S) and on H
         const int nS = N - nb;
-        for (int c = tid; c < nS + N; c += LU_THREADS) {
+        const int nH = Bm ? N : 0;
+        for (int c = tid; c < nS + nH; c += LU_THREADS) {
             double2* col;
             if (c < nS) {
                 const int cc = c < k0 ? c : c + nb;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_solve(int N, double2* __restr
         // ---- 3. U12 = L11^{-1} A12 for trailing S columns and all H columns:
         //         one warp per column, lane i holds row k0 + i (NB == warp size)
         const int nTr = N - k0 - nb;
-        for (int c = warp; c < nTr + N; c += LU_THREADS / 32) {
+        for (int c = warp; c < nTr + nH; c += LU_THREADS / 32) {
             double2* col = (c < nTr) ? A + (size_t)(k0 + nb + c) * N + k0 : Bm + (size_t)(c - nTr) * N + k0;
             double2 x = lane < nb ? col[lane] : make_double2(0.0, 0.0);
             for (int j = 0; j < nb - 1; ++j) {
@@ -234,14 +235,14 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_solve(int N, double2* __restr
             if (nTr > 0)
                 cta_gemm_sub(A + (size_t)(k0 + nb) + (size_t)(k0 + nb) * N, N, L21, N,
                              A + (size_t)k0 + (size_t)(k0 + nb) * N, N, m, nTr, nb, sA, sB);
-            cta_gemm_sub(Bm + (size_t)(k0 + nb), N, L21, N, Bm + (size_t)k0, N, m, N, nb, sA, sB);
+            if (Bm) cta_gemm_sub(Bm + (size_t)(k0 + nb), N, L21, N, Bm + (size_t)k0, N, m, N, nb, sA, sB);
         }
         __syncthreads();
     }
 
     const int info = s_info;
     if (tid == 0) info_all[sys] = info;
-    if (info != 0) return;   // no solution for a singular system (as ZGESV)
+    if (info != 0 || !Bm) return;   // factor only, or no solution for a singular system (as ZGESV)
 
     // ---- back substitution X = U^{-1} Y
     const int last = ((N - 1) / NB) * NB;
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(LU_THREADS) k_lu_solve(int N, double2* __restr
 
 size_t solve_smem_bytes() { return sizeof(double2) * (TM * NB + NB * TN + NB * NB + NB); }
 
+// H == nullptr: factorisation only (P S = L U), no right-hand sides.
 wpccc_status launch_solve(int N, int batch, double2* S, double2* H, int* ipiv, int* info, cudaStream_t st) {
     if (batch == 0) return WPCCC_OK;
     const int smem = (int)solve_smem_bytes();

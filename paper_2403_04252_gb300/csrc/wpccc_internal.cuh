@@ -96,6 +96,7 @@ struct wpccc_basis_s {
     void* ws_ptr = nullptr;
     size_t ws_bytes = 0;
     size_t ws_limit = (size_t)8 << 30;
+    int solve_mode = WPCCC_SOLVE_STAGE;
     wpccc::Profiler prof;
 };
 

@@ -178,10 +178,13 @@ def test_propagate_one_centre_full_paths(config1):
     assert abs(Pg.sum(axis=1) - 1.0).max() < 1e-5
 
 
-def test_propagate_two_centre_ragged_paths_and_chunks(small2c):
-    # uneven path lengths and a workspace limit that forces several chunks of steps
+@pytest.mark.parametrize("mode", [0, 1])
+def test_propagate_two_centre_ragged_paths_and_chunks(small2c, mode):
+    # uneven path lengths and a workspace limit that forces several chunks of steps;
+    # both ways of applying S^-1 (LU per RK4 stage, and the paper's X = S^-1 H)
     w = _w()
     g = w.Basis(small2c)
+    g.set_solve_mode(mode)
     g.set_workspace_limit(64 << 20)
     bs = np.array([0.4, 1.7, 3.0])
     zgs = [wi.uniform_zgrid(-6.0, 6.0, 0.25), wi.uniform_zgrid(-5.0, 4.0, 0.3), wi.uniform_zgrid(-2.0, -1.0, 0.5)]
@@ -212,12 +215,14 @@ def test_propagate_rejects_bad_paths(small2c):
     assert e.value.status == w.EINVAL
 
 
-def test_propagate_full_two_centre_sampled_paths(config2):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_propagate_full_two_centre_sampled_paths(config2, mode):
     # the bench launch configuration (all 32 paths of the two-centre p + H workload batched),
     # two RK4 steps from z = -0.2; two sampled paths recomputed by the oracle
     basis, paths = config2
     w = _w()
     g = w.Basis(basis)
+    g.set_solve_mode(mode)
     zg = np.array([-0.2, -0.1, 0.0])
     c = g.propagate(paths.b, paths.v, zg)
     Pg = w.probabilities(c).cpu().numpy()
