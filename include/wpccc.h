@@ -159,6 +159,31 @@ WPCCC_API wpccc_status wpccc_matrix_elements(wpccc_basis basis, double b, double
                                    void* S, void* H, void* stream);
 
 /*
+ * wpccc_matrix_elements without any device allocation.  The paper has no
+ * counterpart: this is for callers that cannot let the library allocate device
+ * memory inside a call, e.g. a host framework that reserved the device memory up
+ * front (a further cudaMalloc would fail or fragment its pool), or a
+ * latency-critical loop that cannot absorb the device-wide synchronisation of
+ * cudaMalloc/cudaFree.  Same arguments and results as wpccc_matrix_elements
+ * (S and H are written by the same kernels; the caller still owns them).
+ * Scratch memory: a fixed array of WPCCC_NOALLOC_SCRATCH_BYTES (64 MiB) inside
+ * the library, which every GPU that loads the library holds until the process
+ * exits.  Nothing in it needs clearing (every byte a call reads it first writes),
+ * and it keeps the last call's contents.  All calls on a device share it:
+ * calls whose GPU work overlaps (other streams, other threads, other bases) race
+ * and corrupt each other's results; serialise them.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Positions are
+ * processed in groups that fit the array, and the call waits for each group on
+ * `stream`.  Errors: EINVAL (as wpccc_matrix_elements, or a basis whose single
+ * position needs more scratch than the array holds; the message states both
+ * sizes), ECUDA.  The basis itself must have been created beforehand.
+ */
+#define WPCCC_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+WPCCC_API wpccc_status wpccc_matrix_elements_noalloc(wpccc_basis basis, double b, double v, int nz,
+                                                     const double* z, void* S, void* H, void* stream);
+
+/*
  * Batched complex solve S X = H with partial pivoting (Sec. II: the paper calls
  * LAPACK/cuSOLVER/hipSOLVER ZGESV; this is a hand-written blocked LU).
  *   S     device [batch][N][N] complex128; overwritten by the factors L and U of

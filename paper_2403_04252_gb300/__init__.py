@@ -57,6 +57,8 @@ _lib.wpccc_basis_destroy.argtypes = [C.c_void_p]
 _lib.wpccc_basis_info.argtypes = [C.c_void_p, _pi, _pi]
 _lib.wpccc_matrix_elements.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, _pd,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.wpccc_matrix_elements_noalloc.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, _pd,
+                                               C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.wpccc_solve.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_int, C.c_void_p]
 _lib.wpccc_propagate.argtypes = [C.c_void_p, C.POINTER(_PathsDesc), C.c_int, C.c_int, C.c_void_p, C.c_void_p]
@@ -68,12 +70,15 @@ _lib.wpccc_profile_read.argtypes = [C.c_void_p, _pd, C.POINTER(C.c_longlong)]
 _lib.wpccc_last_error.restype = C.c_char_p
 for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
            "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
-           "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode"):
+           "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode",
+           "wpccc_matrix_elements_noalloc"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
             "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
-            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error")
+            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error",
+            "wpccc_matrix_elements_noalloc")
+NOALLOC_SCRATCH_BYTES = 64 << 20
 SOLVE_STAGE, SOLVE_MATRIX = 0, 1
 PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4")
 
@@ -194,6 +199,14 @@ class Basis:
             H = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
         _check(_lib.wpccc_matrix_elements(self._h, float(b), float(v), int(z.size), zp, _ptr(S), _ptr(H),
                                           _stream(stream)), "wpccc_matrix_elements")
+        return S, H
+
+    def matrix_elements_noalloc(self, b: float, v: float, z, S, H, stream=None):
+        """Same as matrix_elements into caller-owned S, H, but the library allocates no device memory:
+        its scratch is a fixed 64 MiB array shared by every call on the device (serialise calls)."""
+        z, zp = _arr(np.atleast_1d(z), np.float64)
+        _check(_lib.wpccc_matrix_elements_noalloc(self._h, float(b), float(v), int(z.size), zp, _ptr(S), _ptr(H),
+                                                  _stream(stream)), "wpccc_matrix_elements_noalloc")
         return S, H
 
     def propagate(self, b, v, zgrids, c=None, precision_mode: int = 0, batch_mode: int = 0, stream=None):

@@ -254,7 +254,8 @@ class Quadrature:
 
 def make_quadrature(Geta: int = 48, Gtau: int = 48, gamma: float = 0.5) -> Quadrature:
     s, w = special.roots_laguerre(Geta)
-    ws = np.exp(np.log(w) + s)
+    with np.errstate(divide="ignore"):   # weights that underflow (very large rules) drop their nodes
+        ws = np.exp(np.log(w) + s)
     tau, wtau = np.polynomial.legendre.leggauss(Gtau)
     return Quadrature(s=s.astype(np.float64), ws=ws, tau=tau, wtau=wtau, gamma=float(gamma))
 
