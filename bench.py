@@ -8,7 +8,8 @@ plus 10 Coulomb wave-packet pseudostates per l <= 3 on each centre (N_T = N_P =
 z from -50 to 50 a.u. with h = 0.1 (1000 RK4 steps per path).  Inputs are
 synthetic (generated basis, straight-line paths).
 
-One bench step advances all 32 paths by STEP_RK4 consecutive RK4 steps through
+One bench step advances all 32 paths by STEP_RK4 consecutive RK4 steps (the
+steps of the run are consecutive and centred on z = 0) through
 the public call wpccc_propagate (matrix elements at every z it needs, the solve
 S X = H, the RK4 sweep), in plain FP64.  `value` counts RK4 steps of all paths
 on all ranks per second of device time; `e2e` times the same work with the
@@ -43,6 +44,8 @@ STEP_RK4 = 16           # RK4 steps of every path per bench step
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_DFMA_MEASURED_TFLOPS = 1.20   # FMA microbenchmark on this machine's GB300 (all SMs, register operands)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_FFMA_MEASURED_TFLOPS = 69.9
 CONFIG_DESC = ("two-centre p+H (Z_T=Z_P=1): hydrogenic n<=4 + 10 Coulomb wave-packet bins per l<=3 (k<=3) "
                "on each centre, all m, N_T=N_P=190, N=380; 48x48 (eta,tau) nodes; Nr=2000 to 100 a.u.; "
                "v=1.5; 32 b uniform in [0.2,12]; z in [-50,50], h=0.1")
@@ -165,6 +168,8 @@ def main() -> None:
     ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all 32)")
     ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
     ap.add_argument("--solve-mode", default="stage", choices=["stage", "matrix"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: plain FP64; mixed: FP32 contraction and LU, FP64 refinement and RK4")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -203,14 +208,19 @@ def main() -> None:
     STEP = args.rk4_per_step
     stream = torch.cuda.current_stream(dev)
 
+    # the bench steps cover consecutive segments centred on closest approach (z = 0), where the
+    # couplings are strongest; they wrap around if more steps are asked for than the path holds
+    first = max(0, n_total // 2 - (args.warmup + args.steps) * STEP // 2)
+
     def segment(k: int):
-        k0 = (k * STEP) % (n_total - STEP + 1)
+        k0 = (first + k * STEP) % (n_total - STEP + 1)
         return zg[k0:k0 + STEP + 1]
 
+    prec = 1 if args.precision == "mixed" else 0
     c = torch.zeros((n_paths, N), dtype=torch.complex128, device=dev)
     c[:, 0] = 1.0
     for k in range(args.warmup):
-        g.propagate(b, v, segment(k), c=c)
+        g.propagate(b, v, segment(k), c=c, precision_mode=prec)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -224,7 +234,7 @@ def main() -> None:
     torch.cuda.synchronize()
     e0.record(stream)
     for k in range(args.steps):
-        g.propagate(b, v, segment(args.warmup + k), c=c)
+        g.propagate(b, v, segment(args.warmup + k), c=c, precision_mode=prec)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -250,7 +260,7 @@ def main() -> None:
     t0 = time.perf_counter()
     for k in range(args.steps):
         c_dev.copy_(c_host, non_blocking=True)
-        g.propagate(b, v, segment(args.warmup + k), c=c_dev)
+        g.propagate(b, v, segment(args.warmup + k), c=c_dev, precision_mode=prec)
         P = w.probabilities(c_dev)
         P_host.copy_(P, non_blocking=True)
         torch.cuda.synchronize()
@@ -263,43 +273,73 @@ def main() -> None:
     h2d = c_host.numel() * 16 + seg_bytes
     d2h = P_host.numel() * 8
 
-    # ---- roofline of the dominant kernel (FP64 pipe)
+    # ---- accuracy of the mixed form: the same steps again in plain FP64 (untimed)
+    prob_err = None
+    if prec == 1:
+        c64 = torch.zeros((n_paths, N), dtype=torch.complex128, device=dev)
+        c64[:, 0] = 1.0
+        for k in range(args.warmup + args.steps):
+            g.propagate(b, v, segment(k), c=c64, precision_mode=0)
+        Pm = w.probabilities(c).cpu().numpy()
+        P64 = w.probabilities(c64).cpu().numpy()
+        prob_err = {"max_abs": float(np.abs(Pm - P64).max()),
+                    "per_probability_max": [float(x) for x in np.abs(Pm - P64).max(axis=0)[:8]],
+                    "against": "the plain FP64 form on the same steps (itself within 1e-10 of the oracle)",
+                    "rk4_steps_per_path": (args.warmup + args.steps) * STEP}
+
+    # ---- roofline of the dominant kernel
     NT, NP_, G = basis.T.N, basis.P.N, basis.quad.G
+    n_half = int(sum(1 for m in basis.P.st_m if m >= 0))
     evals = args.steps * n_paths * (2 * STEP + 1)
-    flops_mol = 12.0 * NT * NP_ * G            # Eq. 9 contraction, three integrals, per z
+    # Eq. 9 contraction, three integrals, per z: projectile columns with q >= 0 (the reflection gives the rest)
+    flops_mol = 12.0 * NT * n_half * G
     # LU, plus N right-hand sides in the paper's form; the stage form's triangular solves run in the RK4 kernel
-    flops_solve = (8.0 / 3.0 + (8.0 if args.solve_mode == "matrix" else 0.0)) * N ** 3
-    cand = {"mol_gemm": flops_mol * evals, "solve": flops_solve * evals}
-    dom = max(cand, key=lambda k: prof[k][0])
+    flops_solve = (8.0 / 3.0 + (8.0 if (args.solve_mode == "matrix" and prec == 0) else 0.0)) * N ** 3
+    # RK4 per path-step (FP64): 4 applications of M; matrix form X y, stage form H y + two triangles,
+    # mixed form H y and one refinement residual S x
+    rk4_flops = {"matrix": 32.0, "stage": 64.0}[args.solve_mode] * N * N if prec == 0 else 64.0 * N * N
+    cand = {"mol_gemm": (flops_mol * evals, FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS,
+                         "k_mol_gemm" + ("<float>" if prec else "<double>")),
+            "solve": (flops_solve * evals, FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS,
+                      "k_lu_factor_f32" if prec else "k_lu_solve"),
+            "rk4": (rk4_flops * n_paths * STEP * args.steps, FP64_PEAK_TFLOPS, "k_rk4")}
+    dom = max(cand, key=lambda k: prof[k][0] if k in prof else 0.0)
     dom_ms, dom_launches = prof[dom]
-    achieved = cand[dom] / (dom_ms / 1e3) / 1e12
-    rk4_flops = (32.0 if args.solve_mode == "matrix" else 64.0) * N * N   # per path-step (stage form: H y + 2 triangles)
+    dom_flops, dom_peak, dom_name = cand[dom]
+    achieved = dom_flops / (dom_ms / 1e3) / 1e12
     total_flops = (flops_mol + flops_solve) * evals + rk4_flops * n_paths * STEP * args.steps
-    launches = int(sum(n for _, n in prof.values())) + 0
-    roofline = {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm", "solve": "k_lu_solve"}[dom],
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
-                               f"measured DFMA microbenchmark {FP64_DFMA_MEASURED_TFLOPS} TFLOP/s",
+    launches = int(sum(n for _, n in prof.values()))
+    roofline = {"bound": "alu", "kernel": dom_name,
+                "achieved": achieved, "peak": dom_peak, "unit": "TFLOP/s",
+                "frac": achieved / dom_peak, "traffic": None,
+                "peak_source": ("FP32 pipe from unit counts and clocks (152 SMs x 128 FFMA/clk x 2.07 GHz); "
+                                f"measured FFMA microbenchmark {FP32_FFMA_MEASURED_TFLOPS} TFLOP/s")
+                if dom_peak == FP32_PEAK_TFLOPS else
+                ("FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
+                 f"measured DFMA microbenchmark {FP64_DFMA_MEASURED_TFLOPS} TFLOP/s"),
                 "launch_ms_avg": dom_ms / max(dom_launches, 1),
-                "flop_per_launch": cand[dom] / max(dom_launches, 1)}
+                "flop_per_launch": dom_flops / max(dom_launches, 1)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
             "config": {"workload": CONFIG_DESC, "paths": n_paths,
-                       "form": "plain FP64, all paths batched; S^-1 applied "
-                               + ("per RK4 stage from LU factors" if args.solve_mode == "stage"
-                                  else "as X = S^-1 H with N right-hand sides (the paper's ZGESV form)"),
+                       "form": ("mixed precision: Eq. 9 contraction and LU on the FP32 pipe, FP64 node "
+                                "tables, refinement and RK4; all paths batched" if prec else
+                                "plain FP64, all paths batched; S^-1 applied "
+                                + ("per RK4 stage from LU factors" if args.solve_mode == "stage"
+                                   else "as X = S^-1 H with N right-hand sides (the paper's ZGESV form)")),
                        "bench_step": f"{STEP} RK4 steps of each of the {n_paths} paths per rank",
                        "l2": "inputs larger than L2: S and H of one step are "
                              f"{2 * 16 * N * N * n_paths * (2 * STEP + 1) / 1e9:.1f} GB"},
             "roofline": roofline,
-            "fp64_frac_whole_step": total_flops / (ms / 1e3) * world / 1e12 / FP64_PEAK_TFLOPS / world,
+            "algorithmic_tflops_whole_step": total_flops / (ms / 1e3) / 1e12,
             "matrix_elements_per_s": world * evals * (NT * NT + NP_ * NP_ + 3 * NT * NP_) / (ms / 1e3),
             "kernel_ms": {k: v_[0] for k, v_ in prof.items()},
             "e2e": {"value": world * n_paths * STEP * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks}
+    if prob_err is not None:
+        line["prob_error"] = prob_err
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

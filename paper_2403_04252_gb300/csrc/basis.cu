@@ -275,9 +275,17 @@ static void free_basis(wpccc_basis_s* B) {
     if (!B) return;
     cudaSetDevice(B->device);
     B->prof.release();
+    if (B->rk_stream) {
+        cudaStreamSynchronize(B->rk_stream);
+        cudaStreamDestroy(B->rk_stream);
+    }
+    cudaEvent_t evs[] = {B->ev_asm[0], B->ev_asm[1], B->ev_rk[0], B->ev_rk[1], B->ev_fork, B->ev_join};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
     free_centre(B->T);
     free_centre(B->P);
-    void* ptrs[] = {B->r, B->w, B->s, B->ws, B->tau, B->wtau, B->half_state, B->half_of, B->ws_ptr};
+    void* ptrs[] = {B->r, B->w, B->s, B->ws, B->tau, B->wtau, B->half_state, B->half_of, B->qtile_q,
+                    B->qtile_cols, B->ws_ptr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;
@@ -350,6 +358,20 @@ extern "C" wpccc_status wpccc_basis_create(const wpccc_basis_desc* d, int device
             half_state.push_back(j);
         }
         B->n_half = (int)half_state.size();
+        // column tiles of one q for the FP32 contraction
+        std::vector<int> tq, tc;
+        for (int q = 0; q <= B->P.lmax; ++q) {
+            std::vector<int> cols;
+            for (int h = 0; h < B->n_half; ++h)
+                if (d->P.st_m[half_state[h]] == q) cols.push_back(h);
+            for (size_t k = 0; k < cols.size(); k += 16) {
+                tq.push_back(q);
+                for (size_t c = 0; c < 16; ++c) tc.push_back(k + c < cols.size() ? cols[k + c] : -1);
+            }
+        }
+        B->n_qtiles = (int)tq.size();
+        if ((st = upload(&B->qtile_q, tq.data(), tq.size(), "upload qtile_q")) != WPCCC_OK) return bail(st);
+        if ((st = upload(&B->qtile_cols, tc.data(), tc.size(), "upload qtile_cols")) != WPCCC_OK) return bail(st);
         if ((st = upload(&B->half_state, half_state.data(), half_state.size(), "upload half")) != WPCCC_OK)
             return bail(st);
         if ((st = upload(&B->half_of, half_of.data(), half_of.size(), "upload half_of")) != WPCCC_OK)

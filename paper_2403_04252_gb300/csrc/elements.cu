@@ -65,11 +65,22 @@ struct NodeArgs {
     double gamma, Z_T, Z_P;
     const double *r, *fT, *fP, *s, *ws, *tau, *wtau;
     double* node;            // per evaluation: [fT | fP | thT | thP | pad | W] (see elem_scratch_layout)
-    size_t node_doubles;
-    size_t w_off;            // offset of W in doubles (even, so W is 16-byte aligned)
+    size_t node_doubles;     // stride between evaluations, in doubles
+    size_t w_off;            // offset of W in elements of the table type (even, so W stays aligned)
+    // T = float: per-state products instead of per-radial values (one rounding of f * Theta * sign)
+    int N_T, n_half;
+    const int *stT_index, *half_of, *radT_l, *radP_l;
 };
 
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+// The per-node factors are computed in FP64; T = double keeps them in FP64, T = float (mixed-precision
+// form) stores them rounded to FP32 for the FP32 contraction.
+template <typename T>
 __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc* __restrict__ ev) {
+    using T2 = typename Vec2<T>::type;
     const int e = blockIdx.y;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= A.G) return;
@@ -90,39 +101,23 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
     double sph, cph;
     sincos(0.5 * v * z * eta * tau, &sph, &cph);
 
-    double* base = A.node + (size_t)e * A.node_doubles;
-    double* oT = base;
-    double* oP = oT + (size_t)A.nradT * A.G;
-    double* thT = oP + (size_t)A.nradP * A.G;
-    double* thP = thT + (size_t)A.nlqT * A.G;
-    double2* W = reinterpret_cast<double2*>(base + A.w_off);
+    T* base = reinterpret_cast<T*>(A.node + (size_t)e * A.node_doubles);
+    T* oT = base;
+    T* oP = oT + (size_t)A.nradT * A.G;
+    T* thT = oP + (size_t)A.nradP * A.G;
+    T* thP = thT + (size_t)A.nlqT * A.G;
+    T2* W = reinterpret_cast<T2*>(base + A.w_off);
 
     // radial functions at the node radii
     int sT, sP;
     double LT[5], LP[5];
     const bool inT = stencil5(A.r, A.Nr, rT, sT, LT);
     const bool inP = stencil5(A.r, A.Nr, rP, sP, LP);
-    for (int a = 0; a < A.nradT; ++a) {
-        double val = 0.0;
-        if (inT) {
-            const double* fa = A.fT + (size_t)a * A.Nr + sT;
-            val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
-        }
-        oT[(size_t)a * A.G + g] = val;
-    }
-    for (int a = 0; a < A.nradP; ++a) {
-        double val = 0.0;
-        if (inP) {
-            const double* fa = A.fP + (size_t)a * A.Nr + sP;
-            val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
-        }
-        oP[(size_t)a * A.G + g] = val;
-    }
     // Theta_lq(c) = sqrt((2l+1)/2 (l-q)!/(l+q)!) P_l^q(c), index l(l+1)/2 + q
+    double thv[2][(WPCCC_LMAX + 1) * (WPCCC_LMAX + 2) / 2];
     for (int cen = 0; cen < 2; ++cen) {
         const double c = cen == 0 ? cT : cP;
         const int lmax = cen == 0 ? A.lmaxT : A.lmaxP;
-        double* th = cen == 0 ? thT : thP;
         const double sq = sqrt((1.0 - c) * (1.0 + c));
         double pmm = 1.0;   // P_q^q, built up from P_0^0 = 1
         for (int q = 0; q <= lmax; ++q) {
@@ -138,7 +133,57 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
                     pb = pl;
                 }
                 const double nrm = sqrt((2.0 * l + 1.0) * 0.5 * dfact(l - q) / dfact(l + q));
-                th[(size_t)(l * (l + 1) / 2 + q) * A.G + g] = nrm * pl;
+                thv[cen][l * (l + 1) / 2 + q] = nrm * pl;
+            }
+        }
+    }
+    if (sizeof(T) == 8) {
+        for (int a = 0; a < A.nradT; ++a) {
+            double val = 0.0;
+            if (inT) {
+                const double* fa = A.fT + (size_t)a * A.Nr + sT;
+                val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
+            }
+            oT[(size_t)a * A.G + g] = (T)val;
+        }
+        for (int a = 0; a < A.nradP; ++a) {
+            double val = 0.0;
+            if (inP) {
+                const double* fa = A.fP + (size_t)a * A.Nr + sP;
+                val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
+            }
+            oP[(size_t)a * A.G + g] = (T)val;
+        }
+        for (int t = 0; t < A.nlqT; ++t) thT[(size_t)t * A.G + g] = (T)thv[0][t];
+        for (int t = 0; t < A.nlqP; ++t) thP[(size_t)t * A.G + g] = (T)thv[1][t];
+    } else {
+        // per state: A_T[i][g] = f_a(r_T) Theta_{l|m|}(c_T) (-1)^m [m < 0], A_P[j][g] = f_b(r_P) Theta_{lq}(c_P)
+        T* aT = base;
+        T* aP = aT + (size_t)A.N_T * A.G;
+        for (int a = 0; a < A.nradT; ++a) {
+            double val = 0.0;
+            if (inT) {
+                const double* fa = A.fT + (size_t)a * A.Nr + sT;
+                val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
+            }
+            const int l = A.radT_l[a];
+            for (int m = -l; m <= l; ++m) {
+                const int i = A.stT_index[a * (2 * WPCCC_LMAX + 1) + m + WPCCC_LMAX];
+                const int am = m < 0 ? -m : m;
+                const double sg = (m < 0 && (am & 1)) ? -1.0 : 1.0;
+                aT[(size_t)i * A.G + g] = (T)(val * thv[0][l * (l + 1) / 2 + am] * sg);
+            }
+        }
+        for (int b2 = 0; b2 < A.nradP; ++b2) {
+            double val = 0.0;
+            if (inP) {
+                const double* fa = A.fP + (size_t)b2 * A.Nr + sP;
+                val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
+            }
+            const int l = A.radP_l[b2];
+            for (int q = 0; q <= l; ++q) {
+                const int j = A.half_of[b2 * (WPCCC_LMAX + 1) + q];
+                aP[(size_t)j * A.G + g] = (T)(val * thv[1][l * (l + 1) / 2 + q]);
             }
         }
     }
@@ -157,9 +202,16 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         }
         const double2 w0 = make_double2(J * re, J * im);
         const size_t o = (size_t)d * A.G + g;
-        W[o] = w0;
-        W[stride + o] = make_double2(w0.x * uQ, w0.y * uQ);
-        W[2 * stride + o] = make_double2(w0.x * uQt, w0.y * uQt);
+        T2 a, bq, c;
+        a.x = (T)w0.x;
+        a.y = (T)w0.y;
+        bq.x = (T)(w0.x * uQ);
+        bq.y = (T)(w0.y * uQ);
+        c.x = (T)(w0.x * uQt);
+        c.y = (T)(w0.y * uQt);
+        W[o] = a;
+        W[stride + o] = bq;
+        W[2 * stride + o] = c;
     }
 }
 
@@ -178,25 +230,34 @@ struct GemmArgs {
     double2* mol;                         // [nev][3][N_T][n_half]
 };
 
+template <typename R> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+
+// R = double: FP64 throughout.  R = float (mixed-precision form): node values are rounded to FP32 in
+// shared memory, products and sums run on the FP32 pipe, with the sum over each chunk of GT_K nodes
+// formed separately and then added to the running total (two-level summation).
+template <typename R>
 __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
-    extern __shared__ double smem[];
-    double* sAT = smem;                                   // [GT_K][GT_I + 1]
-    double* sAP = sAT + GT_K * (GT_I + 1);                // [GT_K][GT_J + 1]
-    double2* sW = reinterpret_cast<double2*>(sAP + GT_K * (GT_J + 1));  // [3][dmax+1][GT_K]
+    using R2 = typename Cplx<R>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sAT = reinterpret_cast<R*>(smem_raw);                      // [GT_K][GT_I + 1]
+    R* sAP = sAT + GT_K * (GT_I + 1);                             // [GT_K][GT_J + 1]
+    R2* sW = reinterpret_cast<R2*>(sAP + GT_K * (GT_J + 1));      // [3][dmax+1][GT_K]
     __shared__ int s_rrad[GT_I], s_rlq[GT_I], s_rq[GT_I];
-    __shared__ double s_rsgn[GT_I];
+    __shared__ R s_rsgn[GT_I];
     __shared__ int s_crad[GT_J], s_clq[GT_J], s_cq[GT_J];
 
     const int e = blockIdx.y;
     const int rt = blockIdx.x / A.n_col_tiles, ct = blockIdx.x % A.n_col_tiles;
     const int i0 = rt * GT_I, j0 = ct * GT_J;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const double* base = A.node + (size_t)e * A.node_doubles;
-    const double* fT = base;
-    const double* fP = fT + (size_t)A.nradT * A.G;
-    const double* thT = fP + (size_t)A.nradP * A.G;
-    const double* thP = thT + (size_t)A.nlqT * A.G;
-    const double2* W = reinterpret_cast<const double2*>(base + A.w_off);
+    const R* base = reinterpret_cast<const R*>(A.node + (size_t)e * A.node_doubles);
+    const R* fT = base;
+    const R* fP = fT + (size_t)A.nradT * A.G;
+    const R* thT = fP + (size_t)A.nradP * A.G;
+    const R* thP = thT + (size_t)A.nlqT * A.G;
+    const R2* W = reinterpret_cast<const R2*>(base + A.w_off);
 
     if (tid < GT_I) {
         int i = i0 + tid;
@@ -205,12 +266,12 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
             s_rrad[tid] = A.stT_rad[i];
             s_rlq[tid] = l * (l + 1) / 2 + am;
             s_rq[tid] = m;
-            s_rsgn[tid] = (m < 0 && (am & 1)) ? -1.0 : 1.0;   // Theta_{l,-q} = (-1)^q Theta_{l,q}
+            s_rsgn[tid] = (m < 0 && (am & 1)) ? R(-1) : R(1);   // Theta_{l,-q} = (-1)^q Theta_{l,q}
         } else {
             s_rrad[tid] = -1;
             s_rlq[tid] = 0;
             s_rq[tid] = 0;
-            s_rsgn[tid] = 0.0;
+            s_rsgn[tid] = R(0);
         }
     } else if (tid < GT_I + GT_J) {
         int c = tid - GT_I, j = j0 + c;
@@ -236,41 +297,65 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
             int d = s_cq[tx * 2 + c] - s_rq[ty * 2 + a];
             dd[a][c] = d < 0 ? -d : d;
         }
-    double acc[2][2][6];
+    R acc[2][2][6], tot[2][2][6];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int q = 0; q < 6; ++q) acc[a][c][q] = 0.0;
+            for (int q = 0; q < 6; ++q) {
+                acc[a][c][q] = R(0);
+                tot[a][c][q] = R(0);
+            }
 
     const int nd = A.dmax + 1;
     const size_t wstride = (size_t)nd * A.G;
     for (int g0 = 0; g0 < A.G; g0 += GT_K) {
         // A_T[i][g] = f_a(r_T) Theta_{l|q'|}(c_T) * sign, transposed into sAT[g][i]
-        for (int idx = tid; idx < GT_I * GT_K; idx += 256) {
-            int ii = idx / GT_K, gg = idx % GT_K, g = g0 + gg;
-            double val = 0.0;
-            if (s_rrad[ii] >= 0 && g < A.G)
-                val = fT[(size_t)s_rrad[ii] * A.G + g] * thT[(size_t)s_rlq[ii] * A.G + g] * s_rsgn[ii];
-            sAT[gg * (GT_I + 1) + ii] = val;
-        }
-        for (int idx = tid; idx < GT_J * GT_K; idx += 256) {
-            int cc = idx / GT_K, gg = idx % GT_K, g = g0 + gg;
-            double val = 0.0;
-            if (s_crad[cc] >= 0 && g < A.G)
-                val = fP[(size_t)s_crad[cc] * A.G + g] * thP[(size_t)s_clq[cc] * A.G + g];
-            sAP[gg * (GT_J + 1) + cc] = val;
+        if (sizeof(R) == 8) {
+            for (int idx = tid; idx < GT_I * GT_K; idx += 256) {
+                int ii = idx / GT_K, gg = idx % GT_K, g = g0 + gg;
+                R val = R(0);
+                if (s_rrad[ii] >= 0 && g < A.G)
+                    val = fT[(size_t)s_rrad[ii] * A.G + g] * thT[(size_t)s_rlq[ii] * A.G + g] * s_rsgn[ii];
+                sAT[gg * (GT_I + 1) + ii] = val;
+            }
+            for (int idx = tid; idx < GT_J * GT_K; idx += 256) {
+                int cc = idx / GT_K, gg = idx % GT_K, g = g0 + gg;
+                R val = R(0);
+                if (s_crad[cc] >= 0 && g < A.G)
+                    val = fP[(size_t)s_crad[cc] * A.G + g] * thP[(size_t)s_clq[cc] * A.G + g];
+                sAP[gg * (GT_J + 1) + cc] = val;
+            }
+        } else {
+            // mixed-precision form: per-state products from k_node_tables<float>
+            const R* aT = base;
+            const R* aP = aT + (size_t)A.N_T * A.G;
+            for (int idx = tid; idx < GT_I * GT_K; idx += 256) {
+                int ii = idx / GT_K, gg = idx % GT_K, g = g0 + gg;
+                sAT[gg * (GT_I + 1) + ii] = (s_rrad[ii] >= 0 && g < A.G) ? aT[(size_t)(i0 + ii) * A.G + g] : R(0);
+            }
+            for (int idx = tid; idx < GT_J * GT_K; idx += 256) {
+                int cc = idx / GT_K, gg = idx % GT_K, g = g0 + gg;
+                sAP[gg * (GT_J + 1) + cc] = (s_crad[cc] >= 0 && g < A.G) ? aP[(size_t)(j0 + cc) * A.G + g] : R(0);
+            }
         }
         for (int idx = tid; idx < 3 * nd * GT_K; idx += 256) {
             int gg = idx % GT_K, xd = idx / GT_K, g = g0 + gg;
             int X = xd / nd, d = xd % nd;
-            sW[idx] = (g < A.G) ? W[(size_t)X * wstride + (size_t)d * A.G + g] : make_double2(0.0, 0.0);
+            R2 wr;
+            if (g < A.G) {
+                wr = W[(size_t)X * wstride + (size_t)d * A.G + g];
+            } else {
+                wr.x = R(0);
+                wr.y = R(0);
+            }
+            sW[idx] = wr;
         }
         __syncthreads();
 #pragma unroll 4
         for (int gg = 0; gg < GT_K; ++gg) {
-            double at[2], ap[2];
+            R at[2], ap[2];
             at[0] = sAT[gg * (GT_I + 1) + ty * 2];
             at[1] = sAT[gg * (GT_I + 1) + ty * 2 + 1];
             ap[0] = sAP[gg * (GT_J + 1) + tx * 2];
@@ -279,9 +364,9 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
             for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const double p = at[a] * ap[c];
-                    const double2* wp = sW + dd[a][c] * GT_K + gg;
-                    const double2 w0 = wp[0], w1 = wp[nd * GT_K], w2 = wp[2 * nd * GT_K];
+                    const R p = at[a] * ap[c];
+                    const R2* wp = sW + dd[a][c] * GT_K + gg;
+                    const R2 w0 = wp[0], w1 = wp[nd * GT_K], w2 = wp[2 * nd * GT_K];
                     acc[a][c][0] = fma(p, w0.x, acc[a][c][0]);
                     acc[a][c][1] = fma(p, w0.y, acc[a][c][1]);
                     acc[a][c][2] = fma(p, w1.x, acc[a][c][2]);
@@ -290,7 +375,26 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
                     acc[a][c][5] = fma(p, w2.y, acc[a][c][5]);
                 }
         }
+        if (sizeof(R) == 4) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        tot[a][c][q] += acc[a][c][q];
+                        acc[a][c][q] = R(0);
+                    }
+        }
         __syncthreads();
+    }
+    if (sizeof(R) == 8) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) tot[a][c][q] = acc[a][c][q];
     }
     const size_t plane = (size_t)A.N_T * A.n_half;
     double2* out = A.mol + (size_t)e * 3 * plane;
@@ -303,9 +407,188 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
             int j = j0 + tx * 2 + c;
             if (j >= A.n_half) continue;
             size_t o = (size_t)i * A.n_half + j;
-            out[o] = make_double2(acc[a][c][0], acc[a][c][1]);
-            out[plane + o] = make_double2(acc[a][c][2], acc[a][c][3]);
-            out[2 * plane + o] = make_double2(acc[a][c][4], acc[a][c][5]);
+            out[o] = make_double2(tot[a][c][0], tot[a][c][1]);
+            out[plane + o] = make_double2(tot[a][c][2], tot[a][c][3]);
+            out[2 * plane + o] = make_double2(tot[a][c][4], tot[a][c][5]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_mol_gemm_f32q: the FP32 contraction of the mixed-precision form with column tiles of one q.
+// All columns of a tile share q, so row i needs the single weight W_{|q - q'_i|}: the row operand is
+// pre-multiplied by it once per node, B_x[i][g] = A_T[i][g] W_x[d_i][g] (x = three complex integrands),
+// and the inner loop is a plain 6-accumulator product with the column operand A_P[j][g].
+// Sums run per chunk of QT_K nodes and are then added to the running totals (two-level summation).
+// ---------------------------------------------------------------------------
+constexpr int QT_I = 32, QT_J = 16, QT_K = 32, QT_THREADS = 64;   // 16 x 4 threads, 2 x 4 per thread
+
+struct Gemm32Args {
+    int G, N_T, n_half, dmax, n_col_tiles;
+    const int* stT_m;
+    const int* ctile_q;       // [n_col_tiles]
+    const int* ctile_cols;    // [n_col_tiles][QT_J] half columns (-1: padding)
+    const double* node;
+    size_t node_doubles, w_off_f;
+    double2* mol;
+};
+
+__global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
+    __shared__ __align__(16) float sB[QT_K][QT_I][6];
+    __shared__ __align__(16) float sP[QT_K][QT_J];
+    __shared__ int s_d[QT_I], s_col[QT_J];
+    const int e = blockIdx.y;
+    const int rt = blockIdx.x / A.n_col_tiles, ct = blockIdx.x % A.n_col_tiles;
+    const int i0 = rt * QT_I;
+    const int tid = threadIdx.x, tx = tid & 3, ty = tid >> 2;
+    const int q = A.ctile_q[ct];
+    const float* base = reinterpret_cast<const float*>(A.node + (size_t)e * A.node_doubles);
+    const float* aT = base;
+    const float* aP = aT + (size_t)A.N_T * A.G;
+    const float2* W = reinterpret_cast<const float2*>(base + A.w_off_f);
+    const size_t wstride = (size_t)(A.dmax + 1) * A.G;
+    for (int r = tid; r < QT_I; r += QT_THREADS) {
+        const int i = i0 + r;
+        int d = -1;
+        if (i < A.N_T) {
+            d = q - A.stT_m[i];
+            d = d < 0 ? -d : d;
+        }
+        s_d[r] = d;
+    }
+    for (int c = tid; c < QT_J; c += QT_THREADS) s_col[c] = A.ctile_cols[ct * QT_J + c];
+    __syncthreads();
+    float acc[2][4][6], tot[2][4][6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int x = 0; x < 6; ++x) {
+                acc[a][c][x] = 0.f;
+                tot[a][c][x] = 0.f;
+            }
+    for (int g0 = 0; g0 < A.G; g0 += QT_K) {
+        for (int idx = tid; idx < QT_I * QT_K; idx += QT_THREADS) {
+            const int r = idx / QT_K, gg = idx % QT_K, g = g0 + gg;
+            const int d = s_d[r];
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (d >= 0 && g < A.G) {
+                const float at = aT[(size_t)(i0 + r) * A.G + g];
+                const float2 w0 = W[(size_t)d * A.G + g];
+                const float2 w1 = W[wstride + (size_t)d * A.G + g];
+                const float2 w2 = W[2 * wstride + (size_t)d * A.G + g];
+                v[0] = at * w0.x;
+                v[1] = at * w0.y;
+                v[2] = at * w1.x;
+                v[3] = at * w1.y;
+                v[4] = at * w2.x;
+                v[5] = at * w2.y;
+            }
+#pragma unroll
+            for (int x = 0; x < 6; ++x) sB[gg][r][x] = v[x];
+        }
+        for (int idx = tid; idx < QT_J * QT_K; idx += QT_THREADS) {
+            const int c = idx / QT_K, gg = idx % QT_K, g = g0 + gg;
+            const int j = s_col[c];
+            sP[gg][c] = (j >= 0 && g < A.G) ? aP[(size_t)j * A.G + g] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int gg = 0; gg < QT_K; ++gg) {
+            const float4 p = *reinterpret_cast<const float4*>(&sP[gg][tx * 4]);
+            const float pc[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const float* bp = &sB[gg][ty * 2 + a][0];
+                const float2 b01 = *reinterpret_cast<const float2*>(bp);
+                const float2 b23 = *reinterpret_cast<const float2*>(bp + 2);
+                const float2 b45 = *reinterpret_cast<const float2*>(bp + 4);
+                const float bv[6] = {b01.x, b01.y, b23.x, b23.y, b45.x, b45.y};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int x = 0; x < 6; ++x) acc[a][c][x] = fmaf(bv[x], pc[c], acc[a][c][x]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int x = 0; x < 6; ++x) {
+                    tot[a][c][x] += acc[a][c][x];
+                    acc[a][c][x] = 0.f;
+                }
+        __syncthreads();
+    }
+    const size_t plane = (size_t)A.N_T * A.n_half;
+    double2* out = A.mol + (size_t)e * 3 * plane;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int i = i0 + ty * 2 + a;
+        if (i >= A.N_T) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = s_col[tx * 4 + c];
+            if (j < 0) continue;
+            const size_t o = (size_t)i * A.n_half + j;
+            out[o] = make_double2(tot[a][c][0], tot[a][c][1]);
+            out[plane + o] = make_double2(tot[a][c][2], tot[a][c][3]);
+            out[2 * plane + o] = make_double2(tot[a][c][4], tot[a][c][5]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_eval_tables: the small per-position tables shared by k_rotate and k_direct:
+//   Wigner d^l_{m q}(theta) for l <= lrot      at [off_l + (m + l)(2l+1) + (q + l)]
+//   Pbar(lam, mu) = sqrt((lam-mu)!/(lam+mu)!) P_lam^mu(cos Theta), lam < nlam, at dtot + lam(lam+1)/2 + mu
+//   the 5-point stencil of Eq. 7's table at R: start, beyond-grid flag, Lagrange weights
+// ---------------------------------------------------------------------------
+struct EtArgs {
+    int lrot, nlam, Nr;
+    int dtot, npb;           // sizes of the d and Pbar parts
+    const double* r;
+    double* et;              // [nev][et_doubles]
+    size_t et_doubles;
+};
+
+__global__ void __launch_bounds__(128) k_eval_tables(EtArgs A, const EvalDesc* __restrict__ ev) {
+    const int e = blockIdx.x;
+    const double b = ev[e].b, z = ev[e].z;
+    const double R = dist_R(b, z);
+    const double cth = z / R;
+    const double ch = sqrt(0.5 * (1.0 + cth)), sh = sqrt(0.5 * (1.0 - cth));
+    double* et = A.et + (size_t)e * A.et_doubles;
+    for (int idx = threadIdx.x; idx < A.dtot; idx += blockDim.x) {
+        int l = 0, off = 0;
+        while (idx >= off + (2 * l + 1) * (2 * l + 1)) {
+            off += (2 * l + 1) * (2 * l + 1);
+            ++l;
+        }
+        int loc = idx - off, m = loc / (2 * l + 1) - l, q = loc % (2 * l + 1) - l;
+        et[idx] = wigner_small_d(l, m, q, ch, sh);
+    }
+    for (int t = threadIdx.x; t < A.npb; t += blockDim.x) {
+        int lam = 0;
+        while ((lam + 1) * (lam + 2) / 2 <= t) ++lam;
+        int mu = t - lam * (lam + 1) / 2;
+        et[A.dtot + t] = sqrt(dfact(lam - mu) / dfact(lam + mu)) * assoc_legendre(lam, mu, cth);
+    }
+    if (threadIdx.x == 0) {
+        double* st = et + A.dtot + A.npb;
+        int s;
+        double L[5];
+        if (R > A.r[A.Nr - 1]) {
+            st[0] = (double)(A.Nr - 1);
+            st[1] = 1.0;
+            for (int k = 0; k < 5; ++k) st[2 + k] = 0.0;
+        } else {
+            stencil5(A.r, A.Nr, R, s, L);
+            st[0] = (double)s;
+            st[1] = 0.0;
+            for (int k = 0; k < 5; ++k) st[2 + k] = L[k];
         }
     }
 }
@@ -314,86 +597,112 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
 // k_rotate: Eq. 8 and the off-diagonal blocks of S and H
 // ---------------------------------------------------------------------------
 struct RotArgs {
-    int N_T, N_P, N, n_half, lmax;
+    int N_T, N_P, N, n_half, lmax, n_radT, n_radP;
+    int rot_block;            // complex entries of one warp's block: 3 (2 lmax_T + 1)(2 lmax_P + 1)
+    int dtot;                 // size of the Wigner-d part of the per-position tables
+    const double* et;         // per-position tables (k_eval_tables)
+    size_t et_doubles;
     const int *stT_rad, *stT_l, *stT_m, *stT_index;
-    const int *stP_rad, *stP_l, *stP_m, *half_of;
+    const int *stP_rad, *stP_l, *stP_m, *half_of, *stP_index;
+    const int *radT_l, *radP_l;
     const double *epsT, *epsP;
     const double2* mol;
     double2 *S, *H;
     size_t mat;   // N*N
 };
 
-__global__ void __launch_bounds__(256) k_rotate(RotArgs A, const EvalDesc* __restrict__ ev) {
-    extern __shared__ double sd[];     // Wigner d^l_{m q}(theta) for l <= lmax
+constexpr int ROT_WARPS_MAX = 8;
+
+// One warp per (target radial a, projectile radial b): the (2l_a+1) x (2l_b+1) molecular-frame block
+// of each integral (q < 0 columns from the reflection) is rotated in two passes through shared
+// memory, T[q'][m_b] = sum_q d^{l_b}_{m_b q} X[q'][q], then K[m_a][m_b] = sum_q' d^{l_a}_{m_a q'} T[q'][m_b].
+__global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const EvalDesc* __restrict__ ev) {
+    extern __shared__ double sd[];     // Wigner d^l_{m q}(theta) for l <= lmax, then per-warp blocks
     const int e = blockIdx.y;
     const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
-    const double R = dist_R(b, z);
-    const double cth = z / R;
-    const double ch = sqrt(0.5 * (1.0 + cth)), sh = sqrt(0.5 * (1.0 - cth));
-    int total = 0;
-    for (int l = 0; l <= A.lmax; ++l) total += (2 * l + 1) * (2 * l + 1);
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int l = 0, off = 0;
-        while (idx >= off + (2 * l + 1) * (2 * l + 1)) {
-            off += (2 * l + 1) * (2 * l + 1);
-            ++l;
-        }
-        int loc = idx - off, m = loc / (2 * l + 1) - l, q = loc % (2 * l + 1) - l;
-        sd[idx] = wigner_small_d(l, m, q, ch, sh);
-    }
+    (void)b;
+    const int total = A.dtot;
+    const double* etd = A.et + (size_t)e * A.et_doubles;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) sd[idx] = etd[idx];
     __syncthreads();
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)A.N_T * A.N_P) return;
-    const int i = (int)(idx / A.N_P), j = (int)(idx % A.N_P);
-    const int ra = A.stT_rad[i], la = A.stT_l[i], ma = A.stT_m[i];
-    const int rb = A.stP_rad[j], lb = A.stP_l[j], mb = A.stP_m[j];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pair = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (pair >= A.n_radT * A.n_radP) return;
+    const int ra = pair / A.n_radP, rb = pair % A.n_radP;
+    const int la = A.radT_l[ra], lb = A.radP_l[rb];
+    const int na = 2 * la + 1, nbq = 2 * lb + 1, blk = na * nbq;
+    const int tot_pad = (total + 1) & ~1;
+    double2* X = reinterpret_cast<double2*>(sd + tot_pad) + (size_t)warp * 2 * A.rot_block;
+    double2* T = X + A.rot_block;
     int offa = 0, offb = 0;
     for (int l = 0; l < la; ++l) offa += (2 * l + 1) * (2 * l + 1);
     for (int l = 0; l < lb; ++l) offb += (2 * l + 1) * (2 * l + 1);
-    const double* da = sd + offa + (ma + la) * (2 * la + 1);   // d^{la}_{ma, q'} at [q' + la]
-    const double* db = sd + offb + (mb + lb) * (2 * lb + 1);
+    const double* da = sd + offa;   // da[(m + la) * na + (q + la)] = d^{la}_{m q}
+    const double* db = sd + offb;
     const size_t plane = (size_t)A.N_T * A.n_half;
     const double2* mol = A.mol + (size_t)e * 3 * plane;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int qp = -la; qp <= la; ++qp) {
-        const double dq = da[qp + la];
-        const int rowp = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + qp + WPCCC_LMAX];
-        const int rowm = A.stT_index[ra * (2 * WPCCC_LMAX + 1) - qp + WPCCC_LMAX];
-        for (int q = -lb; q <= lb; ++q) {
-            double w = dq * db[q + lb];
-            int row, col;
-            if (q >= 0) {
-                row = rowp;
-                col = A.half_of[rb * (WPCCC_LMAX + 1) + q];
-            } else {
-                row = rowm;
-                col = A.half_of[rb * (WPCCC_LMAX + 1) - q];
-                if ((qp + q) & 1) w = -w;
-            }
-            const size_t o = (size_t)row * A.n_half + col;
-            const double2 s0 = mol[o], s1 = mol[plane + o], s2 = mol[2 * plane + o];
-            acc[0] = fma(w, s0.x, acc[0]);
-            acc[1] = fma(w, s0.y, acc[1]);
-            acc[2] = fma(w, s1.x, acc[2]);
-            acc[3] = fma(w, s1.y, acc[3]);
-            acc[4] = fma(w, s2.x, acc[4]);
-            acc[5] = fma(w, s2.y, acc[5]);
+    // molecular block, X[x][q'][q] at x * blk + (q' + la) * nbq + (q + lb)
+    for (int t = lane; t < 3 * blk; t += 32) {
+        const int x = t / blk, r = t % blk, qp = r / nbq - la, q = r % nbq - lb;
+        int row, col;
+        double sg = 1.0;
+        if (q >= 0) {
+            row = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + qp + WPCCC_LMAX];
+            col = A.half_of[rb * (WPCCC_LMAX + 1) + q];
+        } else {
+            row = A.stT_index[ra * (2 * WPCCC_LMAX + 1) - qp + WPCCC_LMAX];
+            col = A.half_of[rb * (WPCCC_LMAX + 1) - q];
+            if ((qp + q) & 1) sg = -1.0;
         }
+        const double2 val = mol[(size_t)x * plane + (size_t)row * A.n_half + col];
+        X[t] = make_double2(sg * val.x, sg * val.y);
     }
-    double sp, cp;
-    sincos((A.epsT[i] - A.epsP[j]) * z / v, &sp, &cp);
-    const double2 ph = make_double2(cp, sp);
-    const double2 K = cmul(make_double2(acc[0], acc[1]), ph);
-    const double2 Q = cmul(make_double2(acc[2], acc[3]), ph);
-    const double2 Qt = cmul(make_double2(acc[4], acc[5]), ph);
+    __syncwarp();
+    // T[x][q'][m_b] = sum_q d^{lb}_{m_b q} X[x][q'][q]
+    for (int t = lane; t < 3 * blk; t += 32) {
+        const int x = t / blk, r = t % blk, qi = r / nbq, mb = r % nbq;
+        const double2* xr = X + x * blk + qi * nbq;
+        const double* dr = db + mb * nbq;
+        double re = 0.0, im = 0.0;
+        for (int q = 0; q < nbq; ++q) {
+            re = fma(dr[q], xr[q].x, re);
+            im = fma(dr[q], xr[q].y, im);
+        }
+        T[t] = make_double2(re, im);
+    }
+    __syncwarp();
+    // K[x][m_a][m_b] = sum_q' d^{la}_{m_a q'} T[x][q'][m_b], energy phases, S and H entries
     double2* S = A.S + (size_t)e * A.mat;
     double2* H = A.H + (size_t)e * A.mat;
-    const size_t up = (size_t)i + (size_t)(A.N_T + j) * A.N;     // row i, column N_T + j
-    const size_t lo = (size_t)(A.N_T + j) + (size_t)i * A.N;     // row N_T + j, column i
-    S[up] = K;
-    S[lo] = cconj(K);
-    H[up] = Q;
-    H[lo] = cconj(Qt);
+    for (int t = lane; t < blk; t += 32) {
+        const int mi = t / nbq, mb = t % nbq;
+        const double* dr = da + mi * na;
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int qi = 0; qi < na; ++qi) {
+            const double w = dr[qi];
+            const double2 t0 = T[qi * nbq + mb], t1 = T[blk + qi * nbq + mb], t2 = T[2 * blk + qi * nbq + mb];
+            acc[0] = fma(w, t0.x, acc[0]);
+            acc[1] = fma(w, t0.y, acc[1]);
+            acc[2] = fma(w, t1.x, acc[2]);
+            acc[3] = fma(w, t1.y, acc[3]);
+            acc[4] = fma(w, t2.x, acc[4]);
+            acc[5] = fma(w, t2.y, acc[5]);
+        }
+        const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
+        const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
+        double sp, cp;
+        sincos((A.epsT[i] - A.epsP[j]) * z / v, &sp, &cp);
+        const double2 ph = make_double2(cp, sp);
+        const double2 K = cmul(make_double2(acc[0], acc[1]), ph);
+        const double2 Q = cmul(make_double2(acc[2], acc[3]), ph);
+        const double2 Qt = cmul(make_double2(acc[4], acc[5]), ph);
+        const size_t up = (size_t)i + (size_t)(A.N_T + j) * A.N;     // row i, column N_T + j
+        const size_t lo = (size_t)(A.N_T + j) + (size_t)i * A.N;     // row N_T + j, column i
+        S[up] = K;
+        S[lo] = cconj(K);
+        H[up] = Q;
+        H[lo] = cconj(Qt);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -401,6 +710,9 @@ __global__ void __launch_bounds__(256) k_rotate(RotArgs A, const EvalDesc* __res
 // ---------------------------------------------------------------------------
 struct DirArgs {
     int Nr, N, off, Nc, n_rad, nlam;
+    int dtot, npb;                // layout of the per-position tables
+    const double* et;
+    size_t et_doubles;
     double Z_other, parity;       // parity = -1: the other nucleus sits at -R
     const double *r, *F, *ang, *eps;
     const int *Foff, *st_rad, *st_m;
@@ -416,28 +728,15 @@ __global__ void __launch_bounds__(256) k_direct(DirArgs A0, DirArgs A1, const Ev
     const int e = blockIdx.y;
     const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
     const double R = dist_R(b, z);
-    const double cth = z / R;
-    // Pbar(lam, mu) = sqrt((lam-mu)!/(lam+mu)!) P_lam^mu(cos Theta), index lam(lam+1)/2 + mu
+    const double* et = A.et + (size_t)e * A.et_doubles;
+    // Pbar(lam, mu), index lam(lam+1)/2 + mu, and the stencil of Eq. 7's table at R
     const int npb = A.nlam * (A.nlam + 1) / 2;
-    for (int t = threadIdx.x; t < npb; t += blockDim.x) {
-        int lam = 0;
-        while ((lam + 1) * (lam + 2) / 2 <= t) ++lam;
-        int mu = t - lam * (lam + 1) / 2;
-        sPb[t] = sqrt(dfact(lam - mu) / dfact(lam + mu)) * assoc_legendre(lam, mu, cth);
-    }
+    for (int t = threadIdx.x; t < npb; t += blockDim.x) sPb[t] = et[A.dtot + t];
     if (threadIdx.x == 0) {
-        int s;
-        double L[5];
-        if (R > A.r[A.Nr - 1]) {
-            // beyond the grid every radial function vanishes: F_lam(R) = F_lam(r_max) (r_max/R)^{lam+1}
-            s_out = 1;
-            s_sten = A.Nr - 1;
-        } else {
-            stencil5(A.r, A.Nr, R, s, L);
-            s_out = 0;
-            s_sten = s;
-            for (int k = 0; k < 5; ++k) sL[k] = L[k];
-        }
+        const double* st = et + A.dtot + A.npb;
+        s_sten = (int)st[0];
+        s_out = st[1] != 0.0;
+        for (int k = 0; k < 5; ++k) sL[k] = st[2 + k];
     }
     __syncthreads();
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -480,16 +779,29 @@ __global__ void __launch_bounds__(256) k_direct(DirArgs A0, DirArgs A1, const Ev
 // host side
 // ---------------------------------------------------------------------------
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
-    ElemScratch L{0, 0, 0, 0};
+    ElemScratch L{0, 0, 0, 0, 0, 0, 0, 0};
+    const int lrot = std::max(B->T.lmax, B->n_centres == 2 ? B->P.lmax : 0);
+    for (int l = 0; l <= lrot; ++l) L.dtot += (2 * l + 1) * (2 * l + 1);
+    const int nlam = 2 * lrot + 1;
+    L.npb = nlam * (nlam + 1) / 2;
+    L.et_doubles = (size_t)L.dtot + L.npb + 7;
+    L.et_doubles += L.et_doubles & 1;
     if (B->n_centres == 2) {
         size_t nd = (size_t)(B->T.n_rad + B->P.n_rad + B->nlq_T + B->nlq_P) * B->G;
         nd += nd & 1;   // keep the complex weights 16-byte aligned
         L.w_off = nd;
         nd += (size_t)3 * (B->dmax + 1) * B->G * 2;
-        L.node_doubles = nd;
+        // FP32 layout of the mixed-precision form: per-state products, then the weights (floats)
+        size_t nf = (size_t)(B->N_T + B->n_half) * B->G;
+        nf += nf & 1;
+        L.w_off_f = nf;
+        nf += (size_t)3 * (B->dmax + 1) * B->G * 2;
+        L.node_doubles = std::max(nd, (nf + 1) / 2);
+        L.node_doubles += L.node_doubles & 1;
         L.mol_elems = (size_t)3 * B->N_T * B->n_half;
-        L.bytes_per_eval = nd * sizeof(double) + L.mol_elems * sizeof(double2);
+        L.bytes_per_eval = L.node_doubles * sizeof(double) + L.mol_elems * sizeof(double2);
     }
+    L.bytes_per_eval += L.et_doubles * sizeof(double);
     return L;
 }
 
@@ -514,17 +826,38 @@ static DirArgs dir_args(const wpccc_basis_s* B, const CentreDev& c, int off, dou
     a.S = S;
     a.H = H;
     a.mat = (size_t)B->N * B->N;
+    const ElemScratch L = elem_scratch_layout(B);
+    a.dtot = L.dtot;
+    a.npb = L.npb;
+    a.et = nullptr;
+    a.et_doubles = L.et_doubles;
     return a;
 }
 
 wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, double2* S,
-                             double2* H, void* scratch, cudaStream_t st) {
+                             double2* H, void* scratch, cudaStream_t st, int precision) {
     if (nev <= 0) return WPCCC_OK;
     const bool two = B->n_centres == 2;
+    const ElemScratch L = elem_scratch_layout(B);
+    double* node = static_cast<double*>(scratch);
+    double2* mol = reinterpret_cast<double2*>(node + L.node_doubles * nev);
+    double* et = reinterpret_cast<double*>(mol + L.mol_elems * nev);
+    {
+        EtArgs ea;
+        ea.lrot = std::max(B->T.lmax, two ? B->P.lmax : 0);
+        ea.nlam = 2 * ea.lrot + 1;
+        ea.Nr = B->Nr;
+        ea.dtot = L.dtot;
+        ea.npb = L.npb;
+        ea.r = B->r;
+        ea.et = et;
+        ea.et_doubles = L.et_doubles;
+        cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
+        k_eval_tables<<<nev, 128, 0, st>>>(ea, evals);
+        WPCCC_CHECK_LAUNCH("k_eval_tables");
+        B->prof.end(PROF_NODES, st, e0);
+    }
     if (two) {
-        const ElemScratch L = elem_scratch_layout(B);
-        double* node = static_cast<double*>(scratch);
-        double2* mol = reinterpret_cast<double2*>(node + L.node_doubles * nev);
         NodeArgs na;
         na.Nr = B->Nr;
         na.G = B->G;
@@ -548,9 +881,16 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         na.wtau = B->wtau;
         na.node = node;
         na.node_doubles = L.node_doubles;
-        na.w_off = L.w_off;
+        na.w_off = precision == 0 ? L.w_off : L.w_off_f;
+        na.N_T = B->N_T;
+        na.n_half = B->n_half;
+        na.stT_index = B->T.st_index;
+        na.half_of = B->half_of;
+        na.radT_l = B->T.rad_l;
+        na.radP_l = B->P.rad_l;
         cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
-        k_node_tables<<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
+        if (precision == 0) k_node_tables<double><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
+        else k_node_tables<float><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
         WPCCC_CHECK_LAUNCH("k_node_tables");
         B->prof.end(PROF_NODES, st, e0);
 
@@ -573,14 +913,33 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         ga.half_state = B->half_state;
         ga.node = node;
         ga.node_doubles = L.node_doubles;
-        ga.w_off = L.w_off;
+        ga.w_off = precision == 0 ? L.w_off : L.w_off_f;
         ga.mol = mol;
         const int n_row_tiles = (B->N_T + GT_I - 1) / GT_I;
-        const size_t gsm = (size_t)GT_K * (GT_I + 1 + GT_J + 1) * sizeof(double) +
-                           (size_t)3 * (B->dmax + 1) * GT_K * sizeof(double2);
-        WPCCC_CUDA(cudaFuncSetAttribute(k_mol_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
         e0 = B->prof.begin(PROF_MOL, st);
-        k_mol_gemm<<<dim3(n_row_tiles * ga.n_col_tiles, nev), 256, gsm, st>>>(ga);
+        if (precision == 0) {
+            const size_t gsm = (size_t)GT_K * (GT_I + 1 + GT_J + 1) * sizeof(double) +
+                               (size_t)3 * (B->dmax + 1) * GT_K * sizeof(double2);
+            WPCCC_CUDA(cudaFuncSetAttribute(k_mol_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)gsm));
+            k_mol_gemm<double><<<dim3(n_row_tiles * ga.n_col_tiles, nev), 256, gsm, st>>>(ga);
+        } else {
+            Gemm32Args g32;
+            g32.G = B->G;
+            g32.N_T = B->N_T;
+            g32.n_half = B->n_half;
+            g32.dmax = B->dmax;
+            g32.n_col_tiles = B->n_qtiles;
+            g32.stT_m = B->T.st_m;
+            g32.ctile_q = B->qtile_q;
+            g32.ctile_cols = B->qtile_cols;
+            g32.node = node;
+            g32.node_doubles = L.node_doubles;
+            g32.w_off_f = L.w_off_f;
+            g32.mol = mol;
+            const int rtiles = (B->N_T + QT_I - 1) / QT_I;
+            k_mol_gemm_f32q<<<dim3(rtiles * B->n_qtiles, nev), QT_THREADS, 0, st>>>(g32);
+        }
         WPCCC_CHECK_LAUNCH("k_mol_gemm");
         B->prof.end(PROF_MOL, st, e0);
 
@@ -598,6 +957,11 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         ra.stP_l = B->P.st_l;
         ra.stP_m = B->P.st_m;
         ra.half_of = B->half_of;
+        ra.stP_index = B->P.st_index;
+        ra.n_radT = B->T.n_rad;
+        ra.n_radP = B->P.n_rad;
+        ra.radT_l = B->T.rad_l;
+        ra.radP_l = B->P.rad_l;
         ra.epsT = B->T.st_eps;
         ra.epsP = B->P.st_eps;
         ra.mol = mol;
@@ -606,14 +970,26 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         ra.mat = (size_t)B->N * B->N;
         int dtot = 0;
         for (int l = 0; l <= ra.lmax; ++l) dtot += (2 * l + 1) * (2 * l + 1);
-        const long long pairs = (long long)B->N_T * B->N_P;
+        ra.rot_block = 3 * (2 * B->T.lmax + 1) * (2 * B->P.lmax + 1);
+        ra.dtot = L.dtot;
+        ra.et = et;
+        ra.et_doubles = L.et_doubles;
+        const size_t per_warp = (size_t)2 * ra.rot_block * sizeof(double2);
+        const size_t dbytes = (size_t)((dtot + 1) & ~1) * sizeof(double);
+        int rwarps = (int)std::min<size_t>(ROT_WARPS_MAX, ((size_t)200 * 1024 - dbytes) / per_warp);
+        if (rwarps < 1) rwarps = 1;
+        const size_t rsm = dbytes + (size_t)rwarps * per_warp;
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+        const int npairs = B->T.n_rad * B->P.n_rad;
         e0 = B->prof.begin(PROF_ROT_DIRECT, st);
-        k_rotate<<<dim3((unsigned)((pairs + 255) / 256), nev), 256, dtot * sizeof(double), st>>>(ra, evals);
+        k_rotate<<<dim3((unsigned)((npairs + rwarps - 1) / rwarps), nev), 32 * rwarps, rsm, st>>>(ra, evals);
         WPCCC_CHECK_LAUNCH("k_rotate");
         B->prof.end(PROF_ROT_DIRECT, st, e0);
     }
     DirArgs d0 = dir_args(B, B->T, 0, B->P.Z, 1.0, S, H);
     DirArgs d1 = two ? dir_args(B, B->P, B->N_T, B->T.Z, -1.0, S, H) : d0;
+    d0.et = et;
+    d1.et = et;
     int ncmax = two ? std::max(B->N_T, B->N_P) : B->N_T;
     long long cells = (long long)ncmax * ncmax;
     cudaEvent_t ed = B->prof.begin(PROF_ROT_DIRECT, st);

@@ -92,11 +92,20 @@ struct wpccc_basis_s {
     int n_half = 0;
     int* half_state = nullptr;  // [n_half] projectile state
     int* half_of = nullptr;     // [n_rad_P][WPCCC_LMAX+1]: half column of (radial, q>=0) or -1
+    // column tiles of the FP32 contraction: up to 16 half columns sharing one q
+    int n_qtiles = 0;
+    int* qtile_q = nullptr;     // [n_qtiles]
+    int* qtile_cols = nullptr;  // [n_qtiles][16], -1 padded
     // scratch owned by the basis
     void* ws_ptr = nullptr;
     size_t ws_bytes = 0;
     size_t ws_limit = (size_t)8 << 30;
     int solve_mode = WPCCC_SOLVE_STAGE;
+    int refine_iters = 2;       // FP64 refinement iterations of the mixed-precision form
+    // second stream of wpccc_propagate (RK4 sweeps overlap the next chunk's assembly) and its events
+    cudaStream_t rk_stream = nullptr;
+    cudaEvent_t ev_asm[2] = {nullptr, nullptr}, ev_rk[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     wpccc::Profiler prof;
 };
 
@@ -113,8 +122,11 @@ struct EvalDesc {
 struct ElemScratch {
     size_t node_doubles;   // node tables per evaluation (in doubles, even)
     size_t w_off;          // offset of the complex node weights within them (even)
+    size_t w_off_f;        // the same in the FP32 layout of the mixed-precision form (floats, even)
     size_t mol_elems;      // molecular-frame integrals per evaluation (complex)
     size_t bytes_per_eval;
+    size_t et_doubles;     // small per-position tables (Wigner d, Legendre, stencil), even
+    int dtot, npb;         // sizes of their Wigner-d and Legendre parts
 };
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B);
 
@@ -122,10 +134,15 @@ ElemScratch elem_scratch_layout(const wpccc_basis_s* B);
 // S and H (matrix k at S + k*N*N).  S may be null (one-centre propagation).
 // `scratch` must hold elem_scratch_layout(B).bytes_per_eval * nev bytes (unused in
 // one-centre mode).
+// precision 0: FP64 throughout; 1: the Eq. 9 contraction on the FP32 pipe (mixed-precision form).
 wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev,
-                             double2* S, double2* H, void* scratch, cudaStream_t st);
+                             double2* S, double2* H, void* scratch, cudaStream_t st, int precision = 0);
 
 enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3, PROF_RK4 = 4 };
+
+// Queue the batched FP32 factorisation P S = L U of FP64 matrices (mixed-precision form).
+wpccc_status launch_factor_f32(int N, int batch, const double2* S, float2* LU, int* ipiv, int* info,
+                               cudaStream_t st);
 
 // Queue the batched solve of S X = H (results in place).
 wpccc_status launch_solve(int N, int batch, double2* S, double2* H, int* ipiv, int* info,

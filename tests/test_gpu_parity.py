@@ -236,3 +236,58 @@ def test_probabilities_kernel():
     c = torch.randn(4, 37, dtype=torch.complex128, device="cuda")
     P = w.probabilities(c)
     assert torch.allclose(P, (c.conj() * c).real, rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- mixed-precision form
+MIXED_TOL = 1e-6     # absolute, per probability
+
+
+def _mixed_errors(basis, bs, v, zgs, workspace=None):
+    w = _w()
+    g = w.Basis(basis)
+    if workspace:
+        g.set_workspace_limit(workspace)
+    c = g.propagate(bs, v, zgs, precision_mode=1)
+    Pg = w.probabilities(c).cpu().numpy()
+    errs = []
+    for p in range(len(bs)):
+        zg = zgs[p] if isinstance(zgs, list) else zgs
+        Po = O.probabilities(O.propagate(basis, float(bs[p]), float(v), zg))
+        errs.append(np.abs(Pg[p] - Po))
+    return np.array(errs)
+
+
+def test_mixed_form_small_two_centre(small2c_uneven):
+    bs = np.array([0.5, 2.0])
+    zgs = [wi.uniform_zgrid(-6.0, 6.0, 0.2), wi.uniform_zgrid(-4.0, 5.0, 0.25)]
+    err = _mixed_errors(small2c_uneven, bs, 1.3, zgs, workspace=64 << 20)
+    assert err.max() <= MIXED_TOL, err.max()
+
+
+def test_mixed_form_full_two_centre_sampled(config2):
+    basis, paths = config2
+    w = _w()
+    g = w.Basis(basis)
+    zg = wi.uniform_zgrid(-0.6, 0.6, 0.1)
+    c = g.propagate(paths.b, paths.v, zg, precision_mode=1)
+    Pg = w.probabilities(c).cpu().numpy()
+    for p in (0, 9):
+        Po = O.probabilities(O.propagate(basis, float(paths.b[p]), float(paths.v[p]), zg))
+        assert np.abs(Pg[p] - Po).max() <= MIXED_TOL
+
+
+def test_mixed_form_full_paths_against_fp64(config2):
+    # whole paths (1000 RK4 steps, z from -50 to 50) of the two-centre p + H workload: the mixed form
+    # against the plain FP64 form on the GPU (itself within 1e-10 of the oracle, tests above)
+    basis, paths = config2
+    w = _w()
+    g = w.Basis(basis)
+    idx = [0, 4, 12, 31]          # b = 0.2, 1.72, 4.77, 12
+    zg = paths.z[0]
+    c64 = g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=0)
+    cmx = g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=1)
+    P64 = w.probabilities(c64).cpu().numpy()
+    Pmx = w.probabilities(cmx).cpu().numpy()
+    err = np.abs(Pmx - P64)
+    print("mixed-form max |dP| per path:", err.max(axis=1))
+    assert err.max() <= MIXED_TOL
