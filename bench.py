@@ -46,6 +46,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_DFMA_MEASURED_TFLOPS = 1.20   # FMA microbenchmark on this machine's GB300 (all SMs, register operands)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP32_FFMA_MEASURED_TFLOPS = 69.9
+CONFIG_DESC_C6 = ("two-centre bare C6+ on H (Z_T=1, Z_P=6): hydrogenic n<=6 + 20 Coulomb wave-packet bins per "
+                  "l<=5 (k<=4) on each centre, all m, N_T=N_P=811, N=1622; 48x48 (eta,tau) nodes; Nr=2000 to "
+                  "100 a.u.; v=2; 16 b uniform in [0.5,15]; the paper's geometric z-grid, z_min=1e-3, "
+                  "|z|<=50, 500 nodes per side (1000 RK4 steps)")
 CONFIG_DESC = ("two-centre p+H (Z_T=Z_P=1): hydrogenic n<=4 + 10 Coulomb wave-packet bins per l<=3 (k<=3) "
                "on each centre, all m, N_T=N_P=190, N=380; 48x48 (eta,tau) nodes; Nr=2000 to 100 a.u.; "
                "v=1.5; 32 b uniform in [0.2,12]; z in [-50,50], h=0.1")
@@ -168,7 +172,11 @@ def main() -> None:
     ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all 32)")
     ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
     ap.add_argument("--solve-mode", default="stage", choices=["stage", "matrix"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5"],
+                    help="p_H_2c_n4l3: two-centre p + H (N = 380, 32 paths); C6_H_2c_n6l5: bare C6+ on H "
+                         "(N = 1622, 16 paths)")
+    ap.add_argument("--workspace-gb", type=float, default=16.0)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed-fp64-elements"],
                     help="fp64: plain FP64; mixed: FP32 contraction and LU, FP64 refinement and RK4")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -191,13 +199,15 @@ def main() -> None:
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    basis, paths = wi.config_inputs(WORKLOAD)
+    basis, paths = wi.config_inputs(args.workload)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(basis, paths, 12)
+        cpu = cpu_oracle_rate(basis, paths, 12 if args.workload == WORKLOAD else 2,
+                              path_index=min(16, paths.n_paths // 2))
 
     import paper_2403_04252_gb300 as w
     g = w.Basis(basis, device=local)
+    g.set_workspace_limit(int(args.workspace_gb * (1 << 30)))
     g.set_solve_mode(w.SOLVE_STAGE if args.solve_mode == "stage" else w.SOLVE_MATRIX)
     n_paths = paths.n_paths if args.paths <= 0 else min(args.paths, paths.n_paths)
     N = g.N
@@ -216,7 +226,7 @@ def main() -> None:
         k0 = (first + k * STEP) % (n_total - STEP + 1)
         return zg[k0:k0 + STEP + 1]
 
-    prec = 1 if args.precision == "mixed" else 0
+    prec = {"fp64": 0, "mixed": 1, "mixed-fp64-elements": 2}[args.precision]
     c = torch.zeros((n_paths, N), dtype=torch.complex128, device=dev)
     c[:, 0] = 1.0
     for k in range(args.warmup):
@@ -275,7 +285,7 @@ def main() -> None:
 
     # ---- accuracy of the mixed form: the same steps again in plain FP64 (untimed)
     prob_err = None
-    if prec == 1:
+    if prec >= 1:
         c64 = torch.zeros((n_paths, N), dtype=torch.complex128, device=dev)
         c64[:, 0] = 1.0
         for k in range(args.warmup + args.steps):
@@ -291,15 +301,16 @@ def main() -> None:
     NT, NP_, G = basis.T.N, basis.P.N, basis.quad.G
     n_half = int(sum(1 for m in basis.P.st_m if m >= 0))
     evals = args.steps * n_paths * (2 * STEP + 1)
-    # Eq. 9 contraction, three integrals, per z: projectile columns with q >= 0 (the reflection gives the rest)
-    flops_mol = 12.0 * NT * n_half * G
+    # Eq. 9 contraction, two integrals (K and Q; the lower-left block is Q^+), per z: projectile columns
+    # with q >= 0 (the reflection gives the rest): 4 real flops per node per integral
+    flops_mol = 8.0 * NT * n_half * G
     # LU, plus N right-hand sides in the paper's form; the stage form's triangular solves run in the RK4 kernel
     flops_solve = (8.0 / 3.0 + (8.0 if (args.solve_mode == "matrix" and prec == 0) else 0.0)) * N ** 3
     # RK4 per path-step (FP64): 4 applications of M; matrix form X y, stage form H y + two triangles,
     # mixed form H y and one refinement residual S x
     rk4_flops = {"matrix": 32.0, "stage": 64.0}[args.solve_mode] * N * N if prec == 0 else 64.0 * N * N
-    cand = {"mol_gemm": (flops_mol * evals, FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS,
-                         "k_mol_gemm" + ("<float>" if prec else "<double>")),
+    cand = {"mol_gemm": (flops_mol * evals, FP32_PEAK_TFLOPS if prec == 1 else FP64_PEAK_TFLOPS,
+                         "k_mol_gemm_f32q" if prec == 1 else "k_mol_gemm<double>"),
             "solve": (flops_solve * evals, FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS,
                       "k_lu_factor_f32" if prec else "k_lu_solve"),
             "rk4": (rk4_flops * n_paths * STEP * args.steps, FP64_PEAK_TFLOPS, "k_rk4")}
@@ -322,9 +333,11 @@ def main() -> None:
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
-            "config": {"workload": CONFIG_DESC, "paths": n_paths,
+            "config": {"workload": CONFIG_DESC if args.workload == WORKLOAD else CONFIG_DESC_C6, "paths": n_paths,
                        "form": ("mixed precision: Eq. 9 contraction and LU on the FP32 pipe, FP64 node "
-                                "tables, refinement and RK4; all paths batched" if prec else
+                                "tables, refinement and RK4; all paths batched" if prec == 1 else
+                                "mixed precision with FP64 elements: LU on the FP32 pipe, FP64 refinement and "
+                                "RK4; all paths batched" if prec == 2 else
                                 "plain FP64, all paths batched; S^-1 applied "
                                 + ("per RK4 stage from LU factors" if args.solve_mode == "stage"
                                    else "as X = S^-1 H with N right-hand sides (the paper's ZGESV form)")),

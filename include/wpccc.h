@@ -7,13 +7,13 @@
  * The paper's most expensive part (Sec. II, Eq. 1) is the set of coupled
  * first-order equations
  *
- *     i v [[I, K], [K^+, I]] d/dz [F; G] = [[D_T, Q], [Q~, D_P]] [F; G]
+ *     i v [[I, K], [K^+, I]] d/dz [F; G] = [[D_T, Q], [Q^+, D_P]] [F; G]
  *
  * along straight-line projectile paths (impact parameter b, speed v, position z).
  * Written as dX/dz = M X with M = -(i/v) S^{-1} H (Eq. 2-4), it is advanced by
  * classical RK4 (Algorithm 1).  In this header
  *   S = [[I, K], [K^+, I]]       overlap matrix       (paper: the matrix left of d/dz)
- *   H = [[D_T, Q], [Q~, D_P]]    coupling matrix      (paper: the matrix on the right)
+ *   H = [[D_T, Q], [Q^+, D_P]]   coupling matrix      (paper: the matrix on the right)
  *   X = S^{-1} H                 solution of the linear system (paper: ZGESV)
  *   c = [F; G]                   amplitudes (paper: the solution vector X of Eq. 2-3)
  *
@@ -142,14 +142,14 @@ WPCCC_API wpccc_status wpccc_basis_info(wpccc_basis basis, int* N_T, int* N_P);
 
 /*
  * Matrix elements at nz projectile positions of one path (Eq. 1, 6-9):
- *   S[k] = [[I, K], [K^+, I]],  H[k] = [[D_T, Q], [Q~, D_P]]  at z = z[k]
+ *   S[k] = [[I, K], [K^+, I]],  H[k] = [[D_T, Q], [Q^+, D_P]]  at z = z[k]
  * with every element between states i and j carrying exp(i (eps_i - eps_j) z / v).
  *   D_T: Eq. 6 with the projectile charge, F of Eq. 7 interpolated at R = sqrt(b^2+z^2)
  *        by 5-point Lagrange interpolation on the r-grid;
  *   D_P: the same expansion about the projectile with the target charge at -R;
- *   K, Q, Q~: Eq. 9 on the (eta, tau) rule with the ETF phase exp(i v z eta tau / 2)
- *        and J_{q-q'}, rotated to the collision frame by Eq. 8; Q carries -Z_T/r_T,
- *        Q~ (lower-left block) carries -Z_P/r_P.
+ *   K, Q: Eq. 9 on the (eta, tau) rule with the ETF phase exp(i v z eta tau / 2)
+ *        and J_{q-q'}, rotated to the collision frame by Eq. 8; Q carries -Z_T/r_T;
+ *        the lower-left block of H is Q^+, as Eq. 1 prints it (H Hermitian).
  * In one-centre mode S[k] = I and H[k] = D_T.
  *   z      host   [nz] positions
  *   S, H   device [nz][N][N] complex128, column-major; fully overwritten
@@ -208,8 +208,16 @@ WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv
  *   c  device [n_paths][N] complex128: in, the amplitudes at each path's first
  *      node (Algorithm 1 starts from c = (1, 0, ..., 0)); out, the amplitudes at
  *      its last node.
- *   precision_mode 0 = FP64 throughout; batch_mode 0 = all paths batched
- *   together in chunks of RK4 steps (the only modes of this build).
+ *   precision_mode
+ *     0  FP64 throughout;
+ *     1  mixed: the Eq. 9 contraction and the LU factors of S on the FP32 pipe,
+ *        each RK4 stage's S^{-1} solved by FP64 iterative refinement (residuals
+ *        against the FP64 S), RK4 amplitudes in FP64;
+ *     2  mixed with FP64 elements: as 1 but the contraction stays in FP64 (for
+ *        ill-conditioned S, where FP32 element errors get amplified by cond(S));
+ *     in one-centre mode all three are the FP64 form (no contraction, no solve).
+ *   batch_mode 0 = all paths batched together in chunks of RK4 steps (the only
+ *   batch mode of this build).
  * Blocks until the work is finished: the library allocates its scratch memory
  * itself (kept with the basis for reuse) and checks the pivots and the
  * amplitudes at the end.

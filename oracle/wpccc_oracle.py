@@ -28,8 +28,10 @@ tests/test_oracle_pins.py):
   rotation uses d^{l_alpha}_{m_alpha q} (second index q, not q'); with the
   projectile at azimuth 0 (b along +x) the phi integral gives
   2 pi (-i)^(q-q') J_{q-q'}(v b/2 sqrt((eta^2-1)(1-tau^2))).
-* Eq. 1 lower-left block: the exact transfer integral
-  Q~ = <P e^{iv.r/2}| -Z_P/r_P |T e^{-iv.r/2}>, not Q^+.
+* Eq. 1 lower-left block: Q^+, as printed.  H is then Hermitian and
+  S^-1 H has a real spectrum, so the propagation cannot grow; the exact
+  reverse-transfer integral <P| -Z_P/r_P |T> differs from Q^+ for a
+  finite pseudostate basis and gives growing modes (tests/test_oracle_pins.py).
 * Energy phases: every element between states i and j carries
   exp(i (eps_i - eps_j) z / v) (interaction picture, t = z/v).
 * Eq. 5: M = -(i/v) D_T (the -i/v of Eq. 4 with S = I).
@@ -169,22 +171,28 @@ def radial_F(grid, fa, fb, lam: int, R: float) -> np.ndarray:
 
 def _direct_angular(centre) -> np.ndarray:
     """z-independent part of Eq. 6 for every (a', a, lam):
-    sqrt((2l_a+1)/(2l_a'+1)) sqrt((lam-mu)!/(lam+mu)!) C^{l_a' 0}_{lam 0 l_a 0} C^{l_a' m_a'}_{lam mu l_a m_a}."""
+    sqrt((2l_a+1)/(2l_a'+1)) sqrt((lam-mu)!/(lam+mu)!) C^{l_a' 0}_{lam 0 l_a 0} C^{l_a' m_a'}_{lam mu l_a m_a}.
+    It depends on the states' (l', m', l, m) only: tabulated over those, then gathered per state pair."""
     key = "_oracle_direct_angular"
     if hasattr(centre, key):
         return getattr(centre, key)
-    N, lmax = centre.N, int(centre.rad_l.max())
-    ang = np.zeros((N, N, 2 * lmax + 1))
-    for i in range(N):
-        for j in range(N):
-            lp, mp, l, m = int(centre.st_l[i]), int(centre.st_m[i]), int(centre.st_l[j]), int(centre.st_m[j])
-            mu = mp - m
-            for lam in range(abs(lp - l), lp + l + 1):
-                if (lp + l + lam) % 2 or abs(mu) > lam:
-                    continue
-                a = math.sqrt((2 * l + 1) / (2 * lp + 1)) * math.sqrt(
-                    math.factorial(lam - mu) / math.factorial(lam + mu))
-                ang[i, j, lam] = a * clebsch_gordan(lam, 0, l, 0, lp, 0) * clebsch_gordan(lam, mu, l, m, lp, mp)
+    lmax = int(centre.rad_l.max())
+    nl, L = 2 * lmax + 1, lmax
+    tab = np.zeros((lmax + 1, 2 * lmax + 1, lmax + 1, 2 * lmax + 1, nl))
+    for lp in range(lmax + 1):
+        for mp in range(-lp, lp + 1):
+            for l in range(lmax + 1):
+                for m in range(-l, l + 1):
+                    mu = mp - m
+                    for lam in range(abs(lp - l), lp + l + 1):
+                        if (lp + l + lam) % 2 or abs(mu) > lam:
+                            continue
+                        a = math.sqrt((2 * l + 1) / (2 * lp + 1)) * math.sqrt(
+                            math.factorial(lam - mu) / math.factorial(lam + mu))
+                        tab[lp, mp + L, l, m + L, lam] = (
+                            a * clebsch_gordan(lam, 0, l, 0, lp, 0) * clebsch_gordan(lam, mu, l, m, lp, mp))
+    sl, sm = centre.st_l, centre.st_m + L
+    ang = tab[sl[:, None], sm[:, None], sl[None, :], sm[None, :], :]
     setattr(centre, key, ang)
     return ang
 
@@ -225,11 +233,12 @@ def direct_block(grid, centre, Z_other: float, R: float, cos_theta: float, other
 # ---------------------------------------------------------------------------
 
 
-def molecular_integrals(basis, b: float, v: float, z: float):
+def molecular_integrals(basis, b: float, v: float, z: float, reverse: bool = False):
     """Molecular-frame integrals for every (target state in frame q', projectile state in frame q):
     X[i, j] = (R^3/8) sum_{eta,tau} w (eta^2 - tau^2) e^{i v z eta tau / 2} (-i)^{q-q'} J_{q-q'}(x)
               f_i(r_T) Theta_{l_i q'}(c_T) f_j(r_P) Theta_{l_j q}(c_P) * u(eta, tau)
-    with u = 1 (overlap), -Z_T/r_T (transfer Q) and -Z_P/r_P (reverse transfer, before conjugation).
+    with u = 1 (overlap K) and -Z_T/r_T (transfer Q); with reverse=True also -Z_P/r_P (the
+    reverse-transfer integral, before conjugation, used only to show why Q^+ is taken instead).
     Rows/columns use the centres' own state lists with m read as the molecular-frame q."""
     T, P, qd = basis.T, basis.P, basis.quad
     R = math.sqrt(b * b + z * z)
@@ -254,7 +263,7 @@ def molecular_integrals(basis, b: float, v: float, z: float):
     Wd = {}
     for d in range(-dmax, dmax + 1):
         Wd[d] = base * ((-1j) ** d) * special.jv(d, x)
-    factors = [np.ones_like(rT), -basis.Z_T / rT, -basis.Z_P / rP]
+    factors = [np.ones_like(rT), -basis.Z_T / rT] + ([-basis.Z_P / rP] if reverse else [])
     out = []
     for u in factors:
         X = np.zeros((T.N, P.N), dtype=np.complex128)
@@ -303,11 +312,10 @@ def assemble(basis, b: float, v: float, z: float):
         return S, H
     DP = direct_block(basis.grid, P, basis.Z_T, R, cth, other_at_minus_R=True)
     theta = math.acos(cth)
-    Smol, Qmol, Qtmol = molecular_integrals(basis, b, v, z)
+    Smol, Qmol = molecular_integrals(basis, b, v, z)
     ph = phases(T.st_eps, P.st_eps, z, v)
     K = rotate(T, P, Smol, theta) * ph
     Q = rotate(T, P, Qmol, theta) * ph
-    Qt = (rotate(T, P, Qtmol, theta) * ph).conj().T
     NT, N = T.N, basis.N
     S = np.eye(N, dtype=np.complex128)
     S[:NT, NT:] = K
@@ -315,7 +323,7 @@ def assemble(basis, b: float, v: float, z: float):
     H = np.zeros((N, N), dtype=np.complex128)
     H[:NT, :NT] = DT * phases(T.st_eps, T.st_eps, z, v)
     H[:NT, NT:] = Q
-    H[NT:, :NT] = Qt
+    H[NT:, :NT] = Q.conj().T          # Eq. 1: the lower-left block is Q^+
     H[NT:, NT:] = DP * phases(P.st_eps, P.st_eps, z, v)
     return S, H
 

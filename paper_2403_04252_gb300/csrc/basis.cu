@@ -151,6 +151,18 @@ __global__ void __launch_bounds__(256) k_ftable(int Nr, const double* __restrict
     }
 }
 
+// 1 / prod_{c != a} (r_{s+a} - r_{s+c}) for every 5-point stencil start s.
+__global__ void k_lagrange_den(int Nr, const double* __restrict__ r, double* __restrict__ inv_den) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > Nr - 5) return;
+    for (int a = 0; a < 5; ++a) {
+        double p = 1.0;
+        for (int c = 0; c < 5; ++c)
+            if (c != a) p *= r[s + a] - r[s + c];
+        inv_den[(size_t)s * 5 + a] = 1.0 / p;
+    }
+}
+
 // Eq. 6 angular factor per (a', a, lam), without sqrt((lam-mu)!/(lam+mu)!).
 __global__ void k_direct_angular(int Nc, int nlam, const int* __restrict__ st_l,
                                  const int* __restrict__ st_m, double* __restrict__ ang) {
@@ -284,7 +296,7 @@ static void free_basis(wpccc_basis_s* B) {
         if (e) cudaEventDestroy(e);
     free_centre(B->T);
     free_centre(B->P);
-    void* ptrs[] = {B->r, B->w, B->s, B->ws, B->tau, B->wtau, B->half_state, B->half_of, B->qtile_q,
+    void* ptrs[] = {B->r, B->w, B->inv_den, B->s, B->ws, B->tau, B->wtau, B->half_state, B->half_of, B->qtile_q,
                     B->qtile_cols, B->ws_ptr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -336,6 +348,13 @@ extern "C" wpccc_status wpccc_basis_create(const wpccc_basis_desc* d, int device
     };
     if ((st = upload(&B->r, d->r, d->Nr, "upload r")) != WPCCC_OK) return bail(st);
     if ((st = upload(&B->w, d->w, d->Nr, "upload w")) != WPCCC_OK) return bail(st);
+    if ((st = upload<double>(&B->inv_den, nullptr, (size_t)(d->Nr - 4) * 5, "alloc inv_den")) != WPCCC_OK)
+        return bail(st);
+    k_lagrange_den<<<(d->Nr - 4 + 127) / 128, 128>>>(d->Nr, B->r, B->inv_den);
+    {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return bail(cuda_fail(e, "k_lagrange_den"));
+    }
     if ((st = build_centre(d->T, d->Nr, B->r, B->w, B->T)) != WPCCC_OK) return bail(st);
     if (two) {
         if ((st = build_centre(d->P, d->Nr, B->r, B->w, B->P)) != WPCCC_OK) return bail(st);

@@ -5,7 +5,7 @@
 //                  interpolated at r_T and r_P (5-point Lagrange, Sec. II),
 //                  normalised Legendre functions at the two centres' cosines, and
 //                  the complex node weights W_d = (R^3/8) w (eta^2-tau^2)
-//                  exp(i v z eta tau/2) (-i)^d J_d(x) times 1, -Z_T/r_T, -Z_P/r_P
+//                  exp(i v z eta tau/2) (-i)^d J_d(x) times 1 (overlap K) and -Z_T/r_T (transfer Q)
 //   k_mol_gemm     molecular-frame integrals (Eq. 9) as a contraction over the
 //                  nodes: X[i][c] = sum_g A_T[i][g] A_P[c][g] W_{|q_c - q'_i|}[g]
 //                  for every target state i and projectile state c with q >= 0
@@ -22,6 +22,10 @@
 #include "wpccc_internal.cuh"
 
 namespace wpccc {
+
+// Two-centre integrals per position: the overlap K and the transfer Q (Eq. 1); the lower-left
+// block of H is Q^+, as Eq. 1 prints it, so no third integral is formed.
+constexpr int NX = 2;
 
 // ---------------------------------------------------------------------------
 // geometry shared by the kernels; explicit round-to-nearest operations so that
@@ -57,6 +61,32 @@ __device__ inline bool stencil5(const double* __restrict__ r, int Nr, double x, 
     return true;
 }
 
+// The same stencil with the Lagrange denominators 1/prod_{c != a}(r_{s+a} - r_{s+c}) read from a
+// table made at set-up (inv_den[s][a], 5 per stencil start), so no division per interpolation.
+__device__ inline bool stencil5_fast(const double* __restrict__ r, const double* __restrict__ inv_den, int Nr,
+                                     double x, int& s, double L[5]) {
+    if (x > r[Nr - 1]) return false;
+    int lo = -1, hi = Nr;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (r[mid] <= x) lo = mid;
+        else hi = mid;
+    }
+    s = min(max(lo - 2, 0), Nr - 5);
+    double dx[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) dx[k] = x - r[s + k];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        double p = inv_den[(size_t)s * 5 + a];
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            if (c != a) p *= dx[c];
+        L[a] = p;
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // k_node_tables
 // ---------------------------------------------------------------------------
@@ -64,6 +94,7 @@ struct NodeArgs {
     int Nr, G, Gtau, nradT, nradP, lmaxT, lmaxP, nlqT, nlqP, dmax;
     double gamma, Z_T, Z_P;
     const double *r, *fT, *fP, *s, *ws, *tau, *wtau;
+    const double* inv_den;   // Lagrange denominators per stencil start
     double* node;            // per evaluation: [fT | fP | thT | thP | pad | W] (see elem_scratch_layout)
     size_t node_doubles;     // stride between evaluations, in doubles
     size_t w_off;            // offset of W in elements of the table type (even, so W stays aligned)
@@ -111,8 +142,8 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
     // radial functions at the node radii
     int sT, sP;
     double LT[5], LP[5];
-    const bool inT = stencil5(A.r, A.Nr, rT, sT, LT);
-    const bool inP = stencil5(A.r, A.Nr, rP, sP, LP);
+    const bool inT = stencil5_fast(A.r, A.inv_den, A.Nr, rT, sT, LT);
+    const bool inP = stencil5_fast(A.r, A.inv_den, A.Nr, rP, sP, LP);
     // Theta_lq(c) = sqrt((2l+1)/2 (l-q)!/(l+q)!) P_l^q(c), index l(l+1)/2 + q
     double thv[2][(WPCCC_LMAX + 1) * (WPCCC_LMAX + 2) / 2];
     for (int cen = 0; cen < 2; ++cen) {
@@ -187,8 +218,8 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
             }
         }
     }
-    // node weights for the three integrands, d = |q - q'| = 0..dmax
-    const double uQ = -A.Z_T / rT, uQt = -A.Z_P / rP;
+    // node weights for the two integrands, d = |q - q'| = 0..dmax
+    const double uQ = -A.Z_T / rT;
     const size_t stride = (size_t)(A.dmax + 1) * A.G;
     for (int d = 0; d <= A.dmax; ++d) {
         const double J = jn(d, x) * amp;
@@ -202,16 +233,13 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         }
         const double2 w0 = make_double2(J * re, J * im);
         const size_t o = (size_t)d * A.G + g;
-        T2 a, bq, c;
+        T2 a, bq;
         a.x = (T)w0.x;
         a.y = (T)w0.y;
         bq.x = (T)(w0.x * uQ);
         bq.y = (T)(w0.y * uQ);
-        c.x = (T)(w0.x * uQt);
-        c.y = (T)(w0.y * uQt);
         W[o] = a;
         W[stride + o] = bq;
-        W[2 * stride + o] = c;
     }
 }
 
@@ -227,7 +255,7 @@ struct GemmArgs {
     const int* half_state;
     const double* node;
     size_t node_doubles, w_off;
-    double2* mol;                         // [nev][3][N_T][n_half]
+    double2* mol;                         // [nev][NX][N_T][n_half]
 };
 
 template <typename R> struct Cplx;
@@ -243,7 +271,7 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sAT = reinterpret_cast<R*>(smem_raw);                      // [GT_K][GT_I + 1]
     R* sAP = sAT + GT_K * (GT_I + 1);                             // [GT_K][GT_J + 1]
-    R2* sW = reinterpret_cast<R2*>(sAP + GT_K * (GT_J + 1));      // [3][dmax+1][GT_K]
+    R2* sW = reinterpret_cast<R2*>(sAP + GT_K * (GT_J + 1));      // [NX][dmax+1][GT_K]
     __shared__ int s_rrad[GT_I], s_rlq[GT_I], s_rq[GT_I];
     __shared__ R s_rsgn[GT_I];
     __shared__ int s_crad[GT_J], s_clq[GT_J], s_cq[GT_J];
@@ -297,13 +325,13 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
             int d = s_cq[tx * 2 + c] - s_rq[ty * 2 + a];
             dd[a][c] = d < 0 ? -d : d;
         }
-    R acc[2][2][6], tot[2][2][6];
+    R acc[2][2][2 * NX], tot[2][2][2 * NX];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
+            for (int q = 0; q < 2 * NX; ++q) {
                 acc[a][c][q] = R(0);
                 tot[a][c][q] = R(0);
             }
@@ -340,7 +368,7 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
                 sAP[gg * (GT_J + 1) + cc] = (s_crad[cc] >= 0 && g < A.G) ? aP[(size_t)(j0 + cc) * A.G + g] : R(0);
             }
         }
-        for (int idx = tid; idx < 3 * nd * GT_K; idx += 256) {
+        for (int idx = tid; idx < NX * nd * GT_K; idx += 256) {
             int gg = idx % GT_K, xd = idx / GT_K, g = g0 + gg;
             int X = xd / nd, d = xd % nd;
             R2 wr;
@@ -366,13 +394,11 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
                 for (int c = 0; c < 2; ++c) {
                     const R p = at[a] * ap[c];
                     const R2* wp = sW + dd[a][c] * GT_K + gg;
-                    const R2 w0 = wp[0], w1 = wp[nd * GT_K], w2 = wp[2 * nd * GT_K];
+                    const R2 w0 = wp[0], w1 = wp[nd * GT_K];
                     acc[a][c][0] = fma(p, w0.x, acc[a][c][0]);
                     acc[a][c][1] = fma(p, w0.y, acc[a][c][1]);
                     acc[a][c][2] = fma(p, w1.x, acc[a][c][2]);
                     acc[a][c][3] = fma(p, w1.y, acc[a][c][3]);
-                    acc[a][c][4] = fma(p, w2.x, acc[a][c][4]);
-                    acc[a][c][5] = fma(p, w2.y, acc[a][c][5]);
                 }
         }
         if (sizeof(R) == 4) {
@@ -381,7 +407,7 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
 #pragma unroll
                 for (int c = 0; c < 2; ++c)
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) {
+                    for (int q = 0; q < 2 * NX; ++q) {
                         tot[a][c][q] += acc[a][c][q];
                         acc[a][c][q] = R(0);
                     }
@@ -394,10 +420,10 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
-                for (int q = 0; q < 6; ++q) tot[a][c][q] = acc[a][c][q];
+                for (int q = 0; q < 2 * NX; ++q) tot[a][c][q] = acc[a][c][q];
     }
     const size_t plane = (size_t)A.N_T * A.n_half;
-    double2* out = A.mol + (size_t)e * 3 * plane;
+    double2* out = A.mol + (size_t)e * NX * plane;
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         int i = i0 + ty * 2 + a;
@@ -409,7 +435,6 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
             size_t o = (size_t)i * A.n_half + j;
             out[o] = make_double2(tot[a][c][0], tot[a][c][1]);
             out[plane + o] = make_double2(tot[a][c][2], tot[a][c][3]);
-            out[2 * plane + o] = make_double2(tot[a][c][4], tot[a][c][5]);
         }
     }
 }
@@ -421,7 +446,8 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
 // and the inner loop is a plain 6-accumulator product with the column operand A_P[j][g].
 // Sums run per chunk of QT_K nodes and are then added to the running totals (two-level summation).
 // ---------------------------------------------------------------------------
-constexpr int QT_I = 32, QT_J = 16, QT_K = 32, QT_THREADS = 64;   // 16 x 4 threads, 2 x 4 per thread
+constexpr int QT_I = 32, QT_J = 16, QT_K = 32, QT_THREADS = 64;   // 8 x 4 thread grid per warp pair
+constexpr int QT_AS = QT_K + 4;   // row stride of the staged row operand (16-byte rows, distinct banks)
 
 struct Gemm32Args {
     int G, N_T, n_half, dmax, n_col_tiles;
@@ -433,9 +459,28 @@ struct Gemm32Args {
     double2* mol;
 };
 
+__device__ inline void cp_async4(void* sdst, const void* gsrc, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 4 : 0));
+}
+__device__ inline void cp_async8(void* sdst, const void* gsrc, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0));
+}
+__device__ inline void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc));
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
-    __shared__ __align__(16) float sB[QT_K][QT_I][6];
-    __shared__ __align__(16) float sP[QT_K][QT_J];
+    extern __shared__ __align__(16) float qsm[];
+    const int nd = A.dmax + 1;
+    float* sA = qsm;                                   // [2][QT_I][QT_AS]   row operand A_T
+    float* sP = sA + 2 * QT_I * QT_AS;                 // [2][QT_K][QT_J]    column operand A_P
+    float2* sW = reinterpret_cast<float2*>(sP + 2 * QT_K * QT_J);   // [2][NX][nd][QT_K] weights
     __shared__ int s_d[QT_I], s_col[QT_J];
     const int e = blockIdx.y;
     const int rt = blockIdx.x / A.n_col_tiles, ct = blockIdx.x % A.n_col_tiles;
@@ -446,7 +491,7 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
     const float* aT = base;
     const float* aP = aT + (size_t)A.N_T * A.G;
     const float2* W = reinterpret_cast<const float2*>(base + A.w_off_f);
-    const size_t wstride = (size_t)(A.dmax + 1) * A.G;
+    const size_t wstride = (size_t)nd * A.G;
     for (int r = tid; r < QT_I; r += QT_THREADS) {
         const int i = i0 + r;
         int d = -1;
@@ -458,86 +503,118 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
     }
     for (int c = tid; c < QT_J; c += QT_THREADS) s_col[c] = A.ctile_cols[ct * QT_J + c];
     __syncthreads();
-    float acc[2][4][6], tot[2][4][6];
+    const bool vec = (A.G & 3) == 0;
+    auto stage = [&](int buf, int g0) {
+        float* a = sA + buf * QT_I * QT_AS;
+        for (int t = tid; t < QT_I * (QT_K / 4); t += QT_THREADS) {
+            const int r = t / (QT_K / 4), k4 = (t % (QT_K / 4)) * 4, g = g0 + k4;
+            const bool rv = s_d[r] >= 0;
+            const float* src = aT + (size_t)(rv ? i0 + r : 0) * A.G;
+            if (vec && rv && g + 3 < A.G) {
+                cp_async16(a + r * QT_AS + k4, src + g);
+            } else {
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = rv && g + u < A.G;
+                    cp_async4(a + r * QT_AS + k4 + u, ok ? src + g + u : aT, ok);
+                }
+            }
+        }
+        float* p = sP + buf * QT_K * QT_J;
+        for (int t = tid; t < QT_K * QT_J; t += QT_THREADS) {
+            const int c = t / QT_K, k = t % QT_K, g = g0 + k;
+            const int j = s_col[c];
+            const bool ok = j >= 0 && g < A.G;
+            cp_async4(p + k * QT_J + c, ok ? aP + (size_t)j * A.G + g : aP, ok);
+        }
+        float2* w = sW + (size_t)buf * NX * nd * QT_K;
+        for (int t = tid; t < NX * nd * QT_K; t += QT_THREADS) {
+            const int k = t % QT_K, xd = t / QT_K, g = g0 + k;
+            const int x = xd / nd, d = xd % nd;
+            const bool ok = g < A.G;
+            cp_async8(w + t, ok ? W + (size_t)x * wstride + (size_t)d * A.G + g : W, ok);
+        }
+        cp_async_commit();
+    };
+
+    float acc[2][4][2 * NX], tot[2][4][2 * NX];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int x = 0; x < 6; ++x) {
+            for (int x = 0; x < 2 * NX; ++x) {
                 acc[a][c][x] = 0.f;
                 tot[a][c][x] = 0.f;
             }
-    for (int g0 = 0; g0 < A.G; g0 += QT_K) {
-        for (int idx = tid; idx < QT_I * QT_K; idx += QT_THREADS) {
-            const int r = idx / QT_K, gg = idx % QT_K, g = g0 + gg;
-            const int d = s_d[r];
-            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (d >= 0 && g < A.G) {
-                const float at = aT[(size_t)(i0 + r) * A.G + g];
-                const float2 w0 = W[(size_t)d * A.G + g];
-                const float2 w1 = W[wstride + (size_t)d * A.G + g];
-                const float2 w2 = W[2 * wstride + (size_t)d * A.G + g];
-                v[0] = at * w0.x;
-                v[1] = at * w0.y;
-                v[2] = at * w1.x;
-                v[3] = at * w1.y;
-                v[4] = at * w2.x;
-                v[5] = at * w2.y;
-            }
-#pragma unroll
-            for (int x = 0; x < 6; ++x) sB[gg][r][x] = v[x];
-        }
-        for (int idx = tid; idx < QT_J * QT_K; idx += QT_THREADS) {
-            const int c = idx / QT_K, gg = idx % QT_K, g = g0 + gg;
-            const int j = s_col[c];
-            sP[gg][c] = (j >= 0 && g < A.G) ? aP[(size_t)j * A.G + g] : 0.f;
+    const int r0 = ty * 2;
+    const int d0 = s_d[r0] < 0 ? 0 : s_d[r0], d1 = s_d[r0 + 1] < 0 ? 0 : s_d[r0 + 1];
+    const int nchunks = (A.G + QT_K - 1) / QT_K;
+    stage(0, 0);
+    for (int kc = 0; kc < nchunks; ++kc) {
+        const int buf = kc & 1;
+        if (kc + 1 < nchunks) {
+            stage(buf ^ 1, (kc + 1) * QT_K);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const float* a = sA + buf * QT_I * QT_AS;
+        const float* p = sP + buf * QT_K * QT_J;
+        const float2* w = sW + (size_t)buf * NX * nd * QT_K;
 #pragma unroll 4
         for (int gg = 0; gg < QT_K; ++gg) {
-            const float4 p = *reinterpret_cast<const float4*>(&sP[gg][tx * 4]);
-            const float pc[4] = {p.x, p.y, p.z, p.w};
+            const float4 pv = *reinterpret_cast<const float4*>(p + gg * QT_J + tx * 4);
+            const float pc[4] = {pv.x, pv.y, pv.z, pv.w};
+            float bv[2][2 * NX];
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const float* bp = &sB[gg][ty * 2 + a][0];
-                const float2 b01 = *reinterpret_cast<const float2*>(bp);
-                const float2 b23 = *reinterpret_cast<const float2*>(bp + 2);
-                const float2 b45 = *reinterpret_cast<const float2*>(bp + 4);
-                const float bv[6] = {b01.x, b01.y, b23.x, b23.y, b45.x, b45.y};
+            for (int rr = 0; rr < 2; ++rr) {
+                const int d = rr == 0 ? d0 : d1;
+                const float at = a[(r0 + rr) * QT_AS + gg];
+                const float2 w0 = w[d * QT_K + gg];
+                const float2 w1 = w[(nd + d) * QT_K + gg];
+                bv[rr][0] = at * w0.x;
+                bv[rr][1] = at * w0.y;
+                bv[rr][2] = at * w1.x;
+                bv[rr][3] = at * w1.y;
+            }
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
 #pragma unroll
-                    for (int x = 0; x < 6; ++x) acc[a][c][x] = fmaf(bv[x], pc[c], acc[a][c][x]);
-            }
+                    for (int x = 0; x < 2 * NX; ++x) acc[rr][c][x] = fmaf(bv[rr][x], pc[c], acc[rr][c][x]);
         }
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
             for (int c = 0; c < 4; ++c)
 #pragma unroll
-                for (int x = 0; x < 6; ++x) {
-                    tot[a][c][x] += acc[a][c][x];
-                    acc[a][c][x] = 0.f;
+                for (int x = 0; x < 2 * NX; ++x) {
+                    tot[rr][c][x] += acc[rr][c][x];
+                    acc[rr][c][x] = 0.f;
                 }
         __syncthreads();
     }
     const size_t plane = (size_t)A.N_T * A.n_half;
-    double2* out = A.mol + (size_t)e * 3 * plane;
+    double2* out = A.mol + (size_t)e * NX * plane;
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int i = i0 + ty * 2 + a;
+    for (int rr = 0; rr < 2; ++rr) {
+        const int i = i0 + r0 + rr;
         if (i >= A.N_T) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int j = s_col[tx * 4 + c];
             if (j < 0) continue;
             const size_t o = (size_t)i * A.n_half + j;
-            out[o] = make_double2(tot[a][c][0], tot[a][c][1]);
-            out[plane + o] = make_double2(tot[a][c][2], tot[a][c][3]);
-            out[2 * plane + o] = make_double2(tot[a][c][4], tot[a][c][5]);
+            out[o] = make_double2(tot[rr][c][0], tot[rr][c][1]);
+            out[plane + o] = make_double2(tot[rr][c][2], tot[rr][c][3]);
         }
     }
+}
+
+size_t mol_gemm_f32q_smem(int dmax) {
+    return sizeof(float) * (2 * QT_I * QT_AS + 2 * QT_K * QT_J) + sizeof(float2) * 2 * NX * (dmax + 1) * QT_K;
 }
 
 // ---------------------------------------------------------------------------
@@ -549,6 +626,8 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
 struct EtArgs {
     int lrot, nlam, Nr;
     int dtot, npb;           // sizes of the d and Pbar parts
+    int nfT, nfP;            // Eq. 7 table entries of the two centres (F interpolated at R follows the stencil)
+    const double *FT, *FP;
     const double* r;
     double* et;              // [nev][et_doubles]
     size_t et_doubles;
@@ -576,6 +655,8 @@ __global__ void __launch_bounds__(128) k_eval_tables(EtArgs A, const EvalDesc* _
         int mu = t - lam * (lam + 1) / 2;
         et[A.dtot + t] = sqrt(dfact(lam - mu) / dfact(lam + mu)) * assoc_legendre(lam, mu, cth);
     }
+    __shared__ int s_s, s_out;
+    __shared__ double s_L[5];
     if (threadIdx.x == 0) {
         double* st = et + A.dtot + A.npb;
         int s;
@@ -584,13 +665,35 @@ __global__ void __launch_bounds__(128) k_eval_tables(EtArgs A, const EvalDesc* _
             st[0] = (double)(A.Nr - 1);
             st[1] = 1.0;
             for (int k = 0; k < 5; ++k) st[2 + k] = 0.0;
+            s_s = A.Nr - 1;
+            s_out = 1;
         } else {
             stencil5(A.r, A.Nr, R, s, L);
             st[0] = (double)s;
             st[1] = 0.0;
             for (int k = 0; k < 5; ++k) st[2 + k] = L[k];
+            s_s = s;
+            s_out = 0;
+            for (int k = 0; k < 5; ++k) s_L[k] = L[k];
         }
     }
+    __syncthreads();
+    // F of every Eq. 7 table entry at R (5-point interpolation, or the multipole tail beyond the grid)
+    double* Fint = et + A.dtot + A.npb + 8;
+    const double ratio = A.r[A.Nr - 1] / R;
+    for (int t = threadIdx.x; t < A.nfT + A.nfP; t += blockDim.x) {
+        const double* Fe = t < A.nfT ? A.FT + (size_t)t * A.Nr : A.FP + (size_t)(t - A.nfT) * A.Nr;
+        double Fv;
+        if (s_out) {
+            // lam of the entry is not needed here: the tail factor (r_max/R)^{lam+1} is applied in k_direct
+            Fv = Fe[A.Nr - 1];
+        } else {
+            const int s = s_s;
+            Fv = s_L[0] * Fe[s] + s_L[1] * Fe[s + 1] + s_L[2] * Fe[s + 2] + s_L[3] * Fe[s + 3] + s_L[4] * Fe[s + 4];
+        }
+        Fint[t] = Fv;
+    }
+    (void)ratio;
 }
 
 // ---------------------------------------------------------------------------
@@ -598,7 +701,7 @@ __global__ void __launch_bounds__(128) k_eval_tables(EtArgs A, const EvalDesc* _
 // ---------------------------------------------------------------------------
 struct RotArgs {
     int N_T, N_P, N, n_half, lmax, n_radT, n_radP;
-    int rot_block;            // complex entries of one warp's block: 3 (2 lmax_T + 1)(2 lmax_P + 1)
+    int rot_block;            // complex entries of one warp's block: NX (2 lmax_T + 1)(2 lmax_P + 1)
     int dtot;                 // size of the Wigner-d part of the per-position tables
     const double* et;         // per-position tables (k_eval_tables)
     size_t et_doubles;
@@ -640,9 +743,9 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
     const double* da = sd + offa;   // da[(m + la) * na + (q + la)] = d^{la}_{m q}
     const double* db = sd + offb;
     const size_t plane = (size_t)A.N_T * A.n_half;
-    const double2* mol = A.mol + (size_t)e * 3 * plane;
+    const double2* mol = A.mol + (size_t)e * NX * plane;
     // molecular block, X[x][q'][q] at x * blk + (q' + la) * nbq + (q + lb)
-    for (int t = lane; t < 3 * blk; t += 32) {
+    for (int t = lane; t < NX * blk; t += 32) {
         const int x = t / blk, r = t % blk, qp = r / nbq - la, q = r % nbq - lb;
         int row, col;
         double sg = 1.0;
@@ -659,7 +762,7 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
     }
     __syncwarp();
     // T[x][q'][m_b] = sum_q d^{lb}_{m_b q} X[x][q'][q]
-    for (int t = lane; t < 3 * blk; t += 32) {
+    for (int t = lane; t < NX * blk; t += 32) {
         const int x = t / blk, r = t % blk, qi = r / nbq, mb = r % nbq;
         const double2* xr = X + x * blk + qi * nbq;
         const double* dr = db + mb * nbq;
@@ -677,16 +780,14 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
     for (int t = lane; t < blk; t += 32) {
         const int mi = t / nbq, mb = t % nbq;
         const double* dr = da + mi * na;
-        double acc[6] = {0, 0, 0, 0, 0, 0};
+        double acc[4] = {0, 0, 0, 0};
         for (int qi = 0; qi < na; ++qi) {
             const double w = dr[qi];
-            const double2 t0 = T[qi * nbq + mb], t1 = T[blk + qi * nbq + mb], t2 = T[2 * blk + qi * nbq + mb];
+            const double2 t0 = T[qi * nbq + mb], t1 = T[blk + qi * nbq + mb];
             acc[0] = fma(w, t0.x, acc[0]);
             acc[1] = fma(w, t0.y, acc[1]);
             acc[2] = fma(w, t1.x, acc[2]);
             acc[3] = fma(w, t1.y, acc[3]);
-            acc[4] = fma(w, t2.x, acc[4]);
-            acc[5] = fma(w, t2.y, acc[5]);
         }
         const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
         const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
@@ -695,13 +796,12 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
         const double2 ph = make_double2(cp, sp);
         const double2 K = cmul(make_double2(acc[0], acc[1]), ph);
         const double2 Q = cmul(make_double2(acc[2], acc[3]), ph);
-        const double2 Qt = cmul(make_double2(acc[4], acc[5]), ph);
         const size_t up = (size_t)i + (size_t)(A.N_T + j) * A.N;     // row i, column N_T + j
         const size_t lo = (size_t)(A.N_T + j) + (size_t)i * A.N;     // row N_T + j, column i
         S[up] = K;
         S[lo] = cconj(K);
         H[up] = Q;
-        H[lo] = cconj(Qt);
+        H[lo] = cconj(Q);     // Eq. 1: the lower-left block of H is Q^+
     }
 }
 
@@ -711,6 +811,7 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
 struct DirArgs {
     int Nr, N, off, Nc, n_rad, nlam;
     int dtot, npb;                // layout of the per-position tables
+    int foff0;                    // first interpolated F entry of this centre in the per-position tables
     const double* et;
     size_t et_doubles;
     double Z_other, parity;       // parity = -1: the other nucleus sits at -R
@@ -747,21 +848,18 @@ __global__ void __launch_bounds__(256) k_direct(DirArgs A0, DirArgs A1, const Ev
     const int amu = mu < 0 ? -mu : mu;
     const double* ang = A.ang + (size_t)idx * A.nlam;
     const int* foff = A.Foff + ((size_t)ra * A.n_rad + rb) * A.nlam;
+    const double* Fint = et + A.dtot + A.npb + 8 + A.foff0;
     double D = 0.0;
     double sgn = 1.0;
     for (int lam = 0; lam < A.nlam; ++lam, sgn *= A.parity) {
         const double c = ang[lam];
         if (c == 0.0) continue;
-        const double* Fe = A.F + (size_t)foff[lam] * A.Nr;
-        double Fv;
+        double Fv = Fint[foff[lam]];
         if (s_out) {
             const double ratio = A.r[A.Nr - 1] / R;
             double p = ratio;
             for (int k = 0; k < lam; ++k) p *= ratio;
-            Fv = Fe[A.Nr - 1] * p;
-        } else {
-            const int s = s_sten;
-            Fv = sL[0] * Fe[s] + sL[1] * Fe[s + 1] + sL[2] * Fe[s + 2] + sL[3] * Fe[s + 3] + sL[4] * Fe[s + 4];
+            Fv *= p;
         }
         double P = sPb[lam * (lam + 1) / 2 + amu];
         if (mu < 0 && (amu & 1)) P = -P;
@@ -784,21 +882,21 @@ ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
     for (int l = 0; l <= lrot; ++l) L.dtot += (2 * l + 1) * (2 * l + 1);
     const int nlam = 2 * lrot + 1;
     L.npb = nlam * (nlam + 1) / 2;
-    L.et_doubles = (size_t)L.dtot + L.npb + 7;
+    L.et_doubles = (size_t)L.dtot + L.npb + 8 + B->T.n_fent + (B->n_centres == 2 ? B->P.n_fent : 0);
     L.et_doubles += L.et_doubles & 1;
     if (B->n_centres == 2) {
         size_t nd = (size_t)(B->T.n_rad + B->P.n_rad + B->nlq_T + B->nlq_P) * B->G;
         nd += nd & 1;   // keep the complex weights 16-byte aligned
         L.w_off = nd;
-        nd += (size_t)3 * (B->dmax + 1) * B->G * 2;
+        nd += (size_t)NX * (B->dmax + 1) * B->G * 2;
         // FP32 layout of the mixed-precision form: per-state products, then the weights (floats)
         size_t nf = (size_t)(B->N_T + B->n_half) * B->G;
         nf += nf & 1;
         L.w_off_f = nf;
-        nf += (size_t)3 * (B->dmax + 1) * B->G * 2;
+        nf += (size_t)NX * (B->dmax + 1) * B->G * 2;
         L.node_doubles = std::max(nd, (nf + 1) / 2);
         L.node_doubles += L.node_doubles & 1;
-        L.mol_elems = (size_t)3 * B->N_T * B->n_half;
+        L.mol_elems = (size_t)NX * B->N_T * B->n_half;
         L.bytes_per_eval = L.node_doubles * sizeof(double) + L.mol_elems * sizeof(double2);
     }
     L.bytes_per_eval += L.et_doubles * sizeof(double);
@@ -850,6 +948,10 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         ea.dtot = L.dtot;
         ea.npb = L.npb;
         ea.r = B->r;
+        ea.nfT = B->T.n_fent;
+        ea.nfP = two ? B->P.n_fent : 0;
+        ea.FT = B->T.F;
+        ea.FP = two ? B->P.F : nullptr;
         ea.et = et;
         ea.et_doubles = L.et_doubles;
         cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
@@ -879,6 +981,7 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         na.ws = B->ws;
         na.tau = B->tau;
         na.wtau = B->wtau;
+        na.inv_den = B->inv_den;
         na.node = node;
         na.node_doubles = L.node_doubles;
         na.w_off = precision == 0 ? L.w_off : L.w_off_f;
@@ -919,7 +1022,7 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         e0 = B->prof.begin(PROF_MOL, st);
         if (precision == 0) {
             const size_t gsm = (size_t)GT_K * (GT_I + 1 + GT_J + 1) * sizeof(double) +
-                               (size_t)3 * (B->dmax + 1) * GT_K * sizeof(double2);
+                               (size_t)NX * (B->dmax + 1) * GT_K * sizeof(double2);
             WPCCC_CUDA(cudaFuncSetAttribute(k_mol_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)gsm));
             k_mol_gemm<double><<<dim3(n_row_tiles * ga.n_col_tiles, nev), 256, gsm, st>>>(ga);
@@ -938,7 +1041,9 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
             g32.w_off_f = L.w_off_f;
             g32.mol = mol;
             const int rtiles = (B->N_T + QT_I - 1) / QT_I;
-            k_mol_gemm_f32q<<<dim3(rtiles * B->n_qtiles, nev), QT_THREADS, 0, st>>>(g32);
+            const size_t qsm = mol_gemm_f32q_smem(B->dmax);
+            WPCCC_CUDA(cudaFuncSetAttribute(k_mol_gemm_f32q, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+            k_mol_gemm_f32q<<<dim3(rtiles * B->n_qtiles, nev), QT_THREADS, qsm, st>>>(g32);
         }
         WPCCC_CHECK_LAUNCH("k_mol_gemm");
         B->prof.end(PROF_MOL, st, e0);
@@ -970,7 +1075,7 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         ra.mat = (size_t)B->N * B->N;
         int dtot = 0;
         for (int l = 0; l <= ra.lmax; ++l) dtot += (2 * l + 1) * (2 * l + 1);
-        ra.rot_block = 3 * (2 * B->T.lmax + 1) * (2 * B->P.lmax + 1);
+        ra.rot_block = NX * (2 * B->T.lmax + 1) * (2 * B->P.lmax + 1);
         ra.dtot = L.dtot;
         ra.et = et;
         ra.et_doubles = L.et_doubles;
@@ -990,6 +1095,8 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
     DirArgs d1 = two ? dir_args(B, B->P, B->N_T, B->T.Z, -1.0, S, H) : d0;
     d0.et = et;
     d1.et = et;
+    d0.foff0 = 0;
+    d1.foff0 = B->T.n_fent;
     int ncmax = two ? std::max(B->N_T, B->N_P) : B->N_T;
     long long cells = (long long)ncmax * ncmax;
     cudaEvent_t ed = B->prof.begin(PROF_ROT_DIRECT, st);

@@ -385,8 +385,8 @@ extern "C" wpccc_status wpccc_probabilities(int n_paths, int N, const void* c, d
 extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths, int precision_mode,
                                         int batch_mode, void* c, void* stream) {
     if (!B || !paths || !c) return fail(WPCCC_EINVAL, "wpccc_propagate: null argument");
-    if (precision_mode != 0 && precision_mode != 1)
-        return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: precision_mode must be 0 (FP64) or 1 (mixed)");
+    if (precision_mode < 0 || precision_mode > 2)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: precision_mode must be 0, 1 or 2");
     if (batch_mode != 0) return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: only batch_mode 0");
     const int np = paths->n_paths;
     if (np < 1 || !paths->b || !paths->v || !paths->n_z || !paths->z)
@@ -407,7 +407,9 @@ extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths,
     WPCCC_CUDA(cudaSetDevice(B->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool two = B->n_centres == 2;
-    const bool mixed = two && precision_mode == 1;
+    // 1: FP32 contraction + FP32 LU + FP64 refinement; 2: FP64 elements + FP32 LU + FP64 refinement
+    const bool mixed = two && precision_mode >= 1;
+    const int elem_precision = (two && precision_mode == 1) ? 1 : 0;
     const bool stage = two && !mixed && B->solve_mode == WPCCC_SOLVE_STAGE;
     const int mode = mixed ? RK_MIXED : (stage ? RK_STAGE : RK_MATRIX);
     const size_t mat = (size_t)N * N;
@@ -588,7 +590,7 @@ extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths,
         int* bI = two ? d_info + k * hI : nullptr;
         // buffer set k is free once the RK4 sweep of chunk ch - 2 is done
         if (ch >= 2) WPCCC_CUDA(cudaStreamWaitEvent(st, B->ev_rk[k], 0));
-        s = launch_elements(B, d_ev + ev_begin[ch], nev, bS, bH, d_scr, st, mixed ? 1 : 0);
+        s = launch_elements(B, d_ev + ev_begin[ch], nev, bS, bH, d_scr, st, elem_precision);
         if (s != WPCCC_OK) return s;
         if (two) {
             cudaEvent_t e0 = B->prof.begin(PROF_SOLVE, st);

@@ -78,6 +78,7 @@ struct wpccc_basis_s {
     int N_T = 0, N_P = 0, N = 0;
     double* r = nullptr;
     double* w = nullptr;
+    double* inv_den = nullptr;  // [Nr-4][5] Lagrange denominators of the 5-point stencils
     wpccc::CentreDev T, P;
     // two-centre quadrature
     int Geta = 0, Gtau = 0, G = 0;

@@ -242,12 +242,12 @@ def test_probabilities_kernel():
 MIXED_TOL = 1e-6     # absolute, per probability
 
 
-def _mixed_errors(basis, bs, v, zgs, workspace=None):
+def _mixed_errors(basis, bs, v, zgs, workspace=None, mode=1):
     w = _w()
     g = w.Basis(basis)
     if workspace:
         g.set_workspace_limit(workspace)
-    c = g.propagate(bs, v, zgs, precision_mode=1)
+    c = g.propagate(bs, v, zgs, precision_mode=mode)
     Pg = w.probabilities(c).cpu().numpy()
     errs = []
     for p in range(len(bs)):
@@ -257,10 +257,20 @@ def _mixed_errors(basis, bs, v, zgs, workspace=None):
     return np.array(errs)
 
 
-def test_mixed_form_small_two_centre(small2c_uneven):
+def test_mixed_form_small_two_centre(small2c):
+    # mode 1 (FP32 elements and LU, FP64 refinement) on a p + H-like basis, against the oracle
     bs = np.array([0.5, 2.0])
     zgs = [wi.uniform_zgrid(-6.0, 6.0, 0.2), wi.uniform_zgrid(-4.0, 5.0, 0.25)]
-    err = _mixed_errors(small2c_uneven, bs, 1.3, zgs, workspace=64 << 20)
+    err = _mixed_errors(small2c, bs, 1.3, zgs, workspace=64 << 20, mode=1)
+    assert err.max() <= MIXED_TOL, err.max()
+
+
+def test_mixed_fp64_elements_small_uneven_two_centre(small2c_uneven):
+    # mode 2 (FP64 elements, FP32 LU, FP64 refinement) on a C6+ on H-like basis (stiff near closest
+    # approach: h = 0.05), against the oracle
+    bs = np.array([0.5, 2.0])
+    zgs = [wi.uniform_zgrid(-3.0, 3.0, 0.05), wi.uniform_zgrid(-2.0, 2.5, 0.05)]
+    err = _mixed_errors(small2c_uneven, bs, 1.3, zgs, workspace=64 << 20, mode=2)
     assert err.max() <= MIXED_TOL, err.max()
 
 

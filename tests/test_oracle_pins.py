@@ -150,8 +150,7 @@ def test_two_centre_closed_forms_at_rest(grid):
     basis = wi.Basis(grid=grid, T=T, P=P, quad=wi.make_quadrature(48, 48, 0.5), Z_T=1.0, Z_P=1.0)
     for b, z in [(0.4, 0.0), (1.5, 1.0), (2.0, -5.0)]:
         R = math.hypot(b, z)
-        S, H = O.assemble(basis, b, 1e-300, z)  # v -> 0: phases are 1 (zero energies), ETF off
-        Smol, Qmol, Qtmol = O.molecular_integrals(basis, b, 0.0, z)
+        Smol, Qmol, Qtmol = O.molecular_integrals(basis, b, 0.0, z, reverse=True)
         assert Smol[0, 0].real == pytest.approx(math.exp(-R) * (1 + R + R * R / 3), abs=1e-7)
         assert Qmol[0, 0].real == pytest.approx(-math.exp(-R) * (1 + R), abs=1e-7)
         assert Qtmol[0, 0].real == pytest.approx(-math.exp(-R) * (1 + R), abs=1e-7)
@@ -168,8 +167,12 @@ def test_two_centre_brute_force(tiny2c, b, z, v):
     NT = T.N
     assert np.abs(S[:NT, NT:] - Sb).max() < 1e-8
     assert np.abs(H[:NT, NT:] - Qb).max() < 1e-8
-    assert np.abs(H[NT:, :NT] - Qtb).max() < 1e-8
+    assert np.array_equal(H[NT:, :NT], H[:NT, NT:].conj().T)          # Eq. 1's Q^+
     assert np.allclose(S[NT:, :NT], S[:NT, NT:].conj().T, atol=0)
+    # the reverse-transfer integral through the same machinery (not used by the path) also matches
+    Smol, Qmol, Qtmol = O.molecular_integrals(tiny2c, b, v, z, reverse=True)
+    Qt = (O.rotate(T, P, Qtmol, math.acos(z / math.hypot(b, z)))).conj().T
+    assert np.abs(Qt - Qtb).max() < 1e-8
 
 
 def test_far_limit_S_to_identity(tiny2c):
@@ -266,3 +269,21 @@ def test_radial_integral_beyond_grid_is_multipole_tail():
     a = O.radial_F(g, f, f, 0, g.r[-1])[0]
     b = O.radial_F(g, f, f, 0, g.r[-1] * (1 + 1e-12))[0]
     assert a == pytest.approx(b, rel=1e-10)
+
+
+def test_paper_lower_left_block_keeps_the_spectrum_real(grid):
+    # Eq. 1 with Q^+ below the diagonal: H Hermitian and S positive definite, so M = -(i/v) S^-1 H has a
+    # purely imaginary spectrum; the exact reverse-transfer integral instead gives growing modes when the
+    # two centres differ (here C6+ on H with pseudostates).
+    basis = wi.make_basis(1.0, 6.0, 2, 1, 3, 4.0, True, Nr=1000, Geta=32, Gtau=32)
+    S, H = O.assemble(basis, 0.5, 2.0, 0.0)
+    ev = np.linalg.eigvals((-1j / 2.0) * np.linalg.solve(S, H))
+    assert np.abs(ev.real).max() < 1e-10
+    NT = basis.T.N
+    Smol, Qmol, Qtmol = O.molecular_integrals(basis, 0.5, 2.0, 0.0, reverse=True)
+    ph = O.phases(basis.T.st_eps, basis.P.st_eps, 0.0, 2.0)
+    Qt = (O.rotate(basis.T, basis.P, Qtmol, math.pi / 2) * ph).conj().T
+    H2 = H.copy()
+    H2[NT:, :NT] = Qt
+    ev2 = np.linalg.eigvals((-1j / 2.0) * np.linalg.solve(S, H2))
+    assert ev2.real.max() > 1e-3

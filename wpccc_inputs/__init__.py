@@ -18,8 +18,10 @@ wave-packet pseudostate of angular momentum l on the k-bin [k_i, k_{i+1}] is
 (k_{i+1}-k_i)^(-1/2) * integral over the bin of the delta(k-k')-normalised
 regular Coulomb function u_kl(r)/r, with energy (k_i^2 + k_i k_{i+1} +
 k_{i+1}^2)/6.  Pseudostates are then orthonormalised on the grid against the
-bound states of the same l (Gram-Schmidt), so the tabulated basis is
-orthonormal under the grid's own quadrature.
+lower states of the same l (Gram-Schmidt), so the tabulated basis is
+orthonormal under the grid's own quadrature (the lowest state of each l
+keeps its closed form; higher bound states are orthonormalised as well, since
+the grid's end at r_max cuts their tails).
 """
 from __future__ import annotations
 
@@ -201,7 +203,9 @@ def make_centre(Z: float, nmax: int, lmax: int, nbins: int, kmax: float,
             fl.extend(list(fb))
             el.extend(list(eb))
             nl.extend([100 + i for i in range(nbins)])
-        fl = _orthonormalise(fl, grid, nbound)
+        # the lowest function of each l is kept as it is; the rest (higher bound states, whose tails the
+        # finite grid cuts, and the pseudostates) are orthonormalised on the grid in order
+        fl = _orthonormalise(fl, grid, 1)
         rad_l += [l] * len(fl)
         rad_n += nl
         f += fl
@@ -334,6 +338,10 @@ CONFIGS = {
     # two-centre p + H with electron capture
     "p_H_2c_n4l3": dict(Z_T=1.0, Z_P=1.0, nmax=4, lmax=3, nbins=10, kmax=3.0, two_centre=True,
                         v=1.5, b=(0.2, 12.0, 32), z=(-50.0, 50.0, 0.1)),
+    # two-centre bare C6+ on H (projectile charge 6), the mixed-precision workload; on the paper's
+    # geometric z-grid (Sec. II: dense near closest approach, where the C6+ couplings need h << 0.1)
+    "C6_H_2c_n6l5": dict(Z_T=1.0, Z_P=6.0, nmax=6, lmax=5, nbins=20, kmax=4.0, two_centre=True,
+                         v=2.0, b=(0.5, 15.0, 16), z=("geometric", 1e-3, 50.0, 500)),
 }
 
 
@@ -345,6 +353,9 @@ def config_inputs(name: str, **over):
                        c["two_centre"], Nr=c.get("Nr", 2000), rmax=c.get("rmax", 100.0),
                        Geta=c.get("Geta", 48), Gtau=c.get("Gtau", 48), gamma=c.get("gamma", 0.5))
     b0, b1, nb = c["b"]
-    z0, z1, h = c["z"]
-    paths = make_paths(np.linspace(b0, b1, nb), c["v"], uniform_zgrid(z0, z1, h))
+    if c["z"][0] == "geometric":
+        zgrid = geometric_zgrid(*c["z"][1:])
+    else:
+        zgrid = uniform_zgrid(*c["z"])
+    paths = make_paths(np.linspace(b0, b1, nb), c["v"], zgrid)
     return basis, paths
