@@ -536,7 +536,9 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
         cp_async_commit();
     };
 
-    float acc[2][4][2 * NX], tot[2][4][2 * NX];
+    // chunk sums in FP32, running totals in FP64 (one FP64 add per accumulator per chunk of QT_K nodes)
+    float acc[2][4][2 * NX];
+    double tot[2][4][2 * NX];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -544,7 +546,7 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
 #pragma unroll
             for (int x = 0; x < 2 * NX; ++x) {
                 acc[a][c][x] = 0.f;
-                tot[a][c][x] = 0.f;
+                tot[a][c][x] = 0.0;
             }
     const int r0 = ty * 2;
     const int d0 = s_d[r0] < 0 ? 0 : s_d[r0], d1 = s_d[r0 + 1] < 0 ? 0 : s_d[r0 + 1];
@@ -591,7 +593,7 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
             for (int c = 0; c < 4; ++c)
 #pragma unroll
                 for (int x = 0; x < 2 * NX; ++x) {
-                    tot[rr][c][x] += acc[rr][c][x];
+                    tot[rr][c][x] += (double)acc[rr][c][x];
                     acc[rr][c][x] = 0.f;
                 }
         __syncthreads();
