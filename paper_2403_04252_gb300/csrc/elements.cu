@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256) k_mol_gemm(GemmArgs A) {
 // All columns of a tile share q, so row i needs the single weight W_{|q - q'_i|}: the row operand is
 // pre-multiplied by it once per node, B_x[i][g] = A_T[i][g] W_x[d_i][g] (x = three complex integrands),
 // and the inner loop is a plain 6-accumulator product with the column operand A_P[j][g].
-// Sums run per chunk of QT_K nodes and are then added to the running totals (two-level summation).
+// Sums run per chunk of QT_K nodes and are then added to the running totals by compensated summation.
 // ---------------------------------------------------------------------------
 constexpr int QT_I = 32, QT_J = 16, QT_K = 32, QT_THREADS = 64;   // 8 x 4 thread grid per warp pair
 constexpr int QT_AS = QT_K + 4;   // row stride of the staged row operand (16-byte rows, distinct banks)
@@ -536,9 +536,9 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
         cp_async_commit();
     };
 
-    // chunk sums in FP32, running totals in FP64 (one FP64 add per accumulator per chunk of QT_K nodes)
-    float acc[2][4][2 * NX];
-    double tot[2][4][2 * NX];
+    // chunk sums in FP32; running totals as compensated (Kahan) FP32 sums of the chunk sums, whose
+    // rounding error does not grow with the number of chunks
+    float acc[2][4][2 * NX], tot[2][4][2 * NX], cmp[2][4][2 * NX];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -546,7 +546,8 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
 #pragma unroll
             for (int x = 0; x < 2 * NX; ++x) {
                 acc[a][c][x] = 0.f;
-                tot[a][c][x] = 0.0;
+                tot[a][c][x] = 0.f;
+                cmp[a][c][x] = 0.f;
             }
     const int r0 = ty * 2;
     const int d0 = s_d[r0] < 0 ? 0 : s_d[r0], d1 = s_d[r0 + 1] < 0 ? 0 : s_d[r0 + 1];
@@ -593,7 +594,10 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
             for (int c = 0; c < 4; ++c)
 #pragma unroll
                 for (int x = 0; x < 2 * NX; ++x) {
-                    tot[rr][c][x] += (double)acc[rr][c][x];
+                    const float y = __fsub_rn(acc[rr][c][x], cmp[rr][c][x]);
+                    const float t = __fadd_rn(tot[rr][c][x], y);
+                    cmp[rr][c][x] = __fsub_rn(__fsub_rn(t, tot[rr][c][x]), y);
+                    tot[rr][c][x] = t;
                     acc[rr][c][x] = 0.f;
                 }
         __syncthreads();
@@ -609,8 +613,10 @@ __global__ void __launch_bounds__(QT_THREADS) k_mol_gemm_f32q(Gemm32Args A) {
             const int j = s_col[tx * 4 + c];
             if (j < 0) continue;
             const size_t o = (size_t)i * A.n_half + j;
-            out[o] = make_double2(tot[rr][c][0], tot[rr][c][1]);
-            out[plane + o] = make_double2(tot[rr][c][2], tot[rr][c][3]);
+            out[o] = make_double2((double)tot[rr][c][0] - (double)cmp[rr][c][0],
+                                  (double)tot[rr][c][1] - (double)cmp[rr][c][1]);
+            out[plane + o] = make_double2((double)tot[rr][c][2] - (double)cmp[rr][c][2],
+                                          (double)tot[rr][c][3] - (double)cmp[rr][c][3]);
         }
     }
 }
