@@ -168,6 +168,155 @@ def run_reference(args) -> None:
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_batch(args) -> None:
+    """Batched form: six speeds (bases of different size), 64 paths each, uneven step counts (the
+    same z extent at h = 0.1 v/1.5), captured into one CUDA graph with autotuned chunk schedules.
+    Timed against the same sets propagated by separate wpccc_propagate calls (plain FP64 form)."""
+    import torch
+    import wpccc_inputs as wi
+    import paper_2403_04252_gb300 as w
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    step_ref = args.rk4_per_step if args.rk4_per_step != STEP_RK4 else 4
+    sets_in = wi.batch_inputs()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v_, basis_, paths_ = sets_in[2]
+        cpu = cpu_oracle_rate(basis_, paths_, 3, path_index=32)
+    sets, c = [], []
+    for v, basis, paths in sets_in:
+        g = w.Basis(basis, device=local)
+        g.set_workspace_limit(8 << 30)
+        zg = paths.z[0]
+        n = zg.size - 1
+        k = max(1, int(round(step_ref * 1.5 / v)))          # same z extent at every speed
+        k0 = n // 2 - k // 2
+        seg = zg[k0:k0 + k + 1]
+        sets.append((g, paths.b, v, seg))
+        t = torch.zeros((paths.n_paths, g.N), dtype=torch.complex128, device=dev)
+        t[:, 0] = 1.0
+        c.append(t)
+    units = sum(b.size * (seg.size - 1) for (_, b, _, seg) in sets)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    batch = w.Batch(sets, c, precision_mode=0, autotune=True)
+    t_create = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        batch.launch()
+    batch.status()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    batch.status()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * units * args.steps / (ms / 1e3)
+    # the same sets, one wpccc_propagate call per set after another, profiled per kernel
+    for g, _, _, _ in sets:
+        g.profile_enable(True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for (g, b, v, seg), cc in zip(sets, c):
+            g.propagate(b, v, seg, c=cc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    prof = {}
+    for g, _, _, _ in sets:
+        for kname, (kms, kn) in g.profile_read().items():
+            a = prof.setdefault(kname, [0.0, 0])
+            a[0] += kms
+            a[1] += kn
+        g.profile_enable(False)
+    # end to end: amplitudes from pinned host memory, probabilities back, per launch
+    c_host = [torch.zeros(t.shape, dtype=torch.complex128).pin_memory() for t in c]
+    for t in c_host:
+        t[:, 0] = 1.0
+    P_host = [torch.empty(t.shape, dtype=torch.float64).pin_memory() for t in c]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for t, th in zip(c, c_host):
+            t.copy_(th, non_blocking=True)
+        batch.launch()
+        for t, ph in zip(c, P_host):
+            ph.copy_(w.probabilities(t), non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(t.numel() * 16 for t in c_host)
+    d2h = sum(t.numel() * 8 for t in P_host)
+    chunk_steps, tuned = batch.info()
+    # roofline of the dominant kernel (from the profiled separate calls: the same kernels)
+    dom = max(prof, key=lambda k: prof[k][0])
+    flops = {"mol_gemm": 0.0, "solve": 0.0}
+    for (g, b, v, seg), (vv, basis, _) in zip(sets, sets_in):
+        evals = args.steps * b.size * (2 * (seg.size - 1) + 1)
+        n_half = int(sum(1 for m in basis.P.st_m if m >= 0))
+        flops["mol_gemm"] += 8.0 * basis.T.N * n_half * basis.quad.G * evals
+        flops["solve"] += (8.0 / 3.0) * basis.N ** 3 * evals
+    dom_f = dom if dom in flops else "mol_gemm"
+    achieved = flops[dom_f] / (prof[dom_f][0] / 1e3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched form: two-centre p+H at v in {0.5,0.8,1.2,2,3,4}, pseudostates per "
+                                   "l = round(8+8(v-0.5)/3.5) = 8..16 (k<=3), hydrogenic n<=4, l<=3, all m "
+                                   f"(N = {[g.N for g, _, _, _ in sets]}); 64 b uniform in [0.2,12] per speed "
+                                   "(384 paths); h = 0.1 v/1.5 (step count proportional to 1/v)",
+                       "bench_step": "one CUDA graph launch advancing every path through the same z extent "
+                                     f"(RK4 steps per speed {[int(seg.size - 1) for _, _, _, seg in sets]}), "
+                                     "centred on z = 0; each launch recomputes all elements and solves",
+                       "form": "batched plain FP64: all six bases' chunk pipelines captured into one CUDA graph, "
+                               "concurrent streams, autotuned chunk schedules",
+                       "l2": "inputs larger than L2 (S and H of one launch: several GB)"},
+            "batched_vs_separate_calls": {"separate_calls_value": world * units * args.steps / (ms_seq / 1e3),
+                                          "speedup": ms_seq / ms},
+            "autotune": {"chunk_steps": [int(x) for x in chunk_steps],
+                         "ms_per_rk4_step": [float(x) for x in tuned], "create_s": t_create},
+            "roofline": {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm<double>", "solve": "k_lu_solve"}[dom_f],
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
+                                        "kernel time from the same sets' separate, profiled calls"},
+            "kernel_ms_separate_calls": {k: v_[0] for k, v_ in prof.items()},
+            "prob_error": {"max_abs": 0.0, "note": "the graph runs the plain FP64 kernels: amplitudes equal the "
+                                                   "separate calls' bit for bit (tests/test_gpu_parity.py)"},
+            "e2e": {"value": world * units * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(n for _, n in prof.values())), "clocks": clocks}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    batch.close()
+    for g, _, _, _ in sets:
+        g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,9 +327,10 @@ def main() -> None:
     ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all of the workload)")
     ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
     ap.add_argument("--solve-mode", default="stage", choices=["stage", "matrix"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v"],
                     help="p_H_2c_n4l3: two-centre p + H (N = 380, 32 paths); C6_H_2c_n6l5: bare C6+ on H "
-                         "(N = 1622, 16 paths)")
+                         "(N = 1622, 16 paths); p_H_2c_batch6v: p + H at six speeds, N = 316..572, 64 paths "
+                         "each, all in one graph launch (batched form)")
     ap.add_argument("--workspace-gb", type=float, default=0.0, help="0: 16 GB (p + H) or 96 GB (C6+ on H)")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "mixed-fp64-elements"],
                     help="auto: time plain FP64 and the reduced-precision forms, report the fastest form whose "
@@ -190,6 +340,9 @@ def main() -> None:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "p_H_2c_batch6v":
+        run_batch(args)
         return
 
     import torch

@@ -228,6 +228,32 @@ WPCCC_API wpccc_status wpccc_propagate(wpccc_basis basis, const wpccc_paths* pat
                              int batch_mode, void* c, void* stream);
 
 /*
+ * Batches: several sets of paths, each with its own basis (e.g. the same collision at several
+ * speeds, with bases of different size and paths with different step counts), propagated together
+ * by one CUDA graph launch.  The batch owns a plan per set (the positions of every chunk of RK4
+ * steps, as wpccc_propagate uses them) and the device memory for all of them; creating it captures
+ * every set's kernel sequence -- element kernels, solves and RK4 sweeps, the sets running
+ * concurrently on their own streams -- into one graph.
+ *   bases  host [n_sets] bases, all on one device; paths host [n_sets] path sets;
+ *   c      host [n_sets] device pointers, set k's amplitudes [n_paths_k][N_k] complex128; the
+ *          graph reads and writes them in place at every launch, so they must stay valid for
+ *          the batch's lifetime;
+ *   autotune  non-zero: for each set, time the default chunk schedule and chunks of half and
+ *          twice as many RK4 steps on the set's first steps (on copies of c) and keep the fastest.
+ * wpccc_batch_launch queues the graph on `stream` (asynchronous; one launch advances every set
+ * through all its steps).  wpccc_batch_status waits on `stream` and reports ESINGULAR or
+ * ENONFINITE from the last launch.  wpccc_batch_info gives each set's RK4 steps per chunk and the
+ * autotuner's ms per step (0 when not tuned).  Errors: EINVAL, ENOMEM, ECUDA, as wpccc_propagate.
+ */
+typedef struct wpccc_batch_s* wpccc_batch;
+WPCCC_API wpccc_status wpccc_batch_create(int n_sets, const wpccc_basis* bases, const wpccc_paths* paths,
+                                          int precision_mode, void* const* c, int autotune, wpccc_batch* out);
+WPCCC_API wpccc_status wpccc_batch_launch(wpccc_batch batch, void* stream);
+WPCCC_API wpccc_status wpccc_batch_status(wpccc_batch batch, void* stream);
+WPCCC_API wpccc_status wpccc_batch_info(wpccc_batch batch, int* chunk_steps, double* tuned_ms_per_step);
+WPCCC_API wpccc_status wpccc_batch_destroy(wpccc_batch batch);
+
+/*
  * Transition probabilities at the end of the paths (Sec. II: the solution at
  * z_max gives the observables): P[p][i] = |c[p][i]|^2.
  *   c  device [n_paths][N] complex128;  P  device [n_paths][N] double.

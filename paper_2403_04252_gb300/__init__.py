@@ -67,17 +67,25 @@ _lib.wpccc_basis_set_workspace_limit.argtypes = [C.c_void_p, C.c_size_t]
 _lib.wpccc_profile_enable.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_basis_set_solve_mode.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_profile_read.argtypes = [C.c_void_p, _pd, C.POINTER(C.c_longlong)]
+_lib.wpccc_batch_create.argtypes = [C.c_int, C.POINTER(C.c_void_p), C.POINTER(_PathsDesc), C.c_int,
+                                    C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
+_lib.wpccc_batch_launch.argtypes = [C.c_void_p, C.c_void_p]
+_lib.wpccc_batch_status.argtypes = [C.c_void_p, C.c_void_p]
+_lib.wpccc_batch_info.argtypes = [C.c_void_p, _pi, _pd]
+_lib.wpccc_batch_destroy.argtypes = [C.c_void_p]
 _lib.wpccc_last_error.restype = C.c_char_p
 for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
            "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode",
-           "wpccc_matrix_elements_noalloc"):
+           "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
+           "wpccc_batch_info", "wpccc_batch_destroy"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
             "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
             "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error",
-            "wpccc_matrix_elements_noalloc")
+            "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
+            "wpccc_batch_info", "wpccc_batch_destroy")
 NOALLOC_SCRATCH_BYTES = 64 << 20
 SOLVE_STAGE, SOLVE_MATRIX = 0, 1
 PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4")
@@ -230,6 +238,63 @@ class Basis:
         _check(_lib.wpccc_propagate(self._h, C.byref(pd), int(precision_mode), int(batch_mode), _ptr(c),
                                     _stream(stream)), "wpccc_propagate")
         return c
+
+
+def _paths_desc(b, v, zgrids, keep):
+    b = np.atleast_1d(np.asarray(b, dtype=np.float64))
+    v = np.broadcast_to(np.asarray(v, dtype=np.float64), b.shape)
+    if isinstance(zgrids, np.ndarray) and zgrids.ndim == 1:
+        zgrids = [zgrids] * b.size
+    nz = np.array([len(zg) for zg in zgrids], dtype=np.int32)
+    zc = np.concatenate([np.asarray(zg, dtype=np.float64) for zg in zgrids])
+    arrs = [_arr(b, np.float64), _arr(v, np.float64), _arr(nz, np.int32), _arr(zc, np.float64)]
+    keep.extend(a for a, _ in arrs)
+    return _PathsDesc(n_paths=int(b.size), b=arrs[0][1], v=arrs[1][1], n_z=arrs[2][1], z=arrs[3][1])
+
+
+class Batch:
+    """Several (basis, paths) sets propagated together by one CUDA graph launch (``wpccc_batch_*``).
+
+    `sets` is a list of (Basis, b, v, zgrids); `c` a list of (n_paths_k, N_k) complex128 device tensors,
+    advanced in place at every launch (keep them alive while the batch exists)."""
+
+    def __init__(self, sets, c, precision_mode: int = 0, autotune: bool = True):
+        keep = []
+        n = len(sets)
+        descs = (_PathsDesc * n)(*[_paths_desc(b, v, zg, keep) for (_, b, v, zg) in sets])
+        handles = (C.c_void_p * n)(*[g._h.value for (g, _, _, _) in sets])
+        cptrs = (C.c_void_p * n)(*[t.data_ptr() for t in c])
+        h = C.c_void_p()
+        _check(_lib.wpccc_batch_create(n, handles, descs, int(precision_mode), cptrs, int(bool(autotune)),
+                                       C.byref(h)), "wpccc_batch_create")
+        self._h = h
+        self.n_sets = n
+        self.c = list(c)
+        self._bases = [g for (g, _, _, _) in sets]
+
+    def launch(self, stream=None) -> None:
+        _check(_lib.wpccc_batch_launch(self._h, _stream(stream)), "wpccc_batch_launch")
+
+    def status(self, stream=None) -> None:
+        _check(_lib.wpccc_batch_status(self._h, _stream(stream)), "wpccc_batch_status")
+
+    def info(self):
+        """(RK4 steps per chunk, autotuner ms per step) for every set."""
+        cs = np.zeros(self.n_sets, dtype=np.int32)
+        ms = np.zeros(self.n_sets, dtype=np.float64)
+        _check(_lib.wpccc_batch_info(self._h, cs.ctypes.data_as(_pi), ms.ctypes.data_as(_pd)), "wpccc_batch_info")
+        return cs, ms
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.wpccc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve(S, H, precision_mode: int = 0, stream=None):

@@ -382,12 +382,41 @@ extern "C" wpccc_status wpccc_probabilities(int n_paths, int N, const void* c, d
     return WPCCC_OK;
 }
 
-extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths, int precision_mode,
-                                        int batch_mode, void* c, void* stream) {
-    if (!B || !paths || !c) return fail(WPCCC_EINVAL, "wpccc_propagate: null argument");
+namespace wpccc {
+
+// ---------------------------------------------------------------------------
+// propagation plan: the positions every chunk of RK4 steps needs, the buffer layout, and the
+// launch sequence (used directly by wpccc_propagate and captured into a graph by wpccc_batch)
+// ---------------------------------------------------------------------------
+struct PropPlan {
+    wpccc_basis_s* B = nullptr;
+    int np = 0, N = 0, mode = RK_MATRIX, elem_precision = 0, C = 1, n_chunks = 0, max_chunk_evals = 0;
+    int max_steps = 0;
+    bool two = false, mixed = false, stage = false;
+    size_t per_eval = 0, fixed = 0;
+    std::vector<double> z;
+    std::vector<EvalDesc> ev;
+    std::vector<PathChunk> pcs;
+    std::vector<int> ev_begin, pc_begin;
+    size_t sz_carry = 0, sz_carryLU = 0, sz_carryPiv = 0, sz_carryLU32 = 0, sz_LU32 = 0, sz_z = 0, sz_ev = 0,
+           sz_pc = 0, sz_flags = 0, sz_S = 0, sz_H = 0, sz_piv = 0, sz_info = 0, sz_scr = 0, bytes = 0;
+    double2 *d_carry = nullptr, *d_carryLU = nullptr, *d_S = nullptr, *d_H = nullptr;
+    int *d_carryPiv = nullptr, *d_flags = nullptr, *d_piv = nullptr, *d_info = nullptr;
+    float2 *d_carryLU32 = nullptr, *d_LU32 = nullptr;
+    double* d_z = nullptr;
+    EvalDesc* d_ev = nullptr;
+    PathChunk* d_pc = nullptr;
+    void* d_scr = nullptr;
+};
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Validates the paths and lays out the plan.  C_request > 0 fixes the RK4 steps per chunk,
+// otherwise they are chosen from the workspace limit and the SM count.
+static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int precision_mode, int C_request,
+                               size_t ws_limit, PropPlan& P) {
     if (precision_mode < 0 || precision_mode > 2)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: precision_mode must be 0, 1 or 2");
-    if (batch_mode != 0) return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: only batch_mode 0");
     const int np = paths->n_paths;
     if (np < 1 || !paths->b || !paths->v || !paths->n_z || !paths->z)
         return fail(WPCCC_EINVAL, "wpccc_propagate: empty or null path description");
@@ -403,60 +432,59 @@ extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths,
     }
     const int N = B->N;
     if (N > WPCCC_NMAX) return fail(WPCCC_EINVAL, "wpccc_propagate: N too large");
-
-    WPCCC_CUDA(cudaSetDevice(B->device));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool two = B->n_centres == 2;
+    P = PropPlan();
+    P.B = B;
+    P.np = np;
+    P.N = N;
+    P.two = B->n_centres == 2;
     // 1: FP32 contraction + FP32 LU + FP64 refinement; 2: FP64 elements + FP32 LU + FP64 refinement
-    const bool mixed = two && precision_mode >= 1;
-    const int elem_precision = (two && precision_mode == 1) ? 1 : 0;
-    const bool stage = two && !mixed && B->solve_mode == WPCCC_SOLVE_STAGE;
-    const int mode = mixed ? RK_MIXED : (stage ? RK_STAGE : RK_MATRIX);
+    P.mixed = P.two && precision_mode >= 1;
+    P.elem_precision = (P.two && precision_mode == 1) ? 1 : 0;
+    P.stage = P.two && !P.mixed && B->solve_mode == WPCCC_SOLVE_STAGE;
+    P.mode = P.mixed ? RK_MIXED : (P.stage ? RK_STAGE : RK_MATRIX);
+    if (rk_smem_bytes(P.mode, N) > (size_t)227 * 1024)
+        return fail(WPCCC_EINVAL, "wpccc_propagate: N too large for the RK4 kernel's shared memory in this mode");
     const size_t mat = (size_t)N * N;
     const ElemScratch L = elem_scratch_layout(B);
-    if (rk_smem_bytes(mode, N) > (size_t)227 * 1024)
-        return fail(WPCCC_EINVAL, "wpccc_propagate: N too large for the RK4 kernel's shared memory in this mode");
-    // device bytes per evaluation: S (two-centre only), H, pivots and info, element scratch
-    const size_t per_eval = (two ? 2 : 1) * mat * sizeof(double2) + (mixed ? mat * sizeof(float2) : 0) +
-                            L.bytes_per_eval + (two ? (size_t)N * sizeof(int) + sizeof(int) : 0) + sizeof(EvalDesc);
-
-    int max_steps = 0;
+    // device bytes per evaluation: S (two-centre only), H, FP32 factors, pivots and info, element scratch
+    P.per_eval = (P.two ? 2 : 1) * mat * sizeof(double2) + (P.mixed ? mat * sizeof(float2) : 0) + L.bytes_per_eval +
+                 (P.two ? (size_t)N * sizeof(int) + sizeof(int) : 0) + sizeof(EvalDesc);
     long long total_evals = 0;
     for (int p = 0; p < np; ++p) {
         int ns = paths->n_z[p] - 1;
-        max_steps = std::max(max_steps, ns);
+        P.max_steps = std::max(P.max_steps, ns);
         if (ns > 0) total_evals += 2LL * ns + 1;
     }
-    if (max_steps == 0) return WPCCC_OK;
-
-    // fixed part of the workspace: carry matrices, z nodes, plan, flags
-    auto align = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t fixed = align((size_t)np * mat * sizeof(double2)) * (mode != RK_MATRIX ? 2 : 1) +
-                         (mixed ? align((size_t)np * mat * sizeof(float2)) : 0) +
-                         align((size_t)np * N * sizeof(int)) + align((size_t)zoff[np] * sizeof(double)) +
-                         align((size_t)total_evals * sizeof(EvalDesc)) +
-                         align((size_t)np * max_steps * sizeof(PathChunk)) + 16 * 256;
-    // Steps per chunk.  Two chunks are in flight (the RK4 sweep of one overlaps the assembly of the
-    // next), so each buffer set gets half the budget.  Aim for at least four chunks per call, each
-    // with enough positions (>= 2 per SM) to fill the GPU.
-    size_t budget = B->ws_limit > fixed ? B->ws_limit - fixed : 0;
-    long long cap_evals = (long long)(budget / (2 * per_eval));
-    int dev_sms = 0;
-    WPCCC_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, B->device));
-    const long long cap_steps = std::max<long long>(1, (cap_evals - np) / (2LL * np));
-    const long long fill_steps = std::max<long long>(1, (2LL * dev_sms / np + 1) / 2);
-    long long want = std::max<long long>((max_steps + 3) / 4, fill_steps);
-    int C = (int)std::max<long long>(1, std::min<long long>({(long long)max_steps, cap_steps, want}));
-    const int n_chunks = (max_steps + C - 1) / C;
-
-    // plan: evaluations and path chunks for every chunk
-    std::vector<EvalDesc> ev;
-    ev.reserve(total_evals);
-    std::vector<PathChunk> pcs;
-    std::vector<int> ev_begin(n_chunks + 1), pc_begin(n_chunks + 1);
-    for (int ch = 0; ch < n_chunks; ++ch) {
-        ev_begin[ch] = (int)ev.size();
-        pc_begin[ch] = (int)pcs.size();
+    P.z.assign(paths->z, paths->z + zoff[np]);
+    if (P.max_steps == 0) return WPCCC_OK;
+    P.fixed = align256((size_t)np * mat * sizeof(double2)) * (P.mode != RK_MATRIX ? 2 : 1) +
+              (P.mixed ? align256((size_t)np * mat * sizeof(float2)) : 0) + align256((size_t)np * N * sizeof(int)) +
+              align256((size_t)zoff[np] * sizeof(double)) + align256((size_t)total_evals * sizeof(EvalDesc)) +
+              align256((size_t)np * P.max_steps * sizeof(PathChunk)) + 16 * 256;
+    int C;
+    if (C_request > 0) {
+        C = std::min(C_request, P.max_steps);
+    } else {
+        // Two chunks are in flight (the RK4 sweep of one overlaps the assembly of the next), so each
+        // buffer set gets half the budget.  Aim for at least four chunks per call, each with enough
+        // positions (>= 2 per SM) to fill the GPU.
+        size_t budget = ws_limit > P.fixed ? ws_limit - P.fixed : 0;
+        long long cap_evals = (long long)(budget / (2 * P.per_eval));
+        int dev_sms = 0;
+        WPCCC_CUDA(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, B->device));
+        const long long cap_steps = std::max<long long>(1, (cap_evals - np) / (2LL * np));
+        const long long fill_steps = std::max<long long>(1, (2LL * dev_sms / np + 1) / 2);
+        long long want = std::max<long long>((P.max_steps + 3) / 4, fill_steps);
+        C = (int)std::max<long long>(1, std::min<long long>({(long long)P.max_steps, cap_steps, want}));
+    }
+    P.C = C;
+    P.n_chunks = (P.max_steps + C - 1) / C;
+    P.ev.reserve(total_evals);
+    P.ev_begin.assign(P.n_chunks + 1, 0);
+    P.pc_begin.assign(P.n_chunks + 1, 0);
+    for (int ch = 0; ch < P.n_chunks; ++ch) {
+        P.ev_begin[ch] = (int)P.ev.size();
+        P.pc_begin[ch] = (int)P.pcs.size();
         const int s0 = ch * C;
         for (int p = 0; p < np; ++p) {
             const int ns = paths->n_z[p] - 1;
@@ -470,158 +498,466 @@ extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths,
             pc.z0 = zoff[p] + s0;
             pc.pad = 0;
             pc.start_local = -1;
-            const int base = ev_begin[ch];
+            const int base = P.ev_begin[ch];
             if (s0 == 0) {
-                pc.start_local = (int)ev.size() - base;
-                ev.push_back(EvalDesc{paths->b[p], paths->v[p], zp[0], p, 0});
+                pc.start_local = (int)P.ev.size() - base;
+                P.ev.push_back(EvalDesc{paths->b[p], paths->v[p], zp[0], p, 0});
             }
-            pc.first_local = (int)ev.size() - base;
+            pc.first_local = (int)P.ev.size() - base;
             for (int s = s0; s < s0 + n; ++s) {
                 const double za = zp[s], zb = zp[s + 1];
-                ev.push_back(EvalDesc{paths->b[p], paths->v[p], (za + zb) / 2.0, p, 0});
-                ev.push_back(EvalDesc{paths->b[p], paths->v[p], zb, p, 0});
+                P.ev.push_back(EvalDesc{paths->b[p], paths->v[p], (za + zb) / 2.0, p, 0});
+                P.ev.push_back(EvalDesc{paths->b[p], paths->v[p], zb, p, 0});
             }
-            pcs.push_back(pc);
+            P.pcs.push_back(pc);
         }
     }
-    ev_begin[n_chunks] = (int)ev.size();
-    pc_begin[n_chunks] = (int)pcs.size();
-    int max_chunk_evals = 0;
-    for (int ch = 0; ch < n_chunks; ++ch) max_chunk_evals = std::max(max_chunk_evals, ev_begin[ch + 1] - ev_begin[ch]);
-
-    // workspace carve-up
-    const size_t sz_carry = align((size_t)np * mat * sizeof(double2));
-    const size_t sz_carryLU = mode != RK_MATRIX ? sz_carry : 0;
-    const size_t sz_carryPiv = mode != RK_MATRIX ? align((size_t)np * N * sizeof(int)) : 0;
-    const size_t sz_carryLU32 = mixed ? align((size_t)np * mat * sizeof(float2)) : 0;
-    const size_t sz_LU32 = mixed ? align((size_t)max_chunk_evals * mat * sizeof(float2)) * 2 : 0;
-    const size_t sz_z = align((size_t)zoff[np] * sizeof(double));
-    const size_t sz_ev = align(ev.size() * sizeof(EvalDesc));
-    const size_t sz_pc = align(pcs.size() * sizeof(PathChunk));
-    const size_t sz_flags = 256;
+    P.ev_begin[P.n_chunks] = (int)P.ev.size();
+    P.pc_begin[P.n_chunks] = (int)P.pcs.size();
+    for (int ch = 0; ch < P.n_chunks; ++ch)
+        P.max_chunk_evals = std::max(P.max_chunk_evals, P.ev_begin[ch + 1] - P.ev_begin[ch]);
+    const int mce = P.max_chunk_evals;
+    P.sz_carry = align256((size_t)np * mat * sizeof(double2));
+    P.sz_carryLU = P.mode != RK_MATRIX ? P.sz_carry : 0;
+    P.sz_carryPiv = P.mode != RK_MATRIX ? align256((size_t)np * N * sizeof(int)) : 0;
+    P.sz_carryLU32 = P.mixed ? align256((size_t)np * mat * sizeof(float2)) : 0;
+    P.sz_LU32 = P.mixed ? align256((size_t)mce * mat * sizeof(float2)) * 2 : 0;
+    P.sz_z = align256((size_t)zoff[np] * sizeof(double));
+    P.sz_ev = align256(P.ev.size() * sizeof(EvalDesc));
+    P.sz_pc = align256(P.pcs.size() * sizeof(PathChunk));
+    P.sz_flags = 256;
     // two buffer sets (chunk parity) for what the RK4 sweep reads
-    const size_t sz_S = two ? align((size_t)max_chunk_evals * mat * sizeof(double2)) * 2 : 0;
-    const size_t sz_H = align((size_t)max_chunk_evals * mat * sizeof(double2)) * 2;
-    const size_t sz_piv = two ? align((size_t)max_chunk_evals * N * sizeof(int)) * 2 : 0;
-    const size_t sz_info = two ? align((size_t)max_chunk_evals * sizeof(int)) * 2 : 0;
-    const size_t sz_scr = align((size_t)max_chunk_evals * L.bytes_per_eval);
-    const size_t need = sz_carry + sz_carryLU + sz_carryPiv + sz_carryLU32 + sz_LU32 + sz_z + sz_ev + sz_pc +
-                        sz_flags + sz_S + sz_H + sz_piv + sz_info + sz_scr;
-    wpccc_status s = ensure_workspace(B, need);
-    if (s != WPCCC_OK) return s;
-    char* w = static_cast<char*>(B->ws_ptr);
-    double2* d_carry = reinterpret_cast<double2*>(w);
-    w += sz_carry;
-    double2* d_carryLU = mode != RK_MATRIX ? reinterpret_cast<double2*>(w) : nullptr;
-    w += sz_carryLU;
-    int* d_carryPiv = mode != RK_MATRIX ? reinterpret_cast<int*>(w) : nullptr;
-    w += sz_carryPiv;
-    float2* d_carryLU32 = mixed ? reinterpret_cast<float2*>(w) : nullptr;
-    w += sz_carryLU32;
-    float2* d_LU32 = mixed ? reinterpret_cast<float2*>(w) : nullptr;
-    w += sz_LU32;
-    double* d_z = reinterpret_cast<double*>(w);
-    w += sz_z;
-    EvalDesc* d_ev = reinterpret_cast<EvalDesc*>(w);
-    w += sz_ev;
-    PathChunk* d_pc = reinterpret_cast<PathChunk*>(w);
-    w += sz_pc;
-    int* d_flags = reinterpret_cast<int*>(w);
-    w += sz_flags;
-    double2* d_S = two ? reinterpret_cast<double2*>(w) : nullptr;
-    w += sz_S;
-    double2* d_H = reinterpret_cast<double2*>(w);
-    w += sz_H;
-    int* d_piv = two ? reinterpret_cast<int*>(w) : nullptr;
-    w += sz_piv;
-    int* d_info = two ? reinterpret_cast<int*>(w) : nullptr;
-    w += sz_info;
-    void* d_scr = w;
+    P.sz_S = P.two ? align256((size_t)mce * mat * sizeof(double2)) * 2 : 0;
+    P.sz_H = align256((size_t)mce * mat * sizeof(double2)) * 2;
+    P.sz_piv = P.two ? align256((size_t)mce * N * sizeof(int)) * 2 : 0;
+    P.sz_info = P.two ? align256((size_t)mce * sizeof(int)) * 2 : 0;
+    P.sz_scr = align256((size_t)mce * L.bytes_per_eval);
+    P.bytes = P.sz_carry + P.sz_carryLU + P.sz_carryPiv + P.sz_carryLU32 + P.sz_LU32 + P.sz_z + P.sz_ev + P.sz_pc +
+              P.sz_flags + P.sz_S + P.sz_H + P.sz_piv + P.sz_info + P.sz_scr;
+    return WPCCC_OK;
+}
 
-    // half-buffers of each set
-    const size_t hS = sz_S / 2 / sizeof(double2), hH = sz_H / 2 / sizeof(double2);
-    const size_t hL = sz_LU32 / 2 / sizeof(float2), hP = sz_piv / 2 / sizeof(int), hI = sz_info / 2 / sizeof(int);
-    if (!B->rk_stream) {
-        WPCCC_CUDA(cudaStreamCreateWithFlags(&B->rk_stream, cudaStreamNonBlocking));
-        for (int k = 0; k < 2; ++k) {
-            WPCCC_CUDA(cudaEventCreateWithFlags(&B->ev_asm[k], cudaEventDisableTiming));
-            WPCCC_CUDA(cudaEventCreateWithFlags(&B->ev_rk[k], cudaEventDisableTiming));
-        }
-        WPCCC_CUDA(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
-        WPCCC_CUDA(cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming));
-    }
-    cudaStream_t rs = B->rk_stream;
+static void plan_bind(PropPlan& P, void* ws) {
+    char* w = static_cast<char*>(ws);
+    auto take = [&](size_t n) {
+        char* p = n ? w : nullptr;
+        w += n;
+        return p;
+    };
+    P.d_carry = reinterpret_cast<double2*>(take(P.sz_carry));
+    P.d_carryLU = reinterpret_cast<double2*>(take(P.sz_carryLU));
+    P.d_carryPiv = reinterpret_cast<int*>(take(P.sz_carryPiv));
+    P.d_carryLU32 = reinterpret_cast<float2*>(take(P.sz_carryLU32));
+    P.d_LU32 = reinterpret_cast<float2*>(take(P.sz_LU32));
+    P.d_z = reinterpret_cast<double*>(take(P.sz_z));
+    P.d_ev = reinterpret_cast<EvalDesc*>(take(P.sz_ev));
+    P.d_pc = reinterpret_cast<PathChunk*>(take(P.sz_pc));
+    P.d_flags = reinterpret_cast<int*>(take(P.sz_flags));
+    P.d_S = reinterpret_cast<double2*>(take(P.sz_S));
+    P.d_H = reinterpret_cast<double2*>(take(P.sz_H));
+    P.d_piv = reinterpret_cast<int*>(take(P.sz_piv));
+    P.d_info = reinterpret_cast<int*>(take(P.sz_info));
+    P.d_scr = take(P.sz_scr);
+}
 
-    WPCCC_CUDA(cudaMemcpyAsync(d_z, paths->z, (size_t)zoff[np] * sizeof(double), cudaMemcpyHostToDevice, st));
-    WPCCC_CUDA(cudaMemcpyAsync(d_ev, ev.data(), ev.size() * sizeof(EvalDesc), cudaMemcpyHostToDevice, st));
-    WPCCC_CUDA(cudaMemcpyAsync(d_pc, pcs.data(), pcs.size() * sizeof(PathChunk), cudaMemcpyHostToDevice, st));
-    WPCCC_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int), st));
-    const int rk_smem = (int)rk_smem_bytes(mode, N);
+// Copies the plan's node, position and chunk lists to the device (from its host vectors, which
+// must stay alive until the copies have run).
+static wpccc_status plan_upload(PropPlan& P, cudaStream_t st) {
+    if (P.max_steps == 0) return WPCCC_OK;
+    WPCCC_CUDA(cudaMemcpyAsync(P.d_z, P.z.data(), P.z.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    WPCCC_CUDA(cudaMemcpyAsync(P.d_ev, P.ev.data(), P.ev.size() * sizeof(EvalDesc), cudaMemcpyHostToDevice, st));
+    WPCCC_CUDA(cudaMemcpyAsync(P.d_pc, P.pcs.data(), P.pcs.size() * sizeof(PathChunk), cudaMemcpyHostToDevice, st));
+    return WPCCC_OK;
+}
+
+struct PlanStreams {
+    cudaStream_t st, rs;          // assembly (and the caller's order), RK4 sweeps
+    cudaEvent_t asm_done[2], rk_done[2], fork, join;
+};
+
+// Queues every kernel of the plan: the flags reset, then per chunk the element kernels and the
+// solve on S.st, the RK4 sweep on S.rs, with double-buffered chunks.  Capturable into a graph.
+static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) {
+    if (P.max_steps == 0) return WPCCC_OK;
+    wpccc_basis_s* B = P.B;
+    const int N = P.N;
+    const size_t mat = (size_t)N * N;
+    cudaStream_t st = S.st, rs = S.rs;
+    WPCCC_CUDA(cudaMemsetAsync(P.d_flags, 0, sizeof(int), st));
+    const int rk_smem = (int)rk_smem_bytes(P.mode, N);
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MATRIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+    const size_t hS = P.sz_S / 2 / sizeof(double2), hH = P.sz_H / 2 / sizeof(double2);
+    const size_t hL = P.sz_LU32 / 2 / sizeof(float2), hP = P.sz_piv / 2 / sizeof(int), hI = P.sz_info / 2 / sizeof(int);
     RkArgs ra;
     ra.N = N;
     ra.iters = B->refine_iters;
-    ra.H = d_H;
-    ra.LU = mode != RK_MATRIX ? d_S : nullptr;
-    ra.LU32 = d_LU32;
-    ra.carryLU32 = d_carryLU32;
-    ra.piv = mode != RK_MATRIX ? d_piv : nullptr;
-    ra.info = d_info;
-    ra.carryH = d_carry;
-    ra.carryLU = d_carryLU;
-    ra.carryPiv = d_carryPiv;
-    ra.c = static_cast<double2*>(c);
-    ra.z = d_z;
-    ra.flags = d_flags;
-
-    // the RK4 stream starts after everything queued so far on the caller's stream
-    WPCCC_CUDA(cudaEventRecord(B->ev_fork, st));
-    WPCCC_CUDA(cudaStreamWaitEvent(rs, B->ev_fork, 0));
-    for (int ch = 0; ch < n_chunks; ++ch) {
-        const int nev = ev_begin[ch + 1] - ev_begin[ch];
-        const int npc = pc_begin[ch + 1] - pc_begin[ch];
+    ra.carryH = P.d_carry;
+    ra.carryLU = P.d_carryLU;
+    ra.carryPiv = P.d_carryPiv;
+    ra.carryLU32 = P.d_carryLU32;
+    ra.c = c;
+    ra.z = P.d_z;
+    ra.flags = P.d_flags;
+    // the RK4 stream starts after everything queued so far on the assembly stream
+    WPCCC_CUDA(cudaEventRecord(S.fork, st));
+    WPCCC_CUDA(cudaStreamWaitEvent(rs, S.fork, 0));
+    wpccc_status s;
+    for (int ch = 0; ch < P.n_chunks; ++ch) {
+        const int nev = P.ev_begin[ch + 1] - P.ev_begin[ch];
+        const int npc = P.pc_begin[ch + 1] - P.pc_begin[ch];
         const int k = ch & 1;
-        double2* bS = two ? d_S + k * hS : nullptr;
-        double2* bH = d_H + k * hH;
-        float2* bL = mixed ? d_LU32 + k * hL : nullptr;
-        int* bP = two ? d_piv + k * hP : nullptr;
-        int* bI = two ? d_info + k * hI : nullptr;
+        double2* bS = P.two ? P.d_S + k * hS : nullptr;
+        double2* bH = P.d_H + k * hH;
+        float2* bL = P.mixed ? P.d_LU32 + k * hL : nullptr;
+        int* bP = P.two ? P.d_piv + k * hP : nullptr;
+        int* bI = P.two ? P.d_info + k * hI : nullptr;
         // buffer set k is free once the RK4 sweep of chunk ch - 2 is done
-        if (ch >= 2) WPCCC_CUDA(cudaStreamWaitEvent(st, B->ev_rk[k], 0));
-        s = launch_elements(B, d_ev + ev_begin[ch], nev, bS, bH, d_scr, st, elem_precision);
+        if (ch >= 2) WPCCC_CUDA(cudaStreamWaitEvent(st, S.rk_done[k], 0));
+        s = launch_elements(B, P.d_ev + P.ev_begin[ch], nev, bS, bH, P.d_scr, st, P.elem_precision);
         if (s != WPCCC_OK) return s;
-        if (two) {
+        if (P.two) {
             cudaEvent_t e0 = B->prof.begin(PROF_SOLVE, st);
-            if (mixed) s = launch_factor_f32(N, nev, bS, bL, bP, bI, st);
-            else s = launch_solve(N, nev, bS, stage ? nullptr : bH, bP, bI, st);
+            if (P.mixed) s = launch_factor_f32(N, nev, bS, bL, bP, bI, st);
+            else s = launch_solve(N, nev, bS, P.stage ? nullptr : bH, bP, bI, st);
             if (s != WPCCC_OK) return s;
             B->prof.end(PROF_SOLVE, st, e0);
         }
-        WPCCC_CUDA(cudaEventRecord(B->ev_asm[k], st));
-        WPCCC_CUDA(cudaStreamWaitEvent(rs, B->ev_asm[k], 0));
+        WPCCC_CUDA(cudaEventRecord(S.asm_done[k], st));
+        WPCCC_CUDA(cudaStreamWaitEvent(rs, S.asm_done[k], 0));
         cudaEvent_t e1 = B->prof.begin(PROF_RK4, rs);
-        ra.pcs = d_pc + pc_begin[ch];
+        ra.pcs = P.d_pc + P.pc_begin[ch];
         ra.H = bH;
-        ra.LU = mode != RK_MATRIX ? bS : nullptr;
+        ra.LU = P.mode != RK_MATRIX ? bS : nullptr;
         ra.LU32 = bL;
-        ra.piv = mode != RK_MATRIX ? bP : nullptr;
+        ra.piv = P.mode != RK_MATRIX ? bP : nullptr;
         ra.info = bI;
-        if (mode == RK_MIXED) k_rk4<RK_MIXED><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
-        else if (mode == RK_STAGE) k_rk4<RK_STAGE><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
+        if (P.mode == RK_MIXED) k_rk4<RK_MIXED><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
+        else if (P.mode == RK_STAGE) k_rk4<RK_STAGE><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else k_rk4<RK_MATRIX><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         WPCCC_CHECK_LAUNCH("k_rk4");
         B->prof.end(PROF_RK4, rs, e1);
-        WPCCC_CUDA(cudaEventRecord(B->ev_rk[k], rs));
+        WPCCC_CUDA(cudaEventRecord(S.rk_done[k], rs));
     }
-    // the caller's stream resumes after the last sweep
-    WPCCC_CUDA(cudaEventRecord(B->ev_join, rs));
-    WPCCC_CUDA(cudaStreamWaitEvent(st, B->ev_join, 0));
+    // the assembly stream resumes after the last sweep
+    WPCCC_CUDA(cudaEventRecord(S.join, rs));
+    WPCCC_CUDA(cudaStreamWaitEvent(st, S.join, 0));
+    return WPCCC_OK;
+}
+
+static wpccc_status flags_status(int flags) {
+    if (flags & FLAG_SINGULAR) return fail(WPCCC_ESINGULAR, "an overlap matrix had a zero pivot");
+    if (flags & FLAG_NONFINITE) return fail(WPCCC_ENONFINITE, "amplitudes became non-finite");
+    return WPCCC_OK;
+}
+
+static wpccc_status basis_streams(wpccc_basis_s* B) {
+    if (B->rk_stream) return WPCCC_OK;
+    WPCCC_CUDA(cudaStreamCreateWithFlags(&B->rk_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        WPCCC_CUDA(cudaEventCreateWithFlags(&B->ev_asm[k], cudaEventDisableTiming));
+        WPCCC_CUDA(cudaEventCreateWithFlags(&B->ev_rk[k], cudaEventDisableTiming));
+    }
+    WPCCC_CUDA(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
+    WPCCC_CUDA(cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming));
+    return WPCCC_OK;
+}
+
+}  // namespace wpccc
+
+extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths, int precision_mode,
+                                        int batch_mode, void* c, void* stream) {
+    if (!B || !paths || !c) return fail(WPCCC_EINVAL, "wpccc_propagate: null argument");
+    if (batch_mode != 0) return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: only batch_mode 0");
+    WPCCC_CUDA(cudaSetDevice(B->device));
+    PropPlan P;
+    wpccc_status s = plan_build(B, paths, precision_mode, 0, B->ws_limit, P);
+    if (s != WPCCC_OK) return s;
+    if (P.max_steps == 0) return WPCCC_OK;
+    if ((s = ensure_workspace(B, P.bytes)) != WPCCC_OK) return s;
+    plan_bind(P, B->ws_ptr);
+    if ((s = basis_streams(B)) != WPCCC_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((s = plan_upload(P, st)) != WPCCC_OK) return s;
+    PlanStreams S{st, B->rk_stream, {B->ev_asm[0], B->ev_asm[1]}, {B->ev_rk[0], B->ev_rk[1]}, B->ev_fork,
+                  B->ev_join};
+    if ((s = plan_enqueue(P, static_cast<double2*>(c), S)) != WPCCC_OK) return s;
     int flags = 0;
-    WPCCC_CUDA(cudaMemcpyAsync(&flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WPCCC_CUDA(cudaMemcpyAsync(&flags, P.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     WPCCC_CUDA(cudaStreamSynchronize(st));
-    if (flags & FLAG_SINGULAR) return fail(WPCCC_ESINGULAR, "wpccc_propagate: an overlap matrix had a zero pivot");
-    if (flags & FLAG_NONFINITE) return fail(WPCCC_ENONFINITE, "wpccc_propagate: amplitudes became non-finite");
+    s = flags_status(flags);
+    if (s != WPCCC_OK) set_error(std::string("wpccc_propagate: ") + wpccc_last_error());
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// batches: several (basis, paths) sets propagated together by one CUDA graph launch
+// ---------------------------------------------------------------------------
+struct wpccc_batch_s {
+    int device = 0;
+    int n_sets = 0;
+    std::vector<wpccc::PropPlan> plans;
+    std::vector<double2*> c;
+    void* ws = nullptr;
+    std::vector<cudaStream_t> streams;      // two per set (assembly, RK4), plus the capture stream
+    std::vector<cudaEvent_t> events;        // six per set, plus the capture fork
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> chunk_steps;
+    std::vector<double> tuned_ms_per_step;
+};
+
+namespace wpccc {
+
+static void batch_free(wpccc_batch_s* X) {
+    if (!X) return;
+    cudaSetDevice(X->device);
+    for (cudaStream_t s : X->streams)
+        if (s) cudaStreamSynchronize(s);
+    if (X->exec) cudaGraphExecDestroy(X->exec);
+    if (X->graph) cudaGraphDestroy(X->graph);
+    for (cudaEvent_t e : X->events)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : X->streams)
+        if (s) cudaStreamDestroy(s);
+    if (X->ws) cudaFree(X->ws);
+    delete X;
+}
+
+// Times one candidate schedule of a set on its first steps: a warm run, then a timed run.
+static wpccc_status tune_trial(wpccc_basis_s* B, const wpccc_paths* paths, int precision, int C, double2* c_src,
+                               double* ms_per_step) {
+    // the set's paths cut to 2C steps (at least two chunks, so the overlap is part of the timing)
+    const int np = paths->n_paths;
+    std::vector<int> nz(np);
+    std::vector<double> z;
+    int steps = 0;
+    int off = 0;
+    for (int p = 0; p < np; ++p) {
+        const int n = std::min(paths->n_z[p], 2 * C + 1);
+        nz[p] = n;
+        z.insert(z.end(), paths->z + off, paths->z + off + n);
+        off += paths->n_z[p];
+        steps = std::max(steps, n - 1);
+    }
+    if (steps == 0) {
+        *ms_per_step = 0.0;
+        return WPCCC_OK;
+    }
+    wpccc_paths tp{np, paths->b, paths->v, nz.data(), z.data()};
+    PropPlan P;
+    wpccc_status s = plan_build(B, &tp, precision, C, B->ws_limit, P);
+    if (s != WPCCC_OK) return s;
+    void* ws = nullptr;
+    double2* c = nullptr;
+    cudaStream_t st = nullptr, rs = nullptr;
+    cudaEvent_t ev[8] = {};
+    float ms = 0.f;
+    auto cleanup = [&]() {
+        if (st) cudaStreamSynchronize(st);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (st) cudaStreamDestroy(st);
+        if (rs) cudaStreamDestroy(rs);
+        if (ws) cudaFree(ws);
+        if (c) cudaFree(c);
+    };
+    cudaError_t e = cudaMalloc(&ws, P.bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c, (size_t)np * P.N * sizeof(double2));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    for (int k = 6; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c, c_src, (size_t)np * P.N * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "autotuner trial set-up");
+    }
+    plan_bind(P, ws);
+    PlanStreams S{st, rs, {ev[0], ev[1]}, {ev[2], ev[3]}, ev[4], ev[5]};
+    for (int rep = 0; rep < 2 && s == WPCCC_OK; ++rep) {
+        if ((s = plan_upload(P, st)) != WPCCC_OK) break;
+        if (rep == 1) cudaEventRecord(ev[6], st);
+        s = plan_enqueue(P, c, S);
+        if (rep == 1) cudaEventRecord(ev[7], st);
+        if (cudaStreamSynchronize(st) != cudaSuccess && s == WPCCC_OK) s = cuda_fail(cudaGetLastError(), "trial");
+    }
+    if (s == WPCCC_OK) {
+        cudaEventElapsedTime(&ms, ev[6], ev[7]);
+        *ms_per_step = ms / steps;
+    }
+    cleanup();
+    return s;
+}
+
+}  // namespace wpccc
+
+extern "C" wpccc_status wpccc_batch_create(int n_sets, const wpccc_basis* bases, const wpccc_paths* paths,
+                                           int precision_mode, void* const* c, int autotune, wpccc_batch* out) {
+    if (!bases || !paths || !c || !out || n_sets < 1) return fail(WPCCC_EINVAL, "wpccc_batch_create: bad arguments");
+    *out = nullptr;
+    const int device = bases[0] ? bases[0]->device : -1;
+    for (int k = 0; k < n_sets; ++k) {
+        if (!bases[k] || !c[k]) return fail(WPCCC_EINVAL, "wpccc_batch_create: null basis or amplitudes");
+        if (bases[k]->device != device) return fail(WPCCC_EINVAL, "wpccc_batch_create: bases on different devices");
+    }
+    WPCCC_CUDA(cudaSetDevice(device));
+    wpccc_batch_s* X = new wpccc_batch_s();
+    X->device = device;
+    X->n_sets = n_sets;
+    X->plans.resize(n_sets);
+    X->c.resize(n_sets);
+    X->chunk_steps.assign(n_sets, 0);
+    X->tuned_ms_per_step.assign(n_sets, 0.0);
+    auto bail = [&](wpccc_status st) {
+        std::string keep = wpccc_last_error();
+        batch_free(X);
+        set_error(keep);
+        return st;
+    };
+    wpccc_status s;
+    for (int k = 0; k < n_sets; ++k) {
+        wpccc_basis_s* B = bases[k];
+        X->c[k] = static_cast<double2*>(c[k]);
+        PropPlan P;
+        if ((s = plan_build(B, &paths[k], precision_mode, 0, B->ws_limit, P)) != WPCCC_OK) return bail(s);
+        int best = P.C;
+        if (autotune && P.max_steps > 1) {
+            // schedules tried: the default chunk and half and twice as many RK4 steps per chunk
+            std::vector<int> cand{P.C};
+            if (P.C / 2 >= 1) cand.push_back(P.C / 2);
+            if (2 * P.C <= P.max_steps) cand.push_back(2 * P.C);
+            double best_ms = -1.0;
+            for (int C : cand) {
+                double ms = 0.0;
+                const bool was_on = B->prof.on;
+                B->prof.on = false;
+                s = tune_trial(B, &paths[k], precision_mode, C, X->c[k], &ms);
+                B->prof.on = was_on;
+                if (s != WPCCC_OK) return bail(s);
+                if (best_ms < 0.0 || ms < best_ms) {
+                    best_ms = ms;
+                    best = C;
+                }
+            }
+            X->tuned_ms_per_step[k] = best_ms;
+        }
+        if ((s = plan_build(B, &paths[k], precision_mode, best, B->ws_limit, X->plans[k])) != WPCCC_OK) return bail(s);
+        X->chunk_steps[k] = X->plans[k].C;
+    }
+    // one workspace for every set
+    size_t total = 0;
+    for (auto& P : X->plans) total += align256(P.bytes);
+    {
+        cudaError_t e = cudaMalloc(&X->ws, std::max<size_t>(total, 256));
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(batch workspace)"));
+    }
+    size_t off = 0;
+    for (auto& P : X->plans) {
+        plan_bind(P, static_cast<char*>(X->ws) + off);
+        off += align256(P.bytes);
+    }
+    // streams and events, then the plans' lists on the device (before the capture)
+    X->streams.assign(2 * n_sets + 1, nullptr);
+    X->events.assign(6 * n_sets + 1, nullptr);
+    for (auto& st : X->streams) {
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate(batch)"));
+    }
+    for (auto& ev : X->events) {
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate(batch)"));
+    }
+    cudaStream_t cap = X->streams[2 * n_sets];
+    for (int k = 0; k < n_sets; ++k)
+        if ((s = plan_upload(X->plans[k], cap)) != WPCCC_OK) return bail(s);
+    {
+        cudaError_t e = cudaStreamSynchronize(cap);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "batch upload"));
+    }
+    // capture every set's launch sequence into one graph: fork from the capture stream, join back
+    std::vector<bool> prof_on(n_sets);
+    for (int k = 0; k < n_sets; ++k) {
+        prof_on[k] = bases[k]->prof.on;
+        bases[k]->prof.on = false;
+    }
+    auto restore = [&]() {
+        for (int k = 0; k < n_sets; ++k) bases[k]->prof.on = prof_on[k];
+    };
+    {
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            restore();
+            return bail(cuda_fail(e, "cudaStreamBeginCapture"));
+        }
+    }
+    cudaEvent_t fork = X->events[6 * n_sets];
+    wpccc_status cs = WPCCC_OK;
+    if (cudaEventRecord(fork, cap) != cudaSuccess) cs = cuda_fail(cudaGetLastError(), "capture fork");
+    for (int k = 0; k < n_sets && cs == WPCCC_OK; ++k) {
+        cudaStream_t st = X->streams[2 * k], rs = X->streams[2 * k + 1];
+        cudaEvent_t* ev = &X->events[6 * k];
+        if (cudaStreamWaitEvent(st, fork, 0) != cudaSuccess) {
+            cs = cuda_fail(cudaGetLastError(), "capture fork wait");
+            break;
+        }
+        PlanStreams S{st, rs, {ev[0], ev[1]}, {ev[2], ev[3]}, ev[4], ev[5]};
+        cs = plan_enqueue(X->plans[k], X->c[k], S);
+        if (cs != WPCCC_OK) break;
+        // join: the capture stream waits for this set's assembly stream (which waits for its sweeps)
+        if (cudaEventRecord(ev[5], st) != cudaSuccess || cudaStreamWaitEvent(cap, ev[5], 0) != cudaSuccess)
+            cs = cuda_fail(cudaGetLastError(), "capture join");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    restore();
+    if (cs != WPCCC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return bail(cs);
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamEndCapture"));
+    X->graph = graph;
+    e = cudaGraphInstantiate(&X->exec, graph, 0);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGraphInstantiate"));
+    *out = X;
+    return WPCCC_OK;
+}
+
+extern "C" wpccc_status wpccc_batch_launch(wpccc_batch X, void* stream) {
+    if (!X) return fail(WPCCC_EINVAL, "wpccc_batch_launch: null batch");
+    WPCCC_CUDA(cudaSetDevice(X->device));
+    WPCCC_CUDA(cudaGraphLaunch(X->exec, static_cast<cudaStream_t>(stream)));
+    return WPCCC_OK;
+}
+
+extern "C" wpccc_status wpccc_batch_status(wpccc_batch X, void* stream) {
+    if (!X) return fail(WPCCC_EINVAL, "wpccc_batch_status: null batch");
+    WPCCC_CUDA(cudaSetDevice(X->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<int> flags(X->n_sets, 0);
+    for (int k = 0; k < X->n_sets; ++k)
+        if (X->plans[k].d_flags)
+            WPCCC_CUDA(cudaMemcpyAsync(&flags[k], X->plans[k].d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WPCCC_CUDA(cudaStreamSynchronize(st));
+    int all = 0;
+    for (int f : flags) all |= f;
+    wpccc_status s = flags_status(all);
+    if (s != WPCCC_OK) set_error(std::string("wpccc_batch_status: ") + wpccc_last_error());
+    return s;
+}
+
+extern "C" wpccc_status wpccc_batch_info(wpccc_batch X, int* chunk_steps, double* tuned_ms_per_step) {
+    if (!X) return fail(WPCCC_EINVAL, "wpccc_batch_info: null batch");
+    for (int k = 0; k < X->n_sets; ++k) {
+        if (chunk_steps) chunk_steps[k] = X->chunk_steps[k];
+        if (tuned_ms_per_step) tuned_ms_per_step[k] = X->tuned_ms_per_step[k];
+    }
+    return WPCCC_OK;
+}
+
+extern "C" wpccc_status wpccc_batch_destroy(wpccc_batch X) {
+    batch_free(X);
     return WPCCC_OK;
 }

@@ -345,6 +345,26 @@ CONFIGS = {
 }
 
 
+BATCH_SPEEDS = (0.5, 0.8, 1.2, 2.0, 3.0, 4.0)
+
+
+def batch_inputs(n_b: int = 64, speeds=BATCH_SPEEDS, **over):
+    """Two-centre p + H at several speeds: pseudostates per l scaled with v (round(8 + 8 (v - 0.5)/3.5),
+    i.e. 8..16 for v = 0.5..4), hydrogenic n <= 4, l <= 3, k <= 3; n_b impact parameters uniform in
+    [0.2, 12]; z in [-50, 50] with h = 0.1 v / 1.5 (step count proportional to 1/v).
+    Returns a list of (v, basis, paths)."""
+    out = []
+    for v in speeds:
+        nb = int(round(8 + 8 * (v - 0.5) / 3.5))
+        basis = make_basis(1.0, 1.0, over.get("nmax", 4), over.get("lmax", 3), over.get("nbins", nb),
+                           over.get("kmax", 3.0), True, Nr=over.get("Nr", 2000), Geta=over.get("Geta", 48),
+                           Gtau=over.get("Gtau", 48))
+        h = 0.1 * v / 1.5
+        paths = make_paths(np.linspace(0.2, 12.0, n_b), v, uniform_zgrid(-50.0, 50.0, h))
+        out.append((v, basis, paths))
+    return out
+
+
 def config_inputs(name: str, **over):
     """(basis, paths) of a named workload; keyword overrides shrink it for tests."""
     c = dict(CONFIGS[name])
