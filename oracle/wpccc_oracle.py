@@ -15,7 +15,17 @@ computes everything else itself, following the paper's equations in order:
 * Eq. 1  assembly of S = [[I, K], [K^+, I]] and H = [[D_T, Q], [Q~, D_P]];
 * Eq. 4  M = -(i/v) S^{-1} H through a linear solve (LAPACK zgesv, as the
          paper does), Eq. 5 (one-centre: M = -(i/v) D_T, no solve);
-* Algorithm 1  RK4 along the z-grid, then probabilities |c_i|^2.
+* Algorithm 1  RK4 along the z-grid, then probabilities |c_i|^2;
+* differentiation form: derivatives of S, H and of the probabilities with
+  respect to the projectile charge and the parameters of a Li-like target
+  model potential V_T(r) = -[Z_T + c e^{-a r}(1 + b r)]/r, in forward mode
+  (every line of Algorithm 1 differentiated alongside it).
+
+Model-potential target (the paper treats bare Coulomb centres only; these
+are the readings used for it): the transfer integral Q carries V_T(r_T) in
+place of -Z_T/r_T; between projectile states the target's Coulomb part
+keeps the Eq. 6 multipole form and its short-range part is integrated on
+the Eq. 9 (eta, tau) rule, where only equal-q pairs couple.
 
 Readings of garbled or silent passages (each pinned by a test in
 tests/test_oracle_pins.py):
@@ -197,12 +207,15 @@ def _direct_angular(centre) -> np.ndarray:
     return ang
 
 
-def direct_block(grid, centre, Z_other: float, R: float, cos_theta: float, other_at_minus_R: bool) -> np.ndarray:
+def direct_block(grid, centre, Z_other: float, R: float, cos_theta: float, other_at_minus_R: bool,
+                 f_left=None, f_right=None) -> np.ndarray:
     """D[a', a] = -Z sum_lam sqrt((2l_a+1)/(2l_a'+1)) sqrt((lam-mu)!/(lam+mu)!)
     C^{l_a' 0}_{lam 0 l_a 0} C^{l_a' m_a'}_{lam mu l_a m_a} P_lam^mu(cos Theta) F_{a'a lam}(R), mu = m_a' - m_a.
 
     The other nucleus sits at +R (azimuth 0) from this centre, or at -R for the projectile
-    centre (other_at_minus_R), which multiplies the lam-th multipole by (-1)^lam."""
+    centre (other_at_minus_R), which multiplies the lam-th multipole by (-1)^lam.
+    f_left / f_right replace the bra's / ket's radial tables in Eq. 7 (the element is bilinear in them;
+    the differentiation form passes derivative tables here)."""
     lmax = int(centre.rad_l.max())
     nl = 2 * lmax + 1
     ang = _direct_angular(centre)
@@ -215,7 +228,9 @@ def direct_block(grid, centre, Z_other: float, R: float, cos_theta: float, other
             & ((la[:, None] + la[None, :] + lam) % 2 == 0)
         pa, pb = np.nonzero(ok)
         if pa.size:
-            Ftab[pa, pb, lam] = radial_F(grid, centre.f[pa], centre.f[pb], lam, R)
+            fl = centre.f if f_left is None else f_left
+            fr = centre.f if f_right is None else f_right
+            Ftab[pa, pb, lam] = radial_F(grid, fl[pa], fr[pb], lam, R)
     # P_lam^mu(cos Theta) for -lam <= mu <= lam
     Pv = np.zeros((nl, 2 * nl + 1))
     for lam in range(nl):
@@ -233,14 +248,22 @@ def direct_block(grid, centre, Z_other: float, R: float, cos_theta: float, other
 # ---------------------------------------------------------------------------
 
 
-def molecular_integrals(basis, b: float, v: float, z: float, reverse: bool = False):
-    """Molecular-frame integrals for every (target state in frame q', projectile state in frame q):
-    X[i, j] = (R^3/8) sum_{eta,tau} w (eta^2 - tau^2) e^{i v z eta tau / 2} (-i)^{q-q'} J_{q-q'}(x)
-              f_i(r_T) Theta_{l_i q'}(c_T) f_j(r_P) Theta_{l_j q}(c_P) * u(eta, tau)
-    with u = 1 (overlap K) and -Z_T/r_T (transfer Q); with reverse=True also -Z_P/r_P (the
-    reverse-transfer integral, before conjugation, used only to show why Q^+ is taken instead).
-    Rows/columns use the centres' own state lists with m read as the molecular-frame q."""
-    T, P, qd = basis.T, basis.P, basis.quad
+def target_sr_potential(basis, r):
+    """Short-range part of a Li-like target potential, -c e^{-a r}(1 + b r)/r (zero for a bare nucleus)."""
+    return -basis.mp_c * np.exp(-basis.mp_a * r) * (1.0 + basis.mp_b * r) / r
+
+
+def target_potential(basis, r):
+    """V_T(r) = -Z_T/r plus the short-range part of a model potential."""
+    if basis.mp_c == 0.0:
+        return -basis.Z_T / r
+    return -basis.Z_T / r + target_sr_potential(basis, r)
+
+
+def _nodes(basis, b: float, v: float, z: float):
+    """(eta, tau) rule of Eq. 9 at one position: node radii and cosines about both centres, the
+    Bessel argument, and the weights (R^3/8) w (eta^2 - tau^2) with and without the ETF phase."""
+    qd = basis.quad
     R = math.sqrt(b * b + z * z)
     gR = qd.gamma * R
     eta = 1.0 + qd.s / gR                                   # [Ge]
@@ -253,19 +276,45 @@ def molecular_integrals(basis, b: float, v: float, z: float, reverse: bool = Fal
     cT = (E * Tt + 1.0) / (E + Tt)
     cP = (E * Tt - 1.0) / (E - Tt)
     x = 0.5 * v * b * np.sqrt((E * E - 1.0) * (1.0 - Tt * Tt))
-    base = (R ** 3 / 8.0) * W0 * (E * E - Tt * Tt) * np.exp(0.5j * v * z * E * Tt)
+    vol = (R ** 3 / 8.0) * W0 * (E * E - Tt * Tt)
+    base = vol * np.exp(0.5j * v * z * E * Tt)
+    return dict(rT=rT, rP=rP, cT=cT, cP=cP, x=x, base=base, vol=vol)
+
+
+def _state_tables(centre, ftab, rnode, cnode, r):
+    """A[i, g] = f_{a_i}(r_g) Theta_{l_i q_i}(c_g) for every state, with m read as the frame's q."""
+    fn = interp5(r, ftab, rnode)
+    return np.array([fn[centre.st_rad[i]] * norm_legendre(int(centre.st_l[i]), int(centre.st_m[i]), cnode)
+                     for i in range(centre.N)])
+
+
+def molecular_integrals(basis, b: float, v: float, z: float, reverse: bool = False, fT=None, fP=None,
+                        factors=None):
+    """Molecular-frame integrals for every (target state in frame q', projectile state in frame q):
+    X[i, j] = (R^3/8) sum_{eta,tau} w (eta^2 - tau^2) e^{i v z eta tau / 2} (-i)^{q-q'} J_{q-q'}(x)
+              f_i(r_T) Theta_{l_i q'}(c_T) f_j(r_P) Theta_{l_j q}(c_P) * u(eta, tau)
+    with u = 1 (overlap K) and V_T(r_T) (transfer Q: -Z_T/r_T for a bare target); with reverse=True
+    also -Z_P/r_P (the reverse-transfer integral, before conjugation, used only to show why Q^+ is
+    taken instead).  Rows/columns use the centres' own state lists with m read as the molecular-frame q.
+    fT / fP replace the radial tables and `factors` (callables of (r_T, r_P)) the list of u; each
+    integral is linear in each of them (the differentiation form uses that)."""
+    T, P = basis.T, basis.P
+    nd = _nodes(basis, b, v, z)
+    rT, rP, x, base = nd["rT"], nd["rP"], nd["x"], nd["base"]
     r = basis.grid.r
-    fT = interp5(r, T.f, rT)                                # [nradT, G]
-    fP = interp5(r, P.f, rP)
-    AT = np.array([fT[T.st_rad[i]] * norm_legendre(int(T.st_l[i]), int(T.st_m[i]), cT) for i in range(T.N)])
-    AP = np.array([fP[P.st_rad[j]] * norm_legendre(int(P.st_l[j]), int(P.st_m[j]), cP) for j in range(P.N)])
+    AT = _state_tables(T, T.f if fT is None else fT, rT, nd["cT"], r)
+    AP = _state_tables(P, P.f if fP is None else fP, rP, nd["cP"], r)
     dmax = int(T.st_l.max() + P.st_l.max())
     Wd = {}
     for d in range(-dmax, dmax + 1):
         Wd[d] = base * ((-1j) ** d) * special.jv(d, x)
-    factors = [np.ones_like(rT), -basis.Z_T / rT] + ([-basis.Z_P / rP] if reverse else [])
+    if factors is None:
+        factors = [lambda a, c: np.ones_like(a), lambda a, c: target_potential(basis, a)]
+        if reverse:
+            factors.append(lambda a, c: -basis.Z_P / c)
     out = []
-    for u in factors:
+    for fac in factors:
+        u = fac(rT, rP)
         X = np.zeros((T.N, P.N), dtype=np.complex128)
         for q in sorted(set(int(m) for m in P.st_m)):
             cols = np.nonzero(P.st_m == q)[0]
@@ -277,18 +326,37 @@ def molecular_integrals(basis, b: float, v: float, z: float, reverse: bool = Fal
     return out
 
 
+def sr_direct_mol(basis, b: float, z: float, f_left=None, f_right=None, Vs=None) -> np.ndarray:
+    """Short-range part of the target potential between projectile states, in the molecular frame:
+    D[i, j] = delta_{q_i q_j} (R^3/8) sum_{eta,tau} w (eta^2 - tau^2) V_s(r_T) f_i(r_P) Theta_{l_i q}(c_P)
+              f_j(r_P) Theta_{l_j q}(c_P)
+    on the (eta, tau) rule of Eq. 9 (the potential is symmetric about the molecular axis, so the phi
+    integral only couples equal q; both states sit on the projectile, so no ETF phase remains).
+    Vs (a callable of r_T) defaults to the basis's own short-range potential."""
+    P = basis.P
+    nd = _nodes(basis, b, 1.0, z)
+    r = basis.grid.r
+    AL = _state_tables(P, P.f if f_left is None else f_left, nd["rP"], nd["cP"], r)
+    AR = AL if (f_left is None and f_right is None) else \
+        _state_tables(P, P.f if f_right is None else f_right, nd["rP"], nd["cP"], r)
+    u = nd["vol"] * (target_sr_potential(basis, nd["rT"]) if Vs is None else Vs(nd["rT"]))
+    D = (AL * u[None, :]) @ AR.T
+    return D * (P.st_m[:, None] == P.st_m[None, :])
+
+
 def rotate(centre_T, centre_P, Xmol: np.ndarray, theta: float) -> np.ndarray:
     """Eq. 8: K[beta, alpha] = sum_{q', q} d^{l_b}_{m_b q'}(theta) d^{l_a}_{m_a q}(theta) Xmol[(b, q'), (a, q)]."""
-    T, P = centre_T, centre_P
+    return rotation_matrix(centre_T, theta) @ Xmol @ rotation_matrix(centre_P, theta).T
 
-    def dmat(c):
-        Dm = np.zeros((c.N, c.N))
-        for i in range(c.N):
-            for k in range(c.N):
-                if c.st_rad[i] == c.st_rad[k]:
-                    Dm[i, k] = wigner_d(int(c.st_l[i]), int(c.st_m[i]), int(c.st_m[k]), theta)
-        return Dm
-    return dmat(T) @ Xmol @ dmat(P).T
+
+def rotation_matrix(c, theta: float) -> np.ndarray:
+    """D[i, k] = d^{l}_{m_i m_k}(theta) between the states of one radial function (zero otherwise)."""
+    Dm = np.zeros((c.N, c.N))
+    for i in range(c.N):
+        for k in range(c.N):
+            if c.st_rad[i] == c.st_rad[k]:
+                Dm[i, k] = wigner_d(int(c.st_l[i]), int(c.st_m[i]), int(c.st_m[k]), theta)
+    return Dm
 
 
 # ---------------------------------------------------------------------------
@@ -312,6 +380,9 @@ def assemble(basis, b: float, v: float, z: float):
         return S, H
     DP = direct_block(basis.grid, P, basis.Z_T, R, cth, other_at_minus_R=True)
     theta = math.acos(cth)
+    if basis.mp_c != 0.0:
+        DRP = rotation_matrix(P, theta)
+        DP = DP + DRP @ sr_direct_mol(basis, b, z) @ DRP.T
     Smol, Qmol = molecular_integrals(basis, b, v, z)
     ph = phases(T.st_eps, P.st_eps, z, v)
     K = rotate(T, P, Smol, theta) * ph
@@ -378,3 +449,118 @@ def propagate(basis, b: float, v: float, zgrid: np.ndarray, c0=None) -> np.ndarr
 def probabilities(c: np.ndarray) -> np.ndarray:
     """P_i = |c_i|^2 at the end of the path."""
     return (c.conj() * c).real
+
+
+# ---------------------------------------------------------------------------
+# differentiation form: derivatives of S, H and the probabilities with respect to the parameters
+# theta (projectile charge, model-potential parameters), forward mode
+# ---------------------------------------------------------------------------
+
+
+def _sr_potential_tangent(basis, p: int):
+    """d V_s / d theta_p as a callable of r, through d(c, a, b)/d theta_p."""
+    _, dc, da, db = basis.dexplicit[p]
+    c, a, bb = basis.mp_c, basis.mp_a, basis.mp_b
+
+    def dVs(r):
+        e = np.exp(-a * r)
+        return dc * (-e * (1.0 + bb * r) / r) + da * (c * e * (1.0 + bb * r)) + db * (-c * e)
+    return dVs
+
+
+def assemble_with_tangents(basis, b: float, v: float, z: float):
+    """S, H at one position and their derivatives dS[p], dH[p] with respect to every parameter.
+
+    Each block is multilinear in the radial tables of its bra and ket, the nuclear charge and the
+    target potential, so its derivative is the sum of the same integrals with one ingredient replaced
+    by its derivative (basis.tangent_T/P, basis.dexplicit).  The energy phases e^{i(eps_i - eps_j)z/v}
+    contribute (i z/v)(d eps_i - d eps_j) times the element."""
+    T, P, grid = basis.T, basis.P, basis.grid
+    S, H = assemble(basis, b, v, z)
+    NT, N = T.N, basis.N
+    R = math.sqrt(b * b + z * z)
+    cth = z / R
+    theta = math.acos(cth)
+    DRT, DRP = rotation_matrix(T, theta), rotation_matrix(P, theta)
+    eps = np.concatenate([T.st_eps, P.st_eps])
+    npar = basis.dexplicit.shape[0]
+    dS, dH = [], []
+    for p in range(npar):
+        dZP = basis.dexplicit[p][0]
+        dfT, dfP = basis.tangent_T.df[p], basis.tangent_P.df[p]
+        dVs = _sr_potential_tangent(basis, p)
+        # phase-free element derivatives
+        dDT = (direct_block(grid, T, dZP, R, cth, False)
+               + direct_block(grid, T, basis.Z_P, R, cth, False, f_left=dfT)
+               + direct_block(grid, T, basis.Z_P, R, cth, False, f_right=dfT))
+        dDP = (direct_block(grid, P, basis.Z_T, R, cth, True, f_left=dfP)
+               + direct_block(grid, P, basis.Z_T, R, cth, True, f_right=dfP))
+        dsr = (sr_direct_mol(basis, b, z, f_left=dfP) + sr_direct_mol(basis, b, z, f_right=dfP)
+               + sr_direct_mol(basis, b, z, Vs=dVs))
+        dDP = dDP + DRP @ dsr @ DRP.T
+        one = lambda a, c: np.ones_like(a)
+        VT = lambda a, c: target_potential(basis, a)
+        dK1, dQ1 = molecular_integrals(basis, b, v, z, fT=dfT, factors=[one, VT])
+        dK2, dQ2 = molecular_integrals(basis, b, v, z, fP=dfP, factors=[one, VT])
+        dQ3, = molecular_integrals(basis, b, v, z, factors=[lambda a, c: dVs(a)])
+        dK = DRT @ (dK1 + dK2) @ DRP.T
+        dQ = DRT @ (dQ1 + dQ2 + dQ3) @ DRP.T
+        ph = phases(eps, eps, z, v)
+        deps = np.concatenate([basis.tangent_T.deps[p][T.st_rad], basis.tangent_P.deps[p][P.st_rad]])
+        dph = (1j * z / v) * np.subtract.outer(deps, deps)
+        # d(S), d(H): element derivative times the phase plus element times the phase derivative
+        Sd = np.zeros((N, N), dtype=np.complex128)
+        Sd[:NT, NT:] = dK * ph[:NT, NT:] + S[:NT, NT:] * dph[:NT, NT:]
+        Sd[NT:, :NT] = Sd[:NT, NT:].conj().T
+        Hd = np.zeros((N, N), dtype=np.complex128)
+        Hd[:NT, :NT] = dDT * ph[:NT, :NT] + H[:NT, :NT] * dph[:NT, :NT]
+        Hd[:NT, NT:] = dQ * ph[:NT, NT:] + H[:NT, NT:] * dph[:NT, NT:]
+        Hd[NT:, :NT] = Hd[:NT, NT:].conj().T
+        Hd[NT:, NT:] = dDP * ph[NT:, NT:] + H[NT:, NT:] * dph[NT:, NT:]
+        dS.append(Sd)
+        dH.append(Hd)
+    return S, H, dS, dH
+
+
+def coupling_M_with_tangents(basis, b: float, v: float, z: float):
+    """M = -(i/v) S^{-1} H and dM[p] = -(i/v) S^{-1} (dH[p] - dS[p] S^{-1} H)."""
+    S, H, dS, dH = assemble_with_tangents(basis, b, v, z)
+    X = solve(S, H)
+    return (-1j / v) * X, [(-1j / v) * solve(S, dH[p] - dS[p] @ X) for p in range(len(dS))]
+
+
+def gradient(basis, b: float, v: float, zgrid: np.ndarray, g: np.ndarray, c0=None):
+    """Observables P_o = sum_i g[o, i] |c_i|^2 at the end of one path and dP_o/d theta_p.
+
+    Forward mode: every line of Algorithm 1 is differentiated alongside it (dK1 = dM_z X + M_z dX, ...),
+    so the result is the exact derivative of the discrete RK4 propagation.  Returns (P [n_obs],
+    dP [n_obs, n_par], c at the end)."""
+    if c0 is None:
+        c0 = initial_state(basis)
+    npar = basis.dexplicit.shape[0]
+    X = np.array(c0, dtype=np.complex128)
+    dX = np.zeros((npar, X.size), dtype=np.complex128)
+    Mnew, dMnew = coupling_M_with_tangents(basis, b, v, zgrid[0])
+    for i in range(zgrid.size - 1):
+        z, znew = zgrid[i], zgrid[i + 1]
+        zmid = (z + znew) / 2.0
+        h = znew - z
+        h2, h6 = h / 2.0, h / 6.0
+        Mz, dMz = Mnew, dMnew
+        Mmid, dMmid = coupling_M_with_tangents(basis, b, v, zmid)
+        Mnew, dMnew = coupling_M_with_tangents(basis, b, v, znew)
+        K1 = Mz @ X
+        K2 = Mmid @ X + h2 * (Mmid @ K1)
+        K3 = Mmid @ X + h2 * (Mmid @ K2)
+        K4 = Mnew @ X + h * (Mnew @ K3)
+        for p in range(npar):
+            dK1 = dMz[p] @ X + Mz @ dX[p]
+            dK2 = dMmid[p] @ X + Mmid @ dX[p] + h2 * (dMmid[p] @ K1 + Mmid @ dK1)
+            dK3 = dMmid[p] @ X + Mmid @ dX[p] + h2 * (dMmid[p] @ K2 + Mmid @ dK2)
+            dK4 = dMnew[p] @ X + Mnew @ dX[p] + h * (dMnew[p] @ K3 + Mnew @ dK3)
+            dX[p] = dX[p] + h6 * (dK1 + 2.0 * dK2 + 2.0 * dK3 + dK4)
+        X = X + h6 * (K1 + 2.0 * K2 + 2.0 * K3 + K4)
+    g = np.atleast_2d(np.asarray(g, dtype=np.float64))
+    Pobs = g @ probabilities(X)
+    dP = 2.0 * np.real(g @ (X.conj()[:, None] * dX.T))
+    return Pobs, dP, X

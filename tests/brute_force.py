@@ -56,10 +56,10 @@ def prolate_grid(b, z, n_u=160, n_tau=96, n_phi=64, u_max=None):
     return rmid, W.ravel(), Rv
 
 
-def two_centre_elements(T_states, P_states, Z_T, Z_P, b, z, v, **kw):
+def two_centre_elements(T_states, P_states, Z_T, Z_P, b, z, v, VT=None, **kw):
     """Return (S_TP, Q, Qtilde) with S_TP[i,j] = <T_i e^{-iv.r/2}|P_j e^{iv.r/2}>,
-    Q[i,j] = <T_i ..| -Z_T/r_T |P_j ..>, Qtilde[j,i] = <P_j ..| -Z_P/r_P |T_i ..>.
-    States are (n, l, m, Z) tuples; energies are not applied."""
+    Q[i,j] = <T_i ..| V_T(r_T) |P_j ..> (V_T = -Z_T/r_T unless the callable VT is given),
+    Qtilde[j,i] = <P_j ..| -Z_P/r_P |T_i ..>.  States are (n, l, m, Z) tuples; energies are not applied."""
     rmid, W, Rv = prolate_grid(b, z, **kw)
     rT = rmid + 0.5 * Rv
     rP = rmid - 0.5 * Rv
@@ -75,7 +75,7 @@ def two_centre_elements(T_states, P_states, Z_T, Z_P, b, z, v, **kw):
         for j, c in enumerate(PP):
             base = W * np.conj(a) * c * etf
             S[i, j] = base.sum()
-            Q[i, j] = (base * (-Z_T / dT)).sum()
+            Q[i, j] = (base * ((-Z_T / dT) if VT is None else VT(dT))).sum()
             Qt[j, i] = (W * np.conj(c) * a * np.conj(etf) * (-Z_P / dP)).sum()
     return S, Q, Qt
 
@@ -92,4 +92,20 @@ def direct_elements(states, Z_other, b, z, centre_is_projectile=False, **kw):
     for i, a in enumerate(F):
         for j, c in enumerate(F):
             D[i, j] = (W * np.conj(a) * c * (-Z_other / dO)).sum()
+    return D
+
+
+def potential_elements(states, V, b, z, centre_is_projectile=False, **kw):
+    """D[i,j] = <i| V(|r - R_other|) |j> for states on one centre and any central potential V of the
+    distance to the other nucleus, by the same 3-D rule."""
+    rmid, W, Rv = prolate_grid(b, z, **kw)
+    rT = rmid + 0.5 * Rv
+    rP = rmid - 0.5 * Rv
+    own, other = (rP, rT) if centre_is_projectile else (rT, rP)
+    Vo = V(np.linalg.norm(other, axis=-1).ravel())
+    F = [(_psi(n, l, m, Zs, own)).ravel() for (n, l, m, Zs) in states]
+    D = np.zeros((len(F), len(F)), complex)
+    for i, a in enumerate(F):
+        for j, c in enumerate(F):
+            D[i, j] = (W * np.conj(a) * c * Vo).sum()
     return D

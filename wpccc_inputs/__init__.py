@@ -36,7 +36,8 @@ __all__ = [
     "RadialGrid", "Centre", "Basis", "Quadrature", "Paths",
     "radial_grid", "hydrogenic_radial", "coulomb_bins", "make_centre",
     "make_basis", "make_quadrature", "uniform_zgrid", "geometric_zgrid",
-    "make_paths", "CONFIGS", "config_inputs",
+    "make_paths", "CONFIGS", "config_inputs", "CentreTangent", "box_centre", "li_model_potential",
+    "li_basis", "li_parameters", "observable_weights", "cross_section_weights", "li_inputs",
 ]
 
 
@@ -242,6 +243,120 @@ def centre_from_functions(Z: float, rad_l, rad_n, f, eps, all_m: bool = True) ->
                   st_m=np.array(st_m, dtype=np.int32), st_eps=eps[st_rad].copy())
 
 
+# --------------------------------------------------------------------------
+# box eigenstates of a general central potential, with parameter tangents
+# (the Li-like model-potential target of the differentiation workload)
+# --------------------------------------------------------------------------
+def li_model_potential(c: float, a: float, b: float, Z_as: float = 1.0):
+    """V(r) = -[Z_as + c e^{-a r}(1 + b r)]/r and its derivatives with respect to (c, a, b)."""
+    def V(r):
+        return -(Z_as + c * np.exp(-a * r) * (1.0 + b * r)) / r
+
+    def dV_dc(r):
+        return -np.exp(-a * r) * (1.0 + b * r) / r
+
+    def dV_da(r):
+        return c * np.exp(-a * r) * (1.0 + b * r)
+
+    def dV_db(r):
+        return -c * np.exp(-a * r)
+    return V, (dV_dc, dV_da, dV_db)
+
+
+@dataclass
+class CentreTangent:
+    """Derivatives of one centre's radial functions and energies with respect to n_par parameters."""
+    df: np.ndarray           # [n_par, n_rad, Nr]
+    deps: np.ndarray         # [n_par, n_rad]
+
+
+def box_centre(V, dVs, nmax: int, lmax: int, nbins: int, kmax: float, grid: RadialGrid,
+               skip_lowest_s: bool = False, all_m: bool = True, Z: float = 1.0):
+    """Bound states and wave packets of -1/2 u'' + (l(l+1)/(2r^2) + V(r)) u = E u in the box (0, r_max].
+
+    The radial equation is discretised on the grid itself: kinetic energy from the difference quotients
+    (u_i - u_{i-1})/(r_i - r_{i-1}) with u_0 = u(0) = 0 and u(r_max) = 0, potential and norm from the
+    grid's own weights w_i.  The discrete eigenvectors are therefore orthonormal under the rule every
+    matrix element uses.  Kept states of each l:
+      * bound states with principal number n <= nmax (n = l + 1 + index of the eigenvalue; with
+        skip_lowest_s the lowest s state, the Pauli-blocked core orbital of a Li-like target, is
+        dropped, so the s series starts at n = 2);
+      * `nbins` wave packets on uniform k-bins of (0, kmax]: the normalised sum of the box states whose
+        k = sqrt(2E) lies in the bin (each signed so that u > 0 next to the origin), with the bin's
+        mean box energy as its energy.
+    Tangents (one per entry of dVs, the potential's derivative functions) are the exact derivatives
+    of the discrete eigenpairs (first-order perturbation theory over all box states).
+    Returns (Centre, CentreTangent)."""
+    r, w = grid.r, grid.w
+    n = r.size - 1                                  # unknowns u_1 .. u_{Nr-1}; u_{Nr} = 0
+    ri, wi = r[:n], w[:n]
+    h = np.diff(np.concatenate([[0.0], r]))         # h_i = r_i - r_{i-1}, i = 1..Nr
+    kin_d = 0.5 * (1.0 / h[:n] + 1.0 / h[1:n + 1])
+    kin_e = -0.5 / h[1:n]
+    sw = np.sqrt(wi)
+    off = kin_e / (sw[:-1] * sw[1:])
+    edges = np.linspace(0.0, kmax, nbins + 1)
+    npar = len(dVs)
+    dVv = [dv(ri) for dv in dVs]
+    rad_l, rad_n, f, eps, df, deps = [], [], [], [], [], []
+    from scipy.linalg import eigh_tridiagonal
+    for l in range(lmax + 1):
+        diag = kin_d / wi + l * (l + 1) / (2.0 * ri * ri) + V(ri)
+        E, Y = eigh_tridiagonal(diag, off)
+        Y = Y * np.where(Y[0] < 0.0, -1.0, 1.0)[None, :]
+        first = 1 if (skip_lowest_s and l == 0) else 0
+        groups = []                                 # (label, member indices)
+        for idx in range(first, n):
+            nq = l + 1 + idx
+            if nq > nmax or E[idx] >= 0.0:
+                break
+            groups.append((nq, [idx]))
+        if nbins > 0:
+            pos = np.nonzero(E > 0.0)[0]
+            k = np.sqrt(2.0 * E[pos])
+            for ib in range(nbins):
+                sel = pos[(k > edges[ib]) & (k <= edges[ib + 1])]
+                if sel.size == 0:
+                    raise ValueError(f"k-bin {ib} of l={l} holds no box state; widen the bins")
+                groups.append((100 + ib, list(sel)))
+            kk = np.sqrt(2.0 * E[pos[k <= kmax * 1.0001]])
+            clear = np.min(np.abs(kk[:, None] - edges[None, 1:]))
+            if clear < 1e-7:
+                raise ValueError("a box state lies on a k-bin edge; its bin is not well defined")
+        # derivatives of every kept eigenpair: dE_s = y_s.dV y_s, dy_s = sum_{t != s} y_t (y_t.dV y_s)/(E_s - E_t)
+        keep = sorted({i for _, mem in groups for i in mem})
+        dE = {}
+        dY = {}
+        for p in range(npar):
+            C = Y.T @ (dVv[p][:, None] * Y[:, keep])             # [n, len(keep)]
+            for col, s in enumerate(keep):
+                den = E[s] - E
+                den[s] = np.inf
+                dY[p, s] = Y @ (C[:, col] / den)
+                dE[p, s] = C[s, col]
+        for label, mem in groups:
+            norm = 1.0 / math.sqrt(len(mem))
+            y = Y[:, mem].sum(axis=1) * norm
+            fu = np.zeros(r.size)
+            fu[:n] = y / sw / ri
+            rad_l.append(l)
+            rad_n.append(label)
+            f.append(fu)
+            eps.append(float(np.mean(E[mem])))
+            dfp = np.zeros((npar, r.size))
+            dep = np.zeros(npar)
+            for p in range(npar):
+                dy = sum(dY[p, s] for s in mem) * norm
+                dfp[p, :n] = dy / sw / ri
+                dep[p] = float(np.mean([dE[p, s] for s in mem]))
+            df.append(dfp)
+            deps.append(dep)
+    centre = centre_from_functions(Z, rad_l, rad_n, np.array(f), np.array(eps), all_m)
+    tangent = CentreTangent(df=np.ascontiguousarray(np.transpose(np.array(df), (1, 0, 2))),
+                            deps=np.ascontiguousarray(np.array(deps).T))
+    return centre, tangent
+
+
 @dataclass
 class Quadrature:
     """Gauss-Laguerre in s (eta = 1 + s/(gamma R)) and Gauss-Legendre in tau (Eq. 9)."""
@@ -270,8 +385,18 @@ class Basis:
     T: Centre
     P: Centre | None              # None in one-centre mode
     quad: Quadrature | None
-    Z_T: float                    # charge of the target nucleus
+    Z_T: float                    # charge of the target nucleus (asymptotic charge of a model potential)
     Z_P: float                    # charge of the projectile nucleus
+    # short-range part of a Li-like target potential: V_T(r) = -[Z_T + mp_c e^{-mp_a r}(1 + mp_b r)]/r
+    mp_c: float = 0.0
+    mp_a: float = 0.0
+    mp_b: float = 0.0
+    # parameter tangents of the differentiation workload (None otherwise): derivatives of both
+    # centres' functions and energies, and of (Z_P, mp_c, mp_a, mp_b), with respect to each parameter
+    tangent_T: CentreTangent | None = None
+    tangent_P: CentreTangent | None = None
+    dexplicit: np.ndarray | None = None    # [n_par, 4]: d(Z_P, mp_c, mp_a, mp_b)/d theta_p
+    theta_names: tuple = ()
 
     @property
     def n_centres(self) -> int:
@@ -294,6 +419,58 @@ def make_basis(Z_T: float, Z_P: float, nmax, lmax, nbins, kmax, two_centre: bool
     P = make_centre(Z_P, nmax[1], lmax[1], nbins[1], kmax[1], grid, all_m) if two_centre else None
     quad = make_quadrature(Geta, Gtau, gamma) if two_centre else None
     return Basis(grid=grid, T=T, P=P, quad=quad, Z_T=float(Z_T), Z_P=float(Z_P))
+
+
+def li_basis(Z_p: float = 1.0, a: float = 3.0, b: float = 1.5, c: float = 2.0, nmax: int = 4, lmax: int = 3,
+             nbins: int = 10, kmax: float = 3.0, Nr: int = 2000, rmax: float = 100.0, alpha: float = 3.5,
+             Geta: int = 48, Gtau: int = 48, gamma: float = 0.5, all_m: bool = True) -> Basis:
+    """Bare projectile of charge Z_p on a one-electron Li-like target with the model potential
+    V(r) = -[1 + c e^{-a r}(1 + b r)]/r.  Both centres' states are box eigenstates on the grid
+    (box_centre); the target's lowest s state (the core orbital) is left out, so its first state is
+    the valence 2s.  The tangents are with respect to theta = (Z_p, a, b)."""
+    grid = radial_grid(Nr, rmax, alpha)
+    V_T, (dV_dc, dV_da, dV_db) = li_model_potential(c, a, b)
+    zero = lambda r: np.zeros_like(r)
+    T, tT = box_centre(V_T, [zero, dV_da, dV_db], nmax, lmax, nbins, kmax, grid, skip_lowest_s=True,
+                       all_m=all_m, Z=1.0)
+    P, tP = box_centre(lambda r: -Z_p / r, [lambda r: -1.0 / r, zero, zero], nmax, lmax, nbins, kmax, grid,
+                       all_m=all_m, Z=Z_p)
+    dexp = np.array([[1.0, 0.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]])
+    return Basis(grid=grid, T=T, P=P, quad=make_quadrature(Geta, Gtau, gamma), Z_T=1.0, Z_P=float(Z_p),
+                 mp_c=float(c), mp_a=float(a), mp_b=float(b), tangent_T=tT, tangent_P=tP, dexplicit=dexp,
+                 theta_names=("Z_p", "a", "b"))
+
+
+def li_parameters(seed: int = 0, spread: float = 0.05):
+    """Model-potential parameters a = 3.0 (1 + U), b = 1.5 (1 + U), U uniform in (-spread, spread)."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-spread, spread, size=2)
+    return 3.0 * (1.0 + u[0]), 1.5 * (1.0 + u[1])
+
+
+def observable_weights(basis: Basis):
+    """0/1 weights g of two observables P = sum_i g_i |c_i|^2: electron capture (every bound
+    projectile state) and 2p excitation (the target's 2p states, all m)."""
+    N, NT = basis.N, basis.T.N
+    cap = np.zeros(N)
+    P = basis.P
+    cap[NT:] = (P.rad_n[P.st_rad] < 100).astype(np.float64)
+    ex = np.zeros(N)
+    T = basis.T
+    ex[:NT] = ((T.rad_n[T.st_rad] == 2) & (T.st_l == 1)).astype(np.float64)
+    return np.stack([cap, ex])
+
+
+def cross_section_weights(bs) -> np.ndarray:
+    """sigma = 2 pi int_0^inf b P(b) db by the trapezoid rule on the impact parameters plus b = 0
+    (where b P(b) = 0): per-path weights 2 pi b_j w_j."""
+    bs = np.asarray(bs, dtype=np.float64)
+    nodes = np.concatenate([[0.0], bs])
+    w = np.zeros(nodes.size)
+    d = np.diff(nodes)
+    w[:-1] += 0.5 * d
+    w[1:] += 0.5 * d
+    return 2.0 * np.pi * bs * w[1:]
 
 
 # --------------------------------------------------------------------------
@@ -378,4 +555,19 @@ def config_inputs(name: str, **over):
     else:
         zgrid = uniform_zgrid(*c["z"])
     paths = make_paths(np.linspace(b0, b1, nb), c["v"], zgrid)
+    return basis, paths
+
+
+def li_inputs(seed: int = 0, n_b: int = 32, **over):
+    """The differentiation workload: p + Li-like model-potential target with a, b drawn within 5 % of
+    (3.0, 1.5) from `seed`; hydrogen-like projectile, n <= 4, l <= 3, 10 wave packets per l on (0, 3];
+    v = 1.5; n_b impact parameters uniform in [0.2, 12]; z in [-50, 50], h = 0.1 (1000 steps).
+    Keyword overrides shrink it for tests.  Returns (basis, paths)."""
+    a, b = li_parameters(seed)
+    kw = dict(Z_p=1.0, a=a, b=b)
+    kw.update({k: v for k, v in over.items() if k not in ("v", "b_range", "z", "h")})
+    basis = li_basis(**kw)
+    b0, b1 = over.get("b_range", (0.2, 12.0))
+    z0, z1 = over.get("z", (-50.0, 50.0))
+    paths = make_paths(np.linspace(b0, b1, n_b), over.get("v", 1.5), uniform_zgrid(z0, z1, over.get("h", 0.1)))
     return basis, paths
