@@ -106,6 +106,14 @@ typedef struct {
     const double* tau;     /* [Gtau] nodes on (-1, 1) */
     const double* wtau;    /* [Gtau] weights */
     double gamma;          /* eta = 1 + s / (gamma * R) maps the Laguerre variable onto [1, inf) */
+    /* Short-range part of a one-electron (Li-like) target potential.  The paper treats bare
+       nuclei; with mp_c != 0 the target potential is
+         V_T(r) = -[T.Z + mp_c exp(-mp_a r) (1 + mp_b r)] / r,
+       so the transfer integral Q carries V_T(r_T) in place of -T.Z/r_T and D_P gains the
+       short-range part between projectile states (integrated on the Eq. 9 (eta, tau) rule; only
+       equal-q pairs couple in the molecular frame).  The target's states must then be eigenstates
+       of this potential.  mp_c = 0 (zero-initialised descriptors) is the bare-nucleus case. */
+    double mp_c, mp_a, mp_b;
 } wpccc_basis_desc;
 
 /*
@@ -148,7 +156,8 @@ WPCCC_API wpccc_status wpccc_basis_info(wpccc_basis basis, int* N_T, int* N_P);
  *        by 5-point Lagrange interpolation on the r-grid;
  *   D_P: the same expansion about the projectile with the target charge at -R;
  *   K, Q: Eq. 9 on the (eta, tau) rule with the ETF phase exp(i v z eta tau / 2)
- *        and J_{q-q'}, rotated to the collision frame by Eq. 8; Q carries -Z_T/r_T;
+ *        and J_{q-q'}, rotated to the collision frame by Eq. 8; Q carries -Z_T/r_T
+ *        (V_T(r_T) for a model-potential target, see wpccc_basis_desc);
  *        the lower-left block of H is Q^+, as Eq. 1 prints it (H Hermitian).
  * In one-centre mode S[k] = I and H[k] = D_T.
  *   z      host   [nz] positions
@@ -293,6 +302,47 @@ WPCCC_API wpccc_status wpccc_basis_set_workspace_limit(wpccc_basis basis, size_t
 #define WPCCC_PROF_N 5
 WPCCC_API wpccc_status wpccc_profile_enable(wpccc_basis basis, int on);
 WPCCC_API wpccc_status wpccc_profile_read(wpccc_basis basis, double* ms, long long* launches);
+
+/*
+ * Differentiation form (no counterpart in the paper): derivatives of observables of the
+ * propagated amplitudes with respect to n_par <= WPCCC_MAX_PARAMS parameters theta (e.g. the
+ * projectile charge and the model-potential parameters).
+ *
+ * wpccc_basis_set_tangents gives the basis the derivatives of its inputs (host pointers, copied):
+ *   dfT   [n_par][T.n_rad][Nr]  d f_a(r_i) / d theta_p of every target radial function
+ *   depsT [n_par][T.n_rad]      d eps_a / d theta_p (every state of radial a shares it)
+ *   dfP, depsP                  the same for the projectile centre
+ *   dexplicit [n_par][4]        d(P.Z, mp_c, mp_a, mp_b) / d theta_p: how theta enters the
+ *                               operator itself (projectile charge in D_T, target potential in Q
+ *                               and D_P)
+ * and builds, on the device, the derivative of the Eq. 7 table of each centre.  Synchronous.
+ * Errors: EINVAL (one-centre basis, n_par out of range, null pointers), ENOMEM, ECUDA.
+ */
+#define WPCCC_MAX_PARAMS 4
+WPCCC_API wpccc_status wpccc_basis_set_tangents(wpccc_basis basis, int n_par, const double* dfT,
+                                                const double* depsT, const double* dfP, const double* depsP,
+                                                const double* dexplicit);
+
+/*
+ * Observables P[p][o] = sum_i g[o][i] |c_i|^2 at the end of every path (Algorithm 1 in FP64,
+ * stage-form solve) and their derivatives grad[p][o][k] = d P[p][o] / d theta_k, by the discrete
+ * adjoint of the RK4 propagation: a forward sweep keeps the amplitudes every `checkpoint_every`
+ * steps; the reverse sweep recomputes S, H and the amplitudes of one segment at a time and runs the
+ * transposed RK4 stages backwards (S^-1 applied from the same LU factors), while the adjoint of the
+ * element assembly contracts each stage's cotangent vectors with the derivatives of the element
+ * integrals (the same Eq. 6-9 integrals with one radial table, the charge, the potential or the
+ * energy phase differentiated).  The result is the exact derivative of the discrete propagation.
+ *   n_obs  1..4 observables; g host [n_obs][N] real weights
+ *   c      device [n_paths][N] complex128: in, amplitudes at the first node; out, at the last
+ *   P      device [n_paths][n_obs] double, or NULL
+ *   grad   device [n_paths][n_obs][n_par] double
+ * Needs wpccc_basis_set_tangents first.  Two-centre bases only.  Blocks until done; allocates its
+ * own checkpoint and segment buffers (freed before it returns) and uses the basis workspace.
+ * Errors: EINVAL, EUNSUPPORTED (one-centre basis), ENOMEM, ESINGULAR, ENONFINITE, ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_propagate_adjoint(wpccc_basis basis, const wpccc_paths* paths, int n_obs,
+                                               const double* g, int checkpoint_every, void* c, double* P,
+                                               double* grad, void* stream);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 WPCCC_API const char* wpccc_last_error(void);

@@ -45,7 +45,8 @@ class _BasisDesc(C.Structure):
     _fields_ = [("n_centres", C.c_int), ("Nr", C.c_int), ("r", _pd), ("w", _pd),
                 ("T", _CentreDesc), ("P", _CentreDesc),
                 ("Geta", C.c_int), ("s", _pd), ("ws", _pd),
-                ("Gtau", C.c_int), ("tau", _pd), ("wtau", _pd), ("gamma", C.c_double)]
+                ("Gtau", C.c_int), ("tau", _pd), ("wtau", _pd), ("gamma", C.c_double),
+                ("mp_c", C.c_double), ("mp_a", C.c_double), ("mp_b", C.c_double)]
 
 
 class _PathsDesc(C.Structure):
@@ -73,19 +74,23 @@ _lib.wpccc_batch_launch.argtypes = [C.c_void_p, C.c_void_p]
 _lib.wpccc_batch_status.argtypes = [C.c_void_p, C.c_void_p]
 _lib.wpccc_batch_info.argtypes = [C.c_void_p, _pi, _pd]
 _lib.wpccc_batch_destroy.argtypes = [C.c_void_p]
+_lib.wpccc_basis_set_tangents.argtypes = [C.c_void_p, C.c_int, _pd, _pd, _pd, _pd, _pd]
+_lib.wpccc_propagate_adjoint.argtypes = [C.c_void_p, C.POINTER(_PathsDesc), C.c_int, _pd, C.c_int, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.wpccc_last_error.restype = C.c_char_p
 for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
            "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode",
            "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
-           "wpccc_batch_info", "wpccc_batch_destroy"):
+           "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
             "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
             "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error",
             "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
-            "wpccc_batch_info", "wpccc_batch_destroy")
+            "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint")
+MAX_PARAMS = 4
 NOALLOC_SCRATCH_BYTES = 64 << 20
 SOLVE_STAGE, SOLVE_MATRIX = 0, 1
 PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4")
@@ -156,6 +161,9 @@ class Basis:
             d.Geta, d.s, d.ws = int(q.s.size), arr(q.s, np.float64), arr(q.ws, np.float64)
             d.Gtau, d.tau, d.wtau = int(q.tau.size), arr(q.tau, np.float64), arr(q.wtau, np.float64)
             d.gamma = float(q.gamma)
+            d.mp_c = float(getattr(basis, "mp_c", 0.0))
+            d.mp_a = float(getattr(basis, "mp_a", 0.0))
+            d.mp_b = float(getattr(basis, "mp_b", 0.0))
         h = C.c_void_p()
         _check(_lib.wpccc_basis_create(C.byref(d), int(device), C.byref(h)), "wpccc_basis_create")
         self._h = h
@@ -165,6 +173,19 @@ class Basis:
         self.N_T, self.N_P = nt.value, np_.value
         self.N = self.N_T + self.N_P
         self.n_centres = basis.n_centres
+        self.n_par = 0
+        if getattr(basis, "tangent_T", None) is not None:
+            self.set_tangents(basis.tangent_T.df, basis.tangent_T.deps, basis.tangent_P.df, basis.tangent_P.deps,
+                              basis.dexplicit)
+
+    def set_tangents(self, dfT, depsT, dfP, depsP, dexplicit) -> None:
+        """Derivatives of the radial tables and energies of both centres and of (Z_P, mp_c, mp_a, mp_b)
+        with respect to each parameter (``wpccc_basis_set_tangents``)."""
+        dexplicit = np.atleast_2d(np.asarray(dexplicit, dtype=np.float64))
+        n_par = int(dexplicit.shape[0])
+        arrs = [_arr(x, np.float64) for x in (dfT, depsT, dfP, depsP, dexplicit)]
+        _check(_lib.wpccc_basis_set_tangents(self._h, n_par, *[p for _, p in arrs]), "wpccc_basis_set_tangents")
+        self.n_par = n_par
 
     def close(self):
         if getattr(self, "_h", None):
@@ -238,6 +259,29 @@ class Basis:
         _check(_lib.wpccc_propagate(self._h, C.byref(pd), int(precision_mode), int(batch_mode), _ptr(c),
                                     _stream(stream)), "wpccc_propagate")
         return c
+
+
+    def propagate_adjoint(self, b, v, zgrids, g, checkpoint_every: int = 50, c=None, stream=None):
+        """Observables P[p, o] = sum_i g[o, i] |c_i|^2 at the end of each path and their derivatives
+        grad[p, o, k] with respect to the basis parameters (``wpccc_propagate_adjoint``; needs the basis
+        tangents).  Returns (c, P, grad) as device tensors; `c` is advanced in place."""
+        import torch
+        keep = []
+        pd = _paths_desc(b, v, zgrids, keep)
+        n_paths = pd.n_paths
+        dev = torch.device("cuda", self.device)
+        if c is None:
+            c = torch.zeros((n_paths, self.N), dtype=torch.complex128, device=dev)
+            c[:, 0] = 1.0
+        g, gp = _arr(np.atleast_2d(g), np.float64)
+        if g.ndim != 2 or g.shape[1] != self.N:
+            raise ValueError(f"observable weights must have shape (n_obs, {self.N})")
+        n_obs = int(g.shape[0])
+        P = torch.empty((n_paths, n_obs), dtype=torch.float64, device=dev)
+        grad = torch.empty((n_paths, n_obs, max(1, self.n_par)), dtype=torch.float64, device=dev)
+        _check(_lib.wpccc_propagate_adjoint(self._h, C.byref(pd), n_obs, gp, int(checkpoint_every), _ptr(c), _ptr(P),
+                                            _ptr(grad), _stream(stream)), "wpccc_propagate_adjoint")
+        return c, P, grad
 
 
 def _paths_desc(b, v, zgrids, keep):
@@ -316,3 +360,45 @@ def probabilities(c, stream=None):
     _check(_lib.wpccc_probabilities(int(n_paths), int(N), _ptr(c), _ptr(P), _stream(stream)),
            "wpccc_probabilities")
     return P
+
+
+def _observables_function():
+    import torch
+
+    class Observables(torch.autograd.Function):
+        """P[p, o] = sum_i g[o, i] |c_i|^2 at the end of every path as a function of the parameters theta.
+
+        `make_basis(theta)` returns the ``wpccc_inputs`` basis (with its parameter tangents) at theta.
+        The forward pass runs the adjoint propagation when theta needs a gradient (keeping the
+        Jacobian dP/dtheta for the backward pass) and the plain propagation otherwise."""
+
+        @staticmethod
+        def forward(ctx, theta, make_basis, b, v, zgrids, g, checkpoint_every=50, device=0):
+            th = theta.detach().cpu().numpy().astype(np.float64)
+            gb = Basis(make_basis(th), device)
+            try:
+                if ctx.needs_input_grad[0]:
+                    _, P, J = gb.propagate_adjoint(b, v, zgrids, g, checkpoint_every)
+                    ctx.save_for_backward(J)
+                else:
+                    c = gb.propagate(b, v, zgrids)
+                    gw = torch.as_tensor(np.atleast_2d(g), dtype=torch.float64, device=c.device)
+                    P = probabilities(c) @ gw.T
+            finally:
+                gb.close()
+            ctx.theta_device = theta.device
+            return P
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (J,) = ctx.saved_tensors
+            gt = torch.einsum("po,pok->k", grad_out.to(J.dtype), J)
+            return (gt.to(ctx.theta_device),) + (None,) * 7
+
+    return Observables
+
+
+def observables(theta, make_basis, b, v, zgrids, g, checkpoint_every: int = 50, device: int = 0):
+    """Differentiable end-of-path observables (see ``_observables_function``): a torch tensor of shape
+    (n_paths, n_obs); ``.backward()`` gives d/dtheta through the adjoint of the propagation."""
+    return _observables_function().apply(theta, make_basis, b, v, zgrids, g, checkpoint_every, device)

@@ -3,6 +3,7 @@
 // quantities resident on the GPU before the equations are integrated).
 //   * Eq. 7 radial multipole integrals F_{ab lam}(r_i) at every grid radius
 //   * Eq. 6 angular coefficients sqrt((2l+1)/(2l'+1)) C^{l'0}_{lam0 l0} C^{l'm'}_{lam mu lm}
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -96,23 +97,32 @@ __device__ inline double ipow(double x, int n) {
 // F_{ab lam}(r_i) = r_i^{-lam-1} sum_{j<=i} g_j r_j^lam + r_i^lam sum_{j>i} g_j r_j^{-lam-1},
 // g_j = w_j r_j^2 f_a(r_j) f_b(r_j): Eq. 7 on the grid's own rule, split at r = R = r_i.
 // One block per table entry; the two sums are a forward and a backward block scan.
+// With derivative tables df (differentiation form), g_j = w_j r_j^2 (df_a f_b + f_a df_b): the
+// derivative of the table, which is bilinear in the two radial functions.
+__device__ inline double fpair(const double* fa, const double* fb, const double* dfa, const double* dfb, int j) {
+    return dfa ? dfa[j] * fb[j] + fa[j] * dfb[j] : fa[j] * fb[j];
+}
+
 __global__ void __launch_bounds__(256) k_ftable(int Nr, const double* __restrict__ r,
                                                 const double* __restrict__ w,
                                                 const double* __restrict__ f,
                                                 const int* __restrict__ ea, const int* __restrict__ eb,
-                                                const int* __restrict__ elam, double* __restrict__ F) {
+                                                const int* __restrict__ elam, double* __restrict__ F,
+                                                const double* __restrict__ df = nullptr) {
     __shared__ double s_fwd[256], s_bwd[256];
     const int e = blockIdx.x, tid = threadIdx.x;
     const int a = ea[e], b = eb[e], lam = elam[e];
     const double* fa = f + (size_t)a * Nr;
     const double* fb = f + (size_t)b * Nr;
+    const double* dfa = df ? df + (size_t)a * Nr : nullptr;
+    const double* dfb = df ? df + (size_t)b * Nr : nullptr;
     double* out = F + (size_t)e * Nr;
     const int chunk = (Nr + 255) / 256;
     const int j0 = min(Nr, tid * chunk), j1 = min(Nr, j0 + chunk);
     double sa = 0.0, sb = 0.0;
     for (int j = j0; j < j1; ++j) {
         double rj = r[j];
-        double g = w[j] * rj * rj * fa[j] * fb[j];
+        double g = w[j] * rj * rj * fpair(fa, fb, dfa, dfb, j);
         double rl = ipow(rj, lam);
         sa += g * rl;
         sb += g / (rl * rj);
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(256) k_ftable(int Nr, const double* __restrict
     double acc = s_fwd[tid];
     for (int j = j0; j < j1; ++j) {
         double rj = r[j];
-        acc += w[j] * rj * rj * fa[j] * fb[j] * ipow(rj, lam);
+        acc += w[j] * rj * rj * fpair(fa, fb, dfa, dfb, j) * ipow(rj, lam);
         out[j] = acc;  // inclusive inner sum, finished below
     }
     double accb = s_bwd[tid];
@@ -147,7 +157,7 @@ __global__ void __launch_bounds__(256) k_ftable(int Nr, const double* __restrict
         double rl = ipow(rj, lam);
         double inner = out[j];
         out[j] = inner / (rl * rj) + rl * accb;
-        accb += w[j] * rj * rj * fa[j] * fb[j] / (rl * rj);
+        accb += w[j] * rj * rj * fpair(fa, fb, dfa, dfb, j) / (rl * rj);
     }
 }
 
@@ -296,6 +306,9 @@ static void free_basis(wpccc_basis_s* B) {
         if (e) cudaEventDestroy(e);
     free_centre(B->T);
     free_centre(B->P);
+    void* tptrs[] = {B->tanT.df, B->tanT.dF, B->tanP.df, B->tanP.dF, B->deps};
+    for (void* p : tptrs)
+        if (p) cudaFree(p);
     void* ptrs[] = {B->r, B->w, B->inv_den, B->s, B->ws, B->tau, B->wtau, B->half_state, B->half_of, B->qtile_q,
                     B->qtile_cols, B->ws_ptr};
     for (void* p : ptrs)
@@ -366,6 +379,11 @@ extern "C" wpccc_status wpccc_basis_create(const wpccc_basis_desc* d, int device
         if ((st = upload(&B->ws, d->ws, d->Geta, "upload ws")) != WPCCC_OK) return bail(st);
         if ((st = upload(&B->tau, d->tau, d->Gtau, "upload tau")) != WPCCC_OK) return bail(st);
         if ((st = upload(&B->wtau, d->wtau, d->Gtau, "upload wtau")) != WPCCC_OK) return bail(st);
+        if (!std::isfinite(d->mp_c) || !std::isfinite(d->mp_a) || !std::isfinite(d->mp_b))
+            return bail(fail(WPCCC_EINVAL, "model-potential parameters must be finite"));
+        B->mp_c = d->mp_c;
+        B->mp_a = d->mp_a;
+        B->mp_b = d->mp_b;
         B->dmax = B->T.lmax + B->P.lmax;
         B->nlq_T = (B->T.lmax + 1) * (B->T.lmax + 2) / 2;
         B->nlq_P = (B->P.lmax + 1) * (B->P.lmax + 2) / 2;
@@ -455,5 +473,87 @@ extern "C" wpccc_status wpccc_basis_set_workspace_limit(wpccc_basis B, size_t by
     if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_workspace_limit: null basis");
     if (bytes < ((size_t)64 << 20)) return fail(WPCCC_EINVAL, "workspace limit below 64 MiB");
     B->ws_limit = bytes;
+    return WPCCC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// differentiation form: derivative tables of the inputs
+// ---------------------------------------------------------------------------
+namespace wpccc {
+
+// Keeps the derivative tables of one centre for the parameters whose tangent is not identically
+// zero, and builds the derivative of its Eq. 7 table from them.
+static wpccc_status centre_tangents(wpccc_basis_s* B, CentreDev& c, CentreTan& t, int n_par, const double* df) {
+    const size_t per = (size_t)c.n_rad * B->Nr;
+    t = CentreTan();
+    for (int p = 0; p < WPCCC_MAX_PARAMS; ++p) t.slot[p] = -1;
+    std::vector<int> keep;
+    for (int p = 0; p < n_par; ++p) {
+        const double* d = df + (size_t)p * per;
+        bool nz = false;
+        for (size_t k = 0; k < per && !nz; ++k) {
+            if (!std::isfinite(d[k])) return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: non-finite derivative");
+            nz = d[k] != 0.0;
+        }
+        if (nz) {
+            t.slot[p] = (int)keep.size();
+            t.par[keep.size()] = p;
+            keep.push_back(p);
+        }
+    }
+    t.n_tan = (int)keep.size();
+    if (t.n_tan == 0) return WPCCC_OK;
+    std::vector<double> packed(per * t.n_tan);
+    for (int k = 0; k < t.n_tan; ++k)
+        std::memcpy(packed.data() + per * k, df + per * keep[k], per * sizeof(double));
+    wpccc_status st;
+    if ((st = upload(&t.df, packed.data(), packed.size(), "upload df")) != WPCCC_OK) return st;
+    if ((st = upload<double>(&t.dF, nullptr, (size_t)t.n_tan * c.n_fent * B->Nr, "alloc dF")) != WPCCC_OK) return st;
+    for (int k = 0; k < t.n_tan; ++k) {
+        k_ftable<<<c.n_fent, 256>>>(B->Nr, B->r, B->w, c.f, c.fent_a, c.fent_b, c.fent_lam,
+                                    t.dF + (size_t)k * c.n_fent * B->Nr, t.df + per * k);
+        WPCCC_CHECK_LAUNCH("k_ftable (derivative)");
+    }
+    return WPCCC_OK;
+}
+
+}  // namespace wpccc
+
+extern "C" wpccc_status wpccc_basis_set_tangents(wpccc_basis B, int n_par, const double* dfT, const double* depsT,
+                                                 const double* dfP, const double* depsP, const double* dexplicit) {
+    if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: null basis");
+    if (B->n_centres != 2) return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: two-centre bases only");
+    if (n_par < 1 || n_par > WPCCC_MAX_PARAMS)
+        return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: n_par must be 1..WPCCC_MAX_PARAMS");
+    if (!dfT || !depsT || !dfP || !depsP || !dexplicit)
+        return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: null pointer");
+    for (int k = 0; k < 4 * n_par; ++k)
+        if (!std::isfinite(dexplicit[k])) return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: non-finite dexplicit");
+    WPCCC_CUDA(cudaSetDevice(B->device));
+    WPCCC_CUDA(cudaDeviceSynchronize());
+    void* old[] = {B->tanT.df, B->tanT.dF, B->tanP.df, B->tanP.dF, B->deps};
+    for (void* p : old)
+        if (p) cudaFree(p);
+    B->tanT = CentreTan();
+    B->tanP = CentreTan();
+    B->deps = nullptr;
+    B->n_par = 0;
+    // energy derivatives per state, target states first
+    std::vector<double> de((size_t)n_par * B->N);
+    for (int p = 0; p < n_par; ++p) {
+        for (int i = 0; i < B->N_T; ++i) de[(size_t)p * B->N + i] = depsT[(size_t)p * B->T.n_rad + B->T.h_st_rad[i]];
+        for (int j = 0; j < B->N_P; ++j)
+            de[(size_t)p * B->N + B->N_T + j] = depsP[(size_t)p * B->P.n_rad + B->P.h_st_rad[j]];
+    }
+    for (double x : de)
+        if (!std::isfinite(x)) return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: non-finite energy derivative");
+    wpccc_status st;
+    if ((st = upload(&B->deps, de.data(), de.size(), "upload deps")) != WPCCC_OK) return st;
+    if ((st = centre_tangents(B, B->T, B->tanT, n_par, dfT)) != WPCCC_OK) return st;
+    if ((st = centre_tangents(B, B->P, B->tanP, n_par, dfP)) != WPCCC_OK) return st;
+    for (int p = 0; p < n_par; ++p)
+        for (int k = 0; k < 4; ++k) B->dexp[p][k] = dexplicit[4 * p + k];
+    WPCCC_CUDA(cudaDeviceSynchronize());
+    B->n_par = n_par;
     return WPCCC_OK;
 }

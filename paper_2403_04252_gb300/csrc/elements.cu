@@ -14,11 +14,14 @@
 //                  blocks of S and H
 //   k_direct       Eq. 6 direct elements D_T and D_P (F of Eq. 7 interpolated at R),
 //                  energy phases; identity diagonal blocks of S
+//   k_direct_sr    (model-potential target only) the short-range part of the target
+//                  potential between projectile states, on the (eta, tau) rule, added to D_P
 #include <algorithm>
 #include <cstdio>
 #include <vector>
 
 #include "angular.cuh"
+#include "geometry.cuh"
 #include "wpccc_internal.cuh"
 
 namespace wpccc {
@@ -28,71 +31,12 @@ namespace wpccc {
 constexpr int NX = 2;
 
 // ---------------------------------------------------------------------------
-// geometry shared by the kernels; explicit round-to-nearest operations so that
-// the interpolation stencils are chosen from exactly the same radii as a plain
-// IEEE evaluation of the same formulas (no contraction into FMA)
-// ---------------------------------------------------------------------------
-__device__ inline double dist_R(double b, double z) {
-    return __dsqrt_rn(__dadd_rn(__dmul_rn(b, b), __dmul_rn(z, z)));
-}
-
-// Largest j with r[j] <= x (-1 if x < r[0]); 5-point stencil start and Lagrange weights.
-// Returns false when x lies beyond the last grid point (the function is zero there).
-__device__ inline bool stencil5(const double* __restrict__ r, int Nr, double x, int& s, double L[5]) {
-    if (x > r[Nr - 1]) return false;
-    int lo = -1, hi = Nr;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (r[mid] <= x) lo = mid;
-        else hi = mid;
-    }
-    s = min(max(lo - 2, 0), Nr - 5);
-    double rn[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) rn[k] = r[s + k];
-#pragma unroll
-    for (int a = 0; a < 5; ++a) {
-        double p = 1.0;
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-            if (c != a) p *= (x - rn[c]) / (rn[a] - rn[c]);
-        L[a] = p;
-    }
-    return true;
-}
-
-// The same stencil with the Lagrange denominators 1/prod_{c != a}(r_{s+a} - r_{s+c}) read from a
-// table made at set-up (inv_den[s][a], 5 per stencil start), so no division per interpolation.
-__device__ inline bool stencil5_fast(const double* __restrict__ r, const double* __restrict__ inv_den, int Nr,
-                                     double x, int& s, double L[5]) {
-    if (x > r[Nr - 1]) return false;
-    int lo = -1, hi = Nr;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (r[mid] <= x) lo = mid;
-        else hi = mid;
-    }
-    s = min(max(lo - 2, 0), Nr - 5);
-    double dx[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) dx[k] = x - r[s + k];
-#pragma unroll
-    for (int a = 0; a < 5; ++a) {
-        double p = inv_den[(size_t)s * 5 + a];
-#pragma unroll
-        for (int c = 0; c < 5; ++c)
-            if (c != a) p *= dx[c];
-        L[a] = p;
-    }
-    return true;
-}
-
-// ---------------------------------------------------------------------------
 // k_node_tables
 // ---------------------------------------------------------------------------
 struct NodeArgs {
     int Nr, G, Gtau, nradT, nradP, lmaxT, lmaxP, nlqT, nlqP, dmax;
     double gamma, Z_T, Z_P;
+    double mp_c, mp_a, mp_b;   // short-range part of a model-potential target (mp_c = 0: bare nucleus)
     const double *r, *fT, *fP, *s, *ws, *tau, *wtau;
     const double* inv_den;   // Lagrange denominators per stencil start
     double* node;            // per evaluation: [fT | fP | thT | thP | pad | W] (see elem_scratch_layout)
@@ -218,8 +162,9 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
             }
         }
     }
-    // node weights for the two integrands, d = |q - q'| = 0..dmax
-    const double uQ = -A.Z_T / rT;
+    // node weights for the two integrands, d = |q - q'| = 0..dmax; Q carries the target potential
+    const double uQ = A.mp_c == 0.0 ? -A.Z_T / rT
+                                    : -A.Z_T / rT + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT) / rT;
     const size_t stride = (size_t)(A.dmax + 1) * A.G;
     for (int d = 0; d <= A.dmax; ++d) {
         const double J = jn(d, x) * amp;
@@ -882,6 +827,96 @@ __global__ void __launch_bounds__(256) k_direct(DirArgs A0, DirArgs A1, const Ev
 }
 
 // ---------------------------------------------------------------------------
+// k_direct_sr: short-range part of a model-potential target between projectile states.
+// In the molecular frame the potential is symmetric about the axis, so only equal q couple:
+//   I[b][q] = (R^3/8) sum_g w_g (eta^2 - tau^2) V_s(r_T) f_a(r_P) Theta_{l_a q}(c_P) f_b(r_P) Theta_{l_b q}(c_P)
+// (Theta_{l,-q} = (-1)^q Theta_{l,q}, so I does not depend on the sign of q).  One block per
+// (projectile radial a, position): a warp per (b, q) sums over the nodes, then the rows of a are
+// rotated with d^{l}(theta) on both sides, given their energy phases and added to H.
+// ---------------------------------------------------------------------------
+struct SrArgs {
+    int G, Gtau, nradT, nradP, lmaxP, nlqT, N_T, N_P, N, dtot;
+    double gamma, mp_c, mp_a, mp_b;
+    const double *s, *ws, *tau, *wtau;
+    const double* node;        // FP64 node tables per evaluation
+    size_t node_doubles;
+    const double* et;          // per-position tables (Wigner d first)
+    size_t et_doubles;
+    const int *radP_l, *stP_index, *stP_rad, *stP_m;
+    const double* epsP;
+    double2* H;
+    size_t mat;
+};
+
+__global__ void __launch_bounds__(256) k_direct_sr(SrArgs A, const EvalDesc* __restrict__ ev) {
+    extern __shared__ double srm[];   // [G] V_s-weighted f_a, then I[n_radP][lmaxP+1], then Wigner d
+    const int a = blockIdx.x, e = blockIdx.y;
+    const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
+    const double R = dist_R(b, z);
+    const double gR = __dmul_rn(A.gamma, R);
+    const double halfR = __dmul_rn(0.5, R);
+    const double* base = A.node + (size_t)e * A.node_doubles;
+    const double* oP = base + (size_t)A.nradT * A.G;
+    const double* thP = oP + (size_t)A.nradP * A.G + (size_t)A.nlqT * A.G;
+    const int LQ = A.lmaxP + 1;
+    double* ufa = srm;
+    double* I = srm + A.G;
+    double* dt = I + A.nradP * LQ;
+    for (int g = threadIdx.x; g < A.G; g += blockDim.x) {
+        const int k = g / A.Gtau, t = g - k * A.Gtau;
+        const double eta = __dadd_rn(1.0, __ddiv_rn(A.s[k], gR));
+        const double tau = A.tau[t];
+        const double rT = __dmul_rn(halfR, __dadd_rn(eta, tau));
+        const double wgt = (A.ws[k] / gR) * A.wtau[t];
+        const double vol = (R * R * R / 8.0) * wgt * (eta * eta - tau * tau);
+        const double Vs = (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT) / rT;
+        ufa[g] = vol * Vs * oP[(size_t)a * A.G + g];
+    }
+    const double* etd = A.et + (size_t)e * A.et_doubles;
+    for (int t = threadIdx.x; t < A.dtot; t += blockDim.x) dt[t] = etd[t];
+    __syncthreads();
+    const int la = A.radP_l[a];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int pq = warp; pq < A.nradP * LQ; pq += nw) {
+        const int bb = pq / LQ, q = pq - bb * LQ;
+        const int lb = A.radP_l[bb];
+        double acc = 0.0;
+        if (q <= la && q <= lb) {
+            const double* ta = thP + (size_t)(la * (la + 1) / 2 + q) * A.G;
+            const double* tb = thP + (size_t)(lb * (lb + 1) / 2 + q) * A.G;
+            const double* fb = oP + (size_t)bb * A.G;
+            for (int g = lane; g < A.G; g += 32) acc = fma(ufa[g] * ta[g], fb[g] * tb[g], acc);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) I[pq] = acc;
+    }
+    __syncthreads();
+    // lab frame: D[(a, m)][(b, m')] = sum_q d^{la}_{m q} d^{lb}_{m' q} I[b][|q|]
+    int offa = 0;
+    for (int l = 0; l < la; ++l) offa += (2 * l + 1) * (2 * l + 1);
+    double2* H = A.H + (size_t)e * A.mat;
+    for (int idx = threadIdx.x; idx < (2 * la + 1) * A.N_P; idx += blockDim.x) {
+        const int mi = idx / A.N_P - la, j = idx % A.N_P;
+        const int bb = A.stP_rad[j], lb = A.radP_l[bb], mj = A.stP_m[j];
+        int offb = 0;
+        for (int l = 0; l < lb; ++l) offb += (2 * l + 1) * (2 * l + 1);
+        const int qm = la < lb ? la : lb;
+        double D = 0.0;
+        for (int q = -qm; q <= qm; ++q) {
+            const double da = dt[offa + (mi + la) * (2 * la + 1) + (q + la)];
+            const double db = dt[offb + (mj + lb) * (2 * lb + 1) + (q + lb)];
+            D = fma(da * db, I[bb * LQ + (q < 0 ? -q : q)], D);
+        }
+        const int i = A.stP_index[a * (2 * WPCCC_LMAX + 1) + mi + WPCCC_LMAX];
+        double sp, cp;
+        sincos((A.epsP[i] - A.epsP[j]) * z / v, &sp, &cp);
+        const size_t o = (size_t)(A.N_T + i) + (size_t)(A.N_T + j) * A.N;
+        const double2 h = H[o];
+        H[o] = make_double2(fma(D, cp, h.x), fma(D, sp, h.y));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
@@ -940,9 +975,9 @@ static DirArgs dir_args(const wpccc_basis_s* B, const CentreDev& c, int off, dou
     return a;
 }
 
-wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, double2* S,
-                             double2* H, void* scratch, cudaStream_t st, int precision) {
-    if (nev <= 0) return WPCCC_OK;
+// Per-position tables (k_eval_tables) and, two-centre, the node tables of Eq. 9 (k_node_tables).
+static wpccc_status launch_tables(wpccc_basis_s* B, const EvalDesc* evals, int nev, void* scratch,
+                                  cudaStream_t st, int precision) {
     const bool two = B->n_centres == 2;
     const ElemScratch L = elem_scratch_layout(B);
     double* node = static_cast<double*>(scratch);
@@ -967,44 +1002,67 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         WPCCC_CHECK_LAUNCH("k_eval_tables");
         B->prof.end(PROF_NODES, st, e0);
     }
-    if (two) {
-        NodeArgs na;
-        na.Nr = B->Nr;
-        na.G = B->G;
-        na.Gtau = B->Gtau;
-        na.nradT = B->T.n_rad;
-        na.nradP = B->P.n_rad;
-        na.lmaxT = B->T.lmax;
-        na.lmaxP = B->P.lmax;
-        na.nlqT = B->nlq_T;
-        na.nlqP = B->nlq_P;
-        na.dmax = B->dmax;
-        na.gamma = B->gamma;
-        na.Z_T = B->T.Z;
-        na.Z_P = B->P.Z;
-        na.r = B->r;
-        na.fT = B->T.f;
-        na.fP = B->P.f;
-        na.s = B->s;
-        na.ws = B->ws;
-        na.tau = B->tau;
-        na.wtau = B->wtau;
-        na.inv_den = B->inv_den;
-        na.node = node;
-        na.node_doubles = L.node_doubles;
-        na.w_off = precision == 0 ? L.w_off : L.w_off_f;
-        na.N_T = B->N_T;
-        na.n_half = B->n_half;
-        na.stT_index = B->T.st_index;
-        na.half_of = B->half_of;
-        na.radT_l = B->T.rad_l;
-        na.radP_l = B->P.rad_l;
-        cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
-        if (precision == 0) k_node_tables<double><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
-        else k_node_tables<float><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
-        WPCCC_CHECK_LAUNCH("k_node_tables");
-        B->prof.end(PROF_NODES, st, e0);
+    if (!two) return WPCCC_OK;
+    NodeArgs na;
+    na.Nr = B->Nr;
+    na.G = B->G;
+    na.Gtau = B->Gtau;
+    na.nradT = B->T.n_rad;
+    na.nradP = B->P.n_rad;
+    na.lmaxT = B->T.lmax;
+    na.lmaxP = B->P.lmax;
+    na.nlqT = B->nlq_T;
+    na.nlqP = B->nlq_P;
+    na.dmax = B->dmax;
+    na.gamma = B->gamma;
+    na.Z_T = B->T.Z;
+    na.Z_P = B->P.Z;
+    na.mp_c = B->mp_c;
+    na.mp_a = B->mp_a;
+    na.mp_b = B->mp_b;
+    na.r = B->r;
+    na.fT = B->T.f;
+    na.fP = B->P.f;
+    na.s = B->s;
+    na.ws = B->ws;
+    na.tau = B->tau;
+    na.wtau = B->wtau;
+    na.inv_den = B->inv_den;
+    na.node = node;
+    na.node_doubles = L.node_doubles;
+    na.w_off = precision == 0 ? L.w_off : L.w_off_f;
+    na.N_T = B->N_T;
+    na.n_half = B->n_half;
+    na.stT_index = B->T.st_index;
+    na.half_of = B->half_of;
+    na.radT_l = B->T.rad_l;
+    na.radP_l = B->P.rad_l;
+    cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
+    if (precision == 0) k_node_tables<double><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
+    else k_node_tables<float><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
+    WPCCC_CHECK_LAUNCH("k_node_tables");
+    B->prof.end(PROF_NODES, st, e0);
+    return WPCCC_OK;
+}
 
+wpccc_status launch_node_stage(wpccc_basis_s* B, const EvalDesc* evals, int nev, void* scratch, cudaStream_t st) {
+    if (nev <= 0) return WPCCC_OK;
+    return launch_tables(B, evals, nev, scratch, st, 0);
+}
+
+wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, double2* S,
+                             double2* H, void* scratch, cudaStream_t st, int precision) {
+    if (nev <= 0) return WPCCC_OK;
+    const bool two = B->n_centres == 2;
+    if (two && B->mp_c != 0.0 && precision != 0)
+        return fail(WPCCC_EUNSUPPORTED, "model-potential targets need FP64 elements (precision mode 0 or 2)");
+    const ElemScratch L = elem_scratch_layout(B);
+    double* node = static_cast<double*>(scratch);
+    double2* mol = reinterpret_cast<double2*>(node + L.node_doubles * nev);
+    double* et = reinterpret_cast<double*>(mol + L.mol_elems * nev);
+    wpccc_status ts = launch_tables(B, evals, nev, scratch, st, precision);
+    if (ts != WPCCC_OK) return ts;
+    if (two) {
         GemmArgs ga;
         ga.G = B->G;
         ga.N_T = B->N_T;
@@ -1027,7 +1085,7 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         ga.w_off = precision == 0 ? L.w_off : L.w_off_f;
         ga.mol = mol;
         const int n_row_tiles = (B->N_T + GT_I - 1) / GT_I;
-        e0 = B->prof.begin(PROF_MOL, st);
+        cudaEvent_t e0 = B->prof.begin(PROF_MOL, st);
         if (precision == 0) {
             const size_t gsm = (size_t)GT_K * (GT_I + 1 + GT_J + 1) * sizeof(double) +
                                (size_t)NX * (B->dmax + 1) * GT_K * sizeof(double2);
@@ -1111,6 +1169,44 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
     k_direct<<<dim3((unsigned)((cells + 255) / 256), nev, two ? 2 : 1), 256, 0, st>>>(d0, d1, evals);
     WPCCC_CHECK_LAUNCH("k_direct");
     B->prof.end(PROF_ROT_DIRECT, st, ed);
+    if (two && B->mp_c != 0.0) {
+        SrArgs sa;
+        sa.G = B->G;
+        sa.Gtau = B->Gtau;
+        sa.nradT = B->T.n_rad;
+        sa.nradP = B->P.n_rad;
+        sa.lmaxP = B->P.lmax;
+        sa.nlqT = B->nlq_T;
+        sa.N_T = B->N_T;
+        sa.N_P = B->N_P;
+        sa.N = B->N;
+        sa.dtot = L.dtot;
+        sa.gamma = B->gamma;
+        sa.mp_c = B->mp_c;
+        sa.mp_a = B->mp_a;
+        sa.mp_b = B->mp_b;
+        sa.s = B->s;
+        sa.ws = B->ws;
+        sa.tau = B->tau;
+        sa.wtau = B->wtau;
+        sa.node = node;
+        sa.node_doubles = L.node_doubles;
+        sa.et = et;
+        sa.et_doubles = L.et_doubles;
+        sa.radP_l = B->P.rad_l;
+        sa.stP_index = B->P.st_index;
+        sa.stP_rad = B->P.st_rad;
+        sa.stP_m = B->P.st_m;
+        sa.epsP = B->P.st_eps;
+        sa.H = H;
+        sa.mat = (size_t)B->N * B->N;
+        const size_t srsm = ((size_t)B->G + (size_t)B->P.n_rad * (B->P.lmax + 1) + L.dtot) * sizeof(double);
+        WPCCC_CUDA(cudaFuncSetAttribute(k_direct_sr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)srsm));
+        ed = B->prof.begin(PROF_ROT_DIRECT, st);
+        k_direct_sr<<<dim3(B->P.n_rad, nev), 256, srsm, st>>>(sa, evals);
+        WPCCC_CHECK_LAUNCH("k_direct_sr");
+        B->prof.end(PROF_ROT_DIRECT, st, ed);
+    }
     return WPCCC_OK;
 }
 

@@ -11,11 +11,10 @@
 #include <cmath>
 #include <vector>
 
+#include "rk_device.cuh"
 #include "wpccc_internal.cuh"
 
 namespace wpccc {
-
-wpccc_status ensure_workspace(wpccc_basis_s* B, size_t bytes);
 
 struct PathChunk {
     int path;
@@ -28,186 +27,6 @@ struct PathChunk {
 };
 
 enum : int { FLAG_SINGULAR = 1, FLAG_NONFINITE = 2 };
-
-constexpr int RK_THREADS = 512;
-
-// k = -(i/v) X y   (X column-major N x N)
-__device__ inline void apply_X(const double2* __restrict__ X, int N, double v, const double2* y, double2* k) {
-    for (int i = threadIdx.x; i < N; i += RK_THREADS) {
-        double re = 0.0, im = 0.0;
-        const double2* row = X + i;
-        for (int j = 0; j < N; ++j) {
-            const double2 a = row[(size_t)j * N];
-            const double2 b = y[j];
-            re = fma(a.x, b.x, re);
-            re = fma(-a.y, b.y, re);
-            im = fma(a.x, b.y, im);
-            im = fma(a.y, b.x, im);
-        }
-        // -(i/v) (re + i im) = (im - i re)/v
-        k[i] = make_double2(im / v, -re / v);
-    }
-    __syncthreads();
-}
-
-// t <- S^{-1} t in place from the factors P S = L U (LAPACK layout, pivots 1-based);
-// C2 = double2 (FP64 factors) or float2 (FP32 factors of the mixed-precision form).
-// Blocked by 32 rows: each 32 x 32 diagonal block is staged in shared memory (blk) and solved by
-// one warp; the off-diagonal updates run on every thread.
-template <typename C2>
-__device__ void lu_solve_inplace(const C2* __restrict__ LU, const int* __restrict__ piv, int N, C2* t, C2* blk) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0)
-        for (int r = 0; r < N; ++r) {
-            const int p = piv[r] - 1;
-            if (p != r) {
-                const C2 q = t[r];
-                t[r] = t[p];
-                t[p] = q;
-            }
-        }
-    // L z = P t, unit lower triangular
-    for (int kb = 0; kb < N; kb += 32) {
-        const int nb = min(32, N - kb);
-        for (int q = tid; q < 32 * 32; q += RK_THREADS) {
-            const int i = q & 31, j = q >> 5;
-            if (i < nb && j < nb) blk[q] = LU[(size_t)(kb + i) + (size_t)(kb + j) * N];
-        }
-        __syncthreads();
-        if (warp == 0) {
-            C2 x = t[kb + (lane < nb ? lane : 0)];
-            for (int j = 0; j < nb - 1; ++j) {
-                const auto xr = __shfl_sync(0xffffffffu, x.x, j);
-                const auto xi = __shfl_sync(0xffffffffu, x.y, j);
-                if (lane > j && lane < nb) {
-                    const C2 l = blk[j * 32 + lane];
-                    x.x = fma(-l.x, xr, x.x);
-                    x.x = fma(l.y, xi, x.x);
-                    x.y = fma(-l.x, xi, x.y);
-                    x.y = fma(-l.y, xr, x.y);
-                }
-            }
-            if (lane < nb) t[kb + lane] = x;
-        }
-        __syncthreads();
-        for (int i = kb + nb + tid; i < N; i += RK_THREADS) {
-            C2 a = t[i];
-            for (int j = 0; j < nb; ++j) {
-                const C2 l = LU[(size_t)i + (size_t)(kb + j) * N];
-                const C2 b = t[kb + j];
-                a.x = fma(-l.x, b.x, a.x);
-                a.x = fma(l.y, b.y, a.x);
-                a.y = fma(-l.x, b.y, a.y);
-                a.y = fma(-l.y, b.x, a.y);
-            }
-            t[i] = a;
-        }
-        __syncthreads();
-    }
-    // U x = z, upper triangular, from the bottom
-    const int last = ((N - 1) / 32) * 32;
-    for (int kb = last; kb >= 0; kb -= 32) {
-        const int nb = min(32, N - kb);
-        for (int q = tid; q < 32 * 32; q += RK_THREADS) {
-            const int i = q & 31, j = q >> 5;
-            if (i < nb && j < nb) blk[q] = LU[(size_t)(kb + i) + (size_t)(kb + j) * N];
-        }
-        __syncthreads();
-        if (warp == 0) {
-            C2 x = t[kb + (lane < nb ? lane : 0)];
-            for (int j = nb - 1; j >= 0; --j) {
-                if (lane == j) {
-                    const C2 u = blk[j * 32 + j];
-                    const auto d = u.x * u.x + u.y * u.y;
-                    const auto ir = u.x / d, ii = -u.y / d;
-                    const auto xr0 = x.x;
-                    x.x = x.x * ir - x.y * ii;
-                    x.y = xr0 * ii + x.y * ir;
-                }
-                const auto xr = __shfl_sync(0xffffffffu, x.x, j);
-                const auto xi = __shfl_sync(0xffffffffu, x.y, j);
-                if (lane < j) {
-                    const C2 u = blk[j * 32 + lane];
-                    x.x = fma(-u.x, xr, x.x);
-                    x.x = fma(u.y, xi, x.x);
-                    x.y = fma(-u.x, xi, x.y);
-                    x.y = fma(-u.y, xr, x.y);
-                }
-            }
-            if (lane < nb) t[kb + lane] = x;
-        }
-        __syncthreads();
-        for (int i = tid; i < kb; i += RK_THREADS) {
-            C2 a = t[i];
-            for (int j = 0; j < nb; ++j) {
-                const C2 u = LU[(size_t)i + (size_t)(kb + j) * N];
-                const C2 b = t[kb + j];
-                a.x = fma(-u.x, b.x, a.x);
-                a.x = fma(u.y, b.y, a.x);
-                a.y = fma(-u.x, b.y, a.y);
-                a.y = fma(-u.y, b.x, a.y);
-            }
-            t[i] = a;
-        }
-        __syncthreads();
-    }
-}
-
-// out = M y (FP64 matvec, M column-major N x N); out = b - M y when `residual` (b given).
-__device__ inline void matvec(const double2* __restrict__ M, int N, const double2* y, double2* out,
-                              const double2* b = nullptr) {
-    for (int i = threadIdx.x; i < N; i += RK_THREADS) {
-        double re = 0.0, im = 0.0;
-        const double2* row = M + i;
-        for (int j = 0; j < N; ++j) {
-            const double2 a = row[(size_t)j * N];
-            const double2 q = y[j];
-            re = fma(a.x, q.x, re);
-            re = fma(-a.y, q.y, re);
-            im = fma(a.x, q.y, im);
-            im = fma(a.y, q.x, im);
-        }
-        out[i] = b ? make_double2(b[i].x - re, b[i].y - im) : make_double2(re, im);
-    }
-    __syncthreads();
-}
-
-// k = -(i/v) S^{-1} (H y) with S given by its FP64 LU factors.  t: shared scratch of N.
-__device__ void apply_LU(const double2* __restrict__ LU, const int* __restrict__ piv,
-                         const double2* __restrict__ Hm, int N, double v, const double2* y, double2* k,
-                         double2* t, double2* blk) {
-    matvec(Hm, N, y, t);
-    lu_solve_inplace<double2>(LU, piv, N, t, blk);
-    for (int i = threadIdx.x; i < N; i += RK_THREADS) k[i] = make_double2(t[i].y / v, -t[i].x / v);
-    __syncthreads();
-}
-
-// Mixed-precision form: k = -(i/v) x with S x = H y solved by FP64 iterative refinement
-// preconditioned by FP32 factors: x_0 = 0, r = H y - S x_n (FP64), x_{n+1} = x_n + (LU_32)^{-1} r.
-// Shared scratch: b, x, r (double2) and d (float2), N each.
-__device__ void apply_LU_mixed(const double2* __restrict__ S64, const float2* __restrict__ LU32,
-                               const int* __restrict__ piv, const double2* __restrict__ Hm, int N, double v,
-                               int iters, const double2* y, double2* k, double2* b, double2* x, double2* r,
-                               float2* d, float2* blk) {
-    matvec(Hm, N, y, b);
-    for (int it = 0; it < iters; ++it) {
-        const double2* rr = b;
-        if (it > 0) {
-            matvec(S64, N, x, r, b);
-            rr = r;
-        }
-        for (int i = threadIdx.x; i < N; i += RK_THREADS) d[i] = make_float2((float)rr[i].x, (float)rr[i].y);
-        __syncthreads();
-        lu_solve_inplace<float2>(LU32, piv, N, d, blk);
-        for (int i = threadIdx.x; i < N; i += RK_THREADS) {
-            const double2 dx = make_double2((double)d[i].x, (double)d[i].y);
-            x[i] = it == 0 ? dx : make_double2(x[i].x + dx.x, x[i].y + dx.y);
-        }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < N; i += RK_THREADS) k[i] = make_double2(x[i].y / v, -x[i].x / v);
-    __syncthreads();
-}
 
 struct RkArgs {
     int N;
@@ -417,6 +236,8 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
                                size_t ws_limit, PropPlan& P) {
     if (precision_mode < 0 || precision_mode > 2)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: precision_mode must be 0, 1 or 2");
+    if (precision_mode == 1 && B->n_centres == 2 && B->mp_c != 0.0)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: model-potential targets need FP64 elements (mode 0 or 2)");
     const int np = paths->n_paths;
     if (np < 1 || !paths->b || !paths->v || !paths->n_z || !paths->z)
         return fail(WPCCC_EINVAL, "wpccc_propagate: empty or null path description");
@@ -666,11 +487,10 @@ static wpccc_status basis_streams(wpccc_basis_s* B) {
 
 }  // namespace wpccc
 
-extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths, int precision_mode,
-                                        int batch_mode, void* c, void* stream) {
-    if (!B || !paths || !c) return fail(WPCCC_EINVAL, "wpccc_propagate: null argument");
-    if (batch_mode != 0) return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: only batch_mode 0");
-    WPCCC_CUDA(cudaSetDevice(B->device));
+namespace wpccc {
+
+wpccc_status propagate_internal(wpccc_basis_s* B, const wpccc_paths* paths, int precision_mode, double2* c,
+                                cudaStream_t st) {
     PropPlan P;
     wpccc_status s = plan_build(B, paths, precision_mode, 0, B->ws_limit, P);
     if (s != WPCCC_OK) return s;
@@ -678,17 +498,26 @@ extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths,
     if ((s = ensure_workspace(B, P.bytes)) != WPCCC_OK) return s;
     plan_bind(P, B->ws_ptr);
     if ((s = basis_streams(B)) != WPCCC_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((s = plan_upload(P, st)) != WPCCC_OK) return s;
     PlanStreams S{st, B->rk_stream, {B->ev_asm[0], B->ev_asm[1]}, {B->ev_rk[0], B->ev_rk[1]}, B->ev_fork,
                   B->ev_join};
-    if ((s = plan_enqueue(P, static_cast<double2*>(c), S)) != WPCCC_OK) return s;
+    if ((s = plan_enqueue(P, c, S)) != WPCCC_OK) return s;
     int flags = 0;
     WPCCC_CUDA(cudaMemcpyAsync(&flags, P.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     WPCCC_CUDA(cudaStreamSynchronize(st));
     s = flags_status(flags);
     if (s != WPCCC_OK) set_error(std::string("wpccc_propagate: ") + wpccc_last_error());
     return s;
+}
+
+}  // namespace wpccc
+
+extern "C" wpccc_status wpccc_propagate(wpccc_basis B, const wpccc_paths* paths, int precision_mode,
+                                        int batch_mode, void* c, void* stream) {
+    if (!B || !paths || !c) return fail(WPCCC_EINVAL, "wpccc_propagate: null argument");
+    if (batch_mode != 0) return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: only batch_mode 0");
+    WPCCC_CUDA(cudaSetDevice(B->device));
+    return propagate_internal(B, paths, precision_mode, static_cast<double2*>(c), static_cast<cudaStream_t>(stream));
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,171 @@
+// Device helpers shared by the RK4 kernels of the propagation and of its adjoint: the FP64 matrix-vector
+// product, the triangular solves with LAPACK-layout LU factors, and the stage operator -(i/v) S^{-1} H.
+// Every helper is called by all RK_THREADS threads of a block and ends with a block barrier.
+#pragma once
+
+#include "wpccc_internal.cuh"
+
+namespace wpccc {
+
+constexpr int RK_THREADS = 512;
+
+// t <- S^{-1} t in place from the factors P S = L U (LAPACK layout, pivots 1-based);
+// C2 = double2 (FP64 factors) or float2 (FP32 factors of the mixed-precision form).
+// Blocked by 32 rows: each 32 x 32 diagonal block is staged in shared memory (blk) and solved by
+// one warp; the off-diagonal updates run on every thread.
+template <typename C2>
+static __device__ void lu_solve_inplace(const C2* __restrict__ LU, const int* __restrict__ piv, int N, C2* t, C2* blk) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0)
+        for (int r = 0; r < N; ++r) {
+            const int p = piv[r] - 1;
+            if (p != r) {
+                const C2 q = t[r];
+                t[r] = t[p];
+                t[p] = q;
+            }
+        }
+    // L z = P t, unit lower triangular
+    for (int kb = 0; kb < N; kb += 32) {
+        const int nb = min(32, N - kb);
+        for (int q = tid; q < 32 * 32; q += RK_THREADS) {
+            const int i = q & 31, j = q >> 5;
+            if (i < nb && j < nb) blk[q] = LU[(size_t)(kb + i) + (size_t)(kb + j) * N];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            C2 x = t[kb + (lane < nb ? lane : 0)];
+            for (int j = 0; j < nb - 1; ++j) {
+                const auto xr = __shfl_sync(0xffffffffu, x.x, j);
+                const auto xi = __shfl_sync(0xffffffffu, x.y, j);
+                if (lane > j && lane < nb) {
+                    const C2 l = blk[j * 32 + lane];
+                    x.x = fma(-l.x, xr, x.x);
+                    x.x = fma(l.y, xi, x.x);
+                    x.y = fma(-l.x, xi, x.y);
+                    x.y = fma(-l.y, xr, x.y);
+                }
+            }
+            if (lane < nb) t[kb + lane] = x;
+        }
+        __syncthreads();
+        for (int i = kb + nb + tid; i < N; i += RK_THREADS) {
+            C2 a = t[i];
+            for (int j = 0; j < nb; ++j) {
+                const C2 l = LU[(size_t)i + (size_t)(kb + j) * N];
+                const C2 b = t[kb + j];
+                a.x = fma(-l.x, b.x, a.x);
+                a.x = fma(l.y, b.y, a.x);
+                a.y = fma(-l.x, b.y, a.y);
+                a.y = fma(-l.y, b.x, a.y);
+            }
+            t[i] = a;
+        }
+        __syncthreads();
+    }
+    // U x = z, upper triangular, from the bottom
+    const int last = ((N - 1) / 32) * 32;
+    for (int kb = last; kb >= 0; kb -= 32) {
+        const int nb = min(32, N - kb);
+        for (int q = tid; q < 32 * 32; q += RK_THREADS) {
+            const int i = q & 31, j = q >> 5;
+            if (i < nb && j < nb) blk[q] = LU[(size_t)(kb + i) + (size_t)(kb + j) * N];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            C2 x = t[kb + (lane < nb ? lane : 0)];
+            for (int j = nb - 1; j >= 0; --j) {
+                if (lane == j) {
+                    const C2 u = blk[j * 32 + j];
+                    const auto d = u.x * u.x + u.y * u.y;
+                    const auto ir = u.x / d, ii = -u.y / d;
+                    const auto xr0 = x.x;
+                    x.x = x.x * ir - x.y * ii;
+                    x.y = xr0 * ii + x.y * ir;
+                }
+                const auto xr = __shfl_sync(0xffffffffu, x.x, j);
+                const auto xi = __shfl_sync(0xffffffffu, x.y, j);
+                if (lane < j) {
+                    const C2 u = blk[j * 32 + lane];
+                    x.x = fma(-u.x, xr, x.x);
+                    x.x = fma(u.y, xi, x.x);
+                    x.y = fma(-u.x, xi, x.y);
+                    x.y = fma(-u.y, xr, x.y);
+                }
+            }
+            if (lane < nb) t[kb + lane] = x;
+        }
+        __syncthreads();
+        for (int i = tid; i < kb; i += RK_THREADS) {
+            C2 a = t[i];
+            for (int j = 0; j < nb; ++j) {
+                const C2 u = LU[(size_t)i + (size_t)(kb + j) * N];
+                const C2 b = t[kb + j];
+                a.x = fma(-u.x, b.x, a.x);
+                a.x = fma(u.y, b.y, a.x);
+                a.y = fma(-u.x, b.y, a.y);
+                a.y = fma(-u.y, b.x, a.y);
+            }
+            t[i] = a;
+        }
+        __syncthreads();
+    }
+}
+
+// out = M y (FP64 matvec, M column-major N x N); out = b - M y when `residual` (b given).
+__device__ inline void matvec(const double2* __restrict__ M, int N, const double2* y, double2* out,
+                              const double2* b = nullptr) {
+    for (int i = threadIdx.x; i < N; i += RK_THREADS) {
+        double re = 0.0, im = 0.0;
+        const double2* row = M + i;
+        for (int j = 0; j < N; ++j) {
+            const double2 a = row[(size_t)j * N];
+            const double2 q = y[j];
+            re = fma(a.x, q.x, re);
+            re = fma(-a.y, q.y, re);
+            im = fma(a.x, q.y, im);
+            im = fma(a.y, q.x, im);
+        }
+        out[i] = b ? make_double2(b[i].x - re, b[i].y - im) : make_double2(re, im);
+    }
+    __syncthreads();
+}
+
+// k = -(i/v) S^{-1} (H y) with S given by its FP64 LU factors.  t: shared scratch of N.
+static __device__ void apply_LU(const double2* __restrict__ LU, const int* __restrict__ piv,
+                         const double2* __restrict__ Hm, int N, double v, const double2* y, double2* k,
+                         double2* t, double2* blk) {
+    matvec(Hm, N, y, t);
+    lu_solve_inplace<double2>(LU, piv, N, t, blk);
+    for (int i = threadIdx.x; i < N; i += RK_THREADS) k[i] = make_double2(t[i].y / v, -t[i].x / v);
+    __syncthreads();
+}
+
+// Mixed-precision form: k = -(i/v) x with S x = H y solved by FP64 iterative refinement
+// preconditioned by FP32 factors: x_0 = 0, r = H y - S x_n (FP64), x_{n+1} = x_n + (LU_32)^{-1} r.
+// Shared scratch: b, x, r (double2) and d (float2), N each.
+static __device__ void apply_LU_mixed(const double2* __restrict__ S64, const float2* __restrict__ LU32,
+                               const int* __restrict__ piv, const double2* __restrict__ Hm, int N, double v,
+                               int iters, const double2* y, double2* k, double2* b, double2* x, double2* r,
+                               float2* d, float2* blk) {
+    matvec(Hm, N, y, b);
+    for (int it = 0; it < iters; ++it) {
+        const double2* rr = b;
+        if (it > 0) {
+            matvec(S64, N, x, r, b);
+            rr = r;
+        }
+        for (int i = threadIdx.x; i < N; i += RK_THREADS) d[i] = make_float2((float)rr[i].x, (float)rr[i].y);
+        __syncthreads();
+        lu_solve_inplace<float2>(LU32, piv, N, d, blk);
+        for (int i = threadIdx.x; i < N; i += RK_THREADS) {
+            const double2 dx = make_double2((double)d[i].x, (double)d[i].y);
+            x[i] = it == 0 ? dx : make_double2(x[i].x + dx.x, x[i].y + dx.y);
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < N; i += RK_THREADS) k[i] = make_double2(x[i].y / v, -x[i].x / v);
+    __syncthreads();
+}
+
+}  // namespace wpccc

@@ -56,6 +56,16 @@ struct CentreDev {
     std::vector<int> h_rad_l, h_st_rad, h_st_m;
 };
 
+// Derivative tables of one centre (differentiation form), for the parameters whose tangent of this
+// centre's radial functions is not identically zero.
+struct CentreTan {
+    int n_tan = 0;
+    int par[WPCCC_MAX_PARAMS] = {};     // parameter of each stored table
+    int slot[WPCCC_MAX_PARAMS] = {};    // stored table of each parameter, or -1
+    double* df = nullptr;               // [n_tan][n_rad][Nr]
+    double* dF = nullptr;               // [n_tan][n_fent][Nr]: derivative of the Eq. 7 table
+};
+
 // Per-category launch counts and (optionally) event-timed device durations.
 struct Profiler {
     bool on = false;
@@ -102,6 +112,13 @@ struct wpccc_basis_s {
     size_t ws_bytes = 0;
     size_t ws_limit = (size_t)8 << 30;
     int solve_mode = WPCCC_SOLVE_STAGE;
+    // short-range part of a Li-like target potential, V_T(r) = -[Z_T + mp_c e^{-mp_a r}(1 + mp_b r)]/r
+    double mp_c = 0.0, mp_a = 0.0, mp_b = 0.0;
+    // differentiation form
+    int n_par = 0;
+    double dexp[WPCCC_MAX_PARAMS][4] = {};   // d(Z_P, mp_c, mp_a, mp_b)/d theta_p
+    double* deps = nullptr;                  // [n_par][N]: d eps_i / d theta_p per state
+    wpccc::CentreTan tanT, tanP;
     int refine_iters = 2;       // FP64 refinement iterations of the mixed-precision form
     // second stream of wpccc_propagate (RK4 sweeps overlap the next chunk's assembly) and its events
     cudaStream_t rk_stream = nullptr;
@@ -138,6 +155,17 @@ ElemScratch elem_scratch_layout(const wpccc_basis_s* B);
 // precision 0: FP64 throughout; 1: the Eq. 9 contraction on the FP32 pipe (mixed-precision form).
 wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev,
                              double2* S, double2* H, void* scratch, cudaStream_t st, int precision = 0);
+
+// Queue only the per-position tables of the element pipeline (k_eval_tables and, two-centre, the FP64
+// node tables) for `nev` evaluations into `scratch` (layout of elem_scratch_layout).
+wpccc_status launch_node_stage(wpccc_basis_s* B, const EvalDesc* evals, int nev, void* scratch, cudaStream_t st);
+
+// Body of wpccc_propagate (argument checks, plan, kernels, status) on caller-owned amplitudes.
+wpccc_status propagate_internal(wpccc_basis_s* B, const wpccc_paths* paths, int precision_mode, double2* c,
+                                cudaStream_t st);
+
+// Grows the basis-owned scratch buffer to at least `bytes`.
+wpccc_status ensure_workspace(wpccc_basis_s* B, size_t bytes);
 
 enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3, PROF_RK4 = 4 };
 
