@@ -61,6 +61,14 @@ CONFIG_DESC = ("two-centre p+H (Z_T=Z_P=1): hydrogenic n<=4 + 10 Coulomb wave-pa
                "v=1.5; 32 b uniform in [0.2,12]; z in [-50,50], h=0.1")
 
 
+CONFIG_DESC_LI = ("differentiation form: two-centre p + Li-like one-electron target, model potential "
+                  "V(r) = -[1 + 2 e^{-a r}(1 + b r)]/r with a, b drawn within 5% of (3.0, 1.5) (seed 0); target: "
+                  "box eigenstates n<=4 without the core 1s + 10 wave packets per l<=3 (k<=3); projectile "
+                  "hydrogen-like n<=4 + 10 wave packets per l<=3; all m, N = 379; 48x48 (eta,tau) nodes; v = 1.5; "
+                  "32 b uniform in [0.2,12]; z in [-50,50], h = 0.1; observables: capture and 2p excitation; "
+                  "theta = (Z_p, a, b)")
+
+
 def _reasons(mask: int) -> list:
     names = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
              0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
@@ -317,6 +325,178 @@ def run_batch(args) -> None:
         dist.destroy_process_group()
 
 
+def oracle_gradient_rate(basis, paths, gw, n_steps: int, path_index: int = 8) -> dict:
+    """The oracle's forward-mode gradient (every line of Algorithm 1 differentiated) on one path, a few
+    steps around z = 0, on the host cores."""
+    from oracle import wpccc_oracle as O
+    zg = paths.z[path_index]
+    k0 = zg.size // 2
+    seg = zg[k0:k0 + n_steps + 1]
+    b, v = float(paths.b[path_index]), float(paths.v[path_index])
+    t0 = time.perf_counter()
+    O.gradient(basis, b, v, seg, gw)
+    dt = time.perf_counter() - t0
+    return {"value": n_steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 path (b={b:.3f}), {n_steps} RK4 steps around z=0 with the forward-mode gradient of "
+                      f"two observables w.r.t. 3 parameters, {dt:.1f} s; numpy/LAPACK on the host cores"}
+
+
+def run_grad(args) -> None:
+    """Differentiation form: wpccc_propagate_adjoint (forward sweep with checkpoints, reverse sweep
+    with recomputation, element adjoint) on consecutive segments of the 32 paths, timed against the
+    plain FP64 propagation of the same segments; a sampled full-size check against central
+    differences of the GPU's own propagation."""
+    import torch
+    import wpccc_inputs as wi
+    import paper_2403_04252_gb300 as w
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    basis, paths = wi.li_inputs(seed=0)
+    gw = wi.observable_weights(basis)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_gradient_rate(basis, paths, gw, 3)
+    g = w.Basis(basis, device=local)
+    g.set_workspace_limit(int((args.workspace_gb or 16.0) * (1 << 30)))
+    n_paths = paths.n_paths if args.paths <= 0 else min(args.paths, paths.n_paths)
+    bs = paths.b[:n_paths]
+    zg = paths.z[0]
+    S = args.rk4_per_step if args.rk4_per_step != STEP_RK4 else 50
+    K = max(1, min(args.checkpoint_every, S))
+    n_seg = args.warmup + 2 * args.steps + 1
+    k0 = max(0, (zg.size - 1) // 2 - (n_seg * S) // 2)
+
+    def segment(k: int):
+        a = k0 + k * S
+        return zg[a:a + S + 1]
+    c = torch.zeros((n_paths, g.N), dtype=torch.complex128, device=dev)
+    c[:, 0] = 1.0
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        g.propagate_adjoint(bs, 1.5, segment(k), gw, checkpoint_every=K, c=c)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    g.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        _, P, J = g.propagate_adjoint(bs, 1.5, segment(args.warmup + k), gw, checkpoint_every=K, c=c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = g.profile_read()
+    g.profile_enable(False)
+    finite = bool(torch.isfinite(J).all().item())
+    # the plain FP64 form on the next segments
+    e0.record(stream)
+    for k in range(args.steps):
+        g.propagate(bs, 1.5, segment(args.warmup + args.steps + k), c=c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms, ms_fwd], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_fwd = float(t[0].item()), float(t[1].item())
+    units = n_paths * S
+    value = world * units * args.steps / (ms / 1e3)
+    # end to end: amplitudes from pinned host memory, observables and gradients back
+    c_host = torch.zeros((n_paths, g.N), dtype=torch.complex128).pin_memory()
+    c_host[:, 0] = 1.0
+    P_host = torch.empty((n_paths, gw.shape[0]), dtype=torch.float64).pin_memory()
+    J_host = torch.empty((n_paths, gw.shape[0], g.n_par), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        c.copy_(c_host, non_blocking=True)
+        _, P, J = g.propagate_adjoint(bs, 1.5, segment(args.warmup + k), gw, checkpoint_every=K, c=c)
+        P_host.copy_(P, non_blocking=True)
+        J_host.copy_(J, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    # sampled full-size check: one path, 20 steps around z = 0, against central differences
+    fd_check = None
+    if rank == 0 and not args.no_fd_check:
+        zs = zg[(zg.size - 1) // 2 - 10:(zg.size - 1) // 2 + 11]
+        bsel = [float(paths.b[8])]
+        _, _, Jc = g.propagate_adjoint(bsel, 1.5, zs, gw, checkpoint_every=7)
+        Jc = Jc.cpu().numpy()[0]
+        a0, b0 = basis.mp_a, basis.mp_b
+        th0 = (1.0, a0, b0)
+        fd_check = {"path": "b=%.3f, 20 RK4 steps around z=0" % bsel[0], "checkpoint_every": 7}
+        for h in (1e-5, 1e-4):
+            rel = []
+            for p in range(3):
+                vals = []
+                for sg in (1.0, -1.0):
+                    th = list(th0)
+                    th[p] += sg * h
+                    gb = w.Basis(wi.li_basis(Z_p=th[0], a=th[1], b=th[2]), device=local)
+                    cc = gb.propagate(bsel, 1.5, zs)
+                    vals.append((w.probabilities(cc).cpu().numpy() @ gw.T)[0])
+                    gb.close()
+                fd = (vals[0] - vals[1]) / (2 * h)
+                rel.append(float(np.max(np.abs(fd - Jc[:, p]) / np.maximum(np.abs(Jc[:, p]), 1e-300))))
+            fd_check[f"max_rel_diff_h{h:g}"] = dict(zip(("Z_p", "a", "b"), rel))
+        fd_check["dP_dtheta"] = {o: dict(zip(("Z_p", "a", "b"), map(float, Jc[i])))
+                                 for i, o in enumerate(("capture", "2p_excitation"))}
+    flops = {"mol_gemm": 0.0, "solve": 0.0}
+    n_half = int(sum(1 for m in basis.P.st_m if m >= 0))
+    # positions evaluated per call: the forward sweep (2 per step + 1 per segment) and the reverse sweep
+    evals = args.steps * n_paths * 2 * (2 * S + -(-S // K))
+    flops["mol_gemm"] = 8.0 * basis.T.N * n_half * basis.quad.G * evals
+    flops["solve"] = (8.0 / 3.0) * basis.N ** 3 * evals
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_f = dom if dom in flops else "mol_gemm"
+    achieved = flops[dom_f] / (prof[dom_f][0] / 1e3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CONFIG_DESC_LI, "paths": n_paths,
+                       "bench_step": f"wpccc_propagate_adjoint over {S} RK4 steps of each path (checkpoint every "
+                                     f"{K}): observables and their gradient w.r.t. (Z_p, a, b); consecutive "
+                                     "segments centred on z = 0",
+                       "form": "differentiation: forward sweep with checkpoints, reverse sweep recomputing S, H "
+                               "and LU per segment, adjoint RK4 and node-level adjoint of the element assembly",
+                       "l2": "inputs larger than L2 (S and H of one segment: ~15 GB)"},
+            "forms": {"adjoint": {"value": value, "ms_per_step": ms / args.steps},
+                      "plain_fp64_forward": {"value": world * units * args.steps / (ms_fwd / 1e3),
+                                             "ms_per_step": ms_fwd / args.steps}},
+            "adjoint_cost_vs_forward": ms / ms_fwd,
+            "gradient_finite": finite,
+            "fd_check": fd_check,
+            "kernel_ms": {k: v_[0] for k, v_ in prof.items()},
+            "roofline": {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm<double>", "solve": "k_lu_solve"}[dom_f],
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                         "dominant_category": dom},
+            "e2e": {"value": world * units * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": c_host.numel() * 16,
+                    "d2h_bytes_per_step": P_host.numel() * 8 + J_host.numel() * 8},
+            "gpu_launches": int(sum(n for _, n in prof.values())), "clocks": clocks}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,10 +507,15 @@ def main() -> None:
     ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all of the workload)")
     ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
     ap.add_argument("--solve-mode", default="stage", choices=["stage", "matrix"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v",
+                                                             "pLi_2c_grad"],
                     help="p_H_2c_n4l3: two-centre p + H (N = 380, 32 paths); C6_H_2c_n6l5: bare C6+ on H "
                          "(N = 1622, 16 paths); p_H_2c_batch6v: p + H at six speeds, N = 316..572, 64 paths "
-                         "each, all in one graph launch (batched form)")
+                         "each, all in one graph launch (batched form); pLi_2c_grad: p + Li-like model-potential "
+                         "target (N = 379, 32 paths), observables and their gradient by the adjoint "
+                         "(differentiation form)")
+    ap.add_argument("--checkpoint-every", type=int, default=25, help="pLi_2c_grad: RK4 steps per checkpoint")
+    ap.add_argument("--no-fd-check", action="store_true", help="pLi_2c_grad: skip the central-difference sample")
     ap.add_argument("--workspace-gb", type=float, default=0.0, help="0: 16 GB (p + H) or 96 GB (C6+ on H)")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "mixed-fp64-elements"],
                     help="auto: time plain FP64 and the reduced-precision forms, report the fastest form whose "
@@ -343,6 +528,9 @@ def main() -> None:
         return
     if args.workload == "p_H_2c_batch6v":
         run_batch(args)
+        return
+    if args.workload == "pLi_2c_grad":
+        run_grad(args)
         return
 
     import torch

@@ -289,17 +289,18 @@ WPCCC_API wpccc_status wpccc_basis_set_solve_mode(wpccc_basis basis, int mode);
 WPCCC_API wpccc_status wpccc_basis_set_workspace_limit(wpccc_basis basis, size_t bytes);
 
 /*
- * Kernel profiling of the work a basis queues (wpccc_matrix_elements and
- * wpccc_propagate): launches are always counted; when enabled, a pair of CUDA
+ * Kernel profiling of the work a basis queues (wpccc_matrix_elements,
+ * wpccc_propagate and wpccc_propagate_adjoint): launches are always counted; when enabled, a pair of CUDA
  * events on the caller's stream brackets every launch and the device time is
  * accumulated per category.  Categories (WPCCC_PROF_N of them):
  *   0 node tables (Eq. 9 integrand factors), 1 molecular-frame contraction (Eq. 9),
- *   2 rotation (Eq. 8) and direct elements (Eq. 6), 3 linear solve (Eq. 4), 4 RK4.
+ *   2 rotation (Eq. 8) and direct elements (Eq. 6), 3 linear solve (Eq. 4), 4 RK4,
+ *   5 the adjoint kernels of wpccc_propagate_adjoint (reverse RK4 and element adjoint).
  * wpccc_profile_enable resets the counters.  wpccc_profile_read waits for the
  * recorded events and writes ms[WPCCC_PROF_N] (milliseconds, NULL to skip) and
  * launches[WPCCC_PROF_N] (NULL to skip).
  */
-#define WPCCC_PROF_N 5
+#define WPCCC_PROF_N 6
 WPCCC_API wpccc_status wpccc_profile_enable(wpccc_basis basis, int on);
 WPCCC_API wpccc_status wpccc_profile_read(wpccc_basis basis, double* ms, long long* launches);
 

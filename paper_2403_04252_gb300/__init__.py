@@ -93,7 +93,7 @@ EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wp
 MAX_PARAMS = 4
 NOALLOC_SCRATCH_BYTES = 64 << 20
 SOLVE_STAGE, SOLVE_MATRIX = 0, 1
-PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4")
+PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4", "adjoint")
 
 
 class WpcccError(RuntimeError):
@@ -212,8 +212,8 @@ class Basis:
 
     def profile_read(self) -> dict:
         """{category: (milliseconds, launches)} accumulated since profile_enable."""
-        ms = (C.c_double * 5)()
-        n = (C.c_longlong * 5)()
+        ms = (C.c_double * len(PROF_CATEGORIES))()
+        n = (C.c_longlong * len(PROF_CATEGORIES))()
         _check(_lib.wpccc_profile_read(self._h, ms, n), "wpccc_profile_read")
         return {k: (ms[i], n[i]) for i, k in enumerate(PROF_CATEGORIES)}
 

@@ -936,8 +936,10 @@ static wpccc_status adjoint_group(wpccc_basis_s* B, const wpccc_paths* paths, in
         ra.deps = B->deps;
         ra.gphase = gphase;
         ra.flags = flags;
+        cudaEvent_t pa = B->prof.begin(PROF_ADJ, st);
         k_rk4_adjoint<<<(unsigned)slots.size(), RK_THREADS, adj_smem, st>>>(ra);
         WPCCC_CHECK_LAUNCH("k_rk4_adjoint");
+        B->prof.end(PROF_ADJ, st, pa);
         // element adjoint, sub-batch by sub-batch of positions
         size_t t0 = 0;
         for (int p0 = 0; p0 < npos; p0 += NB) {
@@ -949,6 +951,7 @@ static wpccc_status adjoint_group(wpccc_basis_s* B, const wpccc_paths* paths, in
             if ((s = launch_node_stage(B, d_ev + p0, nb, B->ws_ptr, st)) != WPCCC_OK) return s;
             // the per-position tables follow the node tables and the (unused) molecular-frame blocks
             double* et = node + EL.node_doubles * nb + EL.mol_elems * nb * 2;
+            cudaEvent_t pe = B->prof.begin(PROF_ADJ, st);
             TanNodeArgs tna;
             tna.Nr = B->Nr;
             tna.G = B->G;
@@ -1119,6 +1122,7 @@ static wpccc_status adjoint_group(wpccc_basis_s* B, const wpccc_paths* paths, in
             WPCCC_CHECK_LAUNCH("k_adj_direct");
             k_adj_combine<<<(nt * npar + 127) / 128, 128, 0, st>>>(nt, npar, n_tiles, d_terms + t0, part, bd, tg);
             WPCCC_CHECK_LAUNCH("k_adj_combine");
+            B->prof.end(PROF_ADJ, st, pe);
             h_tg.resize((size_t)nt * npar);
             WPCCC_CUDA(cudaMemcpyAsync(h_tg.data(), tg, h_tg.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
             WPCCC_CUDA(cudaStreamSynchronize(st));

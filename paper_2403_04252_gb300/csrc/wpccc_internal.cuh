@@ -167,7 +167,7 @@ wpccc_status propagate_internal(wpccc_basis_s* B, const wpccc_paths* paths, int 
 // Grows the basis-owned scratch buffer to at least `bytes`.
 wpccc_status ensure_workspace(wpccc_basis_s* B, size_t bytes);
 
-enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3, PROF_RK4 = 4 };
+enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3, PROF_RK4 = 4, PROF_ADJ = 5 };
 
 // Queue the batched FP32 factorisation P S = L U of FP64 matrices (mixed-precision form).
 wpccc_status launch_factor_f32(int N, int batch, const double2* S, float2* LU, int* ipiv, int* info,
