@@ -390,7 +390,7 @@ struct VecArgs {
     int N, N_T, N_P, n_obs, dtot, pos_first;
     const AdjTerm* terms;
     const double* et;
-    size_t et_doubles;
+    size_t et_doubles, ph_off;
     const double2 *rx, *rk, *rxi;
     const double *epsT, *epsP;
     const int *stT_rad, *stT_m, *radT_l, *stT_index;
@@ -404,15 +404,13 @@ __global__ void __launch_bounds__(256) k_adj_vec(VecArgs A) {
     const double2* src[3] = {A.rxi + (size_t)T.xi * N, A.rx + (size_t)T.rec * N, A.rk + (size_t)T.rec * N};
     double2* tv = A.tv + (size_t)blockIdx.x * 3 * N;
     double2* mv = A.mv + (size_t)blockIdx.x * 3 * N;
+    const double* d = A.et + (size_t)(T.pos - A.pos_first) * A.et_doubles;
+    const double2* ph = reinterpret_cast<const double2*>(d + A.ph_off);   // exp(i eps_i z / v)
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
         const int k = q / N, i = q - k * N;
-        const double eps = i < A.N_T ? A.epsT[i] : A.epsP[i - A.N_T];
-        double sp, cp;
-        sincos(-eps * T.z / T.v, &sp, &cp);
-        tv[q] = cmul(src[k][i], make_double2(cp, sp));
+        tv[q] = cmul(src[k][i], cconj(ph[i]));
     }
     __syncthreads();
-    const double* d = A.et + (size_t)(T.pos - A.pos_first) * A.et_doubles;
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
         const int k = q / N, i = q - k * N;
         const bool tgt = i < A.N_T;
@@ -1006,6 +1004,7 @@ static wpccc_status adjoint_group(wpccc_basis_s* B, const wpccc_paths* paths, in
             va.terms = d_terms + t0;
             va.et = et;
             va.et_doubles = EL.et_doubles;
+            va.ph_off = EL.ph_off;
             va.rx = rx;
             va.rk = rk;
             va.rxi = rxi;

@@ -31,6 +31,53 @@ namespace wpccc {
 constexpr int NX = 2;
 
 // ---------------------------------------------------------------------------
+// Bessel functions of the first kind J_0(x) .. J_dmax(x), x >= 0, all orders from one pass:
+//   x >= dmax       forward recurrence J_{n+1} = (2n/x) J_n - J_{n-1} from J_0, J_1 (stable while the
+//                   order stays below the argument);
+//   1e-5 <= x < dmax  Miller's backward recurrence (J. C. P. Miller; Abramowitz & Stegun 9.12): start
+//                   from f_{M+1} = 0, f_M = 1 at an order M well above x and dmax, recur downwards with
+//                   the same relation, rescale against overflow, and normalise by J_0 (or J_1 when that
+//                   is larger, so a zero of J_0 costs no accuracy);
+//   x < 1e-5        the first two terms of the power series, (x/2)^n/n! (1 - (x/2)^2/(n+1)).
+// J_0 and J_1 come from CUDA's j0 and j1.
+// ---------------------------------------------------------------------------
+constexpr int BESSEL_MAX = 2 * WPCCC_LMAX;
+
+__device__ inline void bessel_j_orders(int dmax, double x, double* J) {
+    if (x < 1e-5) {
+        const double h = 0.5 * x;
+        double t = 1.0;
+        for (int n = 0; n <= dmax; ++n) {
+            J[n] = t * (1.0 - h * h / (n + 1));
+            t *= h / (n + 1);
+        }
+        return;
+    }
+    const double j0v = j0(x), j1v = j1(x);
+    if (x >= (double)dmax) {
+        J[0] = j0v;
+        if (dmax >= 1) J[1] = j1v;
+        for (int n = 1; n < dmax; ++n) J[n + 1] = (2.0 * n / x) * J[n] - J[n - 1];
+        return;
+    }
+    const int M = dmax + 26 + (int)x;
+    double fn1 = 0.0, fn = 1.0;   // f_{n+1}, f_n
+    for (int n = M; n >= 1; --n) {
+        const double fm = (2.0 * n / x) * fn - fn1;   // f_{n-1}
+        fn1 = fn;
+        fn = fm;
+        if (n - 1 <= dmax) J[n - 1] = fm;
+        if (fabs(fn) > 1e200) {
+            fn *= 1e-200;
+            fn1 *= 1e-200;
+            for (int k = n - 1; k <= dmax; ++k) J[k] *= 1e-200;
+        }
+    }
+    const double scale = fabs(j0v) >= fabs(j1v) ? j0v / J[0] : j1v / J[1];
+    for (int n = 0; n <= dmax; ++n) J[n] *= scale;
+}
+
+// ---------------------------------------------------------------------------
 // k_node_tables
 // ---------------------------------------------------------------------------
 struct NodeArgs {
@@ -166,8 +213,10 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
     const double uQ = A.mp_c == 0.0 ? -A.Z_T / rT
                                     : -A.Z_T / rT + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT) / rT;
     const size_t stride = (size_t)(A.dmax + 1) * A.G;
+    double Jd[BESSEL_MAX + 1];
+    bessel_j_orders(A.dmax, x, Jd);
     for (int d = 0; d <= A.dmax; ++d) {
-        const double J = jn(d, x) * amp;
+        const double J = Jd[d] * amp;
         // (-i)^d exp(i phi)
         double re, im;
         switch (d & 3) {
@@ -575,6 +624,9 @@ size_t mol_gemm_f32q_smem(int dmax) {
 //   Wigner d^l_{m q}(theta) for l <= lrot      at [off_l + (m + l)(2l+1) + (q + l)]
 //   Pbar(lam, mu) = sqrt((lam-mu)!/(lam+mu)!) P_lam^mu(cos Theta), lam < nlam, at dtot + lam(lam+1)/2 + mu
 //   the 5-point stencil of Eq. 7's table at R: start, beyond-grid flag, Lagrange weights
+//   F of every Eq. 7 table entry at R
+//   the energy phase of every state, exp(i eps_i z / v), so that an element's phase
+//   exp(i (eps_i - eps_j) z / v) is one complex product
 // ---------------------------------------------------------------------------
 struct EtArgs {
     int lrot, nlam, Nr;
@@ -582,6 +634,9 @@ struct EtArgs {
     int nfT, nfP;            // Eq. 7 table entries of the two centres (F interpolated at R follows the stencil)
     const double *FT, *FP;
     const double* r;
+    int N_T, N;              // states (target first)
+    const double *epsT, *epsP;
+    size_t ph_off;
     double* et;              // [nev][et_doubles]
     size_t et_doubles;
 };
@@ -647,6 +702,14 @@ __global__ void __launch_bounds__(128) k_eval_tables(EtArgs A, const EvalDesc* _
         Fint[t] = Fv;
     }
     (void)ratio;
+    double2* ph = reinterpret_cast<double2*>(et + A.ph_off);
+    const double v = ev[e].v;
+    for (int i = threadIdx.x; i < A.N; i += blockDim.x) {
+        const double eps = i < A.N_T ? A.epsT[i] : A.epsP[i - A.N_T];
+        double sp, cp;
+        sincos(eps * z / v, &sp, &cp);
+        ph[i] = make_double2(cp, sp);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -657,7 +720,7 @@ struct RotArgs {
     int rot_block;            // complex entries of one warp's block: NX (2 lmax_T + 1)(2 lmax_P + 1)
     int dtot;                 // size of the Wigner-d part of the per-position tables
     const double* et;         // per-position tables (k_eval_tables)
-    size_t et_doubles;
+    size_t et_doubles, ph_off;
     const int *stT_rad, *stT_l, *stT_m, *stT_index;
     const int *stP_rad, *stP_l, *stP_m, *half_of, *stP_index;
     const int *radT_l, *radP_l;
@@ -744,9 +807,8 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
         }
         const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
         const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
-        double sp, cp;
-        sincos((A.epsT[i] - A.epsP[j]) * z / v, &sp, &cp);
-        const double2 ph = make_double2(cp, sp);
+        const double2* phs = reinterpret_cast<const double2*>(etd + A.ph_off);
+        const double2 ph = cmul(phs[i], cconj(phs[A.N_T + j]));
         const double2 K = cmul(make_double2(acc[0], acc[1]), ph);
         const double2 Q = cmul(make_double2(acc[2], acc[3]), ph);
         const size_t up = (size_t)i + (size_t)(A.N_T + j) * A.N;     // row i, column N_T + j
@@ -766,7 +828,7 @@ struct DirArgs {
     int dtot, npb;                // layout of the per-position tables
     int foff0;                    // first interpolated F entry of this centre in the per-position tables
     const double* et;
-    size_t et_doubles;
+    size_t et_doubles, ph_off;
     double Z_other, parity;       // parity = -1: the other nucleus sits at -R
     const double *r, *F, *ang, *eps;
     const int *Foff, *st_rad, *st_m;
@@ -819,10 +881,10 @@ __global__ void __launch_bounds__(256) k_direct(DirArgs A0, DirArgs A1, const Ev
         D += sgn * c * P * Fv;
     }
     D *= -A.Z_other;
-    double sp, cp;
-    sincos((A.eps[i] - A.eps[j]) * z / v, &sp, &cp);
+    const double2* phs = reinterpret_cast<const double2*>(et + A.ph_off);
+    const double2 ph = cmul(phs[A.off + i], cconj(phs[A.off + j]));
     const size_t o = (size_t)(A.off + i) + (size_t)(A.off + j) * A.N;
-    A.H[(size_t)e * A.mat + o] = make_double2(D * cp, D * sp);
+    A.H[(size_t)e * A.mat + o] = make_double2(D * ph.x, D * ph.y);
     if (A.S) A.S[(size_t)e * A.mat + o] = make_double2(i == j ? 1.0 : 0.0, 0.0);
 }
 
@@ -840,8 +902,8 @@ struct SrArgs {
     const double *s, *ws, *tau, *wtau;
     const double* node;        // FP64 node tables per evaluation
     size_t node_doubles;
-    const double* et;          // per-position tables (Wigner d first)
-    size_t et_doubles;
+    const double* et;          // per-position tables (Wigner d first, energy phases at ph_off)
+    size_t et_doubles, ph_off;
     const int *radP_l, *stP_index, *stP_rad, *stP_m;
     const double* epsP;
     double2* H;
@@ -908,11 +970,11 @@ __global__ void __launch_bounds__(256) k_direct_sr(SrArgs A, const EvalDesc* __r
             D = fma(da * db, I[bb * LQ + (q < 0 ? -q : q)], D);
         }
         const int i = A.stP_index[a * (2 * WPCCC_LMAX + 1) + mi + WPCCC_LMAX];
-        double sp, cp;
-        sincos((A.epsP[i] - A.epsP[j]) * z / v, &sp, &cp);
+        const double2* phs = reinterpret_cast<const double2*>(etd + A.ph_off);
+        const double2 ph = cmul(phs[A.N_T + i], cconj(phs[A.N_T + j]));
         const size_t o = (size_t)(A.N_T + i) + (size_t)(A.N_T + j) * A.N;
         const double2 h = H[o];
-        H[o] = make_double2(fma(D, cp, h.x), fma(D, sp, h.y));
+        H[o] = make_double2(fma(D, ph.x, h.x), fma(D, ph.y, h.y));
     }
 }
 
@@ -920,13 +982,15 @@ __global__ void __launch_bounds__(256) k_direct_sr(SrArgs A, const EvalDesc* __r
 // host side
 // ---------------------------------------------------------------------------
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
-    ElemScratch L{0, 0, 0, 0, 0, 0, 0, 0};
+    ElemScratch L{0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int lrot = std::max(B->T.lmax, B->n_centres == 2 ? B->P.lmax : 0);
     for (int l = 0; l <= lrot; ++l) L.dtot += (2 * l + 1) * (2 * l + 1);
     const int nlam = 2 * lrot + 1;
     L.npb = nlam * (nlam + 1) / 2;
     L.et_doubles = (size_t)L.dtot + L.npb + 8 + B->T.n_fent + (B->n_centres == 2 ? B->P.n_fent : 0);
     L.et_doubles += L.et_doubles & 1;
+    L.ph_off = L.et_doubles;
+    L.et_doubles += 2 * (size_t)B->N;
     if (B->n_centres == 2) {
         size_t nd = (size_t)(B->T.n_rad + B->P.n_rad + B->nlq_T + B->nlq_P) * B->G;
         nd += nd & 1;   // keep the complex weights 16-byte aligned
@@ -972,6 +1036,7 @@ static DirArgs dir_args(const wpccc_basis_s* B, const CentreDev& c, int off, dou
     a.npb = L.npb;
     a.et = nullptr;
     a.et_doubles = L.et_doubles;
+    a.ph_off = L.ph_off;
     return a;
 }
 
@@ -995,6 +1060,11 @@ static wpccc_status launch_tables(wpccc_basis_s* B, const EvalDesc* evals, int n
         ea.nfP = two ? B->P.n_fent : 0;
         ea.FT = B->T.F;
         ea.FP = two ? B->P.F : nullptr;
+        ea.N_T = B->N_T;
+        ea.N = B->N;
+        ea.epsT = B->T.st_eps;
+        ea.epsP = two ? B->P.st_eps : nullptr;
+        ea.ph_off = L.ph_off;
         ea.et = et;
         ea.et_doubles = L.et_doubles;
         cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
@@ -1145,6 +1215,7 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         ra.dtot = L.dtot;
         ra.et = et;
         ra.et_doubles = L.et_doubles;
+        ra.ph_off = L.ph_off;
         const size_t per_warp = (size_t)2 * ra.rot_block * sizeof(double2);
         const size_t dbytes = (size_t)((dtot + 1) & ~1) * sizeof(double);
         int rwarps = (int)std::min<size_t>(ROT_WARPS_MAX, ((size_t)200 * 1024 - dbytes) / per_warp);
@@ -1193,6 +1264,7 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         sa.node_doubles = L.node_doubles;
         sa.et = et;
         sa.et_doubles = L.et_doubles;
+        sa.ph_off = L.ph_off;
         sa.radP_l = B->P.rad_l;
         sa.stP_index = B->P.st_index;
         sa.stP_rad = B->P.st_rad;

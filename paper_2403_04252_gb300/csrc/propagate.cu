@@ -30,6 +30,7 @@ enum : int { FLAG_SINGULAR = 1, FLAG_NONFINITE = 2 };
 
 struct RkArgs {
     int N;
+    int N_T;                // target states (two-centre: S = [[I, K], [K^+, I]])
     int iters;              // refinement iterations (mixed-precision form)
     const float2* LU32;     // chunk: FP32 factors per evaluation (mixed form)
     float2* carryLU32;      // per path (mixed form)
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
         } else if (MODE == RK_STAGE) {
             apply_LU(m.S, m.piv, m.H, N, v, in, out, t, static_cast<double2*>(blk));
         } else {
-            apply_LU_mixed(m.S, m.L32, m.piv, m.H, N, v, A.iters, in, out, t, xs, rs, ds, static_cast<float2*>(blk));
+            apply_LU_mixed(m.S, m.L32, m.piv, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds,
+                           static_cast<float2*>(blk));
         }
     };
     PosMats Mz;
@@ -413,6 +415,7 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     const size_t hL = P.sz_LU32 / 2 / sizeof(float2), hP = P.sz_piv / 2 / sizeof(int), hI = P.sz_info / 2 / sizeof(int);
     RkArgs ra;
     ra.N = N;
+    ra.N_T = B->N_T;
     ra.iters = B->refine_iters;
     ra.carryH = P.d_carry;
     ra.carryLU = P.d_carryLU;

@@ -131,6 +131,27 @@ __device__ inline void matvec(const double2* __restrict__ M, int N, const double
     __syncthreads();
 }
 
+// out = b - S y for S = [[I, K], [K^+, I]] (two-centre overlap, FP64, column-major): only the
+// off-diagonal blocks are read, rows i < N_T against columns j >= N_T and the other way round.
+__device__ inline void residual_S(const double2* __restrict__ S, int N, int N_T, const double2* y, const double2* b,
+                                  double2* out) {
+    for (int i = threadIdx.x; i < N; i += RK_THREADS) {
+        double re = 0.0, im = 0.0;
+        const int j0 = i < N_T ? N_T : 0, j1 = i < N_T ? N : N_T;
+        const double2* row = S + i;
+        for (int j = j0; j < j1; ++j) {
+            const double2 a = row[(size_t)j * N];
+            const double2 q = y[j];
+            re = fma(a.x, q.x, re);
+            re = fma(-a.y, q.y, re);
+            im = fma(a.x, q.y, im);
+            im = fma(a.y, q.x, im);
+        }
+        out[i] = make_double2(b[i].x - y[i].x - re, b[i].y - y[i].y - im);
+    }
+    __syncthreads();
+}
+
 // k = -(i/v) S^{-1} (H y) with S given by its FP64 LU factors.  t: shared scratch of N.
 static __device__ void apply_LU(const double2* __restrict__ LU, const int* __restrict__ piv,
                          const double2* __restrict__ Hm, int N, double v, const double2* y, double2* k,
@@ -145,14 +166,14 @@ static __device__ void apply_LU(const double2* __restrict__ LU, const int* __res
 // preconditioned by FP32 factors: x_0 = 0, r = H y - S x_n (FP64), x_{n+1} = x_n + (LU_32)^{-1} r.
 // Shared scratch: b, x, r (double2) and d (float2), N each.
 static __device__ void apply_LU_mixed(const double2* __restrict__ S64, const float2* __restrict__ LU32,
-                               const int* __restrict__ piv, const double2* __restrict__ Hm, int N, double v,
+                               const int* __restrict__ piv, const double2* __restrict__ Hm, int N, int N_T, double v,
                                int iters, const double2* y, double2* k, double2* b, double2* x, double2* r,
                                float2* d, float2* blk) {
     matvec(Hm, N, y, b);
     for (int it = 0; it < iters; ++it) {
         const double2* rr = b;
         if (it > 0) {
-            matvec(S64, N, x, r, b);
+            residual_S(S64, N, N_T, x, b, r);
             rr = r;
         }
         for (int i = threadIdx.x; i < N; i += RK_THREADS) d[i] = make_float2((float)rr[i].x, (float)rr[i].y);

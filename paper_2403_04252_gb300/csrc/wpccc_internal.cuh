@@ -143,7 +143,8 @@ struct ElemScratch {
     size_t w_off_f;        // the same in the FP32 layout of the mixed-precision form (floats, even)
     size_t mol_elems;      // molecular-frame integrals per evaluation (complex)
     size_t bytes_per_eval;
-    size_t et_doubles;     // small per-position tables (Wigner d, Legendre, stencil), even
+    size_t et_doubles;     // small per-position tables (Wigner d, Legendre, stencil, F at R, phases), even
+    size_t ph_off;         // offset of the per-state energy phases exp(i eps_i z / v) (complex, N of them)
     int dtot, npb;         // sizes of their Wigner-d and Legendre parts
 };
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B);
