@@ -188,6 +188,18 @@ WPCCC_API wpccc_status wpccc_matrix_elements(wpccc_basis basis, double b, double
  * position needs more scratch than the array holds; the message states both
  * sizes), ECUDA.  The basis itself must have been created beforehand.
  */
+/*
+ * wpccc_matrix_elements with the element arithmetic of a reduced-precision form, to measure its element
+ * error against the FP64 elements (the paper has no counterpart):
+ *   precision_mode 0 FP64 (= wpccc_matrix_elements), 1 the Eq. 9 contraction on the FP32 pipe,
+ *   3 the Eq. 9 contraction on the tensor cores (see wpccc_propagate).  S and H are returned in FP64.
+ * Errors: as wpccc_matrix_elements; EUNSUPPORTED for other modes, one-centre bases or model-potential
+ * targets in modes 1 and 3.
+ */
+WPCCC_API wpccc_status wpccc_matrix_elements_precision(wpccc_basis basis, double b, double v, int nz,
+                                                       const double* z, void* S, void* H, int precision_mode,
+                                                       void* stream);
+
 #define WPCCC_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 WPCCC_API wpccc_status wpccc_matrix_elements_noalloc(wpccc_basis basis, double b, double v, int nz,
                                                      const double* z, void* S, void* H, void* stream);
@@ -224,6 +236,10 @@ WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv
  *        against the FP64 S), RK4 amplitudes in FP64;
  *     2  mixed with FP64 elements: as 1 but the contraction stays in FP64 (for
  *        ill-conditioned S, where FP32 element errors get amplified by cond(S));
+ *     3  as 1 with the Eq. 9 contraction on the 5th-generation tensor cores: tcgen05.mma
+ *        (kind::f16) on three-part bf16 splits of both operands (six products, FP32-level
+ *        products), FP32 accumulation drained every 32 nodes into compensated sums; operand
+ *        tiles staged by TMA; needs at most 64 target states per molecular-frame projection;
  *     in one-centre mode all three are the FP64 form (no contraction, no solve).
  *   batch_mode 0 = all paths batched together in chunks of RK4 steps (the only
  *   batch mode of this build).

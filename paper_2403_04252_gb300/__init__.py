@@ -74,6 +74,8 @@ _lib.wpccc_batch_launch.argtypes = [C.c_void_p, C.c_void_p]
 _lib.wpccc_batch_status.argtypes = [C.c_void_p, C.c_void_p]
 _lib.wpccc_batch_info.argtypes = [C.c_void_p, _pi, _pd]
 _lib.wpccc_batch_destroy.argtypes = [C.c_void_p]
+_lib.wpccc_matrix_elements_precision.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, _pd,
+                                                 C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 _lib.wpccc_basis_set_tangents.argtypes = [C.c_void_p, C.c_int, _pd, _pd, _pd, _pd, _pd]
 _lib.wpccc_propagate_adjoint.argtypes = [C.c_void_p, C.POINTER(_PathsDesc), C.c_int, _pd, C.c_int, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]
@@ -82,14 +84,16 @@ for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpc
            "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode",
            "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
-           "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint"):
+           "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
+           "wpccc_matrix_elements_precision"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
             "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
             "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error",
             "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
-            "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint")
+            "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
+            "wpccc_matrix_elements_precision")
 MAX_PARAMS = 4
 NOALLOC_SCRATCH_BYTES = 64 << 20
 SOLVE_STAGE, SOLVE_MATRIX = 0, 1
@@ -228,6 +232,21 @@ class Basis:
             H = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
         _check(_lib.wpccc_matrix_elements(self._h, float(b), float(v), int(z.size), zp, _ptr(S), _ptr(H),
                                           _stream(stream)), "wpccc_matrix_elements")
+        return S, H
+
+    def matrix_elements_precision(self, b: float, v: float, z, precision_mode: int, S=None, H=None, stream=None):
+        """S, H with the element arithmetic of a reduced-precision form (0 FP64, 1 FP32 contraction,
+        3 tensor-core contraction), returned in FP64 (``wpccc_matrix_elements_precision``)."""
+        import torch
+        z, zp = _arr(np.atleast_1d(z), np.float64)
+        dev = torch.device("cuda", self.device)
+        if S is None:
+            S = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
+        if H is None:
+            H = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
+        _check(_lib.wpccc_matrix_elements_precision(self._h, float(b), float(v), int(z.size), zp, _ptr(S), _ptr(H),
+                                                    int(precision_mode), _stream(stream)),
+               "wpccc_matrix_elements_precision")
         return S, H
 
     def matrix_elements_noalloc(self, b: float, v: float, z, S, H, stream=None):

@@ -306,7 +306,8 @@ static void free_basis(wpccc_basis_s* B) {
         if (e) cudaEventDestroy(e);
     free_centre(B->T);
     free_centre(B->P);
-    void* tptrs[] = {B->tanT.df, B->tanT.dF, B->tanP.df, B->tanP.dF, B->deps};
+    void* tptrs[] = {B->tanT.df, B->tanT.dF, B->tanP.df, B->tanP.dF, B->deps, B->tc_row, B->qg_off, B->qg_rows,
+                     B->tc_err, B->tc_halfq};
     for (void* p : tptrs)
         if (p) cudaFree(p);
     void* ptrs[] = {B->r, B->w, B->inv_den, B->s, B->ws, B->tau, B->wtau, B->half_state, B->half_of, B->qtile_q,

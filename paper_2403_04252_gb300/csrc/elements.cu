@@ -20,6 +20,8 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "angular.cuh"
 #include "geometry.cuh"
 #include "wpccc_internal.cuh"
@@ -92,6 +94,11 @@ struct NodeArgs {
     // T = float: per-state products instead of per-radial values (one rounding of f * Theta * sign)
     int N_T, n_half;
     const int *stT_index, *half_of, *radT_l, *radP_l;
+    // tensor-core layout (T = float): split tables instead of the per-state A_T
+    int tc;
+    const int* tc_row;          // [2 N_T]: row of each target state in a split table, then its group's size
+    int tc_rows;
+    size_t tc_ap_off, tc_w_off, tc_sc_off;
 };
 
 template <typename T> struct Vec2;
@@ -178,6 +185,68 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         }
         for (int t = 0; t < A.nlqT; ++t) thT[(size_t)t * A.G + g] = (T)thv[0][t];
         for (int t = 0; t < A.nlqP; ++t) thP[(size_t)t * A.G + g] = (T)thv[1][t];
+    } else if (A.tc) {
+        // tensor-core layout: A_T and A_T V_T per target state, rows grouped by q', in fixed point per
+        // 32-node chunk (one warp): x = s (k0 + k1 2^-8 + k2 2^-16) with s a power of two from the
+        // chunk's largest |x| and k0..k2 integers in [-128, 128], stored as bf16 k0, k1, k2 2^-8 (all
+        // exact), and s in the scale table; A_P per half column in FP32
+        // the node weight (R^3/8) w (eta^2 - tau^2) = (R/2) w r_T r_P carries a factor r_T that cancels the
+        // 1/r_T of the transfer potential: it goes with the table rows (A_T r_T and A_T r_T V_T, both
+        // bounded), and the weights of this layout are W_K / r_T
+        const double rTV = A.mp_c == 0.0 ? -A.Z_T : -A.Z_T + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT);
+        __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(base);
+        float* sc = reinterpret_cast<float*>(base) + A.tc_sc_off + (size_t)(g >> 5) * A.tc_rows;
+        const size_t split = (size_t)A.tc_rows * A.G;
+        auto put3 = [&](size_t row, double v64) {
+            const float x = (float)v64;
+            float mx = fabsf(x);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            int E = 0;
+            if (mx > 0.f) frexpf(mx, &E);           // mx = f 2^E, f in [0.5, 1)
+            const int sh = mx > 0.f ? 7 - E : 0;    // |x| 2^sh < 128
+            const float xs = ldexpf(x, sh);
+            const float k0 = rintf(xs);
+            const float r1 = (xs - k0) * 256.f;
+            const float k1 = rintf(r1);
+            const float k2 = rintf((r1 - k1) * 256.f);
+            const size_t o = row * A.G + g;
+            sp[o] = __float2bfloat16_rn(k0);
+            sp[split + o] = __float2bfloat16_rn(k1);
+            sp[2 * split + o] = __float2bfloat16_rn(k2 * (1.f / 256.f));
+            if ((threadIdx.x & 31) == 0) sc[row] = ldexpf(1.f, -sh);
+        };
+        for (int a = 0; a < A.nradT; ++a) {
+            double val = 0.0;
+            if (inT) {
+                const double* fa = A.fT + (size_t)a * A.Nr + sT;
+                val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
+            }
+            const int l = A.radT_l[a];
+            for (int m = -l; m <= l; ++m) {
+                const int i = A.stT_index[a * (2 * WPCCC_LMAX + 1) + m + WPCCC_LMAX];
+                const int am = m < 0 ? -m : m;
+                const double sg = (m < 0 && (am & 1)) ? -1.0 : 1.0;
+                const double v = val * thv[0][l * (l + 1) / 2 + am] * sg;
+                const int row = A.tc_row[i];       // the A_T row; the A_T V_T row follows the group's A_T rows
+                const int gsz = A.tc_row[A.N_T + i];
+                put3((size_t)row, v * rT);
+                put3((size_t)(row + gsz), v * rTV);
+            }
+        }
+        float* aP = reinterpret_cast<float*>(base) + A.tc_ap_off;
+        for (int b2 = 0; b2 < A.nradP; ++b2) {
+            double val = 0.0;
+            if (inP) {
+                const double* fa = A.fP + (size_t)b2 * A.Nr + sP;
+                val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
+            }
+            const int l = A.radP_l[b2];
+            for (int q = 0; q <= l; ++q) {
+                const int j = A.half_of[b2 * (WPCCC_LMAX + 1) + q];
+                aP[(size_t)j * A.G + g] = (float)(val * thv[1][l * (l + 1) / 2 + q]);
+            }
+        }
     } else {
         // per state: A_T[i][g] = f_a(r_T) Theta_{l|m|}(c_T) (-1)^m [m < 0], A_P[j][g] = f_b(r_P) Theta_{lq}(c_P)
         T* aT = base;
@@ -232,8 +301,14 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         a.y = (T)w0.y;
         bq.x = (T)(w0.x * uQ);
         bq.y = (T)(w0.y * uQ);
-        W[o] = a;
-        W[stride + o] = bq;
+        if (sizeof(T) == 4 && A.tc) {
+            // tensor-core layout: W_K / r_T only (r_T and the transfer potential sit in the split tables)
+            reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.tc_w_off)[o] =
+                make_float2((float)(w0.x / rT), (float)(w0.y / rT));
+        } else {
+            W[o] = a;
+            W[stride + o] = bq;
+        }
     }
 }
 
@@ -982,7 +1057,7 @@ __global__ void __launch_bounds__(256) k_direct_sr(SrArgs A, const EvalDesc* __r
 // host side
 // ---------------------------------------------------------------------------
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
-    ElemScratch L{0, 0, 0, 0, 0, 0, 0, 0, 0};
+    ElemScratch L{};
     const int lrot = std::max(B->T.lmax, B->n_centres == 2 ? B->P.lmax : 0);
     for (int l = 0; l <= lrot; ++l) L.dtot += (2 * l + 1) * (2 * l + 1);
     const int nlam = 2 * lrot + 1;
@@ -1002,6 +1077,18 @@ ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
         L.w_off_f = nf;
         nf += (size_t)NX * (B->dmax + 1) * B->G * 2;
         L.node_doubles = std::max(nd, (nf + 1) / 2);
+        if (B->tc_layout) {
+            // bf16 split tables, then A_P (floats) and W_K (complex floats), each 16-byte aligned
+            L.tc_rows = 2 * B->N_T;
+            size_t nt = ((size_t)3 * L.tc_rows * B->G + 7) / 8 * 4;   // floats, multiple of 4
+            L.tc_ap_off = nt;
+            nt += ((size_t)B->n_half * B->G + 3) / 4 * 4;
+            L.tc_w_off = nt;
+            nt += (size_t)(B->dmax + 1) * B->G * 2;
+            L.tc_sc_off = nt;
+            nt += ((size_t)L.tc_rows * ((B->G + 31) / 32) + 3) / 4 * 4;
+            L.node_doubles = std::max(L.node_doubles, (nt + 1) / 2);
+        }
         L.node_doubles += L.node_doubles & 1;
         L.mol_elems = (size_t)NX * B->N_T * B->n_half;
         L.bytes_per_eval = L.node_doubles * sizeof(double) + L.mol_elems * sizeof(double2);
@@ -1107,6 +1194,16 @@ static wpccc_status launch_tables(wpccc_basis_s* B, const EvalDesc* evals, int n
     na.half_of = B->half_of;
     na.radT_l = B->T.rad_l;
     na.radP_l = B->P.rad_l;
+    na.tc = precision == 3;
+    na.tc_row = B->tc_row;
+    na.tc_rows = L.tc_rows;
+    na.tc_ap_off = L.tc_ap_off;
+    na.tc_w_off = L.tc_w_off;
+    na.tc_sc_off = L.tc_sc_off;
+    if (precision == 3) {
+        if (!B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
+        na.w_off = L.tc_w_off;
+    }
     cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
     if (precision == 0) k_node_tables<double><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
     else k_node_tables<float><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
@@ -1162,6 +1259,9 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
             WPCCC_CUDA(cudaFuncSetAttribute(k_mol_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)gsm));
             k_mol_gemm<double><<<dim3(n_row_tiles * ga.n_col_tiles, nev), 256, gsm, st>>>(ga);
+        } else if (precision == 3) {
+            wpccc_status ms = launch_mol_tc(B, nev, node, mol, B->tc_err, st);
+            if (ms != WPCCC_OK) return ms;
         } else {
             Gemm32Args g32;
             g32.G = B->G;
@@ -1304,11 +1404,38 @@ wpccc_status ensure_workspace(wpccc_basis_s* B, size_t bytes) {
 
 using namespace wpccc;
 
+namespace wpccc {
+static wpccc_status matrix_elements_prec(wpccc_basis B, double b, double v, int nz, const double* z, void* S,
+                                         void* H, int precision, void* stream);
+}
+
 extern "C" wpccc_status wpccc_matrix_elements(wpccc_basis B, double b, double v, int nz, const double* z,
                                               void* S, void* H, void* stream) {
+    return matrix_elements_prec(B, b, v, nz, z, S, H, 0, stream);
+}
+
+extern "C" wpccc_status wpccc_matrix_elements_precision(wpccc_basis B, double b, double v, int nz, const double* z,
+                                                        void* S, void* H, int precision_mode, void* stream) {
+    if (precision_mode != 0 && precision_mode != 1 && precision_mode != 3)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: element precision 0, 1 or 3");
+    if (precision_mode != 0 && (!B || B->n_centres != 2))
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: reduced precision needs two centres");
+    if (precision_mode != 0 && B->mp_c != 0.0)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: model-potential targets need FP64");
+    return matrix_elements_prec(B, b, v, nz, z, S, H, precision_mode, stream);
+}
+
+namespace wpccc {
+static wpccc_status matrix_elements_prec(wpccc_basis B, double b, double v, int nz, const double* z, void* S,
+                                         void* H, int precision, void* stream) {
     if (!B || !z || !S || !H) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: null argument");
     if (nz < 1) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: nz < 1");
     if (!(b > 0.0) || !(v > 0.0)) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: b and v must be > 0");
+    if (precision == 3) {
+        WPCCC_CUDA(cudaSetDevice(B->device));
+        wpccc_status ts = tc_prepare(B);
+        if (ts != WPCCC_OK) return ts;
+    }
     WPCCC_CUDA(cudaSetDevice(B->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const ElemScratch L = elem_scratch_layout(B);
@@ -1328,10 +1455,19 @@ extern "C" wpccc_status wpccc_matrix_elements(wpccc_basis B, double b, double v,
         for (int k = 0; k < n; ++k) ev[k] = EvalDesc{b, v, z[k0 + k], 0, 0};
         WPCCC_CUDA(cudaMemcpyAsync(dev_ev, ev.data(), n * sizeof(EvalDesc), cudaMemcpyHostToDevice, st));
         s = launch_elements(B, dev_ev, n, static_cast<double2*>(S) + k0 * mat, static_cast<double2*>(H) + k0 * mat,
-                            scratch, st);
+                            scratch, st, precision);
         if (s != WPCCC_OK) return s;
         // the host list is reused: wait for the copy before refilling it
         WPCCC_CUDA(cudaStreamSynchronize(st));
     }
+    if (precision == 3) {
+        int e = 0;
+        WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
+            return fail(WPCCC_ECUDA, "a wait of the tensor-core contraction timed out (stage " + std::to_string(e) + ")");
+        }
+    }
     return WPCCC_OK;
 }
+}  // namespace wpccc

@@ -236,10 +236,14 @@ static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // otherwise they are chosen from the workspace limit and the SM count.
 static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int precision_mode, int C_request,
                                size_t ws_limit, PropPlan& P) {
-    if (precision_mode < 0 || precision_mode > 2)
-        return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: precision_mode must be 0, 1 or 2");
-    if (precision_mode == 1 && B->n_centres == 2 && B->mp_c != 0.0)
+    if (precision_mode < 0 || precision_mode > 3)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: precision_mode must be 0, 1, 2 or 3");
+    if ((precision_mode == 1 || precision_mode == 3) && B->n_centres == 2 && B->mp_c != 0.0)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: model-potential targets need FP64 elements (mode 0 or 2)");
+    if (precision_mode == 3 && B->n_centres == 2) {
+        wpccc_status ts = tc_prepare(B);
+        if (ts != WPCCC_OK) return ts;
+    }
     const int np = paths->n_paths;
     if (np < 1 || !paths->b || !paths->v || !paths->n_z || !paths->z)
         return fail(WPCCC_EINVAL, "wpccc_propagate: empty or null path description");
@@ -260,9 +264,10 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     P.np = np;
     P.N = N;
     P.two = B->n_centres == 2;
-    // 1: FP32 contraction + FP32 LU + FP64 refinement; 2: FP64 elements + FP32 LU + FP64 refinement
+    // 1: FP32 contraction + FP32 LU + FP64 refinement; 2: FP64 elements + FP32 LU + FP64 refinement;
+    // 3: as 1 with the contraction on the tensor cores (bf16 three-part splits)
     P.mixed = P.two && precision_mode >= 1;
-    P.elem_precision = (P.two && precision_mode == 1) ? 1 : 0;
+    P.elem_precision = P.two && (precision_mode == 1 || precision_mode == 3) ? precision_mode : 0;
     P.stage = P.two && !P.mixed && B->solve_mode == WPCCC_SOLVE_STAGE;
     P.mode = P.mixed ? RK_MIXED : (P.stage ? RK_STAGE : RK_MATRIX);
     if (rk_smem_bytes(P.mode, N) > (size_t)227 * 1024)
@@ -508,6 +513,15 @@ wpccc_status propagate_internal(wpccc_basis_s* B, const wpccc_paths* paths, int 
     int flags = 0;
     WPCCC_CUDA(cudaMemcpyAsync(&flags, P.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     WPCCC_CUDA(cudaStreamSynchronize(st));
+    if (P.elem_precision == 3) {
+        int e = 0;
+        WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
+            return fail(WPCCC_ECUDA, "wpccc_propagate: a wait of the tensor-core contraction timed out (stage " +
+                                         std::to_string(e) + ")");
+        }
+    }
     s = flags_status(flags);
     if (s != WPCCC_OK) set_error(std::string("wpccc_propagate: ") + wpccc_last_error());
     return s;

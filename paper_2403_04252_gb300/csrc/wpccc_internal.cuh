@@ -120,6 +120,15 @@ struct wpccc_basis_s {
     double* deps = nullptr;                  // [n_par][N]: d eps_i / d theta_p per state
     wpccc::CentreTan tanT, tanP;
     int refine_iters = 2;       // FP64 refinement iterations of the mixed-precision form
+    // tensor-core contraction (precision mode 3): node tables carry the split operand tables
+    bool tc_layout = false;
+    int n_qgroups = 0;          // target q' groups (2 lmax_T + 1)
+    int* tc_row = nullptr;      // [2 N_T]: row of each target state in a split table, then its group's size
+    int* tc_err = nullptr;      // device flag: a wait of the tensor-core pipeline gave up
+    int* tc_halfq = nullptr;    // [n_half]: q of each half column
+    int* qg_off = nullptr;      // [n_qgroups + 1]: first split-table row of each group (2 x cumulative size)
+    int* qg_rows = nullptr;     // [n_qgroups][max group size]: target state of each row of a group
+    int qg_max = 0;
     // second stream of wpccc_propagate (RK4 sweeps overlap the next chunk's assembly) and its events
     cudaStream_t rk_stream = nullptr;
     cudaEvent_t ev_asm[2] = {nullptr, nullptr}, ev_rk[2] = {nullptr, nullptr};
@@ -146,6 +155,12 @@ struct ElemScratch {
     size_t et_doubles;     // small per-position tables (Wigner d, Legendre, stencil, F at R, phases), even
     size_t ph_off;         // offset of the per-state energy phases exp(i eps_i z / v) (complex, N of them)
     int dtot, npb;         // sizes of their Wigner-d and Legendre parts
+    // tensor-core layout of the node tables (precision mode 3), when the basis enables it:
+    //   3 bf16 split tables [3][tc_rows][G] (rows: per target q' group, its A_T rows then A_T V_T rows),
+    //   then A_P per half column (floats, at tc_ap_off), then the overlap weights W_K (complex floats, at tc_w_off)
+    int tc_rows;
+    size_t tc_ap_off, tc_w_off;
+    size_t tc_sc_off;      // per (32-node chunk, split-table row) power-of-two scale (floats)
 };
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B);
 
@@ -169,6 +184,11 @@ wpccc_status propagate_internal(wpccc_basis_s* B, const wpccc_paths* paths, int 
 wpccc_status ensure_workspace(wpccc_basis_s* B, size_t bytes);
 
 enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3, PROF_RK4 = 4, PROF_ADJ = 5 };
+
+// Tensor-core form of the Eq. 9 contraction (precision mode 3): from the node tables of the tensor-core
+// layout into the molecular-frame blocks, for `nev` evaluations.
+wpccc_status launch_mol_tc(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st);
+wpccc_status tc_prepare(wpccc_basis_s* B);
 
 // Queue the batched FP32 factorisation P S = L U of FP64 matrices (mixed-precision form).
 wpccc_status launch_factor_f32(int N, int batch, const double2* S, float2* LU, int* ipiv, int* info,

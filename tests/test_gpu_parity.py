@@ -332,3 +332,65 @@ def test_batch_graph_matches_separate_propagation(small2c, small2c_uneven):
         ref = g.propagate(b, v, zg, c=c0.clone())
         assert torch.equal(cb, ref)
     batch.close()
+
+
+def test_tensor_core_elements_match_fp64_as_closely_as_fp32():
+    """Precision mode 3 (Eq. 9 contraction on tcgen05 with fixed-point bf16 slices): element errors
+    against the FP64 elements at the level of the FP32 CUDA-core contraction, and no bias (the tensor
+    core's FP32 accumulation truncates; the sliced main products are integers it holds exactly)."""
+    import paper_2403_04252_gb300 as w
+    basis, _ = wi.config_inputs("p_H_2c_n4l3")
+    g = w.Basis(basis)
+    NT = g.N_T
+    zs = np.array([-7.0, -0.55, 0.0, 0.35, 12.0])
+    for b in (0.2, 3.2, 11.0):
+        S0, H0 = g.matrix_elements_precision(b, 1.5, zs, 0)
+        S1, H1 = g.matrix_elements_precision(b, 1.5, zs, 1)
+        S3, H3 = g.matrix_elements_precision(b, 1.5, zs, 3)
+        torch.cuda.synchronize()
+        e1 = max((S1 - S0).abs().max().item(), (H1 - H0).abs().max().item())
+        e3 = max((S3 - S0).abs().max().item(), (H3 - H0).abs().max().item())
+        assert e3 < 1e-7 and e3 < 3.0 * e1 + 1e-9, (b, e1, e3)
+        # no systematic shrink of the two-centre blocks
+        X0 = torch.cat([S0[:, :NT, NT:], H0[:, :NT, NT:]]).flatten()
+        X3 = torch.cat([S3[:, :NT, NT:], H3[:, :NT, NT:]]).flatten()
+        m = X0.abs() > 1e-3
+        rel = ((X3[m] - X0[m]) / X0[m]).real
+        assert abs(rel.mean().item()) < 2e-8
+    g.close()
+
+
+def test_tensor_core_propagation_within_bound():
+    import paper_2403_04252_gb300 as w
+    basis, paths = wi.config_inputs("p_H_2c_n4l3")
+    g = w.Basis(basis)
+    zg = paths.z[0]
+    k0 = zg.size // 2 - 8
+    seg = zg[k0:k0 + 17]
+    bs = paths.b[::4]
+    P0 = w.probabilities(g.propagate(bs, 1.5, seg, precision_mode=0)).cpu().numpy()
+    P3 = w.probabilities(g.propagate(bs, 1.5, seg, precision_mode=3)).cpu().numpy()
+    assert np.abs(P3 - P0).max() < 1e-6
+    g.close()
+
+
+def test_tensor_core_small_uneven_basis_and_errors():
+    import paper_2403_04252_gb300 as w
+    # groups of different sizes, ragged tiles (N_T = 40, n_half = 27), nodes a multiple of 32
+    basis = wi.make_basis(1.0, 1.0, (3, 2), (2, 2), (3, 2), (3.0, 4.0), True, Nr=600, Geta=16, Gtau=16)
+    g = w.Basis(basis)
+    zs = np.array([-2.0, 0.3, 5.0])
+    S0, H0 = g.matrix_elements_precision(0.9, 1.3, zs, 0)
+    S3, H3 = g.matrix_elements_precision(0.9, 1.3, zs, 3)
+    torch.cuda.synchronize()
+    assert (S3 - S0).abs().max().item() < 1e-6 and (H3 - H0).abs().max().item() < 1e-6
+    with pytest.raises(w.WpcccError) as e:
+        g.matrix_elements_precision(0.9, 1.3, zs, 2)
+    assert e.value.status == w.EUNSUPPORTED
+    g.close()
+    odd = wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=15, Gtau=13)   # 195 nodes
+    go = w.Basis(odd)
+    with pytest.raises(w.WpcccError) as e:
+        go.matrix_elements_precision(0.9, 1.3, zs, 3)
+    assert e.value.status == w.EUNSUPPORTED
+    go.close()
