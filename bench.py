@@ -576,6 +576,12 @@ def main() -> None:
     n_total = zg.size - 1
     b = paths.b[:n_paths]
     v = paths.v[:n_paths]
+    if world > 1:
+        # weak scaling: every rank takes n_paths impact parameters of a world-times finer scan of the
+        # same range (no data-path collective: the paths are independent)
+        from paper_2403_04252_gb300.dist import shard_impact_parameters
+        b0, b1, _ = wi.CONFIGS[args.workload]["b"]
+        b = shard_impact_parameters(b0, b1, n_paths, rank, world)
     STEP = args.rk4_per_step
     stream = torch.cuda.current_stream(dev)
 
@@ -588,11 +594,8 @@ def main() -> None:
         return zg[k0:k0 + STEP + 1]
 
     def reduce_max(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        from paper_2403_04252_gb300.dist import max_over_ranks
+        return max_over_ranks(x, device=dev)
 
     def measure(prec: int) -> dict:
         """warm-up, then the device-timed steps of one form; returns its rate and final amplitudes"""

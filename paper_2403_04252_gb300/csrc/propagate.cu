@@ -787,6 +787,17 @@ extern "C" wpccc_status wpccc_batch_status(wpccc_batch X, void* stream) {
         if (X->plans[k].d_flags)
             WPCCC_CUDA(cudaMemcpyAsync(&flags[k], X->plans[k].d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     WPCCC_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < X->n_sets; ++k) {
+        wpccc_basis_s* B = X->plans[k].B;
+        if (X->plans[k].elem_precision == 3 && B && B->tc_err) {
+            int e = 0;
+            WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (e) {
+                WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
+                return fail(WPCCC_ECUDA, "wpccc_batch_status: a wait of the tensor-core contraction timed out");
+            }
+        }
+    }
     int all = 0;
     for (int f : flags) all |= f;
     wpccc_status s = flags_status(all);

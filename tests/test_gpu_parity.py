@@ -394,3 +394,27 @@ def test_tensor_core_small_uneven_basis_and_errors():
         go.matrix_elements_precision(0.9, 1.3, zs, 3)
     assert e.value.status == w.EUNSUPPORTED
     go.close()
+
+
+def test_batch_graph_tensor_core_matches_separate_propagation():
+    # the tensor-core form captured into the batch graph (tensor maps as launch parameters)
+    w = _w()
+    bA = wi.make_basis(1.0, 1.0, 2, 1, 3, 2.0, True, Nr=600, Geta=16, Gtau=16)
+    bB = wi.make_basis(1.0, 1.0, (3, 2), (2, 2), (3, 2), (3.0, 4.0), True, Nr=600, Geta=16, Gtau=16)
+    gA, gB = w.Basis(bA), w.Basis(bB)
+    sets = [(gA, np.array([0.4, 2.5]), 1.0, wi.uniform_zgrid(-3.0, 3.0, 0.2)),
+            (gB, np.array([1.5, 0.8, 3.0]), 1.3, wi.uniform_zgrid(-1.0, 1.0, 0.1))]
+    c = []
+    for g, b, v, zg in sets:
+        t = torch.zeros((b.size, g.N), dtype=torch.complex128, device="cuda")
+        t[:, 0] = 1.0
+        c.append(t)
+    batch = w.Batch(sets, c, precision_mode=3, autotune=False)
+    batch.launch()
+    batch.status()
+    for (g, b, v, zg), cb in zip(sets, c):
+        ref = g.propagate(b, v, zg, precision_mode=3)
+        assert torch.equal(cb, ref)
+        P0 = w.probabilities(g.propagate(b, v, zg, precision_mode=0))
+        assert (w.probabilities(cb) - P0).abs().max().item() < 1e-6
+    batch.close()
