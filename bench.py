@@ -517,7 +517,9 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all of the workload)")
     ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
-    ap.add_argument("--solve-mode", default="stage", choices=["stage", "matrix"])
+    ap.add_argument("--solve-mode", default="schur", choices=["stage", "matrix", "schur"],
+                    help="FP64 form: S^-1 per RK4 stage through the Schur complement (default), from LU factors, or "
+                         "as X = S^-1 H")
     ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v",
                                                              "pLi_2c_grad"],
                     help="p_H_2c_n4l3: two-centre p + H (N = 380, 32 paths); C6_H_2c_n6l5: bare C6+ on H "
@@ -569,7 +571,7 @@ def main() -> None:
     g = w.Basis(basis, device=local)
     ws_gb = args.workspace_gb or (16.0 if args.workload == WORKLOAD else 96.0)
     g.set_workspace_limit(int(ws_gb * (1 << 30)))
-    g.set_solve_mode(w.SOLVE_STAGE if args.solve_mode == "stage" else w.SOLVE_MATRIX)
+    g.set_solve_mode({"stage": w.SOLVE_STAGE, "matrix": w.SOLVE_MATRIX, "schur": w.SOLVE_SCHUR}[args.solve_mode])
     n_paths = paths.n_paths if args.paths <= 0 else min(args.paths, paths.n_paths)
     N = g.N
     zg = paths.z[0]
@@ -678,16 +680,24 @@ def main() -> None:
     # Eq. 9 contraction, two integrals (K and Q; the lower-left block is Q^+), per z: projectile columns
     # with q >= 0 (the reflection gives the rest): 4 real flops per node per integral
     flops_mol = 8.0 * NT * n_half * G
-    # LU, plus N right-hand sides in the paper's form; the stage form's triangular solves run in the RK4 kernel
-    flops_solve = (8.0 / 3.0 + (8.0 if (args.solve_mode == "matrix" and prec == 0) else 0.0)) * N ** 3
+    # LU, plus N right-hand sides in the paper's form; the stage form's triangular solves run in the RK4 kernel.
+    # Schur form: the lower triangle of K^+ K (4 N_P^2 N_T) and the Cholesky of I - K^+ K (4/3 N_P^3)
+    schur = args.solve_mode == "schur" and prec == 0
+    if schur:
+        flops_solve = 4.0 * NP_ * NP_ * NT + (4.0 / 3.0) * NP_ ** 3
+    else:
+        flops_solve = (8.0 / 3.0 + (8.0 if (args.solve_mode == "matrix" and prec == 0) else 0.0)) * N ** 3
     # RK4 per path-step (FP64): 4 applications of M; matrix form X y, stage form H y + two triangles,
-    # mixed forms H y and one refinement residual S x
-    rk4_flops = {"matrix": 32.0, "stage": 64.0}[args.solve_mode] * N * N if prec == 0 else 64.0 * N * N
+    # Schur form H y, K^+ t_T, K x_P and two triangles of N_P, mixed forms H y and one refinement residual S x
+    if schur:
+        rk4_flops = 4.0 * (8.0 * N * N + 16.0 * NT * NP_ + 8.0 * NP_ * NP_)
+    else:
+        rk4_flops = {"matrix": 32.0, "stage": 64.0}[args.solve_mode] * N * N if prec == 0 else 64.0 * N * N
     mol_peak = {1: FP32_PEAK_TFLOPS, 3: BF16_MEASURED_TFLOPS}.get(prec, FP64_PEAK_TFLOPS)
     cand = {"mol_gemm": (flops_mol * evals, mol_peak,
                          {1: "k_mol_gemm_f32q", 3: "k_mol_tc"}.get(prec, "k_mol_gemm<double>")),
             "solve": (flops_solve * evals, FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS,
-                      "k_lu_factor_f32" if prec else "k_lu_solve"),
+                      "k_lu_factor_f32" if prec else ("k_schur_factor" if schur else "k_lu_solve")),
             "rk4": (rk4_flops * n_paths * STEP * args.steps, FP64_PEAK_TFLOPS, "k_rk4")}
     dom = max(cand, key=lambda k: prof[k][0] if k in prof else 0.0)
     dom_ms, dom_launches = prof[dom]
@@ -709,8 +719,9 @@ def main() -> None:
                 "launch_ms_avg": dom_ms / max(dom_launches, 1),
                 "flop_per_launch": dom_flops / max(dom_launches, 1)}
     form_desc = {0: "plain FP64, all paths batched; S^-1 applied "
-                    + ("per RK4 stage from LU factors" if args.solve_mode == "stage"
-                       else "as X = S^-1 H with N right-hand sides (the paper's ZGESV form)"),
+                    + {"stage": "per RK4 stage from LU factors",
+                       "schur": "per RK4 stage through the Cholesky factor of the Schur complement I - K^+ K",
+                       "matrix": "as X = S^-1 H with N right-hand sides (the paper's ZGESV form)"}[args.solve_mode],
                  1: "mixed precision: Eq. 9 contraction and LU on the FP32 pipe (FP64 running sums), FP64 "
                     "node tables, refinement and RK4; all paths batched",
                  2: "mixed precision with FP64 elements: LU on the FP32 pipe, FP64 refinement and RK4",

@@ -291,11 +291,17 @@ WPCCC_API wpccc_status wpccc_probabilities(int n_paths, int N, const void* c, do
  *   WPCCC_SOLVE_STAGE  (default) LU-factorise S(z) once per position; at every RK4
  *                      stage form H(z) y and solve S(z) k = H(z) y with the factors
  *                      ((8/3) N^3 flops per position plus 16 N^2 per stage).
+ *   WPCCC_SOLVE_SCHUR  S = [[I, K], [K^+, I]] is Hermitian positive definite (a Gram matrix):
+ *                      Cholesky-factorise its Schur complement I - K^+ K once per position
+ *                      (4 N_P^2 N_T + (4/3) N_P^3 flops) and per stage solve
+ *                      k_P = (I - K^+ K)^{-1} (t_P - K^+ t_T), k_T = t_T - K k_P (no pivoting;
+ *                      a non-positive pivot is reported as ESINGULAR);
  *   WPCCC_SOLVE_MATRIX the paper's form: X = S^{-1} H with N right-hand sides per
  *                      position (ZGESV, (8/3 + 8) N^3 flops), then M c = -(i/v) X c.
  */
 #define WPCCC_SOLVE_STAGE 0
 #define WPCCC_SOLVE_MATRIX 1
+#define WPCCC_SOLVE_SCHUR 2
 WPCCC_API wpccc_status wpccc_basis_set_solve_mode(wpccc_basis basis, int mode);
 
 /*

@@ -96,7 +96,7 @@ EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wp
             "wpccc_matrix_elements_precision")
 MAX_PARAMS = 4
 NOALLOC_SCRATCH_BYTES = 64 << 20
-SOLVE_STAGE, SOLVE_MATRIX = 0, 1
+SOLVE_STAGE, SOLVE_MATRIX, SOLVE_SCHUR = 0, 1, 2
 PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4", "adjoint")
 
 
@@ -207,7 +207,8 @@ class Basis:
                "wpccc_basis_set_workspace_limit")
 
     def set_solve_mode(self, mode: int) -> None:
-        """SOLVE_STAGE (factor S once per position, solve per RK4 stage) or SOLVE_MATRIX (X = S^-1 H)."""
+        """SOLVE_STAGE (LU of S once per position, solve per RK4 stage), SOLVE_SCHUR (Cholesky of the Schur
+        complement I - K^+ K once per position, solve per stage) or SOLVE_MATRIX (X = S^-1 H)."""
         _check(_lib.wpccc_basis_set_solve_mode(self._h, int(mode)), "wpccc_basis_set_solve_mode")
 
     def profile_enable(self, on: bool = True) -> None:

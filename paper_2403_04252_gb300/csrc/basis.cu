@@ -464,7 +464,7 @@ extern "C" wpccc_status wpccc_profile_read(wpccc_basis B, double* ms, long long*
 
 extern "C" wpccc_status wpccc_basis_set_solve_mode(wpccc_basis B, int mode) {
     if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_solve_mode: null basis");
-    if (mode != WPCCC_SOLVE_STAGE && mode != WPCCC_SOLVE_MATRIX)
+    if (mode != WPCCC_SOLVE_STAGE && mode != WPCCC_SOLVE_MATRIX && mode != WPCCC_SOLVE_SCHUR)
         return fail(WPCCC_EINVAL, "wpccc_basis_set_solve_mode: unknown mode");
     B->solve_mode = mode;
     return WPCCC_OK;

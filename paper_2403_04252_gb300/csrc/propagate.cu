@@ -47,7 +47,7 @@ struct RkArgs {
     int* flags;
 };
 
-enum RkMode { RK_MATRIX = 0, RK_STAGE = 1, RK_MIXED = 2 };
+enum RkMode { RK_MATRIX = 0, RK_STAGE = 1, RK_MIXED = 2, RK_SCHUR = 3 };
 
 // Matrices of one position as the RK4 kernel sees them.
 struct PosMats {
@@ -60,6 +60,7 @@ struct PosMats {
 // One block per path: the chunk's RK4 steps (Algorithm 1) with M(z) y = -(i/v) S(z)^{-1} H(z) y:
 //   RK_MATRIX  X = S^{-1} H stored (the paper's form; one-centre: X = H)
 //   RK_STAGE   S^{-1} applied from FP64 LU factors at every stage
+//   RK_SCHUR   S^{-1} applied through the Schur complement's Cholesky factor at every stage
 //   RK_MIXED   S^{-1} applied by FP64 refinement on FP32 factors
 template <int MODE>
 __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
@@ -74,7 +75,8 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
     double2* rs = xs + N;                       // mixed: r
     float2* ds = reinterpret_cast<float2*>(rs + N);   // mixed: d
     // 32 x 32 diagonal block of the triangular solves (after the vectors of the mode)
-    void* blk = MODE == RK_MIXED ? (void*)(ds + N + (N & 1)) : (void*)(t + N);
+    double2* us = t + N;                        // Schur: scratch of the projectile part
+    void* blk = MODE == RK_MIXED ? (void*)(ds + N + (N & 1)) : (MODE == RK_SCHUR ? (void*)(us + N) : (void*)(t + N));
     const PathChunk pc = A.pcs[blockIdx.x];
     const size_t mat = (size_t)N * N;
     double2* cg = A.c + (size_t)pc.path * N;
@@ -101,6 +103,8 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
             matvec(m.H, N, in, out);
             for (int i = threadIdx.x; i < N; i += RK_THREADS) out[i] = make_double2(out[i].y / v, -out[i].x / v);
             __syncthreads();
+        } else if (MODE == RK_SCHUR) {
+            apply_schur(m.S, m.H, N, A.N_T, v, in, out, t, us, static_cast<double2*>(blk));
         } else if (MODE == RK_STAGE) {
             apply_LU(m.S, m.piv, m.H, N, v, in, out, t, static_cast<double2*>(blk));
         } else {
@@ -175,6 +179,7 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
 }
 
 size_t rk_smem_bytes(int mode, int N) {
+    if (mode == RK_SCHUR) return (size_t)N * 6 * sizeof(double2) + 32 * 32 * sizeof(double2);
     return mode == RK_MIXED ? (size_t)N * 7 * sizeof(double2) + (size_t)(N + (N & 1)) * sizeof(float2) +
                                   32 * 32 * sizeof(float2)
                             : (size_t)N * 5 * sizeof(double2) + 32 * 32 * sizeof(double2);
@@ -213,7 +218,7 @@ struct PropPlan {
     wpccc_basis_s* B = nullptr;
     int np = 0, N = 0, mode = RK_MATRIX, elem_precision = 0, C = 1, n_chunks = 0, max_chunk_evals = 0;
     int max_steps = 0;
-    bool two = false, mixed = false, stage = false;
+    bool two = false, mixed = false, stage = false, schur = false;
     size_t per_eval = 0, fixed = 0;
     std::vector<double> z;
     std::vector<EvalDesc> ev;
@@ -268,8 +273,9 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     // 3: as 1 with the contraction on the tensor cores (bf16 three-part splits)
     P.mixed = P.two && precision_mode >= 1;
     P.elem_precision = P.two && (precision_mode == 1 || precision_mode == 3) ? precision_mode : 0;
-    P.stage = P.two && !P.mixed && B->solve_mode == WPCCC_SOLVE_STAGE;
-    P.mode = P.mixed ? RK_MIXED : (P.stage ? RK_STAGE : RK_MATRIX);
+    P.stage = P.two && !P.mixed && B->solve_mode != WPCCC_SOLVE_MATRIX;
+    P.schur = P.stage && B->solve_mode == WPCCC_SOLVE_SCHUR;
+    P.mode = P.mixed ? RK_MIXED : (P.schur ? RK_SCHUR : (P.stage ? RK_STAGE : RK_MATRIX));
     if (rk_smem_bytes(P.mode, N) > (size_t)227 * 1024)
         return fail(WPCCC_EINVAL, "wpccc_propagate: N too large for the RK4 kernel's shared memory in this mode");
     const size_t mat = (size_t)N * N;
@@ -415,6 +421,7 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     const int rk_smem = (int)rk_smem_bytes(P.mode, N);
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MATRIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+    WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
     const size_t hS = P.sz_S / 2 / sizeof(double2), hH = P.sz_H / 2 / sizeof(double2);
     const size_t hL = P.sz_LU32 / 2 / sizeof(float2), hP = P.sz_piv / 2 / sizeof(int), hI = P.sz_info / 2 / sizeof(int);
@@ -449,6 +456,7 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
         if (P.two) {
             cudaEvent_t e0 = B->prof.begin(PROF_SOLVE, st);
             if (P.mixed) s = launch_factor_f32(N, nev, bS, bL, bP, bI, st);
+            else if (P.schur) s = launch_schur_factor(N, B->N_T, nev, bS, bI, st);
             else s = launch_solve(N, nev, bS, P.stage ? nullptr : bH, bP, bI, st);
             if (s != WPCCC_OK) return s;
             B->prof.end(PROF_SOLVE, st, e0);
@@ -463,6 +471,7 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
         ra.piv = P.mode != RK_MATRIX ? bP : nullptr;
         ra.info = bI;
         if (P.mode == RK_MIXED) k_rk4<RK_MIXED><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
+        else if (P.mode == RK_SCHUR) k_rk4<RK_SCHUR><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else if (P.mode == RK_STAGE) k_rk4<RK_STAGE><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else k_rk4<RK_MATRIX><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         WPCCC_CHECK_LAUNCH("k_rk4");

@@ -189,4 +189,144 @@ static __device__ void apply_LU_mixed(const double2* __restrict__ S64, const flo
     __syncthreads();
 }
 
+// x <- C^{-1} x with C = L L^+ (L lower, real positive diagonal, column-major with leading dimension ld),
+// n unknowns.  Blocked by 32 rows: the diagonal block is staged in shared memory (blk) and solved by one
+// warp; off-diagonal updates: rows below (forward) by all threads, rows above (backward) a warp per row.
+static __device__ void chol_solve_inplace(const double2* __restrict__ L, int ld, int n, double2* x, double2* blk) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // L z = x
+    for (int kb = 0; kb < n; kb += 32) {
+        const int nb = min(32, n - kb);
+        for (int q = tid; q < 32 * 32; q += RK_THREADS) {
+            const int i = q & 31, j = q >> 5;
+            if (i < nb && j < nb) blk[q] = L[(size_t)(kb + i) + (size_t)(kb + j) * ld];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double2 v = x[kb + (lane < nb ? lane : 0)];
+            for (int j = 0; j < nb; ++j) {
+                if (lane == j) {
+                    const double d = 1.0 / blk[j * 32 + j].x;
+                    v.x *= d;
+                    v.y *= d;
+                }
+                const double vr = __shfl_sync(0xffffffffu, v.x, j);
+                const double vi = __shfl_sync(0xffffffffu, v.y, j);
+                if (lane > j && lane < nb) {
+                    const double2 l = blk[j * 32 + lane];
+                    v.x = fma(-l.x, vr, v.x);
+                    v.x = fma(l.y, vi, v.x);
+                    v.y = fma(-l.x, vi, v.y);
+                    v.y = fma(-l.y, vr, v.y);
+                }
+            }
+            if (lane < nb) x[kb + lane] = v;
+        }
+        __syncthreads();
+        for (int i = kb + nb + tid; i < n; i += RK_THREADS) {
+            double2 a = x[i];
+            for (int j = 0; j < nb; ++j) {
+                const double2 l = L[(size_t)i + (size_t)(kb + j) * ld];
+                const double2 b = x[kb + j];
+                a.x = fma(-l.x, b.x, a.x);
+                a.x = fma(l.y, b.y, a.x);
+                a.y = fma(-l.x, b.y, a.y);
+                a.y = fma(-l.y, b.x, a.y);
+            }
+            x[i] = a;
+        }
+        __syncthreads();
+    }
+    // L^+ x = z, from the bottom: (L^+)[i][j] = conj(L[j][i]), j >= i
+    const int last = ((n - 1) / 32) * 32;
+    for (int kb = last; kb >= 0; kb -= 32) {
+        const int nb = min(32, n - kb);
+        for (int q = tid; q < 32 * 32; q += RK_THREADS) {
+            const int i = q & 31, j = q >> 5;
+            if (i < nb && j < nb) blk[q] = L[(size_t)(kb + i) + (size_t)(kb + j) * ld];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double2 v = x[kb + (lane < nb ? lane : 0)];
+            for (int j = nb - 1; j >= 0; --j) {
+                if (lane == j) {
+                    const double d = 1.0 / blk[j * 32 + j].x;
+                    v.x *= d;
+                    v.y *= d;
+                }
+                const double vr = __shfl_sync(0xffffffffu, v.x, j);
+                const double vi = __shfl_sync(0xffffffffu, v.y, j);
+                if (lane < j) {
+                    const double2 l = blk[lane * 32 + j];   // L[j][lane], conjugated below
+                    v.x = fma(-l.x, vr, v.x);
+                    v.x = fma(-l.y, vi, v.x);
+                    v.y = fma(-l.x, vi, v.y);
+                    v.y = fma(l.y, vr, v.y);
+                }
+            }
+            if (lane < nb) x[kb + lane] = v;
+        }
+        __syncthreads();
+        // rows i < kb: x_i -= sum_jj conj(L[kb + jj][i]) x[kb + jj], a warp per row, lanes over jj
+        for (int i = warp; i < kb; i += RK_THREADS / 32) {
+            double re = 0.0, im = 0.0;
+            if (lane < nb) {
+                const double2 l = L[(size_t)(kb + lane) + (size_t)i * ld];
+                const double2 b = x[kb + lane];
+                re = l.x * b.x + l.y * b.y;
+                im = l.x * b.y - l.y * b.x;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            if (lane == 0) x[i] = make_double2(x[i].x - re, x[i].y - im);
+        }
+        __syncthreads();
+    }
+}
+
+// Schur form of the stage operator: k = -(i/v) S^{-1} (H y) with S = [[I, K], [K^+, I]] held as K (in
+// place) and the Cholesky factor L of I - K^+ K (lower triangle of S's projectile block):
+//   u_P = t_P - K^+ t_T,  x_P = (L L^+)^{-1} u_P,  x_T = t_T - K x_P.   t, u: shared scratch of N.
+static __device__ void apply_schur(const double2* __restrict__ S, const double2* __restrict__ Hm, int N, int N_T,
+                                   double v, const double2* y, double2* k, double2* t, double2* u, double2* blk) {
+    const int NP = N - N_T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    matvec(Hm, N, y, t);
+    const double2* K = S + (size_t)N_T * N;
+    for (int j = warp; j < NP; j += RK_THREADS / 32) {
+        double re = 0.0, im = 0.0;
+        const double2* col = K + (size_t)j * N;
+        for (int i = lane; i < N_T; i += 32) {
+            const double2 a = col[i], b = t[i];
+            re = fma(a.x, b.x, re);
+            re = fma(a.y, b.y, re);
+            im = fma(a.x, b.y, im);
+            im = fma(-a.y, b.x, im);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) u[j] = make_double2(t[N_T + j].x - re, t[N_T + j].y - im);
+    }
+    __syncthreads();
+    chol_solve_inplace(S + N_T + (size_t)N_T * N, N, NP, u, blk);
+    for (int i = threadIdx.x; i < N_T; i += RK_THREADS) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < NP; ++j) {
+            const double2 a = K[(size_t)i + (size_t)j * N];
+            const double2 b = u[j];
+            re = fma(a.x, b.x, re);
+            re = fma(-a.y, b.y, re);
+            im = fma(a.x, b.y, im);
+            im = fma(a.y, b.x, im);
+        }
+        const double2 xt = make_double2(t[i].x - re, t[i].y - im);
+        k[i] = make_double2(xt.y / v, -xt.x / v);
+    }
+    for (int j = threadIdx.x; j < NP; j += RK_THREADS) k[N_T + j] = make_double2(u[j].y / v, -u[j].x / v);
+    __syncthreads();
+}
+
 }  // namespace wpccc

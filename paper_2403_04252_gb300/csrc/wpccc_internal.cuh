@@ -194,6 +194,10 @@ wpccc_status tc_prepare(wpccc_basis_s* B);
 wpccc_status launch_factor_f32(int N, int batch, const double2* S, float2* LU, int* ipiv, int* info,
                                cudaStream_t st);
 
+// Queue the batched Schur-complement factorisation of two-centre overlap matrices S (Cholesky factor of
+// I - K^+ K into the lower triangle of S's projectile block; info as ZPOTRF).
+wpccc_status launch_schur_factor(int N, int N_T, int batch, double2* S, int* info, cudaStream_t st);
+
 // Queue the batched solve of S X = H (results in place).
 wpccc_status launch_solve(int N, int batch, double2* S, double2* H, int* ipiv, int* info,
                           cudaStream_t st);

@@ -178,10 +178,11 @@ def test_propagate_one_centre_full_paths(config1):
     assert abs(Pg.sum(axis=1) - 1.0).max() < 1e-5
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_propagate_two_centre_ragged_paths_and_chunks(small2c, mode):
     # uneven path lengths and a workspace limit that forces several chunks of steps;
-    # both ways of applying S^-1 (LU per RK4 stage, and the paper's X = S^-1 H)
+    # the three ways of applying S^-1 (LU per RK4 stage, the paper's X = S^-1 H, and the
+    # Cholesky factor of the Schur complement I - K^+ K per RK4 stage)
     w = _w()
     g = w.Basis(small2c)
     g.set_solve_mode(mode)
@@ -215,7 +216,7 @@ def test_propagate_rejects_bad_paths(small2c):
     assert e.value.status == w.EINVAL
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_propagate_full_two_centre_sampled_paths(config2, mode):
     # the bench launch configuration (all 32 paths of the two-centre p + H workload batched),
     # two RK4 steps from z = -0.2; two sampled paths recomputed by the oracle
@@ -229,6 +230,28 @@ def test_propagate_full_two_centre_sampled_paths(config2, mode):
     for p in (0, 17):
         Po = O.probabilities(O.propagate(basis, float(paths.b[p]), float(paths.v[p]), zg))
         _prob_close(Pg[p], Po)
+
+
+def test_schur_solve_mode_uneven_centres(small2c_uneven):
+    # N_T != N_P (C6+ + H like): the Schur complement is the projectile block's, of a different size
+    # than the target's; against the oracle, and against the pivoted-LU stage form to FP64 rounding
+    w = _w()
+    g = w.Basis(small2c_uneven)
+    assert g.N_T != g.N - g.N_T
+    bs = np.array([0.6, 2.5])
+    zg = wi.uniform_zgrid(-4.0, 4.0, 0.25)
+    out = {}
+    for mode in (w.SOLVE_STAGE, w.SOLVE_SCHUR):
+        g.set_solve_mode(mode)
+        out[mode] = w.probabilities(g.propagate(bs, 2.0, zg)).cpu().numpy()
+    for p in range(2):
+        Po = O.probabilities(O.propagate(small2c_uneven, float(bs[p]), 2.0, zg))
+        _prob_close(out[w.SOLVE_SCHUR][p], Po)
+    assert np.abs(out[w.SOLVE_SCHUR] - out[w.SOLVE_STAGE]).max() < 1e-12
+    with pytest.raises(w.WpcccError) as e:
+        g.set_solve_mode(3)
+    assert e.value.status == w.EINVAL
+    g.close()
 
 
 def test_probabilities_kernel():
