@@ -54,6 +54,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP32_FFMA_MEASURED_TFLOPS = 69.9
 
 
+SOLVE_MODES = {"stage": lambda w: w.SOLVE_STAGE, "matrix": lambda w: w.SOLVE_MATRIX, "schur": lambda w: w.SOLVE_SCHUR}
+
+
 def _measured_bf16() -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -214,6 +217,7 @@ def run_batch(args) -> None:
     for v, basis, paths in sets_in:
         g = w.Basis(basis, device=local)
         g.set_workspace_limit(8 << 30)
+        g.set_solve_mode(SOLVE_MODES[args.solve_mode](w))
         zg = paths.z[0]
         n = zg.size - 1
         k = max(1, int(round(step_ref * 1.5 / v)))          # same z extent at every speed
@@ -294,7 +298,10 @@ def run_batch(args) -> None:
         evals = args.steps * b.size * (2 * (seg.size - 1) + 1)
         n_half = int(sum(1 for m in basis.P.st_m if m >= 0))
         flops["mol_gemm"] += 8.0 * basis.T.N * n_half * basis.quad.G * evals
-        flops["solve"] += (8.0 / 3.0) * basis.N ** 3 * evals
+        if args.solve_mode == "schur":
+            flops["solve"] += (4.0 * basis.P.N ** 2 * basis.T.N + (4.0 / 3.0) * basis.P.N ** 3) * evals
+        else:
+            flops["solve"] += (8.0 / 3.0) * basis.N ** 3 * evals
     dom_f = dom if dom in flops else "mol_gemm"
     achieved = flops[dom_f] / (prof[dom_f][0] / 1e3) / 1e12
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -308,13 +315,15 @@ def run_batch(args) -> None:
                                      f"(RK4 steps per speed {[int(seg.size - 1) for _, _, _, seg in sets]}), "
                                      "centred on z = 0; each launch recomputes all elements and solves",
                        "form": "batched plain FP64: all six bases' chunk pipelines captured into one CUDA graph, "
-                               "concurrent streams, autotuned chunk schedules",
+                               f"concurrent streams, autotuned chunk schedules; solve mode {args.solve_mode}",
                        "l2": "inputs larger than L2 (S and H of one launch: several GB)"},
             "batched_vs_separate_calls": {"separate_calls_value": world * units * args.steps / (ms_seq / 1e3),
                                           "speedup": ms_seq / ms},
             "autotune": {"chunk_steps": [int(x) for x in chunk_steps],
                          "ms_per_rk4_step": [float(x) for x in tuned], "create_s": t_create},
-            "roofline": {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm<double>", "solve": "k_lu_solve"}[dom_f],
+            "roofline": {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm<double>",
+                                                           "solve": "k_schur_factor" if args.solve_mode == "schur"
+                                                           else "k_lu_solve"}[dom_f],
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                          "peak_source": "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
@@ -490,7 +499,9 @@ def run_grad(args) -> None:
             "gradient_finite": finite,
             "fd_check": fd_check,
             "kernel_ms": {k: v_[0] for k, v_ in prof.items()},
-            "roofline": {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm<double>", "solve": "k_lu_solve"}[dom_f],
+            "roofline": {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm<double>",
+                                                           "solve": "k_schur_factor" if args.solve_mode == "schur"
+                                                           else "k_lu_solve"}[dom_f],
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                          "peak_source": "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz)",
@@ -571,7 +582,7 @@ def main() -> None:
     g = w.Basis(basis, device=local)
     ws_gb = args.workspace_gb or (16.0 if args.workload == WORKLOAD else 96.0)
     g.set_workspace_limit(int(ws_gb * (1 << 30)))
-    g.set_solve_mode({"stage": w.SOLVE_STAGE, "matrix": w.SOLVE_MATRIX, "schur": w.SOLVE_SCHUR}[args.solve_mode])
+    g.set_solve_mode(SOLVE_MODES[args.solve_mode](w))
     n_paths = paths.n_paths if args.paths <= 0 else min(args.paths, paths.n_paths)
     N = g.N
     zg = paths.z[0]

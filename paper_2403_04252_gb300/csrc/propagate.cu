@@ -32,7 +32,7 @@ struct RkArgs {
     int N;
     int N_T;                // target states (two-centre: S = [[I, K], [K^+, I]])
     int iters;              // refinement iterations (mixed-precision form)
-    const float2* LU32;     // chunk: FP32 factors per evaluation (mixed form)
+    const float2* LU32;     // chunk: FP32 factors per evaluation (mixed forms: LU, or K and the Schur factor)
     float2* carryLU32;      // per path (mixed form)
     const double2* H;       // chunk: H (one-centre, or X = S^{-1} H in matrix mode) per evaluation
     const double2* LU;      // chunk: LU factors of S (stage mode) or S itself (mixed form) per evaluation
@@ -47,7 +47,7 @@ struct RkArgs {
     int* flags;
 };
 
-enum RkMode { RK_MATRIX = 0, RK_STAGE = 1, RK_MIXED = 2, RK_SCHUR = 3 };
+enum RkMode { RK_MATRIX = 0, RK_STAGE = 1, RK_MIXED = 2, RK_SCHUR = 3, RK_MIXED_SCHUR = 4 };
 
 // Matrices of one position as the RK4 kernel sees them.
 struct PosMats {
@@ -61,7 +61,8 @@ struct PosMats {
 //   RK_MATRIX  X = S^{-1} H stored (the paper's form; one-centre: X = H)
 //   RK_STAGE   S^{-1} applied from FP64 LU factors at every stage
 //   RK_SCHUR   S^{-1} applied through the Schur complement's Cholesky factor at every stage
-//   RK_MIXED   S^{-1} applied by FP64 refinement on FP32 factors
+//   RK_MIXED   S^{-1} applied by FP64 refinement on FP32 LU factors
+//   RK_MIXED_SCHUR  the same on the FP32 Schur factors
 template <int MODE>
 __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
     extern __shared__ double2 rk_smem[];
@@ -76,7 +77,11 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
     float2* ds = reinterpret_cast<float2*>(rs + N);   // mixed: d
     // 32 x 32 diagonal block of the triangular solves (after the vectors of the mode)
     double2* us = t + N;                        // Schur: scratch of the projectile part
-    void* blk = MODE == RK_MIXED ? (void*)(ds + N + (N & 1)) : (MODE == RK_SCHUR ? (void*)(us + N) : (void*)(t + N));
+    float2* us32 = ds + N + (N & 1);            // mixed Schur: FP32 scratch of the projectile part
+    constexpr bool MIX = MODE == RK_MIXED || MODE == RK_MIXED_SCHUR;
+    void* blk = MODE == RK_MIXED ? (void*)(ds + N + (N & 1))
+                                 : MODE == RK_MIXED_SCHUR ? (void*)(us32 + N + (N & 1))
+                                                          : (MODE == RK_SCHUR ? (void*)(us + N) : (void*)(t + N));
     const PathChunk pc = A.pcs[blockIdx.x];
     const size_t mat = (size_t)N * N;
     double2* cg = A.c + (size_t)pc.path * N;
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
         PosMats m;
         m.H = A.H + (size_t)e * mat;
         m.S = MODE != RK_MATRIX ? A.LU + (size_t)e * mat : nullptr;
-        m.L32 = MODE == RK_MIXED ? A.LU32 + (size_t)e * mat : nullptr;
+        m.L32 = MIX ? A.LU32 + (size_t)e * mat : nullptr;
         m.piv = MODE != RK_MATRIX ? A.piv + (size_t)e * N : nullptr;
         return m;
     };
@@ -107,6 +112,9 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
             apply_schur(m.S, m.H, N, A.N_T, v, in, out, t, us, static_cast<double2*>(blk));
         } else if (MODE == RK_STAGE) {
             apply_LU(m.S, m.piv, m.H, N, v, in, out, t, static_cast<double2*>(blk));
+        } else if (MODE == RK_MIXED_SCHUR) {
+            apply_schur_mixed(m.S, m.L32, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds, us32,
+                              static_cast<float2*>(blk));
         } else {
             apply_LU_mixed(m.S, m.L32, m.piv, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds,
                            static_cast<float2*>(blk));
@@ -118,7 +126,7 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
     } else {
         Mz.H = A.carryH + (size_t)pc.path * mat;
         Mz.S = MODE != RK_MATRIX ? A.carryLU + (size_t)pc.path * mat : nullptr;
-        Mz.L32 = MODE == RK_MIXED ? A.carryLU32 + (size_t)pc.path * mat : nullptr;
+        Mz.L32 = MIX ? A.carryLU32 + (size_t)pc.path * mat : nullptr;
         Mz.piv = MODE != RK_MATRIX ? A.carryPiv + (size_t)pc.path * N : nullptr;
     }
     for (int s = 0; s < pc.nsteps; ++s) {
@@ -171,7 +179,7 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
             for (size_t q = threadIdx.x; q < mat; q += RK_THREADS) cL[q] = Mz.S[q];
             for (int q = threadIdx.x; q < N; q += RK_THREADS) cP[q] = Mz.piv[q];
         }
-        if (MODE == RK_MIXED) {
+        if (MIX) {
             float2* cL32 = A.carryLU32 + (size_t)pc.path * mat;
             for (size_t q = threadIdx.x; q < mat; q += RK_THREADS) cL32[q] = Mz.L32[q];
         }
@@ -180,6 +188,8 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
 
 size_t rk_smem_bytes(int mode, int N) {
     if (mode == RK_SCHUR) return (size_t)N * 6 * sizeof(double2) + 32 * 32 * sizeof(double2);
+    if (mode == RK_MIXED_SCHUR)
+        return (size_t)N * 7 * sizeof(double2) + 2 * (size_t)(N + (N & 1)) * sizeof(float2) + 32 * 32 * sizeof(float2);
     return mode == RK_MIXED ? (size_t)N * 7 * sizeof(double2) + (size_t)(N + (N & 1)) * sizeof(float2) +
                                   32 * 32 * sizeof(float2)
                             : (size_t)N * 5 * sizeof(double2) + 32 * 32 * sizeof(double2);
@@ -274,8 +284,8 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     P.mixed = P.two && precision_mode >= 1;
     P.elem_precision = P.two && (precision_mode == 1 || precision_mode == 3) ? precision_mode : 0;
     P.stage = P.two && !P.mixed && B->solve_mode != WPCCC_SOLVE_MATRIX;
-    P.schur = P.stage && B->solve_mode == WPCCC_SOLVE_SCHUR;
-    P.mode = P.mixed ? RK_MIXED : (P.schur ? RK_SCHUR : (P.stage ? RK_STAGE : RK_MATRIX));
+    P.schur = P.two && B->solve_mode == WPCCC_SOLVE_SCHUR;
+    P.mode = P.mixed ? (P.schur ? RK_MIXED_SCHUR : RK_MIXED) : (P.schur ? RK_SCHUR : (P.stage ? RK_STAGE : RK_MATRIX));
     if (rk_smem_bytes(P.mode, N) > (size_t)227 * 1024)
         return fail(WPCCC_EINVAL, "wpccc_propagate: N too large for the RK4 kernel's shared memory in this mode");
     const size_t mat = (size_t)N * N;
@@ -423,6 +433,7 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
     WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+    WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
     const size_t hS = P.sz_S / 2 / sizeof(double2), hH = P.sz_H / 2 / sizeof(double2);
     const size_t hL = P.sz_LU32 / 2 / sizeof(float2), hP = P.sz_piv / 2 / sizeof(int), hI = P.sz_info / 2 / sizeof(int);
     RkArgs ra;
@@ -455,7 +466,8 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
         if (s != WPCCC_OK) return s;
         if (P.two) {
             cudaEvent_t e0 = B->prof.begin(PROF_SOLVE, st);
-            if (P.mixed) s = launch_factor_f32(N, nev, bS, bL, bP, bI, st);
+            if (P.mixed && P.schur) s = launch_schur_factor_f32(N, B->N_T, nev, bS, bL, bI, st);
+            else if (P.mixed) s = launch_factor_f32(N, nev, bS, bL, bP, bI, st);
             else if (P.schur) s = launch_schur_factor(N, B->N_T, nev, bS, bI, st);
             else s = launch_solve(N, nev, bS, P.stage ? nullptr : bH, bP, bI, st);
             if (s != WPCCC_OK) return s;
@@ -471,6 +483,7 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
         ra.piv = P.mode != RK_MATRIX ? bP : nullptr;
         ra.info = bI;
         if (P.mode == RK_MIXED) k_rk4<RK_MIXED><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
+        else if (P.mode == RK_MIXED_SCHUR) k_rk4<RK_MIXED_SCHUR><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else if (P.mode == RK_SCHUR) k_rk4<RK_SCHUR><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else if (P.mode == RK_STAGE) k_rk4<RK_STAGE><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else k_rk4<RK_MATRIX><<<npc, RK_THREADS, rk_smem, rs>>>(ra);

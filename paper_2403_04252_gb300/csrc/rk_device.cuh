@@ -190,9 +190,12 @@ static __device__ void apply_LU_mixed(const double2* __restrict__ S64, const flo
 }
 
 // x <- C^{-1} x with C = L L^+ (L lower, real positive diagonal, column-major with leading dimension ld),
-// n unknowns.  Blocked by 32 rows: the diagonal block is staged in shared memory (blk) and solved by one
-// warp; off-diagonal updates: rows below (forward) by all threads, rows above (backward) a warp per row.
-static __device__ void chol_solve_inplace(const double2* __restrict__ L, int ld, int n, double2* x, double2* blk) {
+// n unknowns; C2 = double2 (FP64 factor) or float2 (FP32 factor of the mixed-precision form).  Blocked by
+// 32 rows: the diagonal block is staged in shared memory (blk) and solved by one warp; off-diagonal
+// updates: rows below (forward) by all threads, rows above (backward) a warp per row.
+template <typename C2>
+static __device__ void chol_solve_inplace(const C2* __restrict__ L, int ld, int n, C2* x, C2* blk) {
+    using R = decltype(C2().x);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // L z = x
     for (int kb = 0; kb < n; kb += 32) {
@@ -203,17 +206,17 @@ static __device__ void chol_solve_inplace(const double2* __restrict__ L, int ld,
         }
         __syncthreads();
         if (warp == 0) {
-            double2 v = x[kb + (lane < nb ? lane : 0)];
+            C2 v = x[kb + (lane < nb ? lane : 0)];
             for (int j = 0; j < nb; ++j) {
                 if (lane == j) {
-                    const double d = 1.0 / blk[j * 32 + j].x;
+                    const R d = R(1) / blk[j * 32 + j].x;
                     v.x *= d;
                     v.y *= d;
                 }
-                const double vr = __shfl_sync(0xffffffffu, v.x, j);
-                const double vi = __shfl_sync(0xffffffffu, v.y, j);
+                const R vr = __shfl_sync(0xffffffffu, v.x, j);
+                const R vi = __shfl_sync(0xffffffffu, v.y, j);
                 if (lane > j && lane < nb) {
-                    const double2 l = blk[j * 32 + lane];
+                    const C2 l = blk[j * 32 + lane];
                     v.x = fma(-l.x, vr, v.x);
                     v.x = fma(l.y, vi, v.x);
                     v.y = fma(-l.x, vi, v.y);
@@ -224,10 +227,10 @@ static __device__ void chol_solve_inplace(const double2* __restrict__ L, int ld,
         }
         __syncthreads();
         for (int i = kb + nb + tid; i < n; i += RK_THREADS) {
-            double2 a = x[i];
+            C2 a = x[i];
             for (int j = 0; j < nb; ++j) {
-                const double2 l = L[(size_t)i + (size_t)(kb + j) * ld];
-                const double2 b = x[kb + j];
+                const C2 l = L[(size_t)i + (size_t)(kb + j) * ld];
+                const C2 b = x[kb + j];
                 a.x = fma(-l.x, b.x, a.x);
                 a.x = fma(l.y, b.y, a.x);
                 a.y = fma(-l.x, b.y, a.y);
@@ -247,17 +250,17 @@ static __device__ void chol_solve_inplace(const double2* __restrict__ L, int ld,
         }
         __syncthreads();
         if (warp == 0) {
-            double2 v = x[kb + (lane < nb ? lane : 0)];
+            C2 v = x[kb + (lane < nb ? lane : 0)];
             for (int j = nb - 1; j >= 0; --j) {
                 if (lane == j) {
-                    const double d = 1.0 / blk[j * 32 + j].x;
+                    const R d = R(1) / blk[j * 32 + j].x;
                     v.x *= d;
                     v.y *= d;
                 }
-                const double vr = __shfl_sync(0xffffffffu, v.x, j);
-                const double vi = __shfl_sync(0xffffffffu, v.y, j);
+                const R vr = __shfl_sync(0xffffffffu, v.x, j);
+                const R vi = __shfl_sync(0xffffffffu, v.y, j);
                 if (lane < j) {
-                    const double2 l = blk[lane * 32 + j];   // L[j][lane], conjugated below
+                    const C2 l = blk[lane * 32 + j];   // L[j][lane], conjugated below
                     v.x = fma(-l.x, vr, v.x);
                     v.x = fma(-l.y, vi, v.x);
                     v.y = fma(-l.x, vi, v.y);
@@ -269,10 +272,10 @@ static __device__ void chol_solve_inplace(const double2* __restrict__ L, int ld,
         __syncthreads();
         // rows i < kb: x_i -= sum_jj conj(L[kb + jj][i]) x[kb + jj], a warp per row, lanes over jj
         for (int i = warp; i < kb; i += RK_THREADS / 32) {
-            double re = 0.0, im = 0.0;
+            R re = 0, im = 0;
             if (lane < nb) {
-                const double2 l = L[(size_t)(kb + lane) + (size_t)i * ld];
-                const double2 b = x[kb + lane];
+                const C2 l = L[(size_t)(kb + lane) + (size_t)i * ld];
+                const C2 b = x[kb + lane];
                 re = l.x * b.x + l.y * b.y;
                 im = l.x * b.y - l.y * b.x;
             }
@@ -280,25 +283,31 @@ static __device__ void chol_solve_inplace(const double2* __restrict__ L, int ld,
                 re += __shfl_xor_sync(0xffffffffu, re, o);
                 im += __shfl_xor_sync(0xffffffffu, im, o);
             }
-            if (lane == 0) x[i] = make_double2(x[i].x - re, x[i].y - im);
+            if (lane == 0) {
+                C2 q = x[i];
+                q.x -= re;
+                q.y -= im;
+                x[i] = q;
+            }
         }
         __syncthreads();
     }
 }
 
-// Schur form of the stage operator: k = -(i/v) S^{-1} (H y) with S = [[I, K], [K^+, I]] held as K (in
-// place) and the Cholesky factor L of I - K^+ K (lower triangle of S's projectile block):
-//   u_P = t_P - K^+ t_T,  x_P = (L L^+)^{-1} u_P,  x_T = t_T - K x_P.   t, u: shared scratch of N.
-static __device__ void apply_schur(const double2* __restrict__ S, const double2* __restrict__ Hm, int N, int N_T,
-                                   double v, const double2* y, double2* k, double2* t, double2* u, double2* blk) {
+// t <- S^{-1} t for S = [[I, K], [K^+, I]] held as K (rows 0..N_T-1 of columns N_T..N-1 of D) and the
+// Cholesky factor L of the Schur complement I - K^+ K (lower triangle of D's projectile block), D
+// column-major N x N:  u_P = t_P - K^+ t_T,  t_P = (L L^+)^{-1} u_P,  t_T = t_T - K t_P.
+// u: shared scratch of N - N_T.  C2 = double2 (FP64) or float2 (FP32 preconditioner).
+template <typename C2>
+static __device__ void schur_solve_inplace(const C2* __restrict__ D, int N, int N_T, C2* t, C2* u, C2* blk) {
+    using R = decltype(C2().x);
     const int NP = N - N_T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    matvec(Hm, N, y, t);
-    const double2* K = S + (size_t)N_T * N;
+    const C2* K = D + (size_t)N_T * N;
     for (int j = warp; j < NP; j += RK_THREADS / 32) {
-        double re = 0.0, im = 0.0;
-        const double2* col = K + (size_t)j * N;
+        R re = 0, im = 0;
+        const C2* col = K + (size_t)j * N;
         for (int i = lane; i < N_T; i += 32) {
-            const double2 a = col[i], b = t[i];
+            const C2 a = col[i], b = t[i];
             re = fma(a.x, b.x, re);
             re = fma(a.y, b.y, re);
             im = fma(a.x, b.y, im);
@@ -308,24 +317,69 @@ static __device__ void apply_schur(const double2* __restrict__ S, const double2*
             re += __shfl_xor_sync(0xffffffffu, re, o);
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) u[j] = make_double2(t[N_T + j].x - re, t[N_T + j].y - im);
+        if (lane == 0) {
+            C2 q = t[N_T + j];
+            q.x -= re;
+            q.y -= im;
+            u[j] = q;
+        }
     }
     __syncthreads();
-    chol_solve_inplace(S + N_T + (size_t)N_T * N, N, NP, u, blk);
+    chol_solve_inplace<C2>(D + N_T + (size_t)N_T * N, N, NP, u, blk);
     for (int i = threadIdx.x; i < N_T; i += RK_THREADS) {
-        double re = 0.0, im = 0.0;
+        R re = 0, im = 0;
         for (int j = 0; j < NP; ++j) {
-            const double2 a = K[(size_t)i + (size_t)j * N];
-            const double2 b = u[j];
+            const C2 a = K[(size_t)i + (size_t)j * N];
+            const C2 b = u[j];
             re = fma(a.x, b.x, re);
             re = fma(-a.y, b.y, re);
             im = fma(a.x, b.y, im);
             im = fma(a.y, b.x, im);
         }
-        const double2 xt = make_double2(t[i].x - re, t[i].y - im);
-        k[i] = make_double2(xt.y / v, -xt.x / v);
+        C2 q = t[i];
+        q.x -= re;
+        q.y -= im;
+        t[i] = q;
     }
-    for (int j = threadIdx.x; j < NP; j += RK_THREADS) k[N_T + j] = make_double2(u[j].y / v, -u[j].x / v);
+    for (int j = threadIdx.x; j < NP; j += RK_THREADS) t[N_T + j] = u[j];
+    __syncthreads();
+}
+
+// Schur form of the stage operator: k = -(i/v) S^{-1} (H y) with S's Schur factors in place of S
+// (FP64).  t, u: shared scratch of N.
+static __device__ void apply_schur(const double2* __restrict__ S, const double2* __restrict__ Hm, int N, int N_T,
+                                   double v, const double2* y, double2* k, double2* t, double2* u, double2* blk) {
+    matvec(Hm, N, y, t);
+    schur_solve_inplace<double2>(S, N, N_T, t, u, blk);
+    for (int i = threadIdx.x; i < N; i += RK_THREADS) k[i] = make_double2(t[i].y / v, -t[i].x / v);
+    __syncthreads();
+}
+
+// Mixed-precision Schur form: k = -(i/v) x with S x = H y solved by FP64 iterative refinement
+// preconditioned by the FP32 Schur factors D32 (K in FP32 and the FP32 Cholesky factor of I - K^+ K):
+// x_0 = 0, r = H y - S x_n (FP64, S's off-diagonal blocks), x_{n+1} = x_n + S_32^{-1} r.
+// Shared scratch: b, x, r (double2, N each), d (float2, N) and u (float2, N - N_T).
+static __device__ void apply_schur_mixed(const double2* __restrict__ S64, const float2* __restrict__ D32,
+                                         const double2* __restrict__ Hm, int N, int N_T, double v, int iters,
+                                         const double2* y, double2* k, double2* b, double2* x, double2* r, float2* d,
+                                         float2* u, float2* blk) {
+    matvec(Hm, N, y, b);
+    for (int it = 0; it < iters; ++it) {
+        const double2* rr = b;
+        if (it > 0) {
+            residual_S(S64, N, N_T, x, b, r);
+            rr = r;
+        }
+        for (int i = threadIdx.x; i < N; i += RK_THREADS) d[i] = make_float2((float)rr[i].x, (float)rr[i].y);
+        __syncthreads();
+        schur_solve_inplace<float2>(D32, N, N_T, d, u, blk);
+        for (int i = threadIdx.x; i < N; i += RK_THREADS) {
+            const double2 dx = make_double2((double)d[i].x, (double)d[i].y);
+            x[i] = it == 0 ? dx : make_double2(x[i].x + dx.x, x[i].y + dx.y);
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < N; i += RK_THREADS) k[i] = make_double2(x[i].y / v, -x[i].x / v);
     __syncthreads();
 }
 

@@ -9,7 +9,9 @@
 // real flops) and the Cholesky ((4/3) N_P^3), against (8/3) N^3 for the LU of S.
 //
 // One thread block per system; L overwrites the lower triangle of S's projectile-projectile block
-// (the identity block, which the propagation never reads otherwise); K stays in place.
+// (the identity block, which the propagation never reads otherwise); K stays in place.  The mixed-
+// precision forms take the same factorisation in FP32 into a separate buffer, as the preconditioner of
+// their FP64 iterative refinement.
 #include <algorithm>
 
 #include "wpccc_internal.cuh"
@@ -20,32 +22,37 @@ constexpr int SC_NB = 32;          // Cholesky panel width
 constexpr int SC_THREADS = 256;
 constexpr int SC_TM = 64, SC_TN = 32;
 
+template <typename R> struct SchurC;
+template <> struct SchurC<double> { using type = double2; };
+template <> struct SchurC<float> { using type = float2; };
+
 // C[m x n] -= sum_kk A(i, kk) B(kk, j) over the tiles that touch the lower triangle (i >= j) of C, for a
 // reduction of kd terms taken SC_NB at a time; A and B are element loaders.
-template <typename LA, typename LB>
-__device__ void cta_update_lower(double2* __restrict__ C, int ldc, int m, int kd, LA loadA, LB loadB,
-                                 double2* sA, double2* sB) {
+template <typename R, typename LA, typename LB>
+__device__ void cta_update_lower(typename SchurC<R>::type* __restrict__ C, int ldc, int m, int kd, LA loadA,
+                                 LB loadB, typename SchurC<R>::type* sA, typename SchurC<R>::type* sB) {
+    using C2 = typename SchurC<R>::type;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     for (int i0 = 0; i0 < m; i0 += SC_TM) {
         for (int j0 = 0; j0 < m && j0 < i0 + SC_TM; j0 += SC_TN) {
-            double2 acc[4][2];
+            C2 acc[4][2];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int c = 0; c < 2; ++c) acc[a][c] = make_double2(0.0, 0.0);
+                for (int c = 0; c < 2; ++c) acc[a][c] = C2{R(0), R(0)};
             for (int k0 = 0; k0 < kd; k0 += SC_NB) {
                 for (int idx = tid; idx < SC_TM * SC_NB; idx += SC_THREADS) {
                     const int ii = idx % SC_TM, kk = idx / SC_TM;
-                    sA[kk * SC_TM + ii] = (i0 + ii < m && k0 + kk < kd) ? loadA(i0 + ii, k0 + kk) : make_double2(0.0, 0.0);
+                    sA[kk * SC_TM + ii] = (i0 + ii < m && k0 + kk < kd) ? loadA(i0 + ii, k0 + kk) : C2{R(0), R(0)};
                 }
                 for (int idx = tid; idx < SC_NB * SC_TN; idx += SC_THREADS) {
                     const int kk = idx % SC_NB, jj = idx / SC_NB;
-                    sB[kk * SC_TN + jj] = (j0 + jj < m && k0 + kk < kd) ? loadB(k0 + kk, j0 + jj) : make_double2(0.0, 0.0);
+                    sB[kk * SC_TN + jj] = (j0 + jj < m && k0 + kk < kd) ? loadB(k0 + kk, j0 + jj) : C2{R(0), R(0)};
                 }
                 __syncthreads();
                 const int kn = min(SC_NB, kd - k0);
                 for (int kk = 0; kk < kn; ++kk) {
-                    double2 av[4], bv[2];
+                    C2 av[4], bv[2];
 #pragma unroll
                     for (int a = 0; a < 4; ++a) av[a] = sA[kk * SC_TM + ty + 16 * a];
 #pragma unroll
@@ -70,8 +77,8 @@ __device__ void cta_update_lower(double2* __restrict__ C, int ldc, int m, int kd
                 for (int c = 0; c < 2; ++c) {
                     const int j = j0 + tx + 16 * c;
                     if (j >= m || j > i) continue;
-                    double2* p = C + (size_t)i + (size_t)j * ldc;
-                    double2 v = *p;
+                    C2* p = C + (size_t)i + (size_t)j * ldc;
+                    C2 v = *p;
                     v.x -= acc[a][c].x;
                     v.y -= acc[a][c].y;
                     *p = v;
@@ -81,24 +88,46 @@ __device__ void cta_update_lower(double2* __restrict__ C, int ldc, int m, int kd
     }
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, double2* __restrict__ Sall,
+// One system per block.  R = double: D is S itself (FP64, in place).  R = float (preconditioner of the
+// mixed-precision form): D is a separate FP32 N x N buffer that receives K rounded to FP32 in its
+// target-projectile block and the FP32 Cholesky factor in its projectile block; S is only read.
+template <typename R>
+__global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, const double2* Sall,
+                                                             typename SchurC<R>::type* __restrict__ Dall,
                                                              int* __restrict__ info_all) {
-    extern __shared__ double2 sc_smem[];
-    double2* sA = sc_smem;                 // SC_TM * SC_NB
-    double2* sB = sA + SC_TM * SC_NB;      // SC_NB * SC_TN
+    using C2 = typename SchurC<R>::type;
+    extern __shared__ __align__(16) unsigned char sc_smem_raw[];
+    C2* sA = reinterpret_cast<C2*>(sc_smem_raw);   // SC_TM * SC_NB
+    C2* sB = sA + SC_TM * SC_NB;                    // SC_NB * SC_TN
     __shared__ int s_info;
+    __shared__ R s_d;
     const int sys = blockIdx.x, tid = threadIdx.x;
     const int NP = N - N_T;
-    double2* S = Sall + (size_t)sys * N * N;
-    double2* C = S + N_T + (size_t)N_T * N;      // projectile block, leading dimension N
-    const double2* K = S + (size_t)N_T * N;      // K[i][j] = S[i][N_T + j], i < N_T
+    const size_t mat = (size_t)N * N;
+    C2* D = Dall + (size_t)sys * mat;
+    C2* C = D + N_T + (size_t)N_T * N;           // projectile block, leading dimension N
+    const C2* K = D + (size_t)N_T * N;           // K[i][j] = D[i][N_T + j], i < N_T
     if (tid == 0) s_info = 0;
+    if (sizeof(R) == 4) {
+        // K to FP32, identity into the lower triangle of the projectile block
+        const double2* S = Sall + (size_t)sys * mat;
+        for (size_t q = tid; q < (size_t)N_T * NP; q += SC_THREADS) {
+            const int i = (int)(q % N_T), j = (int)(q / N_T);
+            const double2 a = S[(size_t)i + (size_t)(N_T + j) * N];
+            D[(size_t)i + (size_t)(N_T + j) * N] = C2{(R)a.x, (R)a.y};
+        }
+        for (size_t q = tid; q < (size_t)NP * NP; q += SC_THREADS) {
+            const int i = (int)(q % NP), j = (int)(q / NP);
+            if (i >= j) C[(size_t)i + (size_t)j * N] = C2{R(i == j ? 1 : 0), R(0)};
+        }
+        __syncthreads();
+    }
     // C = I - K^+ K on the lower triangle (the block holds I already)
-    cta_update_lower(
+    cta_update_lower<R>(
         C, N, NP, N_T,
         [&](int i, int kk) {   // (K^+)[i][kk] = conj(K[kk][i])
-            const double2 a = K[(size_t)kk + (size_t)i * N];
-            return make_double2(a.x, -a.y);
+            const C2 a = K[(size_t)kk + (size_t)i * N];
+            return C2{a.x, -a.y};
         },
         [&](int kk, int j) { return K[(size_t)kk + (size_t)j * N]; }, sA, sB);
     __syncthreads();
@@ -107,21 +136,20 @@ __global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, dou
         const int nb = min(SC_NB, NP - k0);
         for (int kk = 0; kk < nb; ++kk) {
             const int k = k0 + kk;
-            __shared__ double s_d;
             if (tid == 0) {
-                double d = C[(size_t)k + (size_t)k * N].x;
-                if (!(d > 0.0)) {
+                R d = C[(size_t)k + (size_t)k * N].x;
+                if (!(d > R(0))) {
                     if (s_info == 0) s_info = k + 1;
-                    d = 1.0;
+                    d = R(1);
                 }
                 s_d = sqrt(d);
-                C[(size_t)k + (size_t)k * N] = make_double2(s_d, 0.0);
+                C[(size_t)k + (size_t)k * N] = C2{s_d, R(0)};
             }
             __syncthreads();
-            const double inv = 1.0 / s_d;
+            const R inv = R(1) / s_d;
             for (int i = k + 1 + tid; i < NP; i += SC_THREADS) {
-                double2* q = C + (size_t)i + (size_t)k * N;
-                *q = make_double2(q->x * inv, q->y * inv);
+                C2* q = C + (size_t)i + (size_t)k * N;
+                *q = C2{q->x * inv, q->y * inv};
             }
             __syncthreads();
             // rank-1 update of the rest of the panel: C[i][j] -= C[i][k] conj(C[j][k]), k < j <= i
@@ -129,10 +157,10 @@ __global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, dou
             for (int idx = tid; idx < ncol * nrow; idx += SC_THREADS) {
                 const int j = k + 1 + idx / nrow, i = k + 1 + idx % nrow;
                 if (i < j) continue;
-                const double2 l = C[(size_t)i + (size_t)k * N];
-                const double2 u = C[(size_t)j + (size_t)k * N];
-                double2* q = C + (size_t)i + (size_t)j * N;
-                double2 v = *q;
+                const C2 l = C[(size_t)i + (size_t)k * N];
+                const C2 u = C[(size_t)j + (size_t)k * N];
+                C2* q = C + (size_t)i + (size_t)j * N;
+                C2 v = *q;
                 v.x -= l.x * u.x + l.y * u.y;
                 v.y -= l.y * u.x - l.x * u.y;
                 *q = v;
@@ -142,13 +170,13 @@ __global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, dou
         // trailing update C22 -= L21 L21^+
         const int m2 = NP - (k0 + nb);
         if (m2 > 0) {
-            double2* C22 = C + (size_t)(k0 + nb) + (size_t)(k0 + nb) * N;
-            const double2* L21 = C + (size_t)(k0 + nb) + (size_t)k0 * N;
-            cta_update_lower(
+            C2* C22 = C + (size_t)(k0 + nb) + (size_t)(k0 + nb) * N;
+            const C2* L21 = C + (size_t)(k0 + nb) + (size_t)k0 * N;
+            cta_update_lower<R>(
                 C22, N, m2, nb, [&](int i, int kk) { return L21[(size_t)i + (size_t)kk * N]; },
                 [&](int kk, int j) {
-                    const double2 a = L21[(size_t)j + (size_t)kk * N];
-                    return make_double2(a.x, -a.y);
+                    const C2 a = L21[(size_t)j + (size_t)kk * N];
+                    return C2{a.x, -a.y};
                 },
                 sA, sB);
         }
@@ -160,9 +188,18 @@ __global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, dou
 wpccc_status launch_schur_factor(int N, int N_T, int batch, double2* S, int* info, cudaStream_t st) {
     if (batch == 0) return WPCCC_OK;
     const int smem = (int)(sizeof(double2) * (SC_TM * SC_NB + SC_NB * SC_TN));   // 48 KB: needs the opt-in
-    WPCCC_CUDA(cudaFuncSetAttribute(k_schur_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_schur_factor<<<batch, SC_THREADS, smem, st>>>(N, N_T, S, info);
-    WPCCC_CHECK_LAUNCH("k_schur_factor");
+    WPCCC_CUDA(cudaFuncSetAttribute(k_schur_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_schur_factor<double><<<batch, SC_THREADS, smem, st>>>(N, N_T, S, S, info);
+    WPCCC_CHECK_LAUNCH("k_schur_factor<double>");
+    return WPCCC_OK;
+}
+
+wpccc_status launch_schur_factor_f32(int N, int N_T, int batch, const double2* S, float2* D, int* info,
+                                     cudaStream_t st) {
+    if (batch == 0) return WPCCC_OK;
+    const int smem = (int)(sizeof(float2) * (SC_TM * SC_NB + SC_NB * SC_TN));
+    k_schur_factor<float><<<batch, SC_THREADS, smem, st>>>(N, N_T, S, D, info);
+    WPCCC_CHECK_LAUNCH("k_schur_factor<float>");
     return WPCCC_OK;
 }
 

@@ -197,6 +197,10 @@ wpccc_status launch_factor_f32(int N, int batch, const double2* S, float2* LU, i
 // Queue the batched Schur-complement factorisation of two-centre overlap matrices S (Cholesky factor of
 // I - K^+ K into the lower triangle of S's projectile block; info as ZPOTRF).
 wpccc_status launch_schur_factor(int N, int N_T, int batch, double2* S, int* info, cudaStream_t st);
+// The same in FP32 into D (K rounded to FP32 and the Cholesky factor), S only read: the preconditioner
+// of the mixed-precision forms' refinement.
+wpccc_status launch_schur_factor_f32(int N, int N_T, int batch, const double2* S, float2* D, int* info,
+                                     cudaStream_t st);
 
 // Queue the batched solve of S X = H (results in place).
 wpccc_status launch_solve(int N, int batch, double2* S, double2* H, int* ipiv, int* info,

@@ -265,9 +265,11 @@ def test_probabilities_kernel():
 MIXED_TOL = 1e-6     # absolute, per probability
 
 
-def _mixed_errors(basis, bs, v, zgs, workspace=None, mode=1):
+def _mixed_errors(basis, bs, v, zgs, workspace=None, mode=1, solve=None):
     w = _w()
     g = w.Basis(basis)
+    if solve is not None:
+        g.set_solve_mode(solve)
     if workspace:
         g.set_workspace_limit(workspace)
     c = g.propagate(bs, v, zgs, precision_mode=mode)
@@ -280,20 +282,23 @@ def _mixed_errors(basis, bs, v, zgs, workspace=None, mode=1):
     return np.array(errs)
 
 
-def test_mixed_form_small_two_centre(small2c):
-    # mode 1 (FP32 elements and LU, FP64 refinement) on a p + H-like basis, against the oracle
+@pytest.mark.parametrize("solve", [0, 2])
+def test_mixed_form_small_two_centre(small2c, solve):
+    # mode 1 (FP32 elements, FP32 factors of S, FP64 refinement) on a p + H-like basis, against the
+    # oracle; the FP32 factors are the pivoted LU of S (solve mode 0) or the Schur factors (2)
     bs = np.array([0.5, 2.0])
     zgs = [wi.uniform_zgrid(-6.0, 6.0, 0.2), wi.uniform_zgrid(-4.0, 5.0, 0.25)]
-    err = _mixed_errors(small2c, bs, 1.3, zgs, workspace=64 << 20, mode=1)
+    err = _mixed_errors(small2c, bs, 1.3, zgs, workspace=64 << 20, mode=1, solve=solve)
     assert err.max() <= MIXED_TOL, err.max()
 
 
-def test_mixed_fp64_elements_small_uneven_two_centre(small2c_uneven):
-    # mode 2 (FP64 elements, FP32 LU, FP64 refinement) on a C6+ on H-like basis (stiff near closest
+@pytest.mark.parametrize("solve", [0, 2])
+def test_mixed_fp64_elements_small_uneven_two_centre(small2c_uneven, solve):
+    # mode 2 (FP64 elements, FP32 factors, FP64 refinement) on a C6+ on H-like basis (stiff near closest
     # approach: h = 0.05), against the oracle
     bs = np.array([0.5, 2.0])
     zgs = [wi.uniform_zgrid(-3.0, 3.0, 0.05), wi.uniform_zgrid(-2.0, 2.5, 0.05)]
-    err = _mixed_errors(small2c_uneven, bs, 1.3, zgs, workspace=64 << 20, mode=2)
+    err = _mixed_errors(small2c_uneven, bs, 1.3, zgs, workspace=64 << 20, mode=2, solve=solve)
     assert err.max() <= MIXED_TOL, err.max()
 
 
@@ -311,19 +316,22 @@ def test_mixed_form_full_two_centre_sampled(config2):
 
 def test_mixed_form_full_paths_against_fp64(config2):
     # whole paths (1000 RK4 steps, z from -50 to 50) of the two-centre p + H workload: the mixed form
-    # against the plain FP64 form on the GPU (itself within 1e-10 of the oracle, tests above)
+    # (with either FP32 factorisation) against the plain FP64 form on the GPU (itself within 1e-10 of
+    # the oracle, tests above)
     basis, paths = config2
     w = _w()
     g = w.Basis(basis)
     idx = [0, 4, 12, 31]          # b = 0.2, 1.72, 4.77, 12
     zg = paths.z[0]
     c64 = g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=0)
-    cmx = g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=1)
     P64 = w.probabilities(c64).cpu().numpy()
-    Pmx = w.probabilities(cmx).cpu().numpy()
-    err = np.abs(Pmx - P64)
-    print("mixed-form max |dP| per path:", err.max(axis=1))
-    assert err.max() <= MIXED_TOL
+    for solve in (w.SOLVE_STAGE, w.SOLVE_SCHUR):
+        g.set_solve_mode(solve)
+        cmx = g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=1)
+        Pmx = w.probabilities(cmx).cpu().numpy()
+        err = np.abs(Pmx - P64)
+        print("mixed-form max |dP| per path, solve mode", solve, ":", err.max(axis=1))
+        assert err.max() <= MIXED_TOL
 
 
 # ---------------------------------------------------------------- batched form
