@@ -542,7 +542,8 @@ def main() -> None:
     ap.add_argument("--no-fd-check", action="store_true", help="pLi_2c_grad: skip the central-difference sample")
     ap.add_argument("--workspace-gb", type=float, default=0.0, help="0: 16 GB (p + H) or 96 GB (C6+ on H)")
     ap.add_argument("--precision", default="auto",
-                    choices=["auto", "fp64", "mixed", "mixed-fp64-elements", "mixed-tensor-core"],
+                    choices=["auto", "fp64", "mixed", "mixed-fp64-elements", "mixed-tensor-core", "fp64-tensor-core",
+                             "mixed-fp64-tc-elements"],
                     help="auto: time plain FP64 and the reduced-precision forms, report the fastest form whose "
                          "probabilities stay within 1e-6 of the FP64 form on the same steps")
     args = ap.parse_args()
@@ -639,11 +640,12 @@ def main() -> None:
         return {"prec": prec, "ms": ms, "value": world * n_paths * STEP * args.steps / (ms / 1e3),
                 "prof": prof, "clocks": clocks, "P": w.probabilities(c).cpu().numpy()}
 
-    names = {0: "fp64", 1: "mixed", 2: "mixed-fp64-elements", 3: "mixed-tensor-core"}
+    names = {0: "fp64", 1: "mixed", 2: "mixed-fp64-elements", 3: "mixed-tensor-core", 4: "fp64-tensor-core",
+             5: "mixed-fp64-tc-elements"}
     forms = {}
     if args.precision == "auto":
         forms[0] = measure(0)
-        for prec in (1, 3, 2):
+        for prec in (4, 1, 3, 5, 2):
             if prec == 2 and any(forms[p].get("err", 1.0) <= 1e-6 for p in forms if p != 0):
                 break
             try:
@@ -655,7 +657,7 @@ def main() -> None:
         ok = [p for p in forms if p == 0 or forms[p].get("err", 1.0) <= 1e-6]
         head = max(ok, key=lambda p: forms[p]["value"])
     else:
-        head = {"fp64": 0, "mixed": 1, "mixed-fp64-elements": 2, "mixed-tensor-core": 3}[args.precision]
+        head = {v_: k for k, v_ in names.items()}[args.precision]
         forms[head] = measure(head)
         if head >= 1:
             ref = measure(0)
@@ -692,23 +694,34 @@ def main() -> None:
     # with q >= 0 (the reflection gives the rest): 4 real flops per node per integral
     flops_mol = 8.0 * NT * n_half * G
     # LU, plus N right-hand sides in the paper's form; the stage form's triangular solves run in the RK4 kernel.
-    # Schur form: the lower triangle of K^+ K (4 N_P^2 N_T) and the Cholesky of I - K^+ K (4/3 N_P^3)
-    schur = args.solve_mode == "schur" and prec == 0
+    # Schur form (every two-centre form): the lower triangle of K^+ K (4 N_P^2 N_T) and the Cholesky of
+    # I - K^+ K (4/3 N_P^3), in FP64 (forms 0, 4) or FP32 (the refined forms)
+    mixed_form = prec in (1, 2, 3, 5)
+    schur = args.solve_mode == "schur"
     if schur:
         flops_solve = 4.0 * NP_ * NP_ * NT + (4.0 / 3.0) * NP_ ** 3
     else:
-        flops_solve = (8.0 / 3.0 + (8.0 if (args.solve_mode == "matrix" and prec == 0) else 0.0)) * N ** 3
+        flops_solve = (8.0 / 3.0 + (8.0 if (args.solve_mode == "matrix" and not mixed_form) else 0.0)) * N ** 3
     # RK4 per path-step (FP64): 4 applications of M; matrix form X y, stage form H y + two triangles,
-    # Schur form H y, K^+ t_T, K x_P and two triangles of N_P, mixed forms H y and one refinement residual S x
-    if schur:
+    # Schur form H y, K^+ t_T, K x_P and two triangles of N_P; refined forms H y, two preconditioner
+    # solves and one residual S x (off-diagonal blocks)
+    if mixed_form:
+        solve_once = (16.0 * NT * NP_ + 8.0 * NP_ * NP_) if schur else 8.0 * N * N
+        rk4_flops = 4.0 * (8.0 * N * N + 2.0 * solve_once + 16.0 * NT * NP_)
+    elif schur:
         rk4_flops = 4.0 * (8.0 * N * N + 16.0 * NT * NP_ + 8.0 * NP_ * NP_)
     else:
-        rk4_flops = {"matrix": 32.0, "stage": 64.0}[args.solve_mode] * N * N if prec == 0 else 64.0 * N * N
-    mol_peak = {1: FP32_PEAK_TFLOPS, 3: BF16_MEASURED_TFLOPS}.get(prec, FP64_PEAK_TFLOPS)
-    cand = {"mol_gemm": (flops_mol * evals, mol_peak,
-                         {1: "k_mol_gemm_f32q", 3: "k_mol_tc"}.get(prec, "k_mol_gemm<double>")),
-            "solve": (flops_solve * evals, FP32_PEAK_TFLOPS if prec else FP64_PEAK_TFLOPS,
-                      "k_lu_factor_f32" if prec else ("k_schur_factor" if schur else "k_lu_solve")),
+        rk4_flops = {"matrix": 32.0, "stage": 64.0}[args.solve_mode] * N * N
+    # the FP64-accurate tensor-core contraction issues 28 bf16 slice products per algorithmic product
+    mol_work = 28.0 if prec in (4, 5) else 1.0
+    mol_peak = {1: FP32_PEAK_TFLOPS, 3: BF16_MEASURED_TFLOPS, 4: BF16_MEASURED_TFLOPS,
+                5: BF16_MEASURED_TFLOPS}.get(prec, FP64_PEAK_TFLOPS)
+    solve_name = (("k_schur_factor<float>" if schur else "k_lu_factor_f32") if mixed_form
+                  else ("k_schur_factor<double>" if schur else "k_lu_solve"))
+    cand = {"mol_gemm": (mol_work * flops_mol * evals, mol_peak,
+                         {1: "k_mol_gemm_f32q", 3: "k_mol_tc", 4: "k_mol_tc64", 5: "k_mol_tc64"}.get(
+                             prec, "k_mol_gemm<double>")),
+            "solve": (flops_solve * evals, FP32_PEAK_TFLOPS if mixed_form else FP64_PEAK_TFLOPS, solve_name),
             "rk4": (rk4_flops * n_paths * STEP * args.steps, FP64_PEAK_TFLOPS, "k_rk4")}
     dom = max(cand, key=lambda k: prof[k][0] if k in prof else 0.0)
     dom_ms, dom_launches = prof[dom]
@@ -720,7 +733,9 @@ def main() -> None:
                 "achieved": achieved, "peak": dom_peak, "unit": "TFLOP/s",
                 "frac": achieved / dom_peak, "traffic": None,
                 "peak_source": ("measured bf16 dense tensor peak (MEASURED_PEAKS.json, burst) against the "
-                                "contraction's algorithmic FP32 flops (the sliced operands take 12 bf16 products)")
+                                "contraction's algorithmic flops"
+                                + (" times its 28 slice products (FP64-accurate emulation)" if prec in (4, 5)
+                                   else " (the sliced operands take 12 bf16 products)"))
                 if dom_peak == BF16_MEASURED_TFLOPS else
                 ("FP32 pipe from unit counts and clocks (152 SMs x 128 FFMA/clk x 2.07 GHz); "
                  f"measured FFMA microbenchmark {FP32_FFMA_MEASURED_TFLOPS} TFLOP/s")
@@ -737,10 +752,15 @@ def main() -> None:
                     "node tables, refinement and RK4; all paths batched",
                  2: "mixed precision with FP64 elements: LU on the FP32 pipe, FP64 refinement and RK4",
                  3: "mixed precision, tensor-core contraction: Eq. 9 on tcgen05 (fixed-point bf16 slices, exact "
-                    "main accumulation), LU on the FP32 pipe, FP64 refinement and RK4; all paths batched"}
+                    "main accumulation), FP32 factors of S, FP64 refinement and RK4; all paths batched",
+                 4: "FP64-accurate: Eq. 9 contraction emulated on tcgen05 (seven bf16 slices per operand, 28 "
+                    "slice products, exact level accumulators, double-float sums), FP64 solve and RK4",
+                 5: "mixed precision with FP64-accurate tensor-core elements: FP32 factors of S, FP64 refinement "
+                    "and RK4"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 3: "bf16-slices+f32+f64"}.get(prec, "f32+f64"), "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 3: "bf16-slices+f32+f64", 4: "bf16-slices(fp64-accurate)+f64",
+                                                  5: "bf16-slices(fp64-accurate)+f32+f64"}.get(prec, "f32+f64"), "data": "synthetic",
             "config": {"workload": CONFIG_DESC if args.workload == WORKLOAD else CONFIG_DESC_C6, "paths": n_paths,
                        "form": form_desc[prec],
                        "bench_step": f"{STEP} RK4 steps of each of the {n_paths} paths per rank, consecutive "
@@ -753,6 +773,11 @@ def main() -> None:
                                  if "unsupported" not in f else {"unsupported": f["unsupported"]})
                       for p, f in forms.items()},
             "speedup_vs_plain_fp64": value / forms[0]["value"],
+            "fp64_accurate_forms": {"fp64": forms[0]["value"],
+                                    **({"fp64-tensor-core": forms[4]["value"],
+                                        "speedup": forms[4]["value"] / forms[0]["value"],
+                                        "max_abs_prob_error_vs_fp64": forms[4].get("err", 0.0)}
+                                       if 4 in forms and "unsupported" not in forms[4] else {})},
             "prob_error": {"max_abs": H.get("err", 0.0), "bound": 1e-6,
                            "against": "the plain FP64 form on the same steps (itself within 1e-10 of the oracle)",
                            "rk4_steps_per_path": (args.warmup + args.steps) * STEP},

@@ -192,9 +192,10 @@ WPCCC_API wpccc_status wpccc_matrix_elements(wpccc_basis basis, double b, double
  * wpccc_matrix_elements with the element arithmetic of a reduced-precision form, to measure its element
  * error against the FP64 elements (the paper has no counterpart):
  *   precision_mode 0 FP64 (= wpccc_matrix_elements), 1 the Eq. 9 contraction on the FP32 pipe,
- *   3 the Eq. 9 contraction on the tensor cores (see wpccc_propagate).  S and H are returned in FP64.
+ *   3 the Eq. 9 contraction on the tensor cores at FP32 level, 4 the same to FP64 accuracy (see
+ *   wpccc_propagate).  S and H are returned in FP64.
  * Errors: as wpccc_matrix_elements; EUNSUPPORTED for other modes, one-centre bases or model-potential
- * targets in modes 1 and 3.
+ * targets in modes 1, 3 and 4.
  */
 WPCCC_API wpccc_status wpccc_matrix_elements_precision(wpccc_basis basis, double b, double v, int nz,
                                                        const double* z, void* S, void* H, int precision_mode,
@@ -239,8 +240,15 @@ WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv
  *     3  as 1 with the Eq. 9 contraction on the 5th-generation tensor cores: tcgen05.mma
  *        (kind::f16) on three-part bf16 splits of both operands (six products, FP32-level
  *        products), FP32 accumulation drained every 32 nodes into compensated sums; operand
- *        tiles staged by TMA; needs at most 64 target states per molecular-frame projection;
- *     in one-centre mode all three are the FP64 form (no contraction, no solve).
+ *        tiles staged by TMA;
+ *     4  the FP64 form (solve and RK4 as mode 0) with the Eq. 9 contraction emulated to FP64
+ *        accuracy on the tensor cores: seven bf16 slices of both operands in fixed point per
+ *        32-node chunk (error-free splitting, Ozaki et al.), 28 slice products into five FP32
+ *        accumulators of which four are exact, drained into double-float sums; element errors
+ *        about 2^-47 of the largest quadrature term;
+ *     5  as 2 (FP32 factors and FP64 refinement) with the elements of mode 4;
+ *     modes 3-5 need a node count that is a multiple of 32 and no model potential; in one-centre
+ *     mode all modes are the FP64 form (no contraction, no solve).
  *   batch_mode 0 = all paths batched together in chunks of RK4 steps (the only
  *   batch mode of this build).
  * Blocks until the work is finished: the library allocates its scratch memory

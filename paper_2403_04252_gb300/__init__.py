@@ -236,8 +236,9 @@ class Basis:
         return S, H
 
     def matrix_elements_precision(self, b: float, v: float, z, precision_mode: int, S=None, H=None, stream=None):
-        """S, H with the element arithmetic of a reduced-precision form (0 FP64, 1 FP32 contraction,
-        3 tensor-core contraction), returned in FP64 (``wpccc_matrix_elements_precision``)."""
+        """S, H with the element arithmetic of a precision form (0 FP64, 1 FP32 contraction, 3 tensor-core
+        contraction at FP32 level, 4 tensor-core contraction to FP64 accuracy), returned in FP64
+        (``wpccc_matrix_elements_precision``)."""
         import torch
         z, zp = _arr(np.atleast_1d(z), np.float64)
         dev = torch.device("cuda", self.device)

@@ -24,6 +24,7 @@
 
 #include "angular.cuh"
 #include "geometry.cuh"
+#include "ozaki.cuh"
 #include "wpccc_internal.cuh"
 
 namespace wpccc {
@@ -94,11 +95,14 @@ struct NodeArgs {
     // T = float: per-state products instead of per-radial values (one rounding of f * Theta * sign)
     int N_T, n_half;
     const int *stT_index, *half_of, *radT_l, *radP_l;
-    // tensor-core layout (T = float): split tables instead of the per-state A_T
+    // tensor-core layouts (T = float): split tables instead of the per-state A_T; tc = 1: three bf16
+    // slices per value with FP32 A_P and W (precision mode 3), tc = 2: seven slices with double-float A_P
+    // and W (precision modes 4 and 5)
     int tc;
     const int* tc_row;          // [2 N_T]: row of each target state in a split table, then its group's size
     int tc_rows;
     size_t tc_ap_off, tc_w_off, tc_sc_off;
+    size_t t6_ap_off, t6_w_off, t6_sc_off;
 };
 
 template <typename T> struct Vec2;
@@ -185,6 +189,63 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         }
         for (int t = 0; t < A.nlqT; ++t) thT[(size_t)t * A.G + g] = (T)thv[0][t];
         for (int t = 0; t < A.nlqP; ++t) thP[(size_t)t * A.G + g] = (T)thv[1][t];
+    } else if (A.tc == 2) {
+        // FP64-accurate tensor-core layout: A_T r_T and A_T r_T V_T per target state (rows of the row
+        // tiles), each as seven bf16 slices against a power-of-two scale per 32-node chunk (one warp);
+        // the products are formed in double-float arithmetic from FP64 factors split once per node
+        const double rTV = A.mp_c == 0.0 ? -A.Z_T : -A.Z_T + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT);
+        const float2 frT = df_split(rT), frTV = df_split(rTV);   // r_T and r_T V_T(r_T)
+        float2 fth[(WPCCC_LMAX + 1) * (WPCCC_LMAX + 2) / 2];
+        for (int q = 0; q < (A.lmaxT + 1) * (A.lmaxT + 2) / 2; ++q) fth[q] = df_split(thv[0][q]);
+        __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(base);
+        float* sc = reinterpret_cast<float*>(base) + A.t6_sc_off + (size_t)(g >> 5) * A.tc_rows;
+        const size_t split = (size_t)A.tc_rows * A.G;
+        auto put7 = [&](size_t row, float2 x) {
+            float mx = fabsf(x.x);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const int sh = oz_shift(mx);
+            __nv_bfloat16 q[OZ_SLICES];
+            oz_slices(x.x, x.y, sh, q);
+            const size_t o = row * A.G + g;
+#pragma unroll
+            for (int i = 0; i < OZ_SLICES; ++i) sp[i * split + o] = q[i];
+            if ((threadIdx.x & 31) == 0) sc[row] = ldexpf(1.f, -sh);
+        };
+        for (int a = 0; a < A.nradT; ++a) {
+            double val = 0.0;
+            if (inT) {
+                const double* fa = A.fT + (size_t)a * A.Nr + sT;
+                val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
+            }
+            const float2 fv = df_split(val);
+            const int l = A.radT_l[a];
+            for (int m = -l; m <= l; ++m) {
+                const int i = A.stT_index[a * (2 * WPCCC_LMAX + 1) + m + WPCCC_LMAX];
+                const int am = m < 0 ? -m : m;
+                float2 t = df_mul(fv, fth[l * (l + 1) / 2 + am]);
+                if (m < 0 && (am & 1)) t = make_float2(-t.x, -t.y);
+                const int row = A.tc_row[i];
+                const int tsz = A.tc_row[A.N_T + i];
+                put7((size_t)row, df_mul(t, frT));
+                put7((size_t)(row + tsz), df_mul(t, frTV));
+            }
+        }
+        // A_P per half column as double-floats
+        float2* aP = reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.t6_ap_off);
+        for (int b2 = 0; b2 < A.nradP; ++b2) {
+            double val = 0.0;
+            if (inP) {
+                const double* fa = A.fP + (size_t)b2 * A.Nr + sP;
+                val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
+            }
+            const float2 fv = df_split(val);
+            const int l = A.radP_l[b2];
+            for (int q = 0; q <= l; ++q) {
+                const int j = A.half_of[b2 * (WPCCC_LMAX + 1) + q];
+                aP[(size_t)j * A.G + g] = df_mul(fv, df_split(thv[1][l * (l + 1) / 2 + q]));
+            }
+        }
     } else if (A.tc) {
         // tensor-core layout: A_T and A_T V_T per target state, rows grouped by q', in fixed point per
         // 32-node chunk (one warp): x = s (k0 + k1 2^-8 + k2 2^-16) with s a power of two from the
@@ -301,7 +362,12 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         a.y = (T)w0.y;
         bq.x = (T)(w0.x * uQ);
         bq.y = (T)(w0.y * uQ);
-        if (sizeof(T) == 4 && A.tc) {
+        if (sizeof(T) == 4 && A.tc == 2) {
+            // FP64-accurate tensor-core layout: W_K / r_T as double-floats, [d][re, im][G]
+            float2* w6 = reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.t6_w_off);
+            w6[((size_t)d * 2) * A.G + g] = df_split(w0.x / rT);
+            w6[((size_t)d * 2 + 1) * A.G + g] = df_split(w0.y / rT);
+        } else if (sizeof(T) == 4 && A.tc) {
             // tensor-core layout: W_K / r_T only (r_T and the transfer potential sit in the split tables)
             reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.tc_w_off)[o] =
                 make_float2((float)(w0.x / rT), (float)(w0.y / rT));
@@ -1088,6 +1154,16 @@ ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
             L.tc_sc_off = nt;
             nt += ((size_t)L.tc_rows * ((B->G + 31) / 32) + 3) / 4 * 4;
             L.node_doubles = std::max(L.node_doubles, (nt + 1) / 2);
+            // FP64-accurate layout (precision modes 4, 5): seven bf16 slice planes [7][tc_rows][G], the
+            // chunk scales, A_P [n_half][G] and W_K / r_T [d][re, im][G] as double-floats (float pairs)
+            size_t n6 = ((size_t)OZ_SLICES * L.tc_rows * B->G + 7) / 8 * 4;
+            L.t6_sc_off = n6;
+            n6 += ((size_t)L.tc_rows * ((B->G + 31) / 32) + 3) / 4 * 4;
+            L.t6_ap_off = n6;
+            n6 += (size_t)2 * B->n_half * B->G;
+            L.t6_w_off = n6;
+            n6 += (size_t)4 * (B->dmax + 1) * B->G;
+            L.node_doubles = std::max(L.node_doubles, (n6 + 1) / 2);
         }
         L.node_doubles += L.node_doubles & 1;
         L.mol_elems = (size_t)NX * B->N_T * B->n_half;
@@ -1194,13 +1270,16 @@ static wpccc_status launch_tables(wpccc_basis_s* B, const EvalDesc* evals, int n
     na.half_of = B->half_of;
     na.radT_l = B->T.rad_l;
     na.radP_l = B->P.rad_l;
-    na.tc = precision == 3;
+    na.tc = precision == 3 ? 1 : precision == 4 ? 2 : 0;
     na.tc_row = B->tc_row;
     na.tc_rows = L.tc_rows;
     na.tc_ap_off = L.tc_ap_off;
     na.tc_w_off = L.tc_w_off;
     na.tc_sc_off = L.tc_sc_off;
-    if (precision == 3) {
+    na.t6_ap_off = L.t6_ap_off;
+    na.t6_w_off = L.t6_w_off;
+    na.t6_sc_off = L.t6_sc_off;
+    if (precision == 3 || precision == 4) {
         if (!B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
         na.w_off = L.tc_w_off;
     }
@@ -1261,6 +1340,9 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
             k_mol_gemm<double><<<dim3(n_row_tiles * ga.n_col_tiles, nev), 256, gsm, st>>>(ga);
         } else if (precision == 3) {
             wpccc_status ms = launch_mol_tc(B, nev, node, mol, B->tc_err, st);
+            if (ms != WPCCC_OK) return ms;
+        } else if (precision == 4) {
+            wpccc_status ms = launch_mol_tc64(B, nev, node, mol, B->tc_err, st);
             if (ms != WPCCC_OK) return ms;
         } else {
             Gemm32Args g32;
@@ -1416,8 +1498,8 @@ extern "C" wpccc_status wpccc_matrix_elements(wpccc_basis B, double b, double v,
 
 extern "C" wpccc_status wpccc_matrix_elements_precision(wpccc_basis B, double b, double v, int nz, const double* z,
                                                         void* S, void* H, int precision_mode, void* stream) {
-    if (precision_mode != 0 && precision_mode != 1 && precision_mode != 3)
-        return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: element precision 0, 1 or 3");
+    if (precision_mode != 0 && precision_mode != 1 && precision_mode != 3 && precision_mode != 4)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: element precision 0, 1, 3 or 4");
     if (precision_mode != 0 && (!B || B->n_centres != 2))
         return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: reduced precision needs two centres");
     if (precision_mode != 0 && B->mp_c != 0.0)
@@ -1431,7 +1513,7 @@ static wpccc_status matrix_elements_prec(wpccc_basis B, double b, double v, int 
     if (!B || !z || !S || !H) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: null argument");
     if (nz < 1) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: nz < 1");
     if (!(b > 0.0) || !(v > 0.0)) return fail(WPCCC_EINVAL, "wpccc_matrix_elements: b and v must be > 0");
-    if (precision == 3) {
+    if (precision == 3 || precision == 4) {
         WPCCC_CUDA(cudaSetDevice(B->device));
         wpccc_status ts = tc_prepare(B);
         if (ts != WPCCC_OK) return ts;
@@ -1460,7 +1542,7 @@ static wpccc_status matrix_elements_prec(wpccc_basis B, double b, double v, int 
         // the host list is reused: wait for the copy before refilling it
         WPCCC_CUDA(cudaStreamSynchronize(st));
     }
-    if (precision == 3) {
+    if (precision == 3 || precision == 4) {
         int e = 0;
         WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {

@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "tc_ptx.cuh"
 #include "wpccc_internal.cuh"
 
 namespace wpccc {
@@ -39,11 +40,13 @@ constexpr int TC_STAGES = 4;
 constexpr int TC_PE_WARPS = 8;     // producer / epilogue warps
 constexpr int TC_THREADS = (TC_PE_WARPS + 1) * 32;
 constexpr int TC_BN_MAX = 128;     // table rows per box (MMA N at most), so 64 accumulators per thread
+constexpr int TC_TILE_STATES = TC_BN_MAX / 2;   // target states per row tile
 constexpr int TC_TMEM_COLS = 512;  // two buffers x (main, correction) accumulators of up to 128 columns
 constexpr int TC_A_TILE = TC_M * 64;          // bytes of one slice of the generated tile
 constexpr int TC_A_SLICES = 4;                // k0, k1, k2 2^-8, k1 2^-8
 constexpr int TC_B_SLICES = 3;                // k0', k1', k2' 2^-8
-constexpr long TC_WAIT_LIMIT = 1L << 20;
+
+static __device__ __forceinline__ uint32_t bf16_idesc(int n) { return bf16_idesc_mn(TC_M, n); }
 
 struct TcArgs {
     int G, N_T, n_half, nchunks, BN, n_mtiles, dmax;
@@ -59,86 +62,6 @@ struct TcArgs {
     double* mol;           // [nev][2][N_T][n_half] complex, written as (re, im) doubles
     int* err;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: false when the CTA has given up (another role timed out, or this wait did).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err, int code) {
-    for (long it = 0; it < TC_WAIT_LIMIT; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-    }
-    *abort_flag = 1;
-    atomicExch(err, code);
-    return false;
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-// Shared-memory matrix descriptor of a K-major tile with 64-byte swizzle (8-row atoms of 64-byte rows,
-// 512 bytes apart): start address, leading offset (unused for this layout, 16 bytes), stride offset
-// 512 bytes, descriptor version 1, layout 64-byte swizzle.
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
-}
-
-// Instruction descriptor of kind::f16 with bf16 A and B (K-major), FP32 accumulation, M = 128, N = n.
-__device__ __forceinline__ uint32_t bf16_idesc(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n.reg .pred p;\n"
-        "setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
-}
-
-__device__ __forceinline__ uint32_t bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mol_tc(const __grid_constant__ CUtensorMap tmap, TcArgs A) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
@@ -383,45 +306,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mol_tc(const __grid_constant_
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
-// Group tables of the tensor-core layout (target states grouped by their molecular-frame q'); enables
-// the layout on the basis.
+// Row tiles of the tensor-core layout: the target states grouped by their molecular-frame q', each group
+// cut into tiles of at most 64 states (near-equal sizes).  A tile of n states owns 2 n consecutive rows of
+// the split tables: its A_T rows, then its A_T V_T rows.  Enables the layout on the basis.
 wpccc_status tc_prepare(wpccc_basis_s* B) {
     if (B->tc_layout) return WPCCC_OK;
-    if (B->n_centres != 2) return fail(WPCCC_EUNSUPPORTED, "precision mode 3 needs a two-centre basis");
-    if (!encode_fn()) return fail(WPCCC_EUNSUPPORTED, "precision mode 3: cuTensorMapEncodeTiled unavailable");
-    const int L = B->T.lmax, ngr = 2 * L + 1;
-    std::vector<std::vector<int>> groups(ngr);
+    if (B->n_centres != 2) return fail(WPCCC_EUNSUPPORTED, "the tensor-core contraction needs a two-centre basis");
+    if (!encode_fn()) return fail(WPCCC_EUNSUPPORTED, "tensor-core contraction: cuTensorMapEncodeTiled unavailable");
+    if (B->G % 32 != 0) return fail(WPCCC_EUNSUPPORTED, "tensor-core contraction: the node count must be a multiple of 32");
+    const int L = B->T.lmax;
+    std::vector<std::vector<int>> groups(2 * L + 1);
     for (int i = 0; i < B->N_T; ++i) groups[B->T.h_st_m[i] + L].push_back(i);
+    std::vector<std::vector<int>> tiles;
+    std::vector<int> tq;
+    for (int gq = 0; gq < 2 * L + 1; ++gq) {
+        const int n = (int)groups[gq].size();
+        if (n == 0) continue;
+        const int nt = (n + TC_TILE_STATES - 1) / TC_TILE_STATES;
+        for (int t = 0; t < nt; ++t) {
+            const int a = (int)((long)n * t / nt), b = (int)((long)n * (t + 1) / nt);
+            tiles.emplace_back(groups[gq].begin() + a, groups[gq].begin() + b);
+            tq.push_back(gq - L);
+        }
+    }
+    const int ntl = (int)tiles.size();
     int qmax = 0;
-    for (auto& g : groups) qmax = std::max<int>(qmax, (int)g.size());
-    if ((2 * qmax + 15) / 16 * 16 > TC_BN_MAX)
-        return fail(WPCCC_EUNSUPPORTED, "precision mode 3: a q' group has more than 64 target states");
-    if (B->G % 32 != 0) return fail(WPCCC_EUNSUPPORTED, "precision mode 3: the node count must be a multiple of 32");
-    std::vector<int> off(ngr + 1, 0), qv(ngr), rows((size_t)ngr * qmax, 0), trow(2 * (size_t)B->N_T);
-    for (int gq = 0; gq < ngr; ++gq) {
-        off[gq + 1] = off[gq] + 2 * (int)groups[gq].size();
-        qv[gq] = gq - L;
-        for (size_t n = 0; n < groups[gq].size(); ++n) {
-            const int i = groups[gq][n];
-            rows[(size_t)gq * qmax + n] = i;
-            trow[i] = off[gq] + (int)n;
-            trow[B->N_T + i] = (int)groups[gq].size();
+    for (auto& t : tiles) qmax = std::max<int>(qmax, (int)t.size());
+    std::vector<int> off(ntl + 1, 0), rows((size_t)ntl * qmax, 0), trow(2 * (size_t)B->N_T);
+    for (int t = 0; t < ntl; ++t) {
+        off[t + 1] = off[t] + 2 * (int)tiles[t].size();
+        for (size_t n = 0; n < tiles[t].size(); ++n) {
+            const int i = tiles[t][n];
+            rows[(size_t)t * qmax + n] = i;
+            trow[i] = off[t] + (int)n;
+            trow[B->N_T + i] = (int)tiles[t].size();
         }
     }
     auto up = [&](int** dst, const std::vector<int>& v) -> wpccc_status {
@@ -429,11 +347,10 @@ wpccc_status tc_prepare(wpccc_basis_s* B) {
         WPCCC_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
         return WPCCC_OK;
     };
-    std::vector<int> qg(ngr + 1 + ngr);
+    std::vector<int> qg(ntl + 1 + ntl);
     std::copy(off.begin(), off.end(), qg.begin());
-    std::copy(qv.begin(), qv.end(), qg.begin() + ngr + 1);
+    std::copy(tq.begin(), tq.end(), qg.begin() + ntl + 1);
     std::vector<int> halfq(B->n_half);
-    for (int h = 0; h < B->n_half; ++h) halfq[h] = B->P.h_st_m[0];   // filled below
     {
         std::vector<int> hs(B->n_half);
         WPCCC_CUDA(cudaMemcpy(hs.data(), B->half_state, B->n_half * sizeof(int), cudaMemcpyDeviceToHost));
@@ -446,7 +363,7 @@ wpccc_status tc_prepare(wpccc_basis_s* B) {
     if ((s = up(&B->tc_halfq, halfq)) != WPCCC_OK) return s;
     WPCCC_CUDA(cudaMalloc((void**)&B->tc_err, sizeof(int)));
     WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
-    B->n_qgroups = ngr;
+    B->n_qgroups = ntl;
     B->qg_max = qmax;
     B->tc_layout = true;
     return WPCCC_OK;

@@ -1,0 +1,329 @@
+// Eq. 9 contraction on the 5th-generation tensor cores to FP64 accuracy (precision modes 4 and 5).
+//
+// The two-centre integrals of one row tile (target states of one molecular-frame projection q') are
+//   X_K[i][c] = sum_g (A_T r_T)[i][g] Bw[c][g],   X_Q[i][c] = sum_g (A_T r_T V_T)[i][g] Bw[c][g],
+//   Bw[(c, re/im)][g] = re/im(W_{|q_c - q'|}(g) / r_T(g)) A_P[c][g],
+// one real contraction over the quadrature nodes g of
+//   table rows      m (M = 128: the tile's A_T r_T rows, then its A_T r_T V_T rows), from the node tables
+//   generated rows  n (N = 48: 24 half columns x re/im), formed here from double-float W and A_P
+// into D[m][n].
+//
+// Precision (error-free slicing after Ozaki, Ogita, Oishi and Rump; see ozaki.cuh): per 32-node chunk
+// both operands are written in fixed point with seven bf16 slices, a_g = s_m sum_i alpha_i and
+// b_g = s_n sum_j beta_j with alpha_i, beta_j integers times 2^(-8 i), 2^(-8 j).  The products with
+// i + j = L form level L (weight 2^(-8 L)); levels 0-3 go to four accumulators that hold their sums
+// exactly (integers times 2^(-8 L) below 2^22 units), levels 4-6 to a fifth, whose FP32 rounding over
+// its 36 MMAs stays near 2^-49 of the chunk's largest term; levels >= 7 are dropped (below 2^-53).
+// Per chunk the epilogue forms s_m s_n (L0 + L1 + L2 + L3 + T) with the exact parts folded into
+// double-float running sums (two TwoSums), so the result carries about 2^-47 of the largest term.
+//
+// Pipeline per CTA (416 threads): warps 0-11 generate the Bw tiles (64-byte swizzled K-major rows) and
+// drain the accumulators; warp 12 issues the TMA loads of the table tiles (cp.async.bulk.tensor, 64-byte
+// swizzle) and the tcgen05.mma instructions.  Two shared-memory stages, a ring of four scale slots, two
+// TMEM buffers of five accumulators, mbarriers between the roles; every wait is bounded and records a
+// timeout in a device flag.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ozaki.cuh"
+#include "tc_ptx.cuh"
+#include "wpccc_internal.cuh"
+
+namespace wpccc {
+
+constexpr int T6_M = 128;                              // table rows per CTA (MMA M)
+constexpr int T6_N = 48;                               // generated rows per CTA (MMA N)
+constexpr int T6_K = 32;                               // nodes per chunk: one 64-byte bf16 row
+constexpr int T6_ACC = 5;                              // accumulators: levels 0, 1, 2, 3 and >= 4
+constexpr int T6_STAGES = 2;
+constexpr int T6_SC_SLOTS = 4;                         // scale ring (see the drain)
+constexpr int T6_PE_WARPS = 12;                        // producer / epilogue warps
+constexpr int T6_THREADS = (T6_PE_WARPS + 1) * 32;
+constexpr int T6_TMEM_COLS = 512;                      // 2 buffers x 5 accumulators x 48 columns = 480
+constexpr int T6_BUF_COLS = T6_ACC * T6_N;
+constexpr int T6_A_TILE = T6_M * 64;                   // bytes of one slice of the table tile
+constexpr int T6_B_TILE = T6_N * 64;                   // bytes of one slice of the generated tile
+constexpr int T6_STAGE_BYTES = (OZ_SLICES * (T6_A_TILE + T6_B_TILE) + 1023) / 1024 * 1024;
+constexpr int T6_SC_FLOATS = T6_M + T6_N;              // per slot: table row scales, generated row scales
+constexpr int T6_COLS_PER_WARP = T6_N / (T6_PE_WARPS / 4);   // 16 columns per epilogue warp
+
+static_assert(T6_PE_WARPS * 32 == T6_N * 8, "eight producer threads (4 nodes each) per generated row");
+static_assert(2 * T6_BUF_COLS <= T6_TMEM_COLS, "two buffers of accumulators fit the TMEM allocation");
+
+struct Tc64Args {
+    int G, N_T, n_half, nchunks, n_ntiles, tc_rows, qg_max;
+    const int* qg_off;     // [tiles + 1] first split-table row of each row tile
+    const int* qg_q;       // [tiles] q' of each row tile
+    const int* qg_rows;    // [tiles][qg_max] target state of each A_T row of a tile
+    const int* half_q;     // [n_half] q of each half column
+    const char* node;      // node tables (FP64-accurate tensor-core layout) of the launch's evaluations
+    size_t node_bytes;     // stride between evaluations
+    size_t sc_off_f, ap_off_f, w_off_f;
+    double* mol;           // [nev][2][N_T][n_half] complex, written as (re, im) doubles
+    int* err;
+};
+
+__global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constant__ CUtensorMap tmap, Tc64Args A) {
+    extern __shared__ __align__(1024) unsigned char t6_smem_raw[];
+    unsigned char* sm = t6_smem_raw + ((1024 - (smem_u32(t6_smem_raw) & 1023)) & 1023);
+    float* ring = reinterpret_cast<float*>(sm + T6_STAGES * T6_STAGE_BYTES);     // [slot][T6_SC_FLOATS]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + T6_SC_SLOTS * T6_SC_FLOATS);
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntile = blockIdx.x % A.n_ntiles, tile = blockIdx.x / A.n_ntiles, e = blockIdx.y;
+    const int row0 = A.qg_off[tile], ns = (A.qg_off[tile + 1] - row0) / 2;   // states of the row tile
+    const int qp = A.qg_q[tile];
+    // full[s], empty[s], accf[2], acce[2]
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * T6_STAGES, accf0 = empty0 + 8 * T6_STAGES,
+                   acce0 = accf0 + 16;
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < T6_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, T6_PE_WARPS * 32 + 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, T6_PE_WARPS * 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(T6_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    volatile int* abort_flag = &s_abort;
+    const char* nb = A.node + (size_t)e * A.node_bytes;
+    const int nk = A.nchunks;
+
+    if (warp == T6_PE_WARPS) {
+        // ---- TMA and MMA issue (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = bf16_idesc_mn(T6_M, T6_N);
+            const uint32_t tx = (uint32_t)(OZ_SLICES * T6_A_TILE);
+            auto issue_tma = [&](int k) {
+                const int s = k % T6_STAGES;
+                unsigned char* st = sm + s * T6_STAGE_BYTES;
+                const uint32_t bar = full0 + 8 * s;
+                mbar_arrive_tx(bar, tx);
+                for (int sp = 0; sp < OZ_SLICES; ++sp)
+                    tma_load_3d(smem_u32(st + sp * T6_A_TILE), &tmap, k * T6_K, sp * A.tc_rows + row0, e, bar);
+            };
+            int issued = 0;
+            for (; issued < T6_STAGES && issued < nk; ++issued) issue_tma(issued);
+            bool ok = true;
+            for (int k = 0; k < nk && ok; ++k) {
+                const int s = k % T6_STAGES, b = k & 1;
+                ok = mbar_wait(full0 + 8 * s, (k / T6_STAGES) & 1, abort_flag, A.err, 11);
+                if (ok && k >= 2) ok = mbar_wait(acce0 + 8 * b, ((k - 2) >> 1) & 1, abort_flag, A.err, 12);
+                if (!ok) break;
+                tc_fence_after();
+                unsigned char* st = sm + s * T6_STAGE_BYTES;
+                const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + OZ_SLICES * T6_A_TILE);
+                const uint32_t dbase = tmem + (uint32_t)(b * T6_BUF_COLS);
+                // levels from the smallest up; the first product into each accumulator overwrites it
+                uint32_t written = 0;
+                for (int L = 2 * (OZ_SLICES - 1); L >= 0; --L) {
+                    if (L >= OZ_SLICES) continue;   // levels >= 7: below 2^-53 of the chunk's largest term
+                    const int lv = L < T6_ACC - 1 ? L : T6_ACC - 1;
+                    const uint32_t d = dbase + (uint32_t)(lv * T6_N);
+                    for (int i = 0; i <= L; ++i) {
+                        const int j = L - i;
+                        for (int kk = 0; kk < T6_K / 16; ++kk) {
+                            tc_mma(d, sw64_desc(a0 + i * T6_A_TILE + kk * 32), sw64_desc(b0 + j * T6_B_TILE + kk * 32),
+                                   idesc, (written >> lv) & 1u);
+                            written |= 1u << lv;
+                        }
+                    }
+                }
+                tc_commit(empty0 + 8 * s);
+                tc_commit(accf0 + 8 * b);
+                if (k >= 1 && issued < nk) {
+                    // refill the stage of the previous chunk once its MMAs have completed
+                    const int kp = k - 1, sp = kp % T6_STAGES;
+                    ok = mbar_wait(empty0 + 8 * sp, (kp / T6_STAGES) & 1, abort_flag, A.err, 13);
+                    if (ok) issue_tma(issued++);
+                }
+            }
+            if (!ok) {
+                // give the copies still in flight time to land before the CTA exits
+                for (int k = issued > T6_STAGES ? issued - T6_STAGES : 0; k < issued; ++k) {
+                    const int s = k % T6_STAGES;
+                    for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(full0 + 8 * s, (k / T6_STAGES) & 1); ++it) {
+                    }
+                }
+            }
+        }
+    } else {
+        // ---- producers of the generated operand (eight threads per row, four nodes each), and the epilogue
+        const int n = tid >> 3, part = tid & 7;
+        const int gr = ntile * T6_N + n, c = gr >> 1, ri = gr & 1;
+        const bool valid = c < A.n_half;
+        int d = 0;
+        if (valid) {
+            d = A.half_q[c] - qp;
+            d = d < 0 ? -d : d;
+        }
+        const float* nbf = reinterpret_cast<const float*>(nb);
+        const float2* ap = reinterpret_cast<const float2*>(nbf + A.ap_off_f) + (size_t)(valid ? c : 0) * A.G;
+        const float2* wd = reinterpret_cast<const float2*>(nbf + A.w_off_f) + ((size_t)d * 2 + ri) * A.G;
+        const float* scT = nbf + A.sc_off_f;   // [chunk][tc_rows]
+        // epilogue: accumulator lanes 32 qd .. 32 qd + 31 (table rows), 16 columns from col0
+        const int qd = warp & 3, col0 = (warp >> 2) * T6_COLS_PER_WARP;
+        const int lrow = qd * 32 + lane;
+        const bool live = qd * 32 < 2 * ns;    // warps whose rows all lie past the tile skip the arithmetic
+        float hi[T6_COLS_PER_WARP], lo[T6_COLS_PER_WARP];
+#pragma unroll
+        for (int k = 0; k < T6_COLS_PER_WARP; ++k) {
+            hi[k] = 0.f;
+            lo[k] = 0.f;
+        }
+        bool ok = true;
+        auto drain = [&](int j) {
+            const int b = j & 1;
+            ok = ok && mbar_wait(accf0 + 8 * b, (j >> 1) & 1, abort_flag, A.err, 14);
+            if (!ok) return;
+            tc_fence_after();
+            if (live) {
+                const float* scl = ring + (j % T6_SC_SLOTS) * T6_SC_FLOATS;
+                const float sa = scl[lrow];
+                const uint32_t base =
+                    tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * T6_BUF_COLS + col0);
+#pragma unroll
+                for (int q = 0; q < T6_COLS_PER_WARP / 8; ++q) {
+                    float v[T6_ACC][8];
+#pragma unroll
+                    for (int lv = 0; lv < T6_ACC; ++lv) tmem_ld8(base + lv * T6_N + 8 * q, v[lv]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int k = 8 * q + u;
+                        const float sc = sa * scl[T6_M + col0 + k];
+                        // exact: L0 + round(L1) (integers below 2^22), frac(L1) + L2 (multiples of
+                        // 2^-16 below 2^5); rounded: L3 + T (below 2^-2, its rounding under 2^-26)
+                        const float l1h = rintf(v[1][u]);
+                        const float xa = __fadd_rn(v[0][u], l1h);
+                        const float xb = __fadd_rn(__fsub_rn(v[1][u], l1h), v[2][u]);
+                        const float xc = __fadd_rn(v[3][u], v[4][u]);
+                        float r1, r2;
+                        hi[k] = two_sum(hi[k], xa * sc, r1);
+                        hi[k] = two_sum(hi[k], xb * sc, r2);
+                        lo[k] = __fadd_rn(lo[k], __fadd_rn(__fadd_rn(r1, r2), xc * sc));
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acce0 + 8 * b);
+        };
+        for (int k = 0; k < nk && ok; ++k) {
+            const int s = k % T6_STAGES;
+            if (k >= T6_STAGES)
+                ok = mbar_wait(empty0 + 8 * s, ((k - T6_STAGES) / T6_STAGES) & 1, abort_flag, A.err, 15);
+            if (!ok) break;
+            unsigned char* bt = sm + s * T6_STAGE_BYTES + OZ_SLICES * T6_A_TILE;
+            float* scl = ring + (k % T6_SC_SLOTS) * T6_SC_FLOATS;
+            const int g0 = k * T6_K + part * 4;
+            float2 x[4];
+            float mx = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                x[jj] = make_float2(0.f, 0.f);
+                if (valid) x[jj] = df_mul(wd[g0 + jj], ap[g0 + jj]);
+                mx = fmaxf(mx, fabsf(x[jj].x));
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const int sh = oz_shift(mx);
+            if (part == 0) scl[T6_M + n] = ldexpf(1.f, -sh);
+            // the table rows' scales of this chunk (rows past the table read as zero scale)
+            if (tid < T6_M) {
+                const int row = row0 + tid;
+                scl[tid] = row < A.tc_rows ? scT[(size_t)k * A.tc_rows + row] : 0.f;
+            }
+            __nv_bfloat16 q[4][OZ_SLICES];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) oz_slices(x[jj].x, x[jj].y, sh, q[jj]);
+            // row n of each slice tile: 64 bytes, 16-byte chunk qq at (qq ^ ((n >> 1) & 3)); this thread
+            // holds the 8-byte half (part & 1) of chunk part >> 1
+            const int off = n * 64 + (((part >> 1) ^ ((n >> 1) & 3)) << 4) + (part & 1) * 8;
+#pragma unroll
+            for (int sp = 0; sp < OZ_SLICES; ++sp)
+                *reinterpret_cast<uint2*>(bt + sp * T6_B_TILE + off) =
+                    make_uint2(bf16x2(q[0][sp], q[1][sp]), bf16x2(q[2][sp], q[3][sp]));
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(full0 + 8 * s);
+            if (k >= 1) drain(k - 1);
+        }
+        if (ok) drain(nk - 1);
+        // results: row m of D is A_T row m of the tile (overlap K) or, from ns on, its A_T V_T row (Q)
+        if (ok && live && lrow < 2 * ns) {
+            const int x = lrow < ns ? 0 : 1;
+            const int i = A.qg_rows[tile * A.qg_max + (lrow < ns ? lrow : lrow - ns)];
+            const size_t plane = (size_t)A.N_T * A.n_half;
+            double* out = A.mol + (size_t)e * 2 * plane * 2;
+#pragma unroll
+            for (int k = 0; k < T6_COLS_PER_WARP; ++k) {
+                const int go = ntile * T6_N + col0 + k, co = go >> 1, rio = go & 1;
+                if (co >= A.n_half) continue;
+                out[((size_t)x * plane + (size_t)i * A.n_half + co) * 2 + rio] = (double)hi[k] + (double)lo[k];
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(T6_TMEM_COLS));
+    }
+}
+
+wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st) {
+    if (!B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
+    const ElemScratch L = elem_scratch_layout(B);
+    const size_t node_bytes = L.node_doubles * sizeof(double);
+    // seven slice planes as one 3-D bf16 tensor: x = node (G), y = slice plane row (7 x tc_rows), z = evaluation
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)B->G, (cuuint64_t)OZ_SLICES * L.tc_rows, (cuuint64_t)nev};
+    const cuuint64_t strides[2] = {(cuuint64_t)B->G * 2, (cuuint64_t)node_bytes};
+    const cuuint32_t box[3] = {(cuuint32_t)T6_K, (cuuint32_t)T6_M, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(node), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(WPCCC_ECUDA, "cuTensorMapEncodeTiled failed for the slice planes");
+    Tc64Args a;
+    a.G = B->G;
+    a.N_T = B->N_T;
+    a.n_half = B->n_half;
+    a.nchunks = B->G / T6_K;
+    a.n_ntiles = (2 * B->n_half + T6_N - 1) / T6_N;
+    a.tc_rows = L.tc_rows;
+    a.qg_max = B->qg_max;
+    a.qg_off = B->qg_off;
+    a.qg_q = B->qg_off + B->n_qgroups + 1;
+    a.qg_rows = B->qg_rows;
+    a.half_q = B->tc_halfq;
+    a.node = static_cast<const char*>(node);
+    a.node_bytes = node_bytes;
+    a.sc_off_f = L.t6_sc_off;
+    a.ap_off_f = L.t6_ap_off;
+    a.w_off_f = L.t6_w_off;
+    a.mol = reinterpret_cast<double*>(mol);
+    a.err = err;
+    const size_t smem = 1024 + (size_t)T6_STAGES * T6_STAGE_BYTES + sizeof(float) * T6_SC_SLOTS * T6_SC_FLOATS +
+                        8 * (2 * T6_STAGES + 4);
+    WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_mol_tc64<<<dim3(a.n_ntiles * B->n_qgroups, nev), T6_THREADS, smem, st>>>(map, a);
+    WPCCC_CHECK_LAUNCH("k_mol_tc64");
+    return WPCCC_OK;
+}
+
+}  // namespace wpccc

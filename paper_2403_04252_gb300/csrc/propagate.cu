@@ -251,11 +251,11 @@ static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // otherwise they are chosen from the workspace limit and the SM count.
 static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int precision_mode, int C_request,
                                size_t ws_limit, PropPlan& P) {
-    if (precision_mode < 0 || precision_mode > 3)
-        return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: precision_mode must be 0, 1, 2 or 3");
-    if ((precision_mode == 1 || precision_mode == 3) && B->n_centres == 2 && B->mp_c != 0.0)
+    if (precision_mode < 0 || precision_mode > 5)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: precision_mode must be 0 to 5");
+    if ((precision_mode == 1 || precision_mode >= 3) && B->n_centres == 2 && B->mp_c != 0.0)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: model-potential targets need FP64 elements (mode 0 or 2)");
-    if (precision_mode == 3 && B->n_centres == 2) {
+    if (precision_mode >= 3 && B->n_centres == 2) {
         wpccc_status ts = tc_prepare(B);
         if (ts != WPCCC_OK) return ts;
     }
@@ -279,10 +279,13 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     P.np = np;
     P.N = N;
     P.two = B->n_centres == 2;
-    // 1: FP32 contraction + FP32 LU + FP64 refinement; 2: FP64 elements + FP32 LU + FP64 refinement;
-    // 3: as 1 with the contraction on the tensor cores (bf16 three-part splits)
-    P.mixed = P.two && precision_mode >= 1;
-    P.elem_precision = P.two && (precision_mode == 1 || precision_mode == 3) ? precision_mode : 0;
+    // 1: FP32 contraction + FP32 factors + FP64 refinement; 2: FP64 elements + FP32 factors + FP64
+    // refinement; 3: as 1 with the contraction on the tensor cores (three bf16 slices); 4: FP64 form with
+    // the contraction on the tensor cores to FP64 accuracy (seven slices); 5: as 2 with mode 4's elements
+    P.mixed = P.two && precision_mode >= 1 && precision_mode != 4;
+    P.elem_precision = !P.two ? 0
+                       : (precision_mode == 1 || precision_mode == 3) ? precision_mode
+                       : (precision_mode == 4 || precision_mode == 5) ? 4 : 0;
     P.stage = P.two && !P.mixed && B->solve_mode != WPCCC_SOLVE_MATRIX;
     P.schur = P.two && B->solve_mode == WPCCC_SOLVE_SCHUR;
     P.mode = P.mixed ? (P.schur ? RK_MIXED_SCHUR : RK_MIXED) : (P.schur ? RK_SCHUR : (P.stage ? RK_STAGE : RK_MATRIX));
@@ -535,7 +538,7 @@ wpccc_status propagate_internal(wpccc_basis_s* B, const wpccc_paths* paths, int 
     int flags = 0;
     WPCCC_CUDA(cudaMemcpyAsync(&flags, P.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     WPCCC_CUDA(cudaStreamSynchronize(st));
-    if (P.elem_precision == 3) {
+    if (P.elem_precision == 3 || P.elem_precision == 4) {
         int e = 0;
         WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
@@ -811,7 +814,7 @@ extern "C" wpccc_status wpccc_batch_status(wpccc_batch X, void* stream) {
     WPCCC_CUDA(cudaStreamSynchronize(st));
     for (int k = 0; k < X->n_sets; ++k) {
         wpccc_basis_s* B = X->plans[k].B;
-        if (X->plans[k].elem_precision == 3 && B && B->tc_err) {
+        if ((X->plans[k].elem_precision == 3 || X->plans[k].elem_precision == 4) && B && B->tc_err) {
             int e = 0;
             WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
             if (e) {

@@ -122,12 +122,13 @@ struct wpccc_basis_s {
     int refine_iters = 2;       // FP64 refinement iterations of the mixed-precision form
     // tensor-core contraction (precision mode 3): node tables carry the split operand tables
     bool tc_layout = false;
-    int n_qgroups = 0;          // target q' groups (2 lmax_T + 1)
+    int n_qgroups = 0;          // row tiles: target states of one q', at most 64 per tile
     int* tc_row = nullptr;      // [2 N_T]: row of each target state in a split table, then its group's size
     int* tc_err = nullptr;      // device flag: a wait of the tensor-core pipeline gave up
     int* tc_halfq = nullptr;    // [n_half]: q of each half column
-    int* qg_off = nullptr;      // [n_qgroups + 1]: first split-table row of each group (2 x cumulative size)
-    int* qg_rows = nullptr;     // [n_qgroups][max group size]: target state of each row of a group
+    int* qg_off = nullptr;      // [n_qgroups + 1]: first split-table row of each tile (2 x cumulative size),
+                                // then [n_qgroups]: the tile's q'
+    int* qg_rows = nullptr;     // [n_qgroups][max tile size]: target state of each row of a tile
     int qg_max = 0;
     // second stream of wpccc_propagate (RK4 sweeps overlap the next chunk's assembly) and its events
     cudaStream_t rk_stream = nullptr;
@@ -161,6 +162,9 @@ struct ElemScratch {
     int tc_rows;
     size_t tc_ap_off, tc_w_off;
     size_t tc_sc_off;      // per (32-node chunk, split-table row) power-of-two scale (floats)
+    // FP64-accurate tensor-core layout (precision modes 4, 5): seven bf16 slice planes [7][tc_rows][G],
+    // then (offsets in floats) the chunk scales, A_P and W_K / r_T as double-floats
+    size_t t6_sc_off, t6_ap_off, t6_w_off;
 };
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B);
 
@@ -189,6 +193,8 @@ enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3
 // layout into the molecular-frame blocks, for `nev` evaluations.
 wpccc_status launch_mol_tc(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st);
 wpccc_status tc_prepare(wpccc_basis_s* B);
+// The FP64-accurate tensor-core contraction (precision modes 4, 5) over the seven-slice node tables.
+wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st);
 
 // Queue the batched FP32 factorisation P S = L U of FP64 matrices (mixed-precision form).
 wpccc_status launch_factor_f32(int N, int batch, const double2* S, float2* LU, int* ipiv, int* info,

@@ -1,0 +1,166 @@
+"""The FP64-accurate tensor-core contraction (precision modes 4 and 5) through the C ABI.
+
+Mode 4 is the FP64 form with the Eq. 9 contraction emulated on the tensor cores (seven bf16 slices
+per operand, exact level accumulators); it is held to the FP64 bars against the oracle: elements
+within 1e-12 (scaled like the FP64 element tests) and probabilities within 1e-10 max(P, 1e-4).
+Mode 5 (its elements with FP32 factors and FP64 refinement) is a reduced-precision form: 1e-6.
+"""
+import numpy as np
+import pytest
+
+import wpccc_inputs as wi
+from oracle import wpccc_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P_TOL = 1e-10
+
+
+def _w():
+    import paper_2403_04252_gb300 as w
+    return w
+
+
+def _prob_close(Pg, Po):
+    bound = P_TOL * np.maximum(Po, 1e-4)
+    bad = np.abs(Pg - Po) > bound
+    assert not bad.any(), f"max |dP| = {np.abs(Pg - Po).max():.3e} at {np.nonzero(bad)}"
+
+
+@pytest.fixture(scope="module")
+def small32():
+    # 13 states per centre, 16 x 16 = 256 nodes (eight 32-node chunks)
+    return wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=16, Gtau=16)
+
+
+@pytest.fixture(scope="module")
+def uneven32():
+    # C6+ on H like: different charges and basis sizes on the two centres
+    return wi.make_basis(1.0, 6.0, (3, 2), (2, 1), (3, 2), (3.0, 4.0), True, Nr=600, Geta=16, Gtau=16)
+
+
+@pytest.fixture(scope="module")
+def config2():
+    return wi.config_inputs("p_H_2c_n4l3")
+
+
+def _elements(g, b, v, zs, mode):
+    S, H = g.matrix_elements_precision(b, v, np.asarray(zs), mode)
+    torch.cuda.synchronize()
+    return S, H
+
+
+def test_fp64_tc_elements_match_fp64_full_basis(config2):
+    # the two-centre p + H workload (N = 380, 2304 nodes): mode 4 against the FP64 CUDA-core elements
+    basis, _ = config2
+    w = _w()
+    g = w.Basis(basis)
+    zs = np.array([-7.0, -0.55, 0.0, 0.35, 12.0])
+    worst = 0.0
+    for b in (0.2, 3.2, 11.0):
+        S0, H0 = _elements(g, b, 1.5, zs, 0)
+        S4, H4 = _elements(g, b, 1.5, zs, 4)
+        eS = (S4 - S0).abs().max().item()
+        eH = (H4 - H0).abs().max().item() / max(1.0, H0.abs().max().item())
+        worst = max(worst, eS, eH)
+        assert eS < 1e-12 and eH < 1e-12, (b, eS, eH)
+    print("mode 4 element error vs FP64:", worst)
+    g.close()
+
+
+def test_fp64_tc_elements_match_oracle(small32, uneven32):
+    w = _w()
+    for basis in (small32, uneven32):
+        g = w.Basis(basis)
+        zs = np.array([-6.0, -0.4, 0.0, 0.7, 35.0])
+        for b, v in ((0.8, 1.5), (3.0, 0.9)):
+            S, H = _elements(g, b, v, zs, 4)
+            Sg, Hg = w.natural(S).cpu().numpy(), w.natural(H).cpu().numpy()
+            for k, z in enumerate(zs):
+                So, Ho = O.assemble(basis, b, v, z)
+                assert np.abs(Sg[k] - So).max() < 1e-12
+                assert np.abs(Hg[k] - Ho).max() < 1e-12 * max(1.0, np.abs(Ho).max())
+        g.close()
+
+
+def test_tensor_core_row_tiles_split_large_groups():
+    # 74 target states with q' = 0 (more than 64): the group is cut into two row tiles; both tensor-core
+    # forms against the FP64 elements
+    w = _w()
+    basis = wi.make_basis(1.0, 1.0, 4, 3, 16, 3.0, True, Nr=600, Geta=16, Gtau=16)
+    g = w.Basis(basis)
+    zs = np.array([-3.0, 0.2, 4.0])
+    S0, H0 = _elements(g, 1.1, 1.5, zs, 0)
+    S3, H3 = _elements(g, 1.1, 1.5, zs, 3)
+    S4, H4 = _elements(g, 1.1, 1.5, zs, 4)
+    scale = max(1.0, H0.abs().max().item())
+    assert (S3 - S0).abs().max().item() < 1e-6 and (H3 - H0).abs().max().item() < 1e-6 * scale
+    assert (S4 - S0).abs().max().item() < 1e-12 and (H4 - H0).abs().max().item() < 1e-12 * scale
+    g.close()
+
+
+@pytest.mark.parametrize("solve", [0, 2])
+def test_fp64_tc_propagation_matches_oracle(small32, uneven32, solve):
+    # mode 4 with the LU (0) or Schur (2) solve, ragged paths, against the oracle at the FP64 bar
+    w = _w()
+    for basis, v in ((small32, 1.3), (uneven32, 2.0)):
+        g = w.Basis(basis)
+        g.set_solve_mode(solve)
+        g.set_workspace_limit(64 << 20)
+        bs = np.array([0.5, 2.0, 4.5])
+        zgs = [wi.uniform_zgrid(-4.0, 4.0, 0.25), wi.uniform_zgrid(-3.0, 5.0, 0.2), wi.uniform_zgrid(-1.0, 1.0, 0.5)]
+        Pg = w.probabilities(g.propagate(bs, v, zgs, precision_mode=4)).cpu().numpy()
+        for p in range(3):
+            _prob_close(Pg[p], O.probabilities(O.propagate(basis, float(bs[p]), v, zgs[p])))
+        g.close()
+
+
+def test_fp64_tc_full_basis_sampled_paths(config2):
+    # the bench launch configuration (all 32 paths batched), two RK4 steps; two paths by the oracle
+    basis, paths = config2
+    w = _w()
+    g = w.Basis(basis)
+    g.set_solve_mode(w.SOLVE_SCHUR)
+    zg = np.array([-0.2, -0.1, 0.0])
+    Pg = w.probabilities(g.propagate(paths.b, paths.v, zg, precision_mode=4)).cpu().numpy()
+    for p in (0, 17):
+        _prob_close(Pg[p], O.probabilities(O.propagate(basis, float(paths.b[p]), float(paths.v[p]), zg)))
+    g.close()
+
+
+def test_fp64_tc_full_paths_against_fp64(config2):
+    # whole paths (1000 RK4 steps) of the p + H workload: mode 4 against the FP64 CUDA-core form at the
+    # FP64 bar, and mode 5 within the reduced-precision bound
+    basis, paths = config2
+    w = _w()
+    g = w.Basis(basis)
+    g.set_solve_mode(w.SOLVE_SCHUR)
+    idx = [0, 4, 12, 31]
+    zg = paths.z[0]
+    P0 = w.probabilities(g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=0)).cpu().numpy()
+    P4 = w.probabilities(g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=4)).cpu().numpy()
+    P5 = w.probabilities(g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=5)).cpu().numpy()
+    print("mode 4 max |dP| vs FP64:", np.abs(P4 - P0).max(), " mode 5:", np.abs(P5 - P0).max())
+    _prob_close(P4, P0)
+    assert np.abs(P5 - P0).max() <= 1e-6
+    g.close()
+
+
+def test_fp64_tc_rejections():
+    w = _w()
+    odd = wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=15, Gtau=13)   # 195 nodes
+    g = w.Basis(odd)
+    with pytest.raises(w.WpcccError) as e:
+        g.matrix_elements_precision(0.9, 1.3, np.array([0.0]), 4)
+    assert e.value.status == w.EUNSUPPORTED
+    with pytest.raises(w.WpcccError) as e:
+        g.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])], precision_mode=6)
+    assert e.value.status == w.EUNSUPPORTED
+    g.close()
+    li = wi.li_basis(Z_p=1.0, a=3.1, b=1.45, nmax=2, lmax=1, nbins=2, kmax=1.5, Nr=400, rmax=40.0, Geta=16, Gtau=16)
+    gl = w.Basis(li)
+    with pytest.raises(w.WpcccError) as e:
+        gl.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])], precision_mode=4)
+    assert e.value.status == w.EUNSUPPORTED
+    gl.close()
