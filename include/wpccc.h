@@ -243,12 +243,13 @@ WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv
  *        tiles staged by TMA;
  *     4  the FP64 form (solve and RK4 as mode 0) with the Eq. 9 contraction emulated to FP64
  *        accuracy on the tensor cores: seven bf16 slices of both operands in fixed point per
- *        32-node chunk (error-free splitting, Ozaki et al.), 28 slice products into five FP32
+ *        128-node window (error-free splitting, Ozaki et al.), 28 slice products into five FP32
  *        accumulators of which four are exact, drained into double-float sums; element errors
  *        about 2^-47 of the largest quadrature term;
  *     5  as 2 (FP32 factors and FP64 refinement) with the elements of mode 4;
- *     modes 3-5 need a node count that is a multiple of 32 and no model potential; in one-centre
- *     mode all modes are the FP64 form (no contraction, no solve).
+ *     modes 3-5 need no model potential and a node count that is a multiple of 32 (mode 3) or
+ *     128 (modes 4 and 5: fixed-point scales per 128-node window); in one-centre mode all modes
+ *     are the FP64 form (no contraction, no solve).
  *   batch_mode 0 = all paths batched together in chunks of RK4 steps (the only
  *   batch mode of this build).
  * Blocks until the work is finished: the library allocates its scratch memory
@@ -311,6 +312,16 @@ WPCCC_API wpccc_status wpccc_probabilities(int n_paths, int N, const void* c, do
 #define WPCCC_SOLVE_MATRIX 1
 #define WPCCC_SOLVE_SCHUR 2
 WPCCC_API wpccc_status wpccc_basis_set_solve_mode(wpccc_basis basis, int mode);
+
+/*
+ * Sweeps of FP64 iterative refinement per RK4 stage in the refined precision modes (1, 2, 3, 5):
+ * x_0 from the FP32 factors, then x_{n+1} = x_n + S_32^{-1} (H y - S x_n) with the residual in FP64.
+ * Each sweep shrinks the solve error by about cond(S) 2^-24; the default of 2 leaves it near
+ * FP32-squared level, 3 to 4 reach FP64 rounding for well-conditioned S.  (The paper solves in
+ * FP64 only; no counterpart.)  Errors: EINVAL (null basis, iters outside 1..WPCCC_MAX_REFINE).
+ */
+#define WPCCC_MAX_REFINE 8
+WPCCC_API wpccc_status wpccc_basis_set_refine_iters(wpccc_basis basis, int iters);
 
 /*
  * Upper bound on the scratch memory wpccc_propagate may hold (default 8 GiB).

@@ -67,6 +67,7 @@ _lib.wpccc_probabilities.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C
 _lib.wpccc_basis_set_workspace_limit.argtypes = [C.c_void_p, C.c_size_t]
 _lib.wpccc_profile_enable.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_basis_set_solve_mode.argtypes = [C.c_void_p, C.c_int]
+_lib.wpccc_basis_set_refine_iters.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_profile_read.argtypes = [C.c_void_p, _pd, C.POINTER(C.c_longlong)]
 _lib.wpccc_batch_create.argtypes = [C.c_int, C.POINTER(C.c_void_p), C.POINTER(_PathsDesc), C.c_int,
                                     C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
@@ -85,7 +86,7 @@ for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpc
            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode",
            "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
            "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
-           "wpccc_matrix_elements_precision"):
+           "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
@@ -93,8 +94,9 @@ EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wp
             "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error",
             "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
             "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
-            "wpccc_matrix_elements_precision")
+            "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters")
 MAX_PARAMS = 4
+MAX_REFINE = 8
 NOALLOC_SCRATCH_BYTES = 64 << 20
 SOLVE_STAGE, SOLVE_MATRIX, SOLVE_SCHUR = 0, 1, 2
 PROF_CATEGORIES = ("node_tables", "mol_gemm", "rotate_direct", "solve", "rk4", "adjoint")
@@ -210,6 +212,10 @@ class Basis:
         """SOLVE_STAGE (LU of S once per position, solve per RK4 stage), SOLVE_SCHUR (Cholesky of the Schur
         complement I - K^+ K once per position, solve per stage) or SOLVE_MATRIX (X = S^-1 H)."""
         _check(_lib.wpccc_basis_set_solve_mode(self._h, int(mode)), "wpccc_basis_set_solve_mode")
+
+    def set_refine_iters(self, iters: int) -> None:
+        """FP64 refinement sweeps per RK4 stage of the refined precision modes (1, 2, 3, 5); default 2."""
+        _check(_lib.wpccc_basis_set_refine_iters(self._h, int(iters)), "wpccc_basis_set_refine_iters")
 
     def profile_enable(self, on: bool = True) -> None:
         """Reset the per-kernel counters; with on=True time every launch with CUDA events."""

@@ -470,6 +470,14 @@ extern "C" wpccc_status wpccc_basis_set_solve_mode(wpccc_basis B, int mode) {
     return WPCCC_OK;
 }
 
+extern "C" wpccc_status wpccc_basis_set_refine_iters(wpccc_basis B, int iters) {
+    if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_refine_iters: null basis");
+    if (iters < 1 || iters > WPCCC_MAX_REFINE)
+        return fail(WPCCC_EINVAL, "wpccc_basis_set_refine_iters: iterations must be 1 to " + std::to_string(WPCCC_MAX_REFINE));
+    B->refine_iters = iters;
+    return WPCCC_OK;
+}
+
 extern "C" wpccc_status wpccc_basis_set_workspace_limit(wpccc_basis B, size_t bytes) {
     if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_workspace_limit: null basis");
     if (bytes < ((size_t)64 << 20)) return fail(WPCCC_EINVAL, "workspace limit below 64 MiB");

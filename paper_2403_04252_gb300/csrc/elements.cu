@@ -191,27 +191,28 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         for (int t = 0; t < A.nlqP; ++t) thP[(size_t)t * A.G + g] = (T)thv[1][t];
     } else if (A.tc == 2) {
         // FP64-accurate tensor-core layout: A_T r_T and A_T r_T V_T per target state (rows of the row
-        // tiles), each as seven bf16 slices against a power-of-two scale per 32-node chunk (one warp);
-        // the products are formed in double-float arithmetic from FP64 factors split once per node
+        // tiles), each as seven bf16 slices against a power-of-two scale per 128-node window (this
+        // block: the node count is a multiple of 128 in this layout); the products are formed in
+        // double-float arithmetic from FP64 factors split once per node
+        __shared__ float s_wm[2][4][2];   // per-warp row maxima, double-buffered across states
         const double rTV = A.mp_c == 0.0 ? -A.Z_T : -A.Z_T + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT);
         const float2 frT = df_split(rT), frTV = df_split(rTV);   // r_T and r_T V_T(r_T)
         float2 fth[(WPCCC_LMAX + 1) * (WPCCC_LMAX + 2) / 2];
         for (int q = 0; q < (A.lmaxT + 1) * (A.lmaxT + 2) / 2; ++q) fth[q] = df_split(thv[0][q]);
         __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(base);
-        float* sc = reinterpret_cast<float*>(base) + A.t6_sc_off + (size_t)(g >> 5) * A.tc_rows;
+        float* sc = reinterpret_cast<float*>(base) + A.t6_sc_off + (size_t)(g >> 7) * A.tc_rows;
         const size_t split = (size_t)A.tc_rows * A.G;
-        auto put7 = [&](size_t row, float2 x) {
-            float mx = fabsf(x.x);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int wid = threadIdx.x >> 5, lid = threadIdx.x & 31;
+        auto put7 = [&](size_t row, float2 x, float mx) {
             const int sh = oz_shift(mx);
             __nv_bfloat16 q[OZ_SLICES];
             oz_slices(x.x, x.y, sh, q);
             const size_t o = row * A.G + g;
 #pragma unroll
             for (int i = 0; i < OZ_SLICES; ++i) sp[i * split + o] = q[i];
-            if ((threadIdx.x & 31) == 0) sc[row] = ldexpf(1.f, -sh);
+            if (threadIdx.x == 0) sc[row] = ldexpf(1.f, -sh);
         };
+        int par = 0;
         for (int a = 0; a < A.nradT; ++a) {
             double val = 0.0;
             if (inT) {
@@ -225,10 +226,26 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
                 const int am = m < 0 ? -m : m;
                 float2 t = df_mul(fv, fth[l * (l + 1) / 2 + am]);
                 if (m < 0 && (am & 1)) t = make_float2(-t.x, -t.y);
+                const float2 x1 = df_mul(t, frT), x2 = df_mul(t, frTV);
+                // the two rows' maxima over the block's 128 nodes: warp shuffles, then the four warps
+                float m1 = fabsf(x1.x), m2 = fabsf(x2.x);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+                    m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                }
+                if (lid == 0) {
+                    s_wm[par][wid][0] = m1;
+                    s_wm[par][wid][1] = m2;
+                }
+                __syncthreads();
+                m1 = fmaxf(fmaxf(s_wm[par][0][0], s_wm[par][1][0]), fmaxf(s_wm[par][2][0], s_wm[par][3][0]));
+                m2 = fmaxf(fmaxf(s_wm[par][0][1], s_wm[par][1][1]), fmaxf(s_wm[par][2][1], s_wm[par][3][1]));
+                par ^= 1;
                 const int row = A.tc_row[i];
                 const int tsz = A.tc_row[A.N_T + i];
-                put7((size_t)row, df_mul(t, frT));
-                put7((size_t)(row + tsz), df_mul(t, frTV));
+                put7((size_t)row, x1, m1);
+                put7((size_t)(row + tsz), x2, m2);
             }
         }
         // A_P per half column as double-floats
@@ -1155,10 +1172,10 @@ ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
             nt += ((size_t)L.tc_rows * ((B->G + 31) / 32) + 3) / 4 * 4;
             L.node_doubles = std::max(L.node_doubles, (nt + 1) / 2);
             // FP64-accurate layout (precision modes 4, 5): seven bf16 slice planes [7][tc_rows][G], the
-            // chunk scales, A_P [n_half][G] and W_K / r_T [d][re, im][G] as double-floats (float pairs)
+            // scales per 128-node window, A_P [n_half][G] and W_K / r_T [d][re, im][G] as double-floats
             size_t n6 = ((size_t)OZ_SLICES * L.tc_rows * B->G + 7) / 8 * 4;
             L.t6_sc_off = n6;
-            n6 += ((size_t)L.tc_rows * ((B->G + 31) / 32) + 3) / 4 * 4;
+            n6 += ((size_t)L.tc_rows * ((B->G + 127) / 128) + 3) / 4 * 4;
             L.t6_ap_off = n6;
             n6 += (size_t)2 * B->n_half * B->G;
             L.t6_w_off = n6;
@@ -1504,6 +1521,8 @@ extern "C" wpccc_status wpccc_matrix_elements_precision(wpccc_basis B, double b,
         return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: reduced precision needs two centres");
     if (precision_mode != 0 && B->mp_c != 0.0)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: model-potential targets need FP64");
+    if (precision_mode == 4 && B->G % 128 != 0)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: mode 4 needs a node count that is a multiple of 128");
     return matrix_elements_prec(B, b, v, nz, z, S, H, precision_mode, stream);
 }
 

@@ -8,20 +8,22 @@
 //   generated rows  n (N = 48: 24 half columns x re/im), formed here from double-float W and A_P
 // into D[m][n].
 //
-// Precision (error-free slicing after Ozaki, Ogita, Oishi and Rump; see ozaki.cuh): per 32-node chunk
-// both operands are written in fixed point with seven bf16 slices, a_g = s_m sum_i alpha_i and
-// b_g = s_n sum_j beta_j with alpha_i, beta_j integers times 2^(-8 i), 2^(-8 j).  The products with
-// i + j = L form level L (weight 2^(-8 L)); levels 0-3 go to four accumulators that hold their sums
-// exactly (integers times 2^(-8 L) below 2^22 units), levels 4-6 to a fifth, whose FP32 rounding over
-// its 36 MMAs stays near 2^-49 of the chunk's largest term; levels >= 7 are dropped (below 2^-53).
-// Per chunk the epilogue forms s_m s_n (L0 + L1 + L2 + L3 + T) with the exact parts folded into
-// double-float running sums (two TwoSums), so the result carries about 2^-47 of the largest term.
+// Precision (error-free slicing after Ozaki, Ogita, Oishi and Rump; see ozaki.cuh): per window of four
+// 32-node chunks (128 nodes) both operands are written in fixed point with seven bf16 slices,
+// a_g = s_m sum_i alpha_i and b_g = s_n sum_j beta_j with alpha_i, beta_j integers times 2^(-8 i),
+// 2^(-8 j) and s_m, s_n powers of two per row and window.  The products with i + j = L form level L
+// (weight 2^(-8 L)); levels 0-3 go to four accumulators that hold their window sums exactly (integers
+// times 2^(-8 L) below 2^24 units: at most four products of |k| <= 129 over 128 nodes), levels 4-6 to a
+// fifth, whose FP32 rounding over its 144 MMAs stays near 2^-48 of the window's largest term; levels
+// >= 7 are dropped (below 2^-53).  Per window the epilogue forms s_m s_n (L0 + L1 + L2 + L3 + T) with
+// the exact parts folded into double-float running sums (two TwoSums), so the result carries about
+// 2^-46 of the largest term.
 //
 // Pipeline per CTA (416 threads): warps 0-11 generate the Bw tiles (64-byte swizzled K-major rows) and
 // drain the accumulators; warp 12 issues the TMA loads of the table tiles (cp.async.bulk.tensor, 64-byte
-// swizzle) and the tcgen05.mma instructions.  Two shared-memory stages, a ring of four scale slots, two
-// TMEM buffers of five accumulators, mbarriers between the roles; every wait is bounded and records a
-// timeout in a device flag.
+// swizzle) and the tcgen05.mma instructions.  Three table tiles and two generated tiles in flight in
+// shared memory, a ring of scale slots (one per window), two TMEM buffers of five accumulators (one per
+// window), mbarriers between the roles; every wait is bounded and records a timeout in a device flag.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -37,21 +39,32 @@ namespace wpccc {
 constexpr int T6_M = 128;                              // table rows per CTA (MMA M)
 constexpr int T6_N = 48;                               // generated rows per CTA (MMA N)
 constexpr int T6_K = 32;                               // nodes per chunk: one 64-byte bf16 row
+constexpr int T6_WIN = 4;                              // chunks per scaling window (128 nodes)
 constexpr int T6_ACC = 5;                              // accumulators: levels 0, 1, 2, 3 and >= 4
-constexpr int T6_STAGES = 2;
-constexpr int T6_SC_SLOTS = 4;                         // scale ring (see the drain)
+constexpr int T6_TSTAGES = 3;                          // table tiles in flight (TMA ring)
+constexpr int T6_GSTAGES = 2;                          // generated tiles (producer ring)
+constexpr int T6_SC_SLOTS = 2;                         // scale ring, one slot per window (see the drain)
 constexpr int T6_PE_WARPS = 12;                        // producer / epilogue warps
 constexpr int T6_THREADS = (T6_PE_WARPS + 1) * 32;
 constexpr int T6_TMEM_COLS = 512;                      // 2 buffers x 5 accumulators x 48 columns = 480
 constexpr int T6_BUF_COLS = T6_ACC * T6_N;
 constexpr int T6_A_TILE = T6_M * 64;                   // bytes of one slice of the table tile
 constexpr int T6_B_TILE = T6_N * 64;                   // bytes of one slice of the generated tile
-constexpr int T6_STAGE_BYTES = (OZ_SLICES * (T6_A_TILE + T6_B_TILE) + 1023) / 1024 * 1024;
+constexpr int T6_TSTAGE_BYTES = OZ_SLICES * T6_A_TILE;          // 56 KB, a multiple of 1024
+constexpr int T6_GSTAGE_BYTES = OZ_SLICES * T6_B_TILE;          // 21 KB, a multiple of 1024
+constexpr int T6_BOXES = T6_M / 32;                             // table box heights 32, 64, 96, 128 rows
 constexpr int T6_SC_FLOATS = T6_M + T6_N;              // per slot: table row scales, generated row scales
 constexpr int T6_COLS_PER_WARP = T6_N / (T6_PE_WARPS / 4);   // 16 columns per epilogue warp
 
 static_assert(T6_PE_WARPS * 32 == T6_N * 8, "eight producer threads (4 nodes each) per generated row");
 static_assert(2 * T6_BUF_COLS <= T6_TMEM_COLS, "two buffers of accumulators fit the TMEM allocation");
+
+// Tensor maps of the slice planes with box heights 32, 64, 96 and 128 rows: a row tile loads only the
+// 32-row multiple that covers its rows (rows past its end are loaded from the next tile, or left stale,
+// and only feed accumulator lanes that are never read).
+struct Tc64Maps {
+    CUtensorMap m[T6_BOXES];
+};
 
 struct Tc64Args {
     int G, N_T, n_half, nchunks, n_ntiles, tc_rows, qg_max;
@@ -66,10 +79,11 @@ struct Tc64Args {
     int* err;
 };
 
-__global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constant__ CUtensorMap tmap, Tc64Args A) {
+__global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constant__ Tc64Maps maps, Tc64Args A) {
     extern __shared__ __align__(1024) unsigned char t6_smem_raw[];
     unsigned char* sm = t6_smem_raw + ((1024 - (smem_u32(t6_smem_raw) & 1023)) & 1023);
-    float* ring = reinterpret_cast<float*>(sm + T6_STAGES * T6_STAGE_BYTES);     // [slot][T6_SC_FLOATS]
+    unsigned char* gsm = sm + T6_TSTAGES * T6_TSTAGE_BYTES;                        // generated tiles
+    float* ring = reinterpret_cast<float*>(gsm + T6_GSTAGES * T6_GSTAGE_BYTES);  // [slot][T6_SC_FLOATS]
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + T6_SC_SLOTS * T6_SC_FLOATS);
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -77,14 +91,19 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
     const int ntile = blockIdx.x % A.n_ntiles, tile = blockIdx.x / A.n_ntiles, e = blockIdx.y;
     const int row0 = A.qg_off[tile], ns = (A.qg_off[tile + 1] - row0) / 2;   // states of the row tile
     const int qp = A.qg_q[tile];
-    // full[s], empty[s], accf[2], acce[2]
-    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * T6_STAGES, accf0 = empty0 + 8 * T6_STAGES,
-                   acce0 = accf0 + 16;
+    const int box = (2 * ns + 31) / 32;                  // table box height of this tile, in 32-row units
+    // tfull[3] (TMA), tempty[3], gfull[2] (producers), gempty[2], accf[2], acce[2]
+    const uint32_t tfull0 = smem_u32(bars), tempty0 = tfull0 + 8 * T6_TSTAGES, gfull0 = tempty0 + 8 * T6_TSTAGES,
+                   gempty0 = gfull0 + 8 * T6_GSTAGES, accf0 = gempty0 + 8 * T6_GSTAGES, acce0 = accf0 + 16;
     if (tid == 0) {
         s_abort = 0;
-        for (int s = 0; s < T6_STAGES; ++s) {
-            mbar_init(full0 + 8 * s, T6_PE_WARPS * 32 + 1);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int s = 0; s < T6_TSTAGES; ++s) {
+            mbar_init(tfull0 + 8 * s, 1);
+            mbar_init(tempty0 + 8 * s, 1);
+        }
+        for (int s = 0; s < T6_GSTAGES; ++s) {
+            mbar_init(gfull0 + 8 * s, T6_PE_WARPS * 32);
+            mbar_init(gempty0 + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf0 + 8 * b, 1);
@@ -109,56 +128,62 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
         // ---- TMA and MMA issue (one thread)
         if (lane == 0) {
             const uint32_t idesc = bf16_idesc_mn(T6_M, T6_N);
-            const uint32_t tx = (uint32_t)(OZ_SLICES * T6_A_TILE);
+            const uint32_t tx = (uint32_t)(OZ_SLICES * box * 32 * 64);
+            const CUtensorMap* tmap = &maps.m[box - 1];
             auto issue_tma = [&](int k) {
-                const int s = k % T6_STAGES;
-                unsigned char* st = sm + s * T6_STAGE_BYTES;
-                const uint32_t bar = full0 + 8 * s;
+                const int s = k % T6_TSTAGES;
+                unsigned char* st = sm + s * T6_TSTAGE_BYTES;
+                const uint32_t bar = tfull0 + 8 * s;
                 mbar_arrive_tx(bar, tx);
                 for (int sp = 0; sp < OZ_SLICES; ++sp)
-                    tma_load_3d(smem_u32(st + sp * T6_A_TILE), &tmap, k * T6_K, sp * A.tc_rows + row0, e, bar);
+                    tma_load_3d(smem_u32(st + sp * T6_A_TILE), tmap, k * T6_K, sp * A.tc_rows + row0, e, bar);
             };
             int issued = 0;
-            for (; issued < T6_STAGES && issued < nk; ++issued) issue_tma(issued);
+            for (; issued < T6_TSTAGES && issued < nk; ++issued) issue_tma(issued);
             bool ok = true;
             for (int k = 0; k < nk && ok; ++k) {
-                const int s = k % T6_STAGES, b = k & 1;
-                ok = mbar_wait(full0 + 8 * s, (k / T6_STAGES) & 1, abort_flag, A.err, 11);
-                if (ok && k >= 2) ok = mbar_wait(acce0 + 8 * b, ((k - 2) >> 1) & 1, abort_flag, A.err, 12);
+                const int s = k % T6_TSTAGES, s2 = k % T6_GSTAGES, w = k / T6_WIN, b = w & 1;
+                ok = mbar_wait(tfull0 + 8 * s, (k / T6_TSTAGES) & 1, abort_flag, A.err, 11);
+                if (ok) ok = mbar_wait(gfull0 + 8 * s2, (k / T6_GSTAGES) & 1, abort_flag, A.err, 16);
+                if (ok && k % T6_WIN == 0 && w >= 2) ok = mbar_wait(acce0 + 8 * b, ((w - 2) >> 1) & 1, abort_flag, A.err, 12);
                 if (!ok) break;
                 tc_fence_after();
-                unsigned char* st = sm + s * T6_STAGE_BYTES;
-                const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + OZ_SLICES * T6_A_TILE);
+                const uint32_t a0 = smem_u32(sm + s * T6_TSTAGE_BYTES), b0 = smem_u32(gsm + s2 * T6_GSTAGE_BYTES);
                 const uint32_t dbase = tmem + (uint32_t)(b * T6_BUF_COLS);
-                // levels from the smallest up; the first product into each accumulator overwrites it
-                uint32_t written = 0;
-                for (int L = 2 * (OZ_SLICES - 1); L >= 0; --L) {
-                    if (L >= OZ_SLICES) continue;   // levels >= 7: below 2^-53 of the chunk's largest term
+                // levels from the smallest up; in a window's first chunk the first product into each
+                // accumulator overwrites it.  Fully unrolled: the descriptors of the slices are the base
+                // descriptors plus compile-time offsets (16-byte units; no carry out of the address field)
+                const uint64_t da = sw64_desc(a0), db = sw64_desc(b0);
+                const uint32_t fresh = k % T6_WIN == 0 ? 0u : 1u;
+#pragma unroll
+                for (int L = OZ_SLICES - 1; L >= 0; --L) {
                     const int lv = L < T6_ACC - 1 ? L : T6_ACC - 1;
                     const uint32_t d = dbase + (uint32_t)(lv * T6_N);
+#pragma unroll
                     for (int i = 0; i <= L; ++i) {
-                        const int j = L - i;
+#pragma unroll
                         for (int kk = 0; kk < T6_K / 16; ++kk) {
-                            tc_mma(d, sw64_desc(a0 + i * T6_A_TILE + kk * 32), sw64_desc(b0 + j * T6_B_TILE + kk * 32),
-                                   idesc, (written >> lv) & 1u);
-                            written |= 1u << lv;
+                            const bool first = (L == OZ_SLICES - 1 || L < T6_ACC - 1) && i == 0 && kk == 0;
+                            tc_mma(d, da + (uint64_t)((i * T6_A_TILE + kk * 32) >> 4),
+                                   db + (uint64_t)(((L - i) * T6_B_TILE + kk * 32) >> 4), idesc, first ? fresh : 1u);
                         }
                     }
                 }
-                tc_commit(empty0 + 8 * s);
-                tc_commit(accf0 + 8 * b);
+                tc_commit(tempty0 + 8 * s);
+                tc_commit(gempty0 + 8 * s2);
+                if (k % T6_WIN == T6_WIN - 1) tc_commit(accf0 + 8 * b);
                 if (k >= 1 && issued < nk) {
-                    // refill the stage of the previous chunk once its MMAs have completed
-                    const int kp = k - 1, sp = kp % T6_STAGES;
-                    ok = mbar_wait(empty0 + 8 * sp, (kp / T6_STAGES) & 1, abort_flag, A.err, 13);
+                    // refill the table slot of the previous chunk (for chunk k + 2) once its MMAs have completed
+                    const int kp = k - 1, sp = kp % T6_TSTAGES;
+                    ok = mbar_wait(tempty0 + 8 * sp, (kp / T6_TSTAGES) & 1, abort_flag, A.err, 13);
                     if (ok) issue_tma(issued++);
                 }
             }
             if (!ok) {
                 // give the copies still in flight time to land before the CTA exits
-                for (int k = issued > T6_STAGES ? issued - T6_STAGES : 0; k < issued; ++k) {
-                    const int s = k % T6_STAGES;
-                    for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(full0 + 8 * s, (k / T6_STAGES) & 1); ++it) {
+                for (int k = issued > T6_TSTAGES ? issued - T6_TSTAGES : 0; k < issued; ++k) {
+                    const int s = k % T6_TSTAGES;
+                    for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(tfull0 + 8 * s, (k / T6_TSTAGES) & 1); ++it) {
                     }
                 }
             }
@@ -188,6 +213,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
             lo[k] = 0.f;
         }
         bool ok = true;
+        // drain of window j: its accumulators with the window's scales
         auto drain = [&](int j) {
             const int b = j & 1;
             ok = ok && mbar_wait(accf0 + 8 * b, (j >> 1) & 1, abort_flag, A.err, 14);
@@ -209,7 +235,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
                         const int k = 8 * q + u;
                         const float sc = sa * scl[T6_M + col0 + k];
                         // exact: L0 + round(L1) (integers below 2^22), frac(L1) + L2 (multiples of
-                        // 2^-16 below 2^5); rounded: L3 + T (below 2^-2, its rounding under 2^-26)
+                        // 2^-16 below 2^7); rounded: L3 + T (below 1, its rounding under 2^-24)
                         const float l1h = rintf(v[1][u]);
                         const float xa = __fadd_rn(v[0][u], l1h);
                         const float xb = __fadd_rn(__fsub_rn(v[1][u], l1h), v[2][u]);
@@ -224,46 +250,57 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
             tc_fence_before();
             mbar_arrive(acce0 + 8 * b);
         };
-        for (int k = 0; k < nk && ok; ++k) {
-            const int s = k % T6_STAGES;
-            if (k >= T6_STAGES)
-                ok = mbar_wait(empty0 + 8 * s, ((k - T6_STAGES) / T6_STAGES) & 1, abort_flag, A.err, 15);
-            if (!ok) break;
-            unsigned char* bt = sm + s * T6_STAGE_BYTES + OZ_SLICES * T6_A_TILE;
-            float* scl = ring + (k % T6_SC_SLOTS) * T6_SC_FLOATS;
-            const int g0 = k * T6_K + part * 4;
-            float2 x[4];
+        const int nwin = nk / T6_WIN;
+        const int trow = row0 + tid;
+        for (int w = 0; w < nwin && ok; ++w) {
+            // this thread's 16 generated values of the window (four per chunk), their row maximum over the
+            // window's 128 nodes (the row's eight threads), and the window's scales
+            float2 xw[T6_WIN * 4];
             float mx = 0.f;
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                x[jj] = make_float2(0.f, 0.f);
-                if (valid) x[jj] = df_mul(wd[g0 + jj], ap[g0 + jj]);
-                mx = fmaxf(mx, fabsf(x[jj].x));
+            for (int cc = 0; cc < T6_WIN; ++cc) {
+                const int g0 = (w * T6_WIN + cc) * T6_K + part * 4;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float4 wq = valid ? reinterpret_cast<const float4*>(wd + g0)[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 aq = valid ? reinterpret_cast<const float4*>(ap + g0)[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    xw[4 * cc + 2 * h] = df_mul(make_float2(wq.x, wq.y), make_float2(aq.x, aq.y));
+                    xw[4 * cc + 2 * h + 1] = df_mul(make_float2(wq.z, wq.w), make_float2(aq.z, aq.w));
+                }
             }
+#pragma unroll
+            for (int jj = 0; jj < T6_WIN * 4; ++jj) mx = fmaxf(mx, fabsf(xw[jj].x));
 #pragma unroll
             for (int o = 1; o < 8; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             const int sh = oz_shift(mx);
+            float* scl = ring + (w % T6_SC_SLOTS) * T6_SC_FLOATS;
             if (part == 0) scl[T6_M + n] = ldexpf(1.f, -sh);
-            // the table rows' scales of this chunk (rows past the table read as zero scale)
-            if (tid < T6_M) {
-                const int row = row0 + tid;
-                scl[tid] = row < A.tc_rows ? scT[(size_t)k * A.tc_rows + row] : 0.f;
+            // the table rows' scales of this window (rows past the table read as zero scale)
+            if (tid < T6_M) scl[tid] = trow < A.tc_rows ? scT[(size_t)w * A.tc_rows + trow] : 0.f;
+#pragma unroll
+            for (int cc = 0; cc < T6_WIN; ++cc) {
+                const int k = w * T6_WIN + cc, s = k % T6_GSTAGES;
+                if (k >= T6_GSTAGES)
+                    ok = ok && mbar_wait(gempty0 + 8 * s, ((k - T6_GSTAGES) / T6_GSTAGES) & 1, abort_flag, A.err, 15);
+                if (!ok) break;
+                unsigned char* bt = gsm + s * T6_GSTAGE_BYTES;
+                __nv_bfloat16 q[4][OZ_SLICES];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) oz_slices(xw[4 * cc + jj].x, xw[4 * cc + jj].y, sh, q[jj]);
+                // row n of each slice tile: 64 bytes, 16-byte chunk qq at (qq ^ ((n >> 1) & 3)); this
+                // thread holds the 8-byte half (part & 1) of chunk part >> 1
+                const int off = n * 64 + (((part >> 1) ^ ((n >> 1) & 3)) << 4) + (part & 1) * 8;
+#pragma unroll
+                for (int sp = 0; sp < OZ_SLICES; ++sp)
+                    *reinterpret_cast<uint2*>(bt + sp * T6_B_TILE + off) =
+                        make_uint2(bf16x2(q[0][sp], q[1][sp]), bf16x2(q[2][sp], q[3][sp]));
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(gfull0 + 8 * s);
+                // the previous window's drain overlaps this window's MMAs
+                if (cc == 0 && w >= 1) drain(w - 1);
             }
-            __nv_bfloat16 q[4][OZ_SLICES];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) oz_slices(x[jj].x, x[jj].y, sh, q[jj]);
-            // row n of each slice tile: 64 bytes, 16-byte chunk qq at (qq ^ ((n >> 1) & 3)); this thread
-            // holds the 8-byte half (part & 1) of chunk part >> 1
-            const int off = n * 64 + (((part >> 1) ^ ((n >> 1) & 3)) << 4) + (part & 1) * 8;
-#pragma unroll
-            for (int sp = 0; sp < OZ_SLICES; ++sp)
-                *reinterpret_cast<uint2*>(bt + sp * T6_B_TILE + off) =
-                    make_uint2(bf16x2(q[0][sp], q[1][sp]), bf16x2(q[2][sp], q[3][sp]));
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            mbar_arrive(full0 + 8 * s);
-            if (k >= 1) drain(k - 1);
         }
-        if (ok) drain(nk - 1);
+        if (ok) drain(nwin - 1);
         // results: row m of D is A_T row m of the tile (overlap K) or, from ns on, its A_T V_T row (Q)
         if (ok && live && lrow < 2 * ns) {
             const int x = lrow < ns ? 0 : 1;
@@ -287,18 +324,21 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
 
 wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st) {
     if (!B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
+    if (B->G % (T6_K * T6_WIN) != 0) return fail(WPCCC_EUNSUPPORTED, "the node count must be a multiple of 128");
     const ElemScratch L = elem_scratch_layout(B);
     const size_t node_bytes = L.node_doubles * sizeof(double);
     // seven slice planes as one 3-D bf16 tensor: x = node (G), y = slice plane row (7 x tc_rows), z = evaluation
-    CUtensorMap map;
+    Tc64Maps maps;
     const cuuint64_t dims[3] = {(cuuint64_t)B->G, (cuuint64_t)OZ_SLICES * L.tc_rows, (cuuint64_t)nev};
     const cuuint64_t strides[2] = {(cuuint64_t)B->G * 2, (cuuint64_t)node_bytes};
-    const cuuint32_t box[3] = {(cuuint32_t)T6_K, (cuuint32_t)T6_M, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(node), dims, strides, box,
-                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(WPCCC_ECUDA, "cuTensorMapEncodeTiled failed for the slice planes");
+    for (int h = 0; h < T6_BOXES; ++h) {
+        const cuuint32_t box[3] = {(cuuint32_t)T6_K, (cuuint32_t)(32 * (h + 1)), 1};
+        CUresult r = encode_fn()(&maps.m[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(node), dims, strides,
+                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(WPCCC_ECUDA, "cuTensorMapEncodeTiled failed for the slice planes");
+    }
     Tc64Args a;
     a.G = B->G;
     a.N_T = B->N_T;
@@ -318,10 +358,10 @@ wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double
     a.w_off_f = L.t6_w_off;
     a.mol = reinterpret_cast<double*>(mol);
     a.err = err;
-    const size_t smem = 1024 + (size_t)T6_STAGES * T6_STAGE_BYTES + sizeof(float) * T6_SC_SLOTS * T6_SC_FLOATS +
-                        8 * (2 * T6_STAGES + 4);
+    const size_t smem = 1024 + (size_t)T6_TSTAGES * T6_TSTAGE_BYTES + (size_t)T6_GSTAGES * T6_GSTAGE_BYTES +
+                        sizeof(float) * T6_SC_SLOTS * T6_SC_FLOATS + 8 * (2 * T6_TSTAGES + 2 * T6_GSTAGES + 4);
     WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_mol_tc64<<<dim3(a.n_ntiles * B->n_qgroups, nev), T6_THREADS, smem, st>>>(map, a);
+    k_mol_tc64<<<dim3(a.n_ntiles * B->n_qgroups, nev), T6_THREADS, smem, st>>>(maps, a);
     WPCCC_CHECK_LAUNCH("k_mol_tc64");
     return WPCCC_OK;
 }

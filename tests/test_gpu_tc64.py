@@ -141,9 +141,18 @@ def test_fp64_tc_full_paths_against_fp64(config2):
     P0 = w.probabilities(g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=0)).cpu().numpy()
     P4 = w.probabilities(g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=4)).cpu().numpy()
     P5 = w.probabilities(g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=5)).cpu().numpy()
-    print("mode 4 max |dP| vs FP64:", np.abs(P4 - P0).max(), " mode 5:", np.abs(P5 - P0).max())
+    # mode 5 with four refinement sweeps per stage: the FP32 factors only precondition, the FP64
+    # residual drives the solve to FP64 rounding, so the form meets the FP64 bar too
+    g.set_refine_iters(4)
+    P54 = w.probabilities(g.propagate(paths.b[idx], paths.v[idx], zg, precision_mode=5)).cpu().numpy()
+    print("mode 4 max |dP| vs FP64:", np.abs(P4 - P0).max(), " mode 5:", np.abs(P5 - P0).max(),
+          " mode 5, 4 sweeps:", np.abs(P54 - P0).max())
     _prob_close(P4, P0)
+    _prob_close(P54, P0)
     assert np.abs(P5 - P0).max() <= 1e-6
+    with pytest.raises(w.WpcccError) as e:
+        g.set_refine_iters(0)
+    assert e.value.status == w.EINVAL
     g.close()
 
 
@@ -158,6 +167,16 @@ def test_fp64_tc_rejections():
         g.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])], precision_mode=6)
     assert e.value.status == w.EUNSUPPORTED
     g.close()
+    # 16 x 14 = 224 nodes: seven 32-node chunks (mode 3 takes them) but not whole 128-node windows
+    b224 = wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=16, Gtau=14)
+    g2 = w.Basis(b224)
+    S3, _ = g2.matrix_elements_precision(0.9, 1.3, np.array([0.0]), 3)
+    for call in (lambda: g2.matrix_elements_precision(0.9, 1.3, np.array([0.0]), 4),
+                 lambda: g2.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])], precision_mode=5)):
+        with pytest.raises(w.WpcccError) as e:
+            call()
+        assert e.value.status == w.EUNSUPPORTED
+    g2.close()
     li = wi.li_basis(Z_p=1.0, a=3.1, b=1.45, nmax=2, lmax=1, nbins=2, kmax=1.5, Nr=400, rmax=40.0, Geta=16, Gtau=16)
     gl = w.Basis(li)
     with pytest.raises(w.WpcccError) as e:
