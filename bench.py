@@ -322,7 +322,7 @@ def run_batch(args) -> None:
             "autotune": {"chunk_steps": [int(x) for x in chunk_steps],
                          "ms_per_rk4_step": [float(x) for x in tuned], "create_s": t_create},
             "roofline": {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm<double>",
-                                                           "solve": "k_schur_factor" if args.solve_mode == "schur"
+                                                           "solve": "k_schur_factor<double>" if args.solve_mode == "schur"
                                                            else "k_lu_solve"}[dom_f],
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
@@ -500,8 +500,7 @@ def run_grad(args) -> None:
             "fd_check": fd_check,
             "kernel_ms": {k: v_[0] for k, v_ in prof.items()},
             "roofline": {"bound": "alu", "kernel": {"mol_gemm": "k_mol_gemm<double>",
-                                                           "solve": "k_schur_factor" if args.solve_mode == "schur"
-                                                           else "k_lu_solve"}[dom_f],
+                                                           "solve": "k_lu_solve"}[dom_f],
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                          "peak_source": "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz)",
@@ -528,9 +527,11 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all of the workload)")
     ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
-    ap.add_argument("--solve-mode", default="schur", choices=["stage", "matrix", "schur"],
-                    help="FP64 form: S^-1 per RK4 stage through the Schur complement (default), from LU factors, or "
-                         "as X = S^-1 H")
+    ap.add_argument("--solve-mode", default="auto", choices=["auto", "stage", "matrix", "schur"],
+                    help="S^-1 per RK4 stage through the Schur complement's Cholesky factor (schur), from pivoted LU "
+                         "factors (stage), or as X = S^-1 H (matrix); auto: schur for the fixed-speed p + H workload, "
+                         "stage for the others, whose quadrature-assembled overlap matrices at small b are not "
+                         "positive definite (the Cholesky factor of I - K^+ K meets a non-positive pivot, ESINGULAR)")
     ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v",
                                                              "pLi_2c_grad"],
                     help="p_H_2c_n4l3: two-centre p + H (N = 380, 32 paths); C6_H_2c_n6l5: bare C6+ on H "
@@ -549,6 +550,8 @@ def main() -> None:
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.solve_mode == "auto":
+        args.solve_mode = "schur" if args.workload == WORKLOAD else "stage"
     if args.impl == "reference":
         run_reference(args)
         return

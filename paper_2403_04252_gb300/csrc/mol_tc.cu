@@ -40,7 +40,9 @@ constexpr int TC_STAGES = 4;
 constexpr int TC_PE_WARPS = 8;     // producer / epilogue warps
 constexpr int TC_THREADS = (TC_PE_WARPS + 1) * 32;
 constexpr int TC_BN_MAX = 128;     // table rows per box (MMA N at most), so 64 accumulators per thread
-constexpr int TC_TILE_STATES = TC_BN_MAX / 2;   // target states per row tile
+// target states per row tile: 2 x 56 = 112 table rows keep this kernel's four stages within 227 KB of
+// shared memory (64-state tiles would need 228 KB)
+constexpr int TC_TILE_STATES = 56;
 constexpr int TC_TMEM_COLS = 512;  // two buffers x (main, correction) accumulators of up to 128 columns
 constexpr int TC_A_TILE = TC_M * 64;          // bytes of one slice of the generated tile
 constexpr int TC_A_SLICES = 4;                // k0, k1, k2 2^-8, k1 2^-8
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mol_tc(const __grid_constant_
 // host side
 // ---------------------------------------------------------------------------
 // Row tiles of the tensor-core layout: the target states grouped by their molecular-frame q', each group
-// cut into tiles of at most 64 states (near-equal sizes).  A tile of n states owns 2 n consecutive rows of
+// cut into tiles of at most 56 states (near-equal sizes).  A tile of n states owns 2 n consecutive rows of
 // the split tables: its A_T rows, then its A_T V_T rows.  Enables the layout on the basis.
 wpccc_status tc_prepare(wpccc_basis_s* B) {
     if (B->tc_layout) return WPCCC_OK;

@@ -122,7 +122,7 @@ struct wpccc_basis_s {
     int refine_iters = 2;       // FP64 refinement iterations of the mixed-precision form
     // tensor-core contraction (precision mode 3): node tables carry the split operand tables
     bool tc_layout = false;
-    int n_qgroups = 0;          // row tiles: target states of one q', at most 64 per tile
+    int n_qgroups = 0;          // row tiles: target states of one q', at most 56 per tile
     int* tc_row = nullptr;      // [2 N_T]: row of each target state in a split table, then its group's size
     int* tc_err = nullptr;      // device flag: a wait of the tensor-core pipeline gave up
     int* tc_halfq = nullptr;    // [n_half]: q of each half column

@@ -85,7 +85,7 @@ def test_fp64_tc_elements_match_oracle(small32, uneven32):
 
 
 def test_tensor_core_row_tiles_split_large_groups():
-    # 74 target states with q' = 0 (more than 64): the group is cut into two row tiles; both tensor-core
+    # 74 target states with q' = 0 (more than 56): the group is cut into two row tiles; both tensor-core
     # forms against the FP64 elements
     w = _w()
     basis = wi.make_basis(1.0, 1.0, 4, 3, 16, 3.0, True, Nr=600, Geta=16, Gtau=16)
