@@ -1,10 +1,9 @@
 """The bare C6+ on H workload (projectile charge 6, N_T = N_P = 811, N = 1622): FP64 parity with the oracle
 at sampled positions and steps, and the mixed-precision form against the FP64 form.
 
-The C6+ couplings are strong and the two-centre basis is nearly linearly dependent at intermediate R
-(cond(S) up to ~1e6), so M has eigenvalues up to |lambda| ~ 1e3-1e5: RK4 is only stable for h |lambda| <
-2.8.  The steps used here respect that (h = 2e-4 with the full basis; h = 0.005 with the 6-pseudostate
-variant, |lambda| <= ~110)."""
+The C6+ couplings are strong and the two-centre basis is close to linearly dependent near closest
+approach, so M has large eigenvalues and RK4 needs short steps there (h |lambda| < 2.8).  The steps used
+here are short (h = 2e-4 with the full basis; h = 0.005 with the 6-pseudostate variant)."""
 import numpy as np
 import pytest
 

@@ -183,3 +183,29 @@ def test_fp64_tc_rejections():
         gl.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])], precision_mode=4)
     assert e.value.status == w.EUNSUPPORTED
     gl.close()
+
+
+def test_batch_graph_fp64_tc_forms(small32, uneven32):
+    # modes 4 and 5 (four refinement sweeps) captured into the batch graph: amplitudes equal separate
+    # propagate calls bit for bit, and stay within the FP64 bar of the plain FP64 form
+    w = _w()
+    gA, gB = w.Basis(small32), w.Basis(uneven32)
+    sets = [(gA, np.array([0.4, 2.5]), 1.0, wi.uniform_zgrid(-3.0, 3.0, 0.2)),
+            (gB, np.array([1.5, 0.8, 3.0]), 1.3, wi.uniform_zgrid(-1.0, 1.0, 0.1))]
+    for mode, iters in ((4, 2), (5, 4)):
+        c = []
+        for g, b, v, zg in sets:
+            g.set_refine_iters(iters)
+            t = torch.zeros((b.size, g.N), dtype=torch.complex128, device="cuda")
+            t[:, 0] = 1.0
+            c.append(t)
+        batch = w.Batch(sets, c, precision_mode=mode, autotune=False)
+        batch.launch()
+        batch.status()
+        for (g, b, v, zg), cb in zip(sets, c):
+            assert torch.equal(cb, g.propagate(b, v, zg, precision_mode=mode))
+            P0 = w.probabilities(g.propagate(b, v, zg, precision_mode=0)).cpu().numpy()
+            _prob_close(w.probabilities(cb).cpu().numpy(), P0)
+        batch.close()
+    gA.close()
+    gB.close()

@@ -517,8 +517,11 @@ CONFIGS = {
                         v=1.5, b=(0.2, 12.0, 32), z=(-50.0, 50.0, 0.1)),
     # two-centre bare C6+ on H (projectile charge 6), the mixed-precision workload; on the paper's
     # geometric z-grid (Sec. II: dense near closest approach, where the C6+ couplings need h << 0.1)
+    # 128 eta nodes: the compact C5+ orbitals and the k <= 4 packets need them for a positive-definite S
+    # (sigma_max(K) at b = 0.5, z = 0: 1.56 with 48 nodes, 1.28 with 72, 1.06 with 96, 0.99847 with 128,
+    # 0.99846 with 160 x 64)
     "C6_H_2c_n6l5": dict(Z_T=1.0, Z_P=6.0, nmax=6, lmax=5, nbins=20, kmax=4.0, two_centre=True,
-                         v=2.0, b=(0.5, 15.0, 16), z=("geometric", 1e-3, 50.0, 500)),
+                         v=2.0, b=(0.5, 15.0, 16), z=("geometric", 1e-3, 50.0, 500), Geta=128, Gtau=48),
 }
 
 
@@ -529,12 +532,15 @@ def batch_inputs(n_b: int = 64, speeds=BATCH_SPEEDS, **over):
     """Two-centre p + H at several speeds: pseudostates per l scaled with v (round(8 + 8 (v - 0.5)/3.5),
     i.e. 8..16 for v = 0.5..4), hydrogenic n <= 4, l <= 3, k <= 3; n_b impact parameters uniform in
     [0.2, 12]; z in [-50, 50] with h = 0.1 v / 1.5 (step count proportional to 1/v).
+    The two-centre quadrature has 72 eta nodes (x 48 tau): with 48, the overlaps of the slow-speed bases
+    at R ~ 0.2 come out with sigma_max(K) up to 1.23, i.e. an indefinite S that no set of functions has;
+    72 gives 0.9991, within 5e-6 of 96 nodes.
     Returns a list of (v, basis, paths)."""
     out = []
     for v in speeds:
         nb = int(round(8 + 8 * (v - 0.5) / 3.5))
         basis = make_basis(1.0, 1.0, over.get("nmax", 4), over.get("lmax", 3), over.get("nbins", nb),
-                           over.get("kmax", 3.0), True, Nr=over.get("Nr", 2000), Geta=over.get("Geta", 48),
+                           over.get("kmax", 3.0), True, Nr=over.get("Nr", 2000), Geta=over.get("Geta", 72),
                            Gtau=over.get("Gtau", 48))
         h = 0.1 * v / 1.5
         paths = make_paths(np.linspace(0.2, 12.0, n_b), v, uniform_zgrid(-50.0, 50.0, h))
