@@ -95,13 +95,12 @@ struct NodeArgs {
     // T = float: per-state products instead of per-radial values (one rounding of f * Theta * sign)
     int N_T, n_half;
     const int *stT_index, *half_of, *radT_l, *radP_l;
-    // tensor-core layouts (T = float): split tables instead of the per-state A_T; tc = 1: three bf16
-    // slices per value with FP32 A_P and W (precision mode 3), tc = 2: seven slices with double-float A_P
-    // and W (precision modes 4 and 5)
-    int tc;
-    const int* tc_row;          // [2 N_T]: row of each target state in a split table, then its group's size
+    // tensor-core layout (T = float, precision modes 3-5): bf16 slice planes of A_T r_T and A_T r_T V_T
+    // (tc_slices of them: 3 at FP32 level, 7 for FP64 accuracy) with scales per 128-node window, and
+    // A_P and W_K / r_T as double-floats
+    int tc, tc_slices;
+    const int* tc_row;          // [2 N_T]: row of each target state in the slice planes, then its tile's size
     int tc_rows;
-    size_t tc_ap_off, tc_w_off, tc_sc_off;
     size_t t6_ap_off, t6_w_off, t6_sc_off;
 };
 
@@ -189,11 +188,11 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         }
         for (int t = 0; t < A.nlqT; ++t) thT[(size_t)t * A.G + g] = (T)thv[0][t];
         for (int t = 0; t < A.nlqP; ++t) thP[(size_t)t * A.G + g] = (T)thv[1][t];
-    } else if (A.tc == 2) {
-        // FP64-accurate tensor-core layout: A_T r_T and A_T r_T V_T per target state (rows of the row
-        // tiles), each as seven bf16 slices against a power-of-two scale per 128-node window (this
-        // block: the node count is a multiple of 128 in this layout); the products are formed in
-        // double-float arithmetic from FP64 factors split once per node
+    } else if (A.tc) {
+        // tensor-core layout: A_T r_T and A_T r_T V_T per target state (rows of the row tiles), each as
+        // tc_slices bf16 slices against a power-of-two scale per 128-node window (this block: the node
+        // count is a multiple of 128 in this layout); the products are formed in double-float arithmetic
+        // from FP64 factors split once per node
         __shared__ float s_wm[2][4][2];   // per-warp row maxima, double-buffered across states
         const double rTV = A.mp_c == 0.0 ? -A.Z_T : -A.Z_T + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT);
         const float2 frT = df_split(rT), frTV = df_split(rTV);   // r_T and r_T V_T(r_T)
@@ -206,10 +205,16 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         auto put7 = [&](size_t row, float2 x, float mx) {
             const int sh = oz_shift(mx);
             __nv_bfloat16 q[OZ_SLICES];
-            oz_slices(x.x, x.y, sh, q);
             const size_t o = row * A.G + g;
+            if (A.tc_slices == 3) {
+                oz_slices<3>(x.x, x.y, sh, q);
 #pragma unroll
-            for (int i = 0; i < OZ_SLICES; ++i) sp[i * split + o] = q[i];
+                for (int i = 0; i < 3; ++i) sp[i * split + o] = q[i];
+            } else {
+                oz_slices<OZ_SLICES>(x.x, x.y, sh, q);
+#pragma unroll
+                for (int i = 0; i < OZ_SLICES; ++i) sp[i * split + o] = q[i];
+            }
             if (threadIdx.x == 0) sc[row] = ldexpf(1.f, -sh);
         };
         int par = 0;
@@ -261,68 +266,6 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
             for (int q = 0; q <= l; ++q) {
                 const int j = A.half_of[b2 * (WPCCC_LMAX + 1) + q];
                 aP[(size_t)j * A.G + g] = df_mul(fv, df_split(thv[1][l * (l + 1) / 2 + q]));
-            }
-        }
-    } else if (A.tc) {
-        // tensor-core layout: A_T and A_T V_T per target state, rows grouped by q', in fixed point per
-        // 32-node chunk (one warp): x = s (k0 + k1 2^-8 + k2 2^-16) with s a power of two from the
-        // chunk's largest |x| and k0..k2 integers in [-128, 128], stored as bf16 k0, k1, k2 2^-8 (all
-        // exact), and s in the scale table; A_P per half column in FP32
-        // the node weight (R^3/8) w (eta^2 - tau^2) = (R/2) w r_T r_P carries a factor r_T that cancels the
-        // 1/r_T of the transfer potential: it goes with the table rows (A_T r_T and A_T r_T V_T, both
-        // bounded), and the weights of this layout are W_K / r_T
-        const double rTV = A.mp_c == 0.0 ? -A.Z_T : -A.Z_T + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT);
-        __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(base);
-        float* sc = reinterpret_cast<float*>(base) + A.tc_sc_off + (size_t)(g >> 5) * A.tc_rows;
-        const size_t split = (size_t)A.tc_rows * A.G;
-        auto put3 = [&](size_t row, double v64) {
-            const float x = (float)v64;
-            float mx = fabsf(x);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            int E = 0;
-            if (mx > 0.f) frexpf(mx, &E);           // mx = f 2^E, f in [0.5, 1)
-            const int sh = mx > 0.f ? 7 - E : 0;    // |x| 2^sh < 128
-            const float xs = ldexpf(x, sh);
-            const float k0 = rintf(xs);
-            const float r1 = (xs - k0) * 256.f;
-            const float k1 = rintf(r1);
-            const float k2 = rintf((r1 - k1) * 256.f);
-            const size_t o = row * A.G + g;
-            sp[o] = __float2bfloat16_rn(k0);
-            sp[split + o] = __float2bfloat16_rn(k1);
-            sp[2 * split + o] = __float2bfloat16_rn(k2 * (1.f / 256.f));
-            if ((threadIdx.x & 31) == 0) sc[row] = ldexpf(1.f, -sh);
-        };
-        for (int a = 0; a < A.nradT; ++a) {
-            double val = 0.0;
-            if (inT) {
-                const double* fa = A.fT + (size_t)a * A.Nr + sT;
-                val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
-            }
-            const int l = A.radT_l[a];
-            for (int m = -l; m <= l; ++m) {
-                const int i = A.stT_index[a * (2 * WPCCC_LMAX + 1) + m + WPCCC_LMAX];
-                const int am = m < 0 ? -m : m;
-                const double sg = (m < 0 && (am & 1)) ? -1.0 : 1.0;
-                const double v = val * thv[0][l * (l + 1) / 2 + am] * sg;
-                const int row = A.tc_row[i];       // the A_T row; the A_T V_T row follows the group's A_T rows
-                const int gsz = A.tc_row[A.N_T + i];
-                put3((size_t)row, v * rT);
-                put3((size_t)(row + gsz), v * rTV);
-            }
-        }
-        float* aP = reinterpret_cast<float*>(base) + A.tc_ap_off;
-        for (int b2 = 0; b2 < A.nradP; ++b2) {
-            double val = 0.0;
-            if (inP) {
-                const double* fa = A.fP + (size_t)b2 * A.Nr + sP;
-                val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
-            }
-            const int l = A.radP_l[b2];
-            for (int q = 0; q <= l; ++q) {
-                const int j = A.half_of[b2 * (WPCCC_LMAX + 1) + q];
-                aP[(size_t)j * A.G + g] = (float)(val * thv[1][l * (l + 1) / 2 + q]);
             }
         }
     } else {
@@ -379,15 +322,12 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         a.y = (T)w0.y;
         bq.x = (T)(w0.x * uQ);
         bq.y = (T)(w0.y * uQ);
-        if (sizeof(T) == 4 && A.tc == 2) {
-            // FP64-accurate tensor-core layout: W_K / r_T as double-floats, [d][re, im][G]
+        if (sizeof(T) == 4 && A.tc) {
+            // tensor-core layout: W_K / r_T as double-floats, [d][re, im][G] (r_T and the transfer
+            // potential sit in the slice planes)
             float2* w6 = reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.t6_w_off);
             w6[((size_t)d * 2) * A.G + g] = df_split(w0.x / rT);
             w6[((size_t)d * 2 + 1) * A.G + g] = df_split(w0.y / rT);
-        } else if (sizeof(T) == 4 && A.tc) {
-            // tensor-core layout: W_K / r_T only (r_T and the transfer potential sit in the split tables)
-            reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.tc_w_off)[o] =
-                make_float2((float)(w0.x / rT), (float)(w0.y / rT));
         } else {
             W[o] = a;
             W[stride + o] = bq;
@@ -1161,17 +1101,8 @@ ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
         nf += (size_t)NX * (B->dmax + 1) * B->G * 2;
         L.node_doubles = std::max(nd, (nf + 1) / 2);
         if (B->tc_layout) {
-            // bf16 split tables, then A_P (floats) and W_K (complex floats), each 16-byte aligned
             L.tc_rows = 2 * B->N_T;
-            size_t nt = ((size_t)3 * L.tc_rows * B->G + 7) / 8 * 4;   // floats, multiple of 4
-            L.tc_ap_off = nt;
-            nt += ((size_t)B->n_half * B->G + 3) / 4 * 4;
-            L.tc_w_off = nt;
-            nt += (size_t)(B->dmax + 1) * B->G * 2;
-            L.tc_sc_off = nt;
-            nt += ((size_t)L.tc_rows * ((B->G + 31) / 32) + 3) / 4 * 4;
-            L.node_doubles = std::max(L.node_doubles, (nt + 1) / 2);
-            // FP64-accurate layout (precision modes 4, 5): seven bf16 slice planes [7][tc_rows][G], the
+            // tensor-core layout (precision modes 3-5): up to seven bf16 slice planes [7][tc_rows][G], the
             // scales per 128-node window, A_P [n_half][G] and W_K / r_T [d][re, im][G] as double-floats
             size_t n6 = ((size_t)OZ_SLICES * L.tc_rows * B->G + 7) / 8 * 4;
             L.t6_sc_off = n6;
@@ -1287,19 +1218,14 @@ static wpccc_status launch_tables(wpccc_basis_s* B, const EvalDesc* evals, int n
     na.half_of = B->half_of;
     na.radT_l = B->T.rad_l;
     na.radP_l = B->P.rad_l;
-    na.tc = precision == 3 ? 1 : precision == 4 ? 2 : 0;
+    na.tc = precision == 3 || precision == 4;
+    na.tc_slices = precision == 3 ? 3 : OZ_SLICES;
     na.tc_row = B->tc_row;
     na.tc_rows = L.tc_rows;
-    na.tc_ap_off = L.tc_ap_off;
-    na.tc_w_off = L.tc_w_off;
-    na.tc_sc_off = L.tc_sc_off;
     na.t6_ap_off = L.t6_ap_off;
     na.t6_w_off = L.t6_w_off;
     na.t6_sc_off = L.t6_sc_off;
-    if (precision == 3 || precision == 4) {
-        if (!B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
-        na.w_off = L.tc_w_off;
-    }
+    if (na.tc && !B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
     cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
     if (precision == 0) k_node_tables<double><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
     else k_node_tables<float><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
@@ -1355,11 +1281,8 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
             WPCCC_CUDA(cudaFuncSetAttribute(k_mol_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)gsm));
             k_mol_gemm<double><<<dim3(n_row_tiles * ga.n_col_tiles, nev), 256, gsm, st>>>(ga);
-        } else if (precision == 3) {
-            wpccc_status ms = launch_mol_tc(B, nev, node, mol, B->tc_err, st);
-            if (ms != WPCCC_OK) return ms;
-        } else if (precision == 4) {
-            wpccc_status ms = launch_mol_tc64(B, nev, node, mol, B->tc_err, st);
+        } else if (precision == 3 || precision == 4) {
+            wpccc_status ms = launch_mol_tc64(B, nev, node, mol, B->tc_err, st, precision == 3 ? 3 : OZ_SLICES);
             if (ms != WPCCC_OK) return ms;
         } else {
             Gemm32Args g32;
@@ -1521,8 +1444,8 @@ extern "C" wpccc_status wpccc_matrix_elements_precision(wpccc_basis B, double b,
         return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: reduced precision needs two centres");
     if (precision_mode != 0 && B->mp_c != 0.0)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: model-potential targets need FP64");
-    if (precision_mode == 4 && B->G % 128 != 0)
-        return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: mode 4 needs a node count that is a multiple of 128");
+    if (precision_mode >= 3 && B->G % 128 != 0)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: modes 3 and 4 need a node count that is a multiple of 128");
     return matrix_elements_prec(B, b, v, nz, z, S, H, precision_mode, stream);
 }
 

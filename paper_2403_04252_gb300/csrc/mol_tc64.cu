@@ -1,4 +1,5 @@
-// Eq. 9 contraction on the 5th-generation tensor cores to FP64 accuracy (precision modes 4 and 5).
+// Eq. 9 contraction on the 5th-generation tensor cores: to FP64 accuracy with seven slices per operand
+// (precision modes 4 and 5), at FP32 level with three (precision mode 3).
 //
 // The two-centre integrals of one row tile (target states of one molecular-frame projection q') are
 //   X_K[i][c] = sum_g (A_T r_T)[i][g] Bw[c][g],   X_Q[i][c] = sum_g (A_T r_T V_T)[i][g] Bw[c][g],
@@ -9,7 +10,7 @@
 // into D[m][n].
 //
 // Precision (error-free slicing after Ozaki, Ogita, Oishi and Rump; see ozaki.cuh): per window of four
-// 32-node chunks (128 nodes) both operands are written in fixed point with seven bf16 slices,
+// 32-node chunks (128 nodes) both operands are written in fixed point with SL = 7 bf16 slices,
 // a_g = s_m sum_i alpha_i and b_g = s_n sum_j beta_j with alpha_i, beta_j integers times 2^(-8 i),
 // 2^(-8 j) and s_m, s_n powers of two per row and window.  The products with i + j = L form level L
 // (weight 2^(-8 L)); levels 0-3 go to four accumulators that hold their window sums exactly (integers
@@ -17,7 +18,9 @@
 // fifth, whose FP32 rounding over its 144 MMAs stays near 2^-48 of the window's largest term; levels
 // >= 7 are dropped (below 2^-53).  Per window the epilogue forms s_m s_n (L0 + L1 + L2 + L3 + T) with
 // the exact parts folded into double-float running sums (two TwoSums), so the result carries about
-// 2^-46 of the largest term.
+// 2^-46 of the largest term.  With SL = 3 (levels 0-2, six products, three exact accumulators) the
+// result carries about 2^-22 of the largest term, the FP32 level, without the truncation bias of the
+// tensor core's FP32 accumulation.
 //
 // Pipeline per CTA (416 threads): warps 0-11 generate the Bw tiles (64-byte swizzled K-major rows) and
 // drain the accumulators; warp 12 issues the TMA loads of the table tiles (cp.async.bulk.tensor, 64-byte
@@ -40,17 +43,21 @@ constexpr int T6_M = 128;                              // table rows per CTA (MM
 constexpr int T6_N = 48;                               // generated rows per CTA (MMA N)
 constexpr int T6_K = 32;                               // nodes per chunk: one 64-byte bf16 row
 constexpr int T6_WIN = 4;                              // chunks per scaling window (128 nodes)
-constexpr int T6_ACC = 5;                              // accumulators: levels 0, 1, 2, 3 and >= 4
+// accumulators: SL = 7: levels 0, 1, 2, 3 (exact) and >= 4; SL = 3: levels 0, 1, 2 (exact)
+template <int SL> struct Tc64Cfg {
+    static constexpr int ACC = SL == 7 ? 5 : SL;
+};
+constexpr int T6_ACC_MAX = 5;
 constexpr int T6_TSTAGES = 3;                          // table tiles in flight (TMA ring)
 constexpr int T6_GSTAGES = 2;                          // generated tiles (producer ring)
 constexpr int T6_SC_SLOTS = 2;                         // scale ring, one slot per window (see the drain)
 constexpr int T6_PE_WARPS = 12;                        // producer / epilogue warps
 constexpr int T6_THREADS = (T6_PE_WARPS + 1) * 32;
 constexpr int T6_TMEM_COLS = 512;                      // 2 buffers x 5 accumulators x 48 columns = 480
-constexpr int T6_BUF_COLS = T6_ACC * T6_N;
+constexpr int T6_BUF_COLS = T6_ACC_MAX * T6_N;          // column offset of the second buffer
 constexpr int T6_A_TILE = T6_M * 64;                   // bytes of one slice of the table tile
 constexpr int T6_B_TILE = T6_N * 64;                   // bytes of one slice of the generated tile
-constexpr int T6_TSTAGE_BYTES = OZ_SLICES * T6_A_TILE;          // 56 KB, a multiple of 1024
+constexpr int T6_TSTAGE_BYTES = OZ_SLICES * T6_A_TILE;          // 56 KB (room for seven slices), a multiple of 1024
 constexpr int T6_GSTAGE_BYTES = OZ_SLICES * T6_B_TILE;          // 21 KB, a multiple of 1024
 constexpr int T6_BOXES = T6_M / 32;                             // table box heights 32, 64, 96, 128 rows
 constexpr int T6_SC_FLOATS = T6_M + T6_N;              // per slot: table row scales, generated row scales
@@ -79,7 +86,9 @@ struct Tc64Args {
     int* err;
 };
 
+template <int SL>
 __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constant__ Tc64Maps maps, Tc64Args A) {
+    constexpr int T6_ACC = Tc64Cfg<SL>::ACC;
     extern __shared__ __align__(1024) unsigned char t6_smem_raw[];
     unsigned char* sm = t6_smem_raw + ((1024 - (smem_u32(t6_smem_raw) & 1023)) & 1023);
     unsigned char* gsm = sm + T6_TSTAGES * T6_TSTAGE_BYTES;                        // generated tiles
@@ -128,14 +137,14 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
         // ---- TMA and MMA issue (one thread)
         if (lane == 0) {
             const uint32_t idesc = bf16_idesc_mn(T6_M, T6_N);
-            const uint32_t tx = (uint32_t)(OZ_SLICES * box * 32 * 64);
+            const uint32_t tx = (uint32_t)(SL * box * 32 * 64);
             const CUtensorMap* tmap = &maps.m[box - 1];
             auto issue_tma = [&](int k) {
                 const int s = k % T6_TSTAGES;
                 unsigned char* st = sm + s * T6_TSTAGE_BYTES;
                 const uint32_t bar = tfull0 + 8 * s;
                 mbar_arrive_tx(bar, tx);
-                for (int sp = 0; sp < OZ_SLICES; ++sp)
+                for (int sp = 0; sp < SL; ++sp)
                     tma_load_3d(smem_u32(st + sp * T6_A_TILE), tmap, k * T6_K, sp * A.tc_rows + row0, e, bar);
             };
             int issued = 0;
@@ -156,14 +165,14 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
                 const uint64_t da = sw64_desc(a0), db = sw64_desc(b0);
                 const uint32_t fresh = k % T6_WIN == 0 ? 0u : 1u;
 #pragma unroll
-                for (int L = OZ_SLICES - 1; L >= 0; --L) {
+                for (int L = SL - 1; L >= 0; --L) {
                     const int lv = L < T6_ACC - 1 ? L : T6_ACC - 1;
                     const uint32_t d = dbase + (uint32_t)(lv * T6_N);
 #pragma unroll
                     for (int i = 0; i <= L; ++i) {
 #pragma unroll
                         for (int kk = 0; kk < T6_K / 16; ++kk) {
-                            const bool first = (L == OZ_SLICES - 1 || L < T6_ACC - 1) && i == 0 && kk == 0;
+                            const bool first = (L == SL - 1 || L < T6_ACC - 1) && i == 0 && kk == 0;
                             tc_mma(d, da + (uint64_t)((i * T6_A_TILE + kk * 32) >> 4),
                                    db + (uint64_t)(((L - i) * T6_B_TILE + kk * 32) >> 4), idesc, first ? fresh : 1u);
                         }
@@ -239,7 +248,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
                         const float l1h = rintf(v[1][u]);
                         const float xa = __fadd_rn(v[0][u], l1h);
                         const float xb = __fadd_rn(__fsub_rn(v[1][u], l1h), v[2][u]);
-                        const float xc = __fadd_rn(v[3][u], v[4][u]);
+                        const float xc = T6_ACC > 3 ? __fadd_rn(v[T6_ACC > 3 ? 3 : 0][u], v[T6_ACC - 1][u]) : 0.f;
                         float r1, r2;
                         hi[k] = two_sum(hi[k], xa * sc, r1);
                         hi[k] = two_sum(hi[k], xb * sc, r2);
@@ -284,14 +293,14 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
                     ok = ok && mbar_wait(gempty0 + 8 * s, ((k - T6_GSTAGES) / T6_GSTAGES) & 1, abort_flag, A.err, 15);
                 if (!ok) break;
                 unsigned char* bt = gsm + s * T6_GSTAGE_BYTES;
-                __nv_bfloat16 q[4][OZ_SLICES];
+                __nv_bfloat16 q[4][SL];
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) oz_slices(xw[4 * cc + jj].x, xw[4 * cc + jj].y, sh, q[jj]);
+                for (int jj = 0; jj < 4; ++jj) oz_slices<SL>(xw[4 * cc + jj].x, xw[4 * cc + jj].y, sh, q[jj]);
                 // row n of each slice tile: 64 bytes, 16-byte chunk qq at (qq ^ ((n >> 1) & 3)); this
                 // thread holds the 8-byte half (part & 1) of chunk part >> 1
                 const int off = n * 64 + (((part >> 1) ^ ((n >> 1) & 3)) << 4) + (part & 1) * 8;
 #pragma unroll
-                for (int sp = 0; sp < OZ_SLICES; ++sp)
+                for (int sp = 0; sp < SL; ++sp)
                     *reinterpret_cast<uint2*>(bt + sp * T6_B_TILE + off) =
                         make_uint2(bf16x2(q[0][sp], q[1][sp]), bf16x2(q[2][sp], q[3][sp]));
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -322,14 +331,16 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
     }
 }
 
-wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st) {
+wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st,
+                             int slices) {
+    if (slices != 3 && slices != OZ_SLICES) return fail(WPCCC_EINVAL, "tensor-core contraction: 3 or 7 slices");
     if (!B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
     if (B->G % (T6_K * T6_WIN) != 0) return fail(WPCCC_EUNSUPPORTED, "the node count must be a multiple of 128");
     const ElemScratch L = elem_scratch_layout(B);
     const size_t node_bytes = L.node_doubles * sizeof(double);
     // seven slice planes as one 3-D bf16 tensor: x = node (G), y = slice plane row (7 x tc_rows), z = evaluation
     Tc64Maps maps;
-    const cuuint64_t dims[3] = {(cuuint64_t)B->G, (cuuint64_t)OZ_SLICES * L.tc_rows, (cuuint64_t)nev};
+    const cuuint64_t dims[3] = {(cuuint64_t)B->G, (cuuint64_t)slices * L.tc_rows, (cuuint64_t)nev};
     const cuuint64_t strides[2] = {(cuuint64_t)B->G * 2, (cuuint64_t)node_bytes};
     const cuuint32_t estr[3] = {1, 1, 1};
     for (int h = 0; h < T6_BOXES; ++h) {
@@ -360,8 +371,14 @@ wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double
     a.err = err;
     const size_t smem = 1024 + (size_t)T6_TSTAGES * T6_TSTAGE_BYTES + (size_t)T6_GSTAGES * T6_GSTAGE_BYTES +
                         sizeof(float) * T6_SC_SLOTS * T6_SC_FLOATS + 8 * (2 * T6_TSTAGES + 2 * T6_GSTAGES + 4);
-    WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_mol_tc64<<<dim3(a.n_ntiles * B->n_qgroups, nev), T6_THREADS, smem, st>>>(maps, a);
+    const dim3 grid(a.n_ntiles * B->n_qgroups, nev);
+    if (slices == OZ_SLICES) {
+        WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<OZ_SLICES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mol_tc64<OZ_SLICES><<<grid, T6_THREADS, smem, st>>>(maps, a);
+    } else {
+        WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mol_tc64<3><<<grid, T6_THREADS, smem, st>>>(maps, a);
+    }
     WPCCC_CHECK_LAUNCH("k_mol_tc64");
     return WPCCC_OK;
 }

@@ -17,7 +17,7 @@
 
 namespace wpccc {
 
-constexpr int OZ_SLICES = 7;
+constexpr int OZ_SLICES = 7;   // slices of the FP64-accurate form (the most any layout holds)
 
 // hi + lo = x to about 2^-48 relative (hi = x rounded to FP32, lo = the rest rounded to FP32).
 static __device__ __forceinline__ float2 df_split(double x) {
@@ -53,16 +53,18 @@ static __device__ __forceinline__ int oz_shift(float mx) {
     return mx > 0.f ? 7 - E : 0;
 }
 
-// The OZ_SLICES bf16 slices k_i 2^(-8 i) of the double-float x = (h, l) scaled by 2^sh (|x| 2^sh < 128).
+// The first NS bf16 slices k_i 2^(-8 i) of the double-float x = (h, l) scaled by 2^sh (|x| 2^sh < 128).
 // The pair (p, e) always holds the remaining value exactly: the scalings by 256 are exact, and so is
 // p - k (k is an integer within one of p + e; while p has fraction bits it is below 2^8 in magnitude,
 // afterwards p and k are integers below 2^24).  Only p + e may round, which can move k by one where
 // the remainder is near a half unit; the next remainder then stays within (0.5 + 2^-17) 256 of zero,
 // so |k_i| <= 129.
-static __device__ __forceinline__ void oz_slices(float h, float l, int sh, __nv_bfloat16 out[OZ_SLICES]) {
+// NS slices: 7 for FP64 accuracy, 3 for FP32 level (about 23 bits below the window's largest value).
+template <int NS>
+static __device__ __forceinline__ void oz_slices(float h, float l, int sh, __nv_bfloat16 out[NS]) {
     float p = ldexpf(h, sh), e = ldexpf(l, sh), w = 1.f;
 #pragma unroll
-    for (int i = 0; i < OZ_SLICES; ++i) {
+    for (int i = 0; i < NS; ++i) {
         const float k = rintf(__fadd_rn(p, e));
         p = __fsub_rn(p, k);
         out[i] = __float2bfloat16_rn(k * w);

@@ -256,8 +256,8 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     if ((precision_mode == 1 || precision_mode >= 3) && B->n_centres == 2 && B->mp_c != 0.0)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: model-potential targets need FP64 elements (mode 0 or 2)");
     if (precision_mode >= 3 && B->n_centres == 2) {
-        if (precision_mode >= 4 && B->G % 128 != 0)
-            return fail(WPCCC_EUNSUPPORTED, "precision modes 4 and 5 need a node count that is a multiple of 128");
+        if (B->G % 128 != 0)
+            return fail(WPCCC_EUNSUPPORTED, "precision modes 3-5 need a node count that is a multiple of 128");
         wpccc_status ts = tc_prepare(B);
         if (ts != WPCCC_OK) return ts;
     }

@@ -156,14 +156,9 @@ struct ElemScratch {
     size_t et_doubles;     // small per-position tables (Wigner d, Legendre, stencil, F at R, phases), even
     size_t ph_off;         // offset of the per-state energy phases exp(i eps_i z / v) (complex, N of them)
     int dtot, npb;         // sizes of their Wigner-d and Legendre parts
-    // tensor-core layout of the node tables (precision mode 3), when the basis enables it:
-    //   3 bf16 split tables [3][tc_rows][G] (rows: per target q' group, its A_T rows then A_T V_T rows),
-    //   then A_P per half column (floats, at tc_ap_off), then the overlap weights W_K (complex floats, at tc_w_off)
-    int tc_rows;
-    size_t tc_ap_off, tc_w_off;
-    size_t tc_sc_off;      // per (32-node chunk, split-table row) power-of-two scale (floats)
-    // FP64-accurate tensor-core layout (precision modes 4, 5): seven bf16 slice planes [7][tc_rows][G],
-    // then (offsets in floats) the chunk scales, A_P and W_K / r_T as double-floats
+    int tc_rows;           // rows of the tensor-core slice planes (2 N_T), when the basis enables the layout
+    // tensor-core layout (precision modes 3-5): up to seven bf16 slice planes [7][tc_rows][G], then
+    // (offsets in floats) the window scales, A_P and W_K / r_T as double-floats
     size_t t6_sc_off, t6_ap_off, t6_w_off;
 };
 ElemScratch elem_scratch_layout(const wpccc_basis_s* B);
@@ -191,10 +186,11 @@ enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3
 
 // Tensor-core form of the Eq. 9 contraction (precision mode 3): from the node tables of the tensor-core
 // layout into the molecular-frame blocks, for `nev` evaluations.
-wpccc_status launch_mol_tc(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st);
 wpccc_status tc_prepare(wpccc_basis_s* B);
-// The FP64-accurate tensor-core contraction (precision modes 4, 5) over the seven-slice node tables.
-wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st);
+// The tensor-core contraction over the slice planes: slices = 7 to FP64 accuracy (precision modes 4, 5),
+// 3 at FP32 level (precision mode 3).
+wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st,
+                             int slices);
 
 // Queue the batched FP32 factorisation P S = L U of FP64 matrices (mixed-precision form).
 wpccc_status launch_factor_f32(int N, int batch, const double2* S, float2* LU, int* ipiv, int* info,

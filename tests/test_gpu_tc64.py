@@ -167,11 +167,12 @@ def test_fp64_tc_rejections():
         g.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])], precision_mode=6)
     assert e.value.status == w.EUNSUPPORTED
     g.close()
-    # 16 x 14 = 224 nodes: seven 32-node chunks (mode 3 takes them) but not whole 128-node windows
+    # 16 x 14 = 224 nodes: seven 32-node chunks but not whole 128-node windows (all tensor-core forms)
     b224 = wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=16, Gtau=14)
     g2 = w.Basis(b224)
-    S3, _ = g2.matrix_elements_precision(0.9, 1.3, np.array([0.0]), 3)
-    for call in (lambda: g2.matrix_elements_precision(0.9, 1.3, np.array([0.0]), 4),
+    for call in (lambda: g2.matrix_elements_precision(0.9, 1.3, np.array([0.0]), 3),
+                 lambda: g2.matrix_elements_precision(0.9, 1.3, np.array([0.0]), 4),
+                 lambda: g2.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])], precision_mode=3),
                  lambda: g2.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])], precision_mode=5)):
         with pytest.raises(w.WpcccError) as e:
             call()
