@@ -786,38 +786,47 @@ def main() -> None:
         rk4_flops = 4.0 * (8.0 * N * N + 16.0 * NT * NP_ + 8.0 * NP_ * NP_)
     else:
         rk4_flops = {"matrix": 32.0, "stage": 64.0}[args.solve_mode] * N * N
-    # the FP64-accurate tensor-core contraction issues 28 bf16 slice products per algorithmic product
-    mol_work = 28.0 if mode in (4, 5) else 1.0
+    # the tensor-core contractions issue 6 (three slices) or 28 (seven slices) bf16 slice products per
+    # algorithmic product
+    mol_work = {3: 6.0, 4: 28.0, 5: 28.0}.get(mode, 1.0)
     mol_peak = {1: FP32_PEAK_TFLOPS, 3: BF16_MEASURED_TFLOPS, 4: BF16_MEASURED_TFLOPS,
                 5: BF16_MEASURED_TFLOPS}.get(mode, FP64_PEAK_TFLOPS)
     solve_name = (("k_schur_factor<float>" if schur else "k_lu_factor_f32") if mixed_form
                   else ("k_schur_factor<double>" if schur else "k_lu_solve"))
-    cand = {"mol_gemm": (mol_work * flops_mol * evals, mol_peak,
-                         {1: "k_mol_gemm_f32q", 3: "k_mol_tc", 4: "k_mol_tc64", 5: "k_mol_tc64"}.get(
-                             mode, "k_mol_gemm<double>")),
+    mol_name = {1: "k_mol_gemm_f32q", 3: "k_mol_tc64<3>", 4: "k_mol_tc64<7>", 5: "k_mol_tc64<7>"}.get(
+        mode, "k_mol_gemm<double>")
+    cand = {"mol_gemm": (mol_work * flops_mol * evals, mol_peak, mol_name),
             "solve": (flops_solve * evals, FP32_PEAK_TFLOPS if mixed_form else FP64_PEAK_TFLOPS, solve_name),
             "rk4": (rk4_flops * n_paths * STEP * args.steps, FP64_PEAK_TFLOPS, "k_rk4")}
-    dom = max(cand, key=lambda k: prof[k][0] if k in prof else 0.0)
-    dom_ms, dom_launches = prof[dom]
-    dom_flops, dom_peak, dom_name = cand[dom]
-    achieved = dom_flops / (dom_ms / 1e3) / 1e12
-    total_flops = (flops_mol + flops_solve) * evals + rk4_flops * n_paths * STEP * args.steps
-    launches = int(sum(n for _, n in prof.values()))
-    roofline = {"bound": "tensor" if dom_peak == BF16_MEASURED_TFLOPS else "alu", "kernel": dom_name,
-                "achieved": achieved, "peak": dom_peak, "unit": "TFLOP/s",
-                "frac": achieved / dom_peak, "traffic": None,
+
+    def roof(key: str) -> dict:
+        k_ms, k_launches = prof[key]
+        k_flops, k_peak, k_name = cand[key]
+        ach = k_flops / (k_ms / 1e3) / 1e12
+        # DRAM bytes per position of the tensor-core contractions on this workload (ncu,
+        # dram__bytes_read.sum + dram__bytes_write.sum over 33 positions), scaled to the launch's positions
+        per_pos = {"k_mol_tc64<3>": 8.35e6, "k_mol_tc64<7>": 15.94e6}.get(k_name) if args.workload == WORKLOAD else None
+        return {"bound": "tensor" if k_peak == BF16_MEASURED_TFLOPS else "alu", "kernel": k_name,
+                "achieved": ach, "peak": k_peak, "unit": "TFLOP/s", "frac": ach / k_peak,
+                "traffic": per_pos * evals / max(k_launches, 1) if per_pos else None,
                 "peak_source": ("measured bf16 dense tensor peak (MEASURED_PEAKS.json, burst) against the "
-                                "contraction's algorithmic flops"
-                                + (" times its 28 slice products (FP64-accurate emulation)" if mode in (4, 5)
-                                   else " (the sliced operands take 12 bf16 products)"))
-                if dom_peak == BF16_MEASURED_TFLOPS else
+                                f"contraction's algorithmic flops times its {int(mol_work)} slice products")
+                if k_peak == BF16_MEASURED_TFLOPS else
                 ("FP32 pipe from unit counts and clocks (152 SMs x 128 FFMA/clk x 2.07 GHz); "
                  f"measured FFMA microbenchmark {FP32_FFMA_MEASURED_TFLOPS} TFLOP/s")
-                if dom_peak == FP32_PEAK_TFLOPS else
+                if k_peak == FP32_PEAK_TFLOPS else
                 ("FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
                  f"measured DFMA microbenchmark {FP64_DFMA_MEASURED_TFLOPS} TFLOP/s"),
-                "launch_ms_avg": dom_ms / max(dom_launches, 1),
-                "flop_per_launch": dom_flops / max(dom_launches, 1)}
+                "launch_ms_avg": k_ms / max(k_launches, 1),
+                "flop_per_launch": k_flops / max(k_launches, 1)}
+
+    # the dominant kernel is taken on the assembly stream, which bounds the step (the RK4 sweep overlaps
+    # it on its own stream and is reported beside it)
+    dom = max(("mol_gemm", "solve"), key=lambda k: prof[k][0] if k in prof else 0.0)
+    roofline = roof(dom)
+    roofline["overlapped_rk4"] = roof("rk4")
+    total_flops = (flops_mol + flops_solve) * evals + rk4_flops * n_paths * STEP * args.steps
+    launches = int(sum(n for _, n in prof.values()))
     form_desc = {0: "plain FP64, all paths batched; S^-1 applied "
                     + {"stage": "per RK4 stage from LU factors",
                        "schur": "per RK4 stage through the Cholesky factor of the Schur complement I - K^+ K",
