@@ -425,6 +425,109 @@ def oracle_gradient_rate(basis, paths, gw, n_steps: int, path_index: int = 8) ->
                       f"two observables w.r.t. 3 parameters, {dt:.1f} s; numpy/LAPACK on the host cores"}
 
 
+def run_one_centre_large(args) -> None:
+    """One-centre p + H at l <= 10 (N = 4257): the plain FP64 form with the RK4 vectors in global memory
+    (the shared-memory sweep holds N <= ~2840).  One bench step advances every path by a few RK4 steps
+    around closest approach; every position's D_T is assembled (N^2 complex, 290 MB)."""
+    import torch
+    import wpccc_inputs as wi
+    import paper_2403_04252_gb300 as w
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    basis, paths = wi.config_inputs("p_H_1c_n10l10")
+    g = w.Basis(basis, device=local)
+    g.set_workspace_limit(int((args.workspace_gb or 64.0) * (1 << 30)))
+    N = g.N
+    n_paths = paths.n_paths if args.paths <= 0 else min(args.paths, paths.n_paths)
+    b = paths.b[:n_paths]
+    v = float(paths.v[0])
+    zg = paths.z[0]
+    STEP = args.rk4_per_step if args.rk4_per_step != STEP_RK4 else 4
+    first = max(0, (zg.size - 1) // 2 - (args.warmup + args.steps) * STEP // 2)
+
+    def segment(k):
+        a = first + k * STEP
+        return zg[a:a + STEP + 1]
+    c = torch.zeros((n_paths, N), dtype=torch.complex128, device=dev)
+    c[:, 0] = 1.0
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        g.propagate(b, v, segment(k), c=c)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    g.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        g.propagate(b, v, segment(args.warmup + k), c=c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = g.profile_read()
+    g.profile_enable(False)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    P = w.probabilities(c).cpu().numpy()
+    norm_dev = float(np.abs(P.sum(axis=1) - 1.0).max())
+    value = world * n_paths * STEP * args.steps / (ms / 1e3)
+    # end to end: amplitudes from pinned host memory, probabilities back, every step
+    c_host = torch.zeros((n_paths, N), dtype=torch.complex128).pin_memory()
+    c_host[:, 0] = 1.0
+    P_host = torch.empty((n_paths, N), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        c.copy_(c_host, non_blocking=True)
+        g.propagate(b, v, segment(args.warmup + k), c=c)
+        P_host.copy_(w.probabilities(c), non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    # roofline: the RK4 sweep, four FP64 matrix-vector products of 8 N^2 flops per path-step, against
+    # the element assembly (the direct blocks of Eq. 6)
+    rk_ms, rk_n = prof["rk4"]
+    rk_flops = 4.0 * 8.0 * N * N * n_paths * STEP * args.steps
+    ach = rk_flops / (rk_ms / 1e3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "one-centre p+H (Z=1): hydrogenic n<=10 + 32 Coulomb wave-packet bins per l<=10 "
+                                   f"(k<=2), all m, N={N}; v=2 (100 keV); {n_paths} b in [0.5, 8]; z in [-40, 40], "
+                                   "h=0.1",
+                       "form": "plain FP64, M = -(i/v) D_T; RK4 vectors in global memory (one launch per RK4 "
+                               "stage, GPU-wide matrix-vector products)",
+                       "bench_step": f"{STEP} RK4 steps of each path, consecutive segments centred on z = 0",
+                       "l2": f"inputs larger than L2: D_T of one position is {16 * N * N / 1e6:.0f} MB"},
+            "norm_deviation": norm_dev,
+            "roofline": {"bound": "alu", "kernel": "k_rk4_wide", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                         "launch_ms_avg": rk_ms / max(rk_n, 1)},
+            "kernel_ms": {k: v_[0] for k, v_ in prof.items()},
+            "e2e": {"value": world * n_paths * STEP * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": c_host.numel() * 16, "d2h_bytes_per_step": P_host.numel() * 8},
+            "gpu_launches": int(sum(n for _, n in prof.values())), "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_grad(args) -> None:
     """Differentiation form: wpccc_propagate_adjoint (forward sweep with checkpoints, reverse sweep
     with recomputation, element adjoint) on consecutive segments of the 32 paths, timed against the
@@ -597,7 +700,7 @@ def main() -> None:
                          "stage for the others, whose quadrature-assembled overlap matrices at small b are not "
                          "positive definite (the Cholesky factor of I - K^+ K meets a non-positive pivot, ESINGULAR)")
     ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v",
-                                                             "pLi_2c_grad"],
+                                                             "pLi_2c_grad", "p_H_1c_n10l10"],
                     help="p_H_2c_n4l3: two-centre p + H (N = 380, 32 paths); C6_H_2c_n6l5: bare C6+ on H "
                          "(N = 1622, 16 paths); p_H_2c_batch6v: p + H at six speeds, N = 316..572, 64 paths "
                          "each, all in one graph launch (batched form); pLi_2c_grad: p + Li-like model-potential "
@@ -624,6 +727,9 @@ def main() -> None:
         return
     if args.workload == "pLi_2c_grad":
         run_grad(args)
+        return
+    if args.workload == "p_H_1c_n10l10":
+        run_one_centre_large(args)
         return
 
     import torch

@@ -60,9 +60,12 @@ typedef enum {
     WPCCC_EUNSUPPORTED = 6 /* a mode this build does not provide */
 } wpccc_status;
 
-/* Largest orbital angular momentum a basis may hold, and largest system size. */
+/* Largest orbital angular momentum a basis may hold, and largest system size.  Beyond about 2840 states
+ * the RK4 sweep of the two-centre forms no longer fits one block's shared memory (EINVAL from
+ * wpccc_propagate); one-centre bases then propagate with the vectors in global memory (see
+ * wpccc_basis_set_rk4_layout). */
 #define WPCCC_LMAX 10
-#define WPCCC_NMAX 2900
+#define WPCCC_NMAX 8192
 
 /* Opaque handle: the basis and every z-independent table, resident on one device. */
 typedef struct wpccc_basis_s* wpccc_basis;
@@ -322,6 +325,25 @@ WPCCC_API wpccc_status wpccc_basis_set_solve_mode(wpccc_basis basis, int mode);
  */
 #define WPCCC_MAX_REFINE 8
 WPCCC_API wpccc_status wpccc_basis_set_refine_iters(wpccc_basis basis, int iters);
+
+/*
+ * Where the RK4 sweep of Algorithm 1 keeps its vectors.
+ *   WPCCC_RK4_SHARED  one thread block per path, c and the stage vectors in its shared memory, all the
+ *                     chunk's steps in one launch (fastest; N up to about 2840 in the one-centre form,
+ *                     fewer in the two-centre forms);
+ *   WPCCC_RK4_GLOBAL  one-centre form only: one launch per RK4 stage for all paths of a chunk, the
+ *                     matrix-vector product M(z) y spread over the GPU (a thread per row, the columns of
+ *                     y staged in shared memory), the vectors in global memory; every chunk evaluates its
+ *                     first node again instead of carrying the N x N matrix over (the paper's one-centre
+ *                     runs at large l_max, N in the thousands);
+ *   WPCCC_RK4_AUTO    (default) shared when it fits, else global.
+ * Both give the same amplitudes up to rounding.  Errors: EINVAL (null basis, unknown layout).
+ * EUNSUPPORTED from wpccc_propagate for WPCCC_RK4_GLOBAL with a two-centre basis.
+ */
+#define WPCCC_RK4_AUTO 0
+#define WPCCC_RK4_SHARED 1
+#define WPCCC_RK4_GLOBAL 2
+WPCCC_API wpccc_status wpccc_basis_set_rk4_layout(wpccc_basis basis, int layout);
 
 /*
  * Upper bound on the scratch memory wpccc_propagate may hold (default 8 GiB).

@@ -30,7 +30,7 @@ _lib = C.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ESINGULAR, ENONFINITE, ECUDA, EUNSUPPORTED = range(7)
 _NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENONFINITE", 5: "ECUDA", 6: "EUNSUPPORTED"}
 LMAX = 10
-NMAX = 2900
+NMAX = 8192
 
 _pd = C.POINTER(C.c_double)
 _pi = C.POINTER(C.c_int)
@@ -68,6 +68,7 @@ _lib.wpccc_basis_set_workspace_limit.argtypes = [C.c_void_p, C.c_size_t]
 _lib.wpccc_profile_enable.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_basis_set_solve_mode.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_basis_set_refine_iters.argtypes = [C.c_void_p, C.c_int]
+_lib.wpccc_basis_set_rk4_layout.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_profile_read.argtypes = [C.c_void_p, _pd, C.POINTER(C.c_longlong)]
 _lib.wpccc_batch_create.argtypes = [C.c_int, C.POINTER(C.c_void_p), C.POINTER(_PathsDesc), C.c_int,
                                     C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
@@ -86,7 +87,7 @@ for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpc
            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode",
            "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
            "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
-           "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters"):
+           "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters", "wpccc_basis_set_rk4_layout"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
@@ -94,8 +95,9 @@ EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wp
             "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error",
             "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
             "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
-            "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters")
+            "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters", "wpccc_basis_set_rk4_layout")
 MAX_PARAMS = 4
+RK4_AUTO, RK4_SHARED, RK4_GLOBAL = 0, 1, 2
 MAX_REFINE = 8
 NOALLOC_SCRATCH_BYTES = 64 << 20
 SOLVE_STAGE, SOLVE_MATRIX, SOLVE_SCHUR = 0, 1, 2
@@ -212,6 +214,11 @@ class Basis:
         """SOLVE_STAGE (LU of S once per position, solve per RK4 stage), SOLVE_SCHUR (Cholesky of the Schur
         complement I - K^+ K once per position, solve per stage) or SOLVE_MATRIX (X = S^-1 H)."""
         _check(_lib.wpccc_basis_set_solve_mode(self._h, int(mode)), "wpccc_basis_set_solve_mode")
+
+    def set_rk4_layout(self, layout: int) -> None:
+        """RK4_AUTO (default), RK4_SHARED (one block per path, vectors in shared memory) or RK4_GLOBAL
+        (one-centre form: a launch per RK4 stage, vectors in global memory, any N)."""
+        _check(_lib.wpccc_basis_set_rk4_layout(self._h, int(layout)), "wpccc_basis_set_rk4_layout")
 
     def set_refine_iters(self, iters: int) -> None:
         """FP64 refinement sweeps per RK4 stage of the refined precision modes (1, 2, 3, 5); default 2."""

@@ -601,6 +601,8 @@ struct DirAdjArgs {
     // per centre
     int Nc[2], n_rad[2], nlam[2], nt[2];
     const double* ang[2];
+    const int* st_lm[2];
+    int LM[2];
     const int* Foff[2];
     const int* st_rad[2];
     const int* st_m[2];
@@ -634,7 +636,7 @@ __global__ void __launch_bounds__(256) k_adj_direct(DirAdjArgs A) {
         const int ra = A.st_rad[cen][i], rb = A.st_rad[cen][j];
         const int mu = A.st_m[cen][i] - A.st_m[cen][j];
         const int amu = mu < 0 ? -mu : mu;
-        const double* ang = A.ang[cen] + (size_t)idx * nlam;
+        const double* ang = A.ang[cen] + ((size_t)A.st_lm[cen][i] * A.LM[cen] + A.st_lm[cen][j]) * nlam;
         const int* foff = A.Foff[cen] + ((size_t)ra * nrad + rb) * nlam;
         double D1 = 0.0, dD[ADJ_MAXTAN] = {};
         double sgn = 1.0;
@@ -1111,6 +1113,8 @@ static wpccc_status adjoint_group(wpccc_basis_s* B, const wpccc_paths* paths, in
                 da.nlam[k] = cs[k]->nlam;
                 da.nt[k] = ts[k]->n_tan;
                 da.ang[k] = cs[k]->ang;
+                da.st_lm[k] = cs[k]->st_lm;
+                da.LM[k] = cs[k]->LM;
                 da.Foff[k] = cs[k]->Foff;
                 da.st_rad[k] = cs[k]->st_rad;
                 da.st_m[k] = cs[k]->st_m;

@@ -173,13 +173,16 @@ __global__ void k_lagrange_den(int Nr, const double* __restrict__ r, double* __r
     }
 }
 
-// Eq. 6 angular factor per (a', a, lam), without sqrt((lam-mu)!/(lam+mu)!).
-__global__ void k_direct_angular(int Nc, int nlam, const int* __restrict__ st_l,
-                                 const int* __restrict__ st_m, double* __restrict__ ang) {
+// Eq. 6 angular factor per pair of angular parts ((l', m'), (l, m)) and lam, without
+// sqrt((lam-mu)!/(lam+mu)!); angular index l^2 + l + m.
+__global__ void k_direct_angular(int LM, int nlam, double* __restrict__ ang) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)Nc * Nc) return;
-    int i = (int)(idx / Nc), j = (int)(idx % Nc);
-    int lp = st_l[i], mp = st_m[i], l = st_l[j], m = st_m[j];
+    if (idx >= (long long)LM * LM) return;
+    const int a = (int)(idx / LM), b2 = (int)(idx % LM);
+    int lp = 0, l = 0;
+    while ((lp + 1) * (lp + 1) <= a) ++lp;
+    while ((l + 1) * (l + 1) <= b2) ++l;
+    const int mp = a - lp * lp - lp, m = b2 - l * l - l;
     int mu = mp - m;
     double pre = sqrt((2.0 * l + 1.0) / (2.0 * lp + 1.0));
     for (int lam = 0; lam < nlam; ++lam) {
@@ -207,7 +210,7 @@ static wpccc_status upload(T** dst, const T* src, size_t n, const char* what) {
 
 static void free_centre(CentreDev& c) {
     void* ptrs[] = {c.f, c.rad_l, c.st_rad, c.st_l, c.st_m, c.st_eps, c.st_index,
-                    c.F, c.Foff, c.fent_a, c.fent_b, c.fent_lam, c.ang};
+                    c.F, c.Foff, c.fent_a, c.fent_b, c.fent_lam, c.ang, c.st_lm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     c = CentreDev();
@@ -251,8 +254,12 @@ static wpccc_status build_centre(const wpccc_centre_desc& d, int Nr, const doubl
     c.lmax = 0;
     for (int l : c.h_rad_l) c.lmax = l > c.lmax ? l : c.lmax;
     c.nlam = 2 * c.lmax + 1;
-    std::vector<int> st_l(d.n_states);
-    for (int i = 0; i < d.n_states; ++i) st_l[i] = d.rad_l[d.st_rad[i]];
+    std::vector<int> st_l(d.n_states), st_lm(d.n_states);
+    for (int i = 0; i < d.n_states; ++i) {
+        st_l[i] = d.rad_l[d.st_rad[i]];
+        st_lm[i] = st_l[i] * st_l[i] + st_l[i] + d.st_m[i];
+    }
+    c.LM = (c.lmax + 1) * (c.lmax + 1);
     std::vector<int> st_index((size_t)d.n_rad * (2 * WPCCC_LMAX + 1), -1);
     for (int i = 0; i < d.n_states; ++i)
         st_index[(size_t)d.st_rad[i] * (2 * WPCCC_LMAX + 1) + d.st_m[i] + WPCCC_LMAX] = i;
@@ -260,6 +267,7 @@ static wpccc_status build_centre(const wpccc_centre_desc& d, int Nr, const doubl
     if ((st = upload(&c.rad_l, d.rad_l, d.n_rad, "upload rad_l")) != WPCCC_OK) return st;
     if ((st = upload(&c.st_rad, d.st_rad, d.n_states, "upload st_rad")) != WPCCC_OK) return st;
     if ((st = upload(&c.st_l, st_l.data(), d.n_states, "upload st_l")) != WPCCC_OK) return st;
+    if ((st = upload(&c.st_lm, st_lm.data(), d.n_states, "upload st_lm")) != WPCCC_OK) return st;
     if ((st = upload(&c.st_m, d.st_m, d.n_states, "upload st_m")) != WPCCC_OK) return st;
     if ((st = upload(&c.st_eps, d.st_eps, d.n_states, "upload st_eps")) != WPCCC_OK) return st;
     if ((st = upload(&c.st_index, st_index.data(), st_index.size(), "upload st_index")) != WPCCC_OK) return st;
@@ -286,9 +294,9 @@ static wpccc_status build_centre(const wpccc_centre_desc& d, int Nr, const doubl
     if ((st = upload<double>(&c.F, nullptr, (size_t)c.n_fent * Nr, "alloc F")) != WPCCC_OK) return st;
     k_ftable<<<c.n_fent, 256>>>(Nr, r_dev, w_dev, c.f, c.fent_a, c.fent_b, c.fent_lam, c.F);
     WPCCC_CHECK_LAUNCH("k_ftable");
-    size_t nang = (size_t)c.n_states * c.n_states;
+    size_t nang = (size_t)c.LM * c.LM;
     if ((st = upload<double>(&c.ang, nullptr, nang * c.nlam, "alloc ang")) != WPCCC_OK) return st;
-    k_direct_angular<<<(unsigned)((nang + 255) / 256), 256>>>(c.n_states, c.nlam, c.st_l, c.st_m, c.ang);
+    k_direct_angular<<<(unsigned)((nang + 255) / 256), 256>>>(c.LM, c.nlam, c.ang);
     WPCCC_CHECK_LAUNCH("k_direct_angular");
     return WPCCC_OK;
 }
@@ -467,6 +475,14 @@ extern "C" wpccc_status wpccc_basis_set_solve_mode(wpccc_basis B, int mode) {
     if (mode != WPCCC_SOLVE_STAGE && mode != WPCCC_SOLVE_MATRIX && mode != WPCCC_SOLVE_SCHUR)
         return fail(WPCCC_EINVAL, "wpccc_basis_set_solve_mode: unknown mode");
     B->solve_mode = mode;
+    return WPCCC_OK;
+}
+
+extern "C" wpccc_status wpccc_basis_set_rk4_layout(wpccc_basis B, int layout) {
+    if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_rk4_layout: null basis");
+    if (layout != WPCCC_RK4_AUTO && layout != WPCCC_RK4_SHARED && layout != WPCCC_RK4_GLOBAL)
+        return fail(WPCCC_EINVAL, "wpccc_basis_set_rk4_layout: unknown layout");
+    B->rk4_layout = layout;
     return WPCCC_OK;
 }
 

@@ -929,56 +929,68 @@ struct DirArgs {
     size_t et_doubles, ph_off;
     double Z_other, parity;       // parity = -1: the other nucleus sits at -R
     const double *r, *F, *ang, *eps;
-    const int *Foff, *st_rad, *st_m;
+    const int *Foff, *st_rad, *st_m, *st_lm;
+    int LM;
+    size_t cp_off;                // this centre's Eq. 6 coefficients within the per-position tables
     double2 *S, *H;
     size_t mat;
 };
 
+// Eq. 6 coefficients of one position and centre, per pair of angular parts and multipole:
+//   cp[(l'm', lm)][lam] = -Z_other parity^lam A(l'm', lm, lam) Pbar_lam^|mu|(cos theta) (-1)^mu [mu < 0, odd]
+//                         x (r_max / R)^(lam + 1) when R lies beyond the radial grid,
+// so that D[(a', m')][(a, m)] = sum_lam cp[..][lam] F_lam^{a'a}(R) takes one multiply-add per term.
+__global__ void k_direct_coef(DirArgs A0, DirArgs A1, const EvalDesc* __restrict__ ev) {
+    const DirArgs& A = blockIdx.z == 0 ? A0 : A1;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)A.LM * A.LM * A.nlam;
+    if (idx >= n) return;
+    const int e = blockIdx.y;
+    const int lam = (int)(idx % A.nlam);
+    const long long pr = idx / A.nlam;
+    const int a = (int)(pr / A.LM), b2 = (int)(pr % A.LM);
+    int lp = 0, l = 0;
+    while ((lp + 1) * (lp + 1) <= a) ++lp;
+    while ((l + 1) * (l + 1) <= b2) ++l;
+    const int mu = (a - lp * lp - lp) - (b2 - l * l - l);
+    const int amu = mu < 0 ? -mu : mu;
+    double* et = const_cast<double*>(A.et) + (size_t)e * A.et_doubles;
+    const double c = A.ang[idx];
+    double v = 0.0;
+    if (c != 0.0) {
+        double P = et[A.dtot + lam * (lam + 1) / 2 + amu];
+        if (mu < 0 && (amu & 1)) P = -P;
+        double sc = (lam & 1) ? A.parity : 1.0;
+        const double* st = et + A.dtot + A.npb;
+        if (st[1] != 0.0) {
+            const double R = dist_R(ev[e].b, ev[e].z);
+            const double ratio = A.r[A.Nr - 1] / R;
+            double p = ratio;
+            for (int k = 0; k < lam; ++k) p *= ratio;
+            sc *= p;
+        }
+        v = -A.Z_other * sc * c * P;
+    }
+    et[A.cp_off + idx] = v;
+}
+
 __global__ void __launch_bounds__(256) k_direct(DirArgs A0, DirArgs A1, const EvalDesc* __restrict__ ev) {
     const DirArgs& A = blockIdx.z == 0 ? A0 : A1;
-    __shared__ double sPb[(4 * WPCCC_LMAX + 1) * (4 * WPCCC_LMAX + 2) / 2];
-    __shared__ double sL[5];
-    __shared__ int s_sten, s_out;
     const int e = blockIdx.y;
-    const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
-    const double R = dist_R(b, z);
     const double* et = A.et + (size_t)e * A.et_doubles;
-    // Pbar(lam, mu), index lam(lam+1)/2 + mu, and the stencil of Eq. 7's table at R
-    const int npb = A.nlam * (A.nlam + 1) / 2;
-    for (int t = threadIdx.x; t < npb; t += blockDim.x) sPb[t] = et[A.dtot + t];
-    if (threadIdx.x == 0) {
-        const double* st = et + A.dtot + A.npb;
-        s_sten = (int)st[0];
-        s_out = st[1] != 0.0;
-        for (int k = 0; k < 5; ++k) sL[k] = st[2 + k];
-    }
-    __syncthreads();
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)A.Nc * A.Nc) return;
     const int i = (int)(idx / A.Nc), j = (int)(idx % A.Nc);
     const int ra = A.st_rad[i], rb = A.st_rad[j];
-    const int mu = A.st_m[i] - A.st_m[j];
-    const int amu = mu < 0 ? -mu : mu;
-    const double* ang = A.ang + (size_t)idx * A.nlam;
+    const double* cp = et + A.cp_off + ((size_t)A.st_lm[i] * A.LM + A.st_lm[j]) * A.nlam;
     const int* foff = A.Foff + ((size_t)ra * A.n_rad + rb) * A.nlam;
     const double* Fint = et + A.dtot + A.npb + 8 + A.foff0;
     double D = 0.0;
-    double sgn = 1.0;
-    for (int lam = 0; lam < A.nlam; ++lam, sgn *= A.parity) {
-        const double c = ang[lam];
+    for (int lam = 0; lam < A.nlam; ++lam) {
+        const double c = cp[lam];
         if (c == 0.0) continue;
-        double Fv = Fint[foff[lam]];
-        if (s_out) {
-            const double ratio = A.r[A.Nr - 1] / R;
-            double p = ratio;
-            for (int k = 0; k < lam; ++k) p *= ratio;
-            Fv *= p;
-        }
-        double P = sPb[lam * (lam + 1) / 2 + amu];
-        if (mu < 0 && (amu & 1)) P = -P;
-        D += sgn * c * P * Fv;
+        D = fma(c, Fint[foff[lam]], D);
     }
-    D *= -A.Z_other;
     const double2* phs = reinterpret_cast<const double2*>(et + A.ph_off);
     const double2 ph = cmul(phs[A.off + i], cconj(phs[A.off + j]));
     const size_t o = (size_t)(A.off + i) + (size_t)(A.off + j) * A.N;
@@ -1089,6 +1101,11 @@ ElemScratch elem_scratch_layout(const wpccc_basis_s* B) {
     L.et_doubles += L.et_doubles & 1;
     L.ph_off = L.et_doubles;
     L.et_doubles += 2 * (size_t)B->N;
+    L.cp_off[0] = L.et_doubles;
+    L.et_doubles += (size_t)B->T.LM * B->T.LM * B->T.nlam;
+    L.cp_off[1] = L.et_doubles;
+    if (B->n_centres == 2) L.et_doubles += (size_t)B->P.LM * B->P.LM * B->P.nlam;
+    L.et_doubles += L.et_doubles & 1;
     if (B->n_centres == 2) {
         size_t nd = (size_t)(B->T.n_rad + B->P.n_rad + B->nlq_T + B->nlq_P) * B->G;
         nd += nd & 1;   // keep the complex weights 16-byte aligned
@@ -1135,6 +1152,8 @@ static DirArgs dir_args(const wpccc_basis_s* B, const CentreDev& c, int off, dou
     a.r = B->r;
     a.F = c.F;
     a.ang = c.ang;
+    a.st_lm = c.st_lm;
+    a.LM = c.LM;
     a.eps = c.st_eps;
     a.Foff = c.Foff;
     a.st_rad = c.st_rad;
@@ -1143,6 +1162,7 @@ static DirArgs dir_args(const wpccc_basis_s* B, const CentreDev& c, int off, dou
     a.H = H;
     a.mat = (size_t)B->N * B->N;
     const ElemScratch L = elem_scratch_layout(B);
+    a.cp_off = L.cp_off[off == 0 ? 0 : 1];
     a.dtot = L.dtot;
     a.npb = L.npb;
     a.et = nullptr;
@@ -1359,6 +1379,10 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
     int ncmax = two ? std::max(B->N_T, B->N_P) : B->N_T;
     long long cells = (long long)ncmax * ncmax;
     cudaEvent_t ed = B->prof.begin(PROF_ROT_DIRECT, st);
+    const long long ncoef = std::max((long long)B->T.LM * B->T.LM * B->T.nlam,
+                                     two ? (long long)B->P.LM * B->P.LM * B->P.nlam : 0LL);
+    k_direct_coef<<<dim3((unsigned)((ncoef + 255) / 256), nev, two ? 2 : 1), 256, 0, st>>>(d0, d1, evals);
+    WPCCC_CHECK_LAUNCH("k_direct_coef");
     k_direct<<<dim3((unsigned)((cells + 255) / 256), nev, two ? 2 : 1), 256, 0, st>>>(d0, d1, evals);
     WPCCC_CHECK_LAUNCH("k_direct");
     B->prof.end(PROF_ROT_DIRECT, st, ed);

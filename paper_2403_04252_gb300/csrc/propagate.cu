@@ -186,6 +186,80 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// RK4 with the vectors in global memory (one-centre form, any N): one launch per stage for all paths of
+// a chunk.  Stage 1 reads c and writes y_a, stage 2 reads y_a and writes y_b, stage 3 reads y_b and
+// writes y_a, stage 4 reads y_a and updates c; each thread owns one row of every vector, so the
+// per-row updates need no further synchronisation, and the launch boundary orders the stages.
+// ---------------------------------------------------------------------------
+constexpr int WIDE_ROWS = 128;   // rows (threads) per block
+constexpr int WIDE_TJ = 256;     // columns of the input vector staged in shared memory at a time
+
+struct WideArgs {
+    int N;
+    const double2* H;        // chunk: H per evaluation (M = -(i/v) H)
+    const PathChunk* pcs;
+    double2* c;              // [n_paths][N]
+    double2 *ya, *yb, *acc;  // [chunk paths][N]
+    const double* z;
+    int* flags;
+};
+
+__global__ void __launch_bounds__(WIDE_ROWS) k_rk4_wide(WideArgs A, int s, int stage) {
+    __shared__ double2 sy[WIDE_TJ];
+    const PathChunk pc = A.pcs[blockIdx.y];
+    if (s >= pc.nsteps) return;   // the whole block: the path has fewer steps in this chunk
+    const int N = A.N;
+    const int i = blockIdx.x * WIDE_ROWS + threadIdx.x;
+    // position of the stage: the step's first node (the chunk's first evaluation, or the previous
+    // step's last node), its midpoint twice, then its last node
+    const int e = stage == 1 ? (s == 0 ? pc.start_local : pc.first_local + 2 * s - 1)
+                             : (stage == 4 ? pc.first_local + 2 * s + 1 : pc.first_local + 2 * s);
+    const double2* M = A.H + (size_t)e * N * N;
+    double2* cp = A.c + (size_t)pc.path * N;
+    const size_t vo = (size_t)blockIdx.y * N;
+    const double2* in = stage == 1 ? cp : (stage == 3 ? A.yb + vo : A.ya + vo);
+    double re = 0.0, im = 0.0;
+    for (int j0 = 0; j0 < N; j0 += WIDE_TJ) {
+        const int nj = min(WIDE_TJ, N - j0);
+        for (int q = threadIdx.x; q < nj; q += WIDE_ROWS) sy[q] = in[j0 + q];
+        __syncthreads();
+        if (i < N) {
+            const double2* col = M + i + (size_t)j0 * N;   // column-major: consecutive rows coalesce
+            for (int q = 0; q < nj; ++q) {
+                const double2 a = col[(size_t)q * N];
+                const double2 b = sy[q];
+                re = fma(a.x, b.x, re);
+                re = fma(-a.y, b.y, re);
+                im = fma(a.x, b.y, im);
+                im = fma(a.y, b.x, im);
+            }
+        }
+        __syncthreads();
+    }
+    if (i >= N) return;
+    const double v = pc.v;
+    const double h = A.z[pc.z0 + s + 1] - A.z[pc.z0 + s];
+    const double2 k = make_double2(im / v, -re / v);   // -(i/v) (H y)_i
+    const double2 ci = cp[i];
+    double2* acc = A.acc + vo;
+    if (stage == 1) {
+        acc[i] = k;
+        A.ya[vo + i] = make_double2(ci.x + 0.5 * h * k.x, ci.y + 0.5 * h * k.y);
+    } else if (stage == 2) {
+        acc[i] = make_double2(acc[i].x + 2.0 * k.x, acc[i].y + 2.0 * k.y);
+        A.yb[vo + i] = make_double2(ci.x + 0.5 * h * k.x, ci.y + 0.5 * h * k.y);
+    } else if (stage == 3) {
+        acc[i] = make_double2(acc[i].x + 2.0 * k.x, acc[i].y + 2.0 * k.y);
+        A.ya[vo + i] = make_double2(ci.x + h * k.x, ci.y + h * k.y);
+    } else {
+        const double2 a = acc[i];
+        const double2 cn = make_double2(ci.x + (h / 6.0) * (a.x + k.x), ci.y + (h / 6.0) * (a.y + k.y));
+        if (!isfinite(cn.x) || !isfinite(cn.y)) atomicOr(A.flags, FLAG_NONFINITE);
+        cp[i] = cn;
+    }
+}
+
 size_t rk_smem_bytes(int mode, int N) {
     if (mode == RK_SCHUR) return (size_t)N * 6 * sizeof(double2) + 32 * 32 * sizeof(double2);
     if (mode == RK_MIXED_SCHUR)
@@ -229,14 +303,15 @@ struct PropPlan {
     int np = 0, N = 0, mode = RK_MATRIX, elem_precision = 0, C = 1, n_chunks = 0, max_chunk_evals = 0;
     int max_steps = 0;
     bool two = false, mixed = false, stage = false, schur = false;
+    bool wide = false;       // one-centre RK4 with the vectors in global memory (k_rk4_wide)
     size_t per_eval = 0, fixed = 0;
     std::vector<double> z;
     std::vector<EvalDesc> ev;
     std::vector<PathChunk> pcs;
     std::vector<int> ev_begin, pc_begin;
     size_t sz_carry = 0, sz_carryLU = 0, sz_carryPiv = 0, sz_carryLU32 = 0, sz_LU32 = 0, sz_z = 0, sz_ev = 0,
-           sz_pc = 0, sz_flags = 0, sz_S = 0, sz_H = 0, sz_piv = 0, sz_info = 0, sz_scr = 0, bytes = 0;
-    double2 *d_carry = nullptr, *d_carryLU = nullptr, *d_S = nullptr, *d_H = nullptr;
+           sz_pc = 0, sz_flags = 0, sz_S = 0, sz_H = 0, sz_piv = 0, sz_info = 0, sz_scr = 0, sz_vec = 0, bytes = 0;
+    double2 *d_carry = nullptr, *d_carryLU = nullptr, *d_S = nullptr, *d_H = nullptr, *d_vec = nullptr;
     int *d_carryPiv = nullptr, *d_flags = nullptr, *d_piv = nullptr, *d_info = nullptr;
     float2 *d_carryLU32 = nullptr, *d_LU32 = nullptr;
     double* d_z = nullptr;
@@ -291,7 +366,11 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     P.stage = P.two && !P.mixed && B->solve_mode != WPCCC_SOLVE_MATRIX;
     P.schur = P.two && B->solve_mode == WPCCC_SOLVE_SCHUR;
     P.mode = P.mixed ? (P.schur ? RK_MIXED_SCHUR : RK_MIXED) : (P.schur ? RK_SCHUR : (P.stage ? RK_STAGE : RK_MATRIX));
-    if (rk_smem_bytes(P.mode, N) > (size_t)227 * 1024)
+    const bool fits = rk_smem_bytes(P.mode, N) <= (size_t)227 * 1024;
+    if (P.two && B->rk4_layout == WPCCC_RK4_GLOBAL)
+        return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: the global-memory RK4 layout is one-centre only");
+    P.wide = !P.two && (B->rk4_layout == WPCCC_RK4_GLOBAL || (B->rk4_layout == WPCCC_RK4_AUTO && !fits));
+    if (!P.wide && !fits)
         return fail(WPCCC_EINVAL, "wpccc_propagate: N too large for the RK4 kernel's shared memory in this mode");
     const size_t mat = (size_t)N * N;
     const ElemScratch L = elem_scratch_layout(B);
@@ -306,7 +385,8 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     }
     P.z.assign(paths->z, paths->z + zoff[np]);
     if (P.max_steps == 0) return WPCCC_OK;
-    P.fixed = align256((size_t)np * mat * sizeof(double2)) * (P.mode != RK_MATRIX ? 2 : 1) +
+    P.fixed = (P.wide ? align256((size_t)3 * np * N * sizeof(double2))
+                      : align256((size_t)np * mat * sizeof(double2)) * (P.mode != RK_MATRIX ? 2 : 1)) +
               (P.mixed ? align256((size_t)np * mat * sizeof(float2)) : 0) + align256((size_t)np * N * sizeof(int)) +
               align256((size_t)zoff[np] * sizeof(double)) + align256((size_t)total_evals * sizeof(EvalDesc)) +
               align256((size_t)np * P.max_steps * sizeof(PathChunk)) + 16 * 256;
@@ -348,9 +428,11 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
             pc.pad = 0;
             pc.start_local = -1;
             const int base = P.ev_begin[ch];
-            if (s0 == 0) {
+            if (s0 == 0 || P.wide) {
+                // the path's first node; in the global-memory layout every chunk evaluates its first node
+                // again (instead of carrying an N x N matrix over)
                 pc.start_local = (int)P.ev.size() - base;
-                P.ev.push_back(EvalDesc{paths->b[p], paths->v[p], zp[0], p, 0});
+                P.ev.push_back(EvalDesc{paths->b[p], paths->v[p], zp[s0], p, 0});
             }
             pc.first_local = (int)P.ev.size() - base;
             for (int s = s0; s < s0 + n; ++s) {
@@ -366,7 +448,8 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     for (int ch = 0; ch < P.n_chunks; ++ch)
         P.max_chunk_evals = std::max(P.max_chunk_evals, P.ev_begin[ch + 1] - P.ev_begin[ch]);
     const int mce = P.max_chunk_evals;
-    P.sz_carry = align256((size_t)np * mat * sizeof(double2));
+    P.sz_carry = P.wide ? 0 : align256((size_t)np * mat * sizeof(double2));
+    P.sz_vec = P.wide ? align256((size_t)3 * np * N * sizeof(double2)) : 0;
     P.sz_carryLU = P.mode != RK_MATRIX ? P.sz_carry : 0;
     P.sz_carryPiv = P.mode != RK_MATRIX ? align256((size_t)np * N * sizeof(int)) : 0;
     P.sz_carryLU32 = P.mixed ? align256((size_t)np * mat * sizeof(float2)) : 0;
@@ -382,7 +465,7 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     P.sz_info = P.two ? align256((size_t)mce * sizeof(int)) * 2 : 0;
     P.sz_scr = align256((size_t)mce * L.bytes_per_eval);
     P.bytes = P.sz_carry + P.sz_carryLU + P.sz_carryPiv + P.sz_carryLU32 + P.sz_LU32 + P.sz_z + P.sz_ev + P.sz_pc +
-              P.sz_flags + P.sz_S + P.sz_H + P.sz_piv + P.sz_info + P.sz_scr;
+              P.sz_flags + P.sz_S + P.sz_H + P.sz_piv + P.sz_info + P.sz_scr + P.sz_vec;
     return WPCCC_OK;
 }
 
@@ -407,6 +490,7 @@ static void plan_bind(PropPlan& P, void* ws) {
     P.d_piv = reinterpret_cast<int*>(take(P.sz_piv));
     P.d_info = reinterpret_cast<int*>(take(P.sz_info));
     P.d_scr = take(P.sz_scr);
+    P.d_vec = reinterpret_cast<double2*>(take(P.sz_vec));
 }
 
 // Copies the plan's node, position and chunk lists to the device (from its host vectors, which
@@ -433,12 +517,14 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     const size_t mat = (size_t)N * N;
     cudaStream_t st = S.st, rs = S.rs;
     WPCCC_CUDA(cudaMemsetAsync(P.d_flags, 0, sizeof(int), st));
-    const int rk_smem = (int)rk_smem_bytes(P.mode, N);
-    WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MATRIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
-    WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
-    WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
-    WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
-    WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+    const int rk_smem = P.wide ? 0 : (int)rk_smem_bytes(P.mode, N);
+    if (!P.wide) {
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MATRIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+    }
     const size_t hS = P.sz_S / 2 / sizeof(double2), hH = P.sz_H / 2 / sizeof(double2);
     const size_t hL = P.sz_LU32 / 2 / sizeof(float2), hP = P.sz_piv / 2 / sizeof(int), hI = P.sz_info / 2 / sizeof(int);
     RkArgs ra;
@@ -487,7 +573,22 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
         ra.LU32 = bL;
         ra.piv = P.mode != RK_MATRIX ? bP : nullptr;
         ra.info = bI;
-        if (P.mode == RK_MIXED) k_rk4<RK_MIXED><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
+        if (P.wide) {
+            WideArgs wa;
+            wa.N = N;
+            wa.H = bH;
+            wa.pcs = ra.pcs;
+            wa.c = c;
+            wa.ya = P.d_vec;
+            wa.yb = P.d_vec + (size_t)P.np * N;
+            wa.acc = P.d_vec + (size_t)2 * P.np * N;
+            wa.z = P.d_z;
+            wa.flags = P.d_flags;
+            const int steps = std::min(P.C, P.max_steps - ch * P.C);
+            const dim3 grid((N + WIDE_ROWS - 1) / WIDE_ROWS, npc);
+            for (int s2 = 0; s2 < steps; ++s2)
+                for (int stage = 1; stage <= 4; ++stage) k_rk4_wide<<<grid, WIDE_ROWS, 0, rs>>>(wa, s2, stage);
+        } else if (P.mode == RK_MIXED) k_rk4<RK_MIXED><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else if (P.mode == RK_MIXED_SCHUR) k_rk4<RK_MIXED_SCHUR><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else if (P.mode == RK_SCHUR) k_rk4<RK_SCHUR><<<npc, RK_THREADS, rk_smem, rs>>>(ra);
         else if (P.mode == RK_STAGE) k_rk4<RK_STAGE><<<npc, RK_THREADS, rk_smem, rs>>>(ra);

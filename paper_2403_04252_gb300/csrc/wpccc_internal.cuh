@@ -50,8 +50,11 @@ struct CentreDev {
     int* fent_a = nullptr;      // [n_fent]
     int* fent_b = nullptr;
     int* fent_lam = nullptr;
-    double* ang = nullptr;      // [n_states][n_states][nlam]: Eq. 6 coefficient without the
-                                // sqrt((lam-mu)!/(lam+mu)!) factor (carried by the Legendre table)
+    double* ang = nullptr;      // [LM][LM][nlam]: Eq. 6 coefficient of the angular parts (l', m'), (l, m)
+                                // without the sqrt((lam-mu)!/(lam+mu)!) factor (carried by the Legendre
+                                // table); it does not depend on the radial functions
+    int* st_lm = nullptr;       // [n_states]: angular index l^2 + l + m of each state
+    int LM = 0;                 // (lmax + 1)^2 angular parts
     // host copies used to build launch lists
     std::vector<int> h_rad_l, h_st_rad, h_st_m;
 };
@@ -112,6 +115,7 @@ struct wpccc_basis_s {
     size_t ws_bytes = 0;
     size_t ws_limit = (size_t)8 << 30;
     int solve_mode = WPCCC_SOLVE_STAGE;
+    int rk4_layout = WPCCC_RK4_AUTO;
     // short-range part of a Li-like target potential, V_T(r) = -[Z_T + mp_c e^{-mp_a r}(1 + mp_b r)]/r
     double mp_c = 0.0, mp_a = 0.0, mp_b = 0.0;
     // differentiation form
@@ -156,6 +160,7 @@ struct ElemScratch {
     size_t et_doubles;     // small per-position tables (Wigner d, Legendre, stencil, F at R, phases), even
     size_t ph_off;         // offset of the per-state energy phases exp(i eps_i z / v) (complex, N of them)
     int dtot, npb;         // sizes of their Wigner-d and Legendre parts
+    size_t cp_off[2];      // per centre: Eq. 6 coefficients of the position, [LM][LM][nlam] (see k_direct_coef)
     int tc_rows;           // rows of the tensor-core slice planes (2 N_T), when the basis enables the layout
     // tensor-core layout (precision modes 3-5): up to seven bf16 slice planes [7][tc_rows][G], then
     // (offsets in floats) the window scales, A_P and W_K / r_T as double-floats

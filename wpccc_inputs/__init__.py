@@ -512,6 +512,10 @@ CONFIGS = {
     # one-centre p + H, direct elements only
     "p_H_1c_n3l2": dict(Z_T=1.0, Z_P=1.0, nmax=3, lmax=2, nbins=5, kmax=2.0, two_centre=False,
                         v=1.0, b=(0.5, 8.0, 8), z=(-40.0, 40.0, 0.1)),
+    # one-centre p + H at the paper's large angular momentum: n <= 10, l <= 10, 32 packets per l
+    # (N = 385 + 32 x 121 = 4257), v = 2 a.u. (100 keV)
+    "p_H_1c_n10l10": dict(Z_T=1.0, Z_P=1.0, nmax=10, lmax=10, nbins=32, kmax=2.0, two_centre=False,
+                          v=2.0, b=(0.5, 8.0, 8), z=(-40.0, 40.0, 0.1)),
     # two-centre p + H with electron capture
     "p_H_2c_n4l3": dict(Z_T=1.0, Z_P=1.0, nmax=4, lmax=3, nbins=10, kmax=3.0, two_centre=True,
                         v=1.5, b=(0.2, 12.0, 32), z=(-50.0, 50.0, 0.1)),
