@@ -836,8 +836,6 @@ constexpr int ROT_WARPS_MAX = 8;
 __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const EvalDesc* __restrict__ ev) {
     extern __shared__ double sd[];     // Wigner d^l_{m q}(theta) for l <= lmax, then per-warp blocks
     const int e = blockIdx.y;
-    const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
-    (void)b;
     const int total = A.dtot;
     const double* etd = A.et + (size_t)e * A.et_doubles;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) sd[idx] = etd[idx];
@@ -1023,7 +1021,7 @@ struct SrArgs {
 __global__ void __launch_bounds__(256) k_direct_sr(SrArgs A, const EvalDesc* __restrict__ ev) {
     extern __shared__ double srm[];   // [G] V_s-weighted f_a, then I[n_radP][lmaxP+1], then Wigner d
     const int a = blockIdx.x, e = blockIdx.y;
-    const double b = ev[e].b, v = ev[e].v, z = ev[e].z;
+    const double b = ev[e].b, z = ev[e].z;
     const double R = dist_R(b, z);
     const double gR = __dmul_rn(A.gamma, R);
     const double halfR = __dmul_rn(0.5, R);

@@ -514,7 +514,6 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     if (P.max_steps == 0) return WPCCC_OK;
     wpccc_basis_s* B = P.B;
     const int N = P.N;
-    const size_t mat = (size_t)N * N;
     cudaStream_t st = S.st, rs = S.rs;
     WPCCC_CUDA(cudaMemsetAsync(P.d_flags, 0, sizeof(int), st));
     const int rk_smem = P.wide ? 0 : (int)rk_smem_bytes(P.mode, N);
