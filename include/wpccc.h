@@ -241,9 +241,9 @@ WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv
  *     2  mixed with FP64 elements: as 1 but the contraction stays in FP64 (for
  *        ill-conditioned S, where FP32 element errors get amplified by cond(S));
  *     3  as 1 with the Eq. 9 contraction on the 5th-generation tensor cores: tcgen05.mma
- *        (kind::f16) on three-part bf16 splits of both operands (six products, FP32-level
- *        products), FP32 accumulation drained every 32 nodes into compensated sums; operand
- *        tiles staged by TMA;
+ *        (kind::f16) on three bf16 fixed-point slices of both operands per 128-node window
+ *        (six slice products into three exact FP32 accumulators, FP32-level result), drained
+ *        per window into double-float sums; table tiles staged by TMA;
  *     4  the FP64 form (solve and RK4 as mode 0) with the Eq. 9 contraction emulated to FP64
  *        accuracy on the tensor cores: seven bf16 slices of both operands in fixed point per
  *        128-node window (error-free splitting, Ozaki et al.), 28 slice products into five FP32
