@@ -696,9 +696,8 @@ def main() -> None:
     ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
     ap.add_argument("--solve-mode", default="auto", choices=["auto", "stage", "matrix", "schur"],
                     help="S^-1 per RK4 stage through the Schur complement's Cholesky factor (schur), from pivoted LU "
-                         "factors (stage), or as X = S^-1 H (matrix); auto: schur, except pivoted LU for the velocity "
-                         "scan (its Schur solve is not yet measured); the Cholesky factor needs a positive-definite "
-                         "S, i.e. a converged (eta, tau) rule")
+                         "factors (stage), or as X = S^-1 H (matrix); auto = schur (the Cholesky factor needs a "
+                         "positive-definite S, i.e. the workloads' converged (eta, tau) rules)")
     ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v",
                                                              "pLi_2c_grad", "p_H_1c_n10l10"],
                     help="p_H_2c_n4l3: two-centre p + H (N = 380, 32 paths); C6_H_2c_n6l5: bare C6+ on H "
@@ -718,7 +717,7 @@ def main() -> None:
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.solve_mode == "auto":
-        args.solve_mode = "stage" if args.workload == "p_H_2c_batch6v" else "schur"
+        args.solve_mode = "schur"
     if args.impl == "reference":
         run_reference(args)
         return
