@@ -210,3 +210,24 @@ def test_batch_graph_fp64_tc_forms(small32, uneven32):
         batch.close()
     gA.close()
     gB.close()
+
+
+def test_tensor_core_forms_ragged_paths_with_an_empty_one(small32):
+    # modes 3, 4 and 5 with a path of no steps (amplitudes untouched) beside ragged ones, in several chunks
+    w = _w()
+    g = w.Basis(small32)
+    g.set_solve_mode(w.SOLVE_SCHUR)
+    g.set_workspace_limit(64 << 20)
+    bs = np.array([0.5, 1.7, 3.0])
+    zgs = [wi.uniform_zgrid(-3.0, 3.0, 0.2), np.array([0.4]), wi.uniform_zgrid(-1.0, 2.0, 0.25)]
+    P0 = w.probabilities(g.propagate(bs, 1.3, zgs, precision_mode=0)).cpu().numpy()
+    for mode, bound in ((3, 1e-6), (4, None), (5, 1e-6)):
+        c = torch.zeros((3, g.N), dtype=torch.complex128, device="cuda")
+        c[:, 0] = 1.0
+        P = w.probabilities(g.propagate(bs, 1.3, zgs, c=c, precision_mode=mode)).cpu().numpy()
+        assert P[1, 0] == 1.0 and np.all(P[1, 1:] == 0.0)
+        if bound is None:
+            _prob_close(P, P0)
+        else:
+            assert np.abs(P - P0).max() <= bound
+    g.close()

@@ -75,3 +75,24 @@ def test_global_layout_is_one_centre_only():
         g.propagate(np.array([1.0]), 1.0, [np.array([0.0, 0.1])])
     assert e.value.status == w.EUNSUPPORTED
     g.close()
+
+
+def test_global_layout_edge_paths():
+    # a path without steps keeps its amplitudes; one-step and many-step paths through several chunks
+    # (every chunk evaluates its first node again) equal the shared-memory sweep
+    w = _w()
+    basis, _ = wi.config_inputs("p_H_1c_n3l2")
+    g = w.Basis(basis)
+    g.set_workspace_limit(64 << 20)
+    bs = np.array([0.8, 1.5, 4.0])
+    zgs = [np.array([0.3]), np.array([-0.2, 0.1]), wi.uniform_zgrid(-8.0, 8.0, 0.1)]
+    c0 = torch.zeros((3, g.N), dtype=torch.complex128, device="cuda")
+    c0[:, 0] = 0.6
+    c0[:, 1] = 0.8j
+    res = {}
+    for layout in (w.RK4_SHARED, w.RK4_GLOBAL):
+        g.set_rk4_layout(layout)
+        res[layout] = g.propagate(bs, 1.0, zgs, c=c0.clone())
+    assert torch.equal(res[w.RK4_GLOBAL][0], c0[0])
+    assert (res[w.RK4_GLOBAL] - res[w.RK4_SHARED]).abs().max().item() < 1e-13
+    g.close()
