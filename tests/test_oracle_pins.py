@@ -287,3 +287,22 @@ def test_paper_lower_left_block_keeps_the_spectrum_real(grid):
     H2[NT:, :NT] = Qt
     ev2 = np.linalg.eigvals((-1j / 2.0) * np.linalg.solve(S, H2))
     assert ev2.real.max() > 1e-3
+
+
+def test_schur_complement_solve_of_the_overlap():
+    """The Schur-complement reading of S k = t used by the Schur solve mode: S = [[I, K], [K^+, I]] is a
+    Gram matrix, I - K^+ K = L L^+ (Cholesky, positive pivots), and k_P = (L L^+)^-1 (t_P - K^+ t_T),
+    k_T = t_T - K k_P reproduce the direct solve; on the oracle's own two-centre S at close approach."""
+    basis = wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=20, Gtau=14)
+    S, H = O.assemble(basis, 0.4, 1.3, 0.1)
+    NT = basis.T.N
+    K = S[:NT, NT:]
+    assert np.allclose(S[:NT, :NT], np.eye(NT)) and np.allclose(S[NT:, NT:], np.eye(S.shape[0] - NT))
+    Lc = np.linalg.cholesky(np.eye(S.shape[0] - NT) - K.conj().T @ K)
+    assert np.all(np.diag(Lc).real > 0)
+    t = H @ (np.arange(S.shape[0]) + 1j * np.cos(np.arange(S.shape[0])))
+    uP = t[NT:] - K.conj().T @ t[:NT]
+    kP = np.linalg.solve(Lc.conj().T, np.linalg.solve(Lc, uP))
+    kT = t[:NT] - K @ kP
+    k = np.concatenate([kT, kP])
+    assert np.abs(k - np.linalg.solve(S, t)).max() < 1e-12 * np.abs(k).max()
