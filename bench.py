@@ -748,7 +748,7 @@ def main() -> None:
     basis, paths = wi.config_inputs(args.workload)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(basis, paths, 12 if args.workload == WORKLOAD else 2,
+        cpu = cpu_oracle_rate(basis, paths, 40 if args.workload == WORKLOAD else 2,
                               path_index=min(16, paths.n_paths // 2))
 
     import paper_2403_04252_gb300 as w
