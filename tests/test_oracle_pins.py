@@ -306,3 +306,64 @@ def test_schur_complement_solve_of_the_overlap():
     kT = t[:NT] - K @ kP
     k = np.concatenate([kT, kP])
     assert np.abs(k - np.linalg.solve(S, t)).max() < 1e-12 * np.abs(k).max()
+
+
+
+@pytest.fixture(scope="module")
+def schroedinger_case():
+    # One-centre hydrogen n <= 3 subset, projectile charge 1, v = 0.8. Reference: the Schroedinger
+    # picture i v da/dz = (diag(eps) + D(z)) a, with no energy phases at all, as a product of
+    # exp-midpoint steps (scipy expm), Richardson-extrapolated from two step sizes.
+    g = wi.radial_grid(1000)
+    nl = [(1, 0), (2, 0), (2, 1), (3, 2)]
+    eps = np.array([-0.5, -0.125, -0.125, -1.0 / 18.0])
+    f = [wi.hydrogenic_radial(n, l, 1.0, g.r) for n, l in nl]
+    T = wi.centre_from_functions(1.0, [l for _, l in nl], [n for n, _ in nl], f, eps)
+    basis = wi.Basis(grid=g, T=T, P=None, quad=None, Z_T=1.0, Z_P=1.0)
+    b, v, z0, z1 = 1.0, 0.8, -10.0, 10.0
+    E = np.diag(T.st_eps).astype(np.complex128)
+    D = {}
+
+    def schroedinger(n):
+        zs = np.linspace(z0, z1, n + 1)
+        a = np.zeros(T.N, dtype=np.complex128)
+        a[0] = 1.0
+        for za, zb in zip(zs[:-1], zs[1:]):
+            zm = 0.5 * (za + zb)
+            if zm not in D:
+                R = math.hypot(b, zm)
+                D[zm] = O.direct_block(g, T, 1.0, R, zm / R, other_at_minus_R=False)
+            a = expm((-1j / v) * (zb - za) * (E + D[zm])) @ a
+        return np.abs(a) ** 2
+
+    P1, P2 = schroedinger(1000), schroedinger(2000)
+    return basis, b, v, wi.uniform_zgrid(z0, z1, 0.02), (4.0 * P2 - P1) / 3.0
+
+
+def test_interaction_picture_matches_schroedinger_picture(schroedinger_case):
+    # The oracle propagates interaction-picture amplitudes (Eq. 5 with the energy phases of H);
+    # |a|^2 = |c|^2, so the probabilities must agree with the Schroedinger-picture reference. This
+    # fixes the -(i/v) factor, the sign and the 1/v of the phases and Algorithm 1's use of M.
+    basis, b, v, zg, ref = schroedinger_case
+    P = O.probabilities(O.propagate(basis, b, v, zg))
+    assert P[1] > 0.05 and P[3] > 0.005 and P[7] > 0.005    # a strong collision: far from first order
+    assert np.abs(P - ref).max() < 1e-8
+
+
+_PHASES, _COUPLING = O.phases, O.coupling_M
+
+
+@pytest.mark.parametrize("mistake", ["phase sign", "phase z*v", "M without 1/v", "M with +i"])
+def test_interaction_picture_mistakes_fail(schroedinger_case, mistake, monkeypatch):
+    # each planted mistake in the oracle moves the probabilities far outside the pin's tolerance
+    basis, b, v, zg, ref = schroedinger_case
+    if mistake == "phase sign":
+        monkeypatch.setattr(O, "phases", lambda er, ec, z, v: _PHASES(er, ec, -z, v))
+    elif mistake == "phase z*v":
+        monkeypatch.setattr(O, "phases", lambda er, ec, z, v: _PHASES(er, ec, z * v * v, v))
+    elif mistake == "M without 1/v":
+        monkeypatch.setattr(O, "coupling_M", lambda bs, b, v, z: v * _COUPLING(bs, b, v, z))
+    else:
+        monkeypatch.setattr(O, "coupling_M", lambda bs, b, v, z: -_COUPLING(bs, b, v, z))
+    P = O.probabilities(O.propagate(basis, b, v, zg))
+    assert np.abs(P - ref).max() > 1e-4
