@@ -1460,9 +1460,10 @@ extern "C" wpccc_status wpccc_matrix_elements(wpccc_basis B, double b, double v,
 
 extern "C" wpccc_status wpccc_matrix_elements_precision(wpccc_basis B, double b, double v, int nz, const double* z,
                                                         void* S, void* H, int precision_mode, void* stream) {
+    if (!B) return fail(WPCCC_EINVAL, "wpccc_matrix_elements_precision: null basis");
     if (precision_mode != 0 && precision_mode != 1 && precision_mode != 3 && precision_mode != 4)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: element precision 0, 1, 3 or 4");
-    if (precision_mode != 0 && (!B || B->n_centres != 2))
+    if (precision_mode != 0 && B->n_centres != 2)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: reduced precision needs two centres");
     if (precision_mode != 0 && B->mp_c != 0.0)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_matrix_elements_precision: model-potential targets need FP64");

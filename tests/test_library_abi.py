@@ -55,3 +55,40 @@ def test_argument_errors_without_gpu(lib):
     assert lib.wpccc_probabilities(-1, 4, None, None, None) == 1
     assert lib.wpccc_basis_create(None, 0, None) == 1
     assert lib.wpccc_basis_destroy(None) == 0
+
+
+def test_null_handles_are_argument_errors_without_gpu(lib):
+    # every entry point that takes a basis or a batch handle rejects a null one before any CUDA call
+    EINVAL = 1
+    lib.wpccc_last_error.restype = C.c_char_p
+    P = C.c_void_p
+    calls = {
+        "wpccc_basis_info": ([P, P, P], [None, None, None]),
+        "wpccc_matrix_elements": ([P, C.c_double, C.c_double, C.c_int, P, P, P, P],
+                                  [None, 1.0, 1.0, 1, None, None, None, None]),
+        "wpccc_matrix_elements_precision": ([P, C.c_double, C.c_double, C.c_int, P, P, P, C.c_int, P],
+                                            [None, 1.0, 1.0, 1, None, None, None, 4, None]),
+        "wpccc_matrix_elements_noalloc": ([P, C.c_double, C.c_double, C.c_int, P, P, P, P],
+                                          [None, 1.0, 1.0, 1, None, None, None, None]),
+        "wpccc_propagate": ([P, P, C.c_int, C.c_int, P, P], [None, None, 0, 0, None, None]),
+        "wpccc_propagate_adjoint": ([P, P, C.c_int, P, C.c_int, P, P, P, P],
+                                    [None, None, 1, None, 1, None, None, None, None]),
+        "wpccc_basis_set_solve_mode": ([P, C.c_int], [None, 0]),
+        "wpccc_basis_set_refine_iters": ([P, C.c_int], [None, 1]),
+        "wpccc_basis_set_rk4_layout": ([P, C.c_int], [None, 0]),
+        "wpccc_basis_set_workspace_limit": ([P, C.c_size_t], [None, 1 << 30]),
+        "wpccc_basis_set_tangents": ([P, C.c_int, P, P, P, P, P], [None, 1, None, None, None, None, None]),
+        "wpccc_profile_enable": ([P, C.c_int], [None, 1]),
+        "wpccc_profile_read": ([P, P, P], [None, None, None]),
+        "wpccc_batch_create": ([C.c_int, P, P, C.c_int, P, C.c_int, P], [0, None, None, 0, None, 0, None]),
+        "wpccc_batch_launch": ([P, P], [None, None]),
+        "wpccc_batch_status": ([P, P], [None, None]),
+        "wpccc_batch_info": ([P, P, P], [None, None, None]),
+    }
+    for name, (types, args) in calls.items():
+        f = getattr(lib, name)
+        f.argtypes = types
+        assert f(*args) == EINVAL, name
+        assert name.encode() in lib.wpccc_last_error() or b"null" in lib.wpccc_last_error(), name
+    lib.wpccc_batch_destroy.argtypes = [P]
+    assert lib.wpccc_batch_destroy(None) == 0
