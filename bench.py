@@ -70,7 +70,7 @@ def _measured_bf16() -> float:
 
 BF16_MEASURED_TFLOPS = _measured_bf16()
 CONFIG_DESC_C6 = ("two-centre bare C6+ on H (Z_T=1, Z_P=6): hydrogenic n<=6 + 20 Coulomb wave-packet bins per "
-                  "l<=5 (k<=4) on each centre, all m, N_T=N_P=811, N=1622; 48x48 (eta,tau) nodes; Nr=2000 to "
+                  "l<=5 (k<=4) on each centre, all m, N_T=N_P=811, N=1622; 128x48 (eta,tau) nodes; Nr=2000 to "
                   "100 a.u.; v=2; 16 b uniform in [0.5,15]; the paper's geometric z-grid, z_min=1e-3, "
                   "|z|<=50, 500 nodes per side (1000 RK4 steps)")
 CONFIG_DESC = ("two-centre p+H (Z_T=Z_P=1): hydrogenic n<=4 + 10 Coulomb wave-packet bins per l<=3 (k<=3) "
