@@ -2,14 +2,16 @@
 //
 // Values are carried as unevaluated sums of two floats ("double-float", hi + lo with |lo| <= ulp(hi)),
 // about 48 significant bits, so that the per-node products run on the FP32 pipe instead of the
-// much narrower FP64 pipe.  For the tensor cores, each value of a 32-node chunk is written in fixed
-// point against a power-of-two scale s chosen from the largest |value| of its row in the chunk,
+// much narrower FP64 pipe.  For the tensor cores, each value of a 128-node window (four 32-node
+// chunks) is written in fixed point against a power-of-two scale s chosen from the largest |value| of
+// its row in the window,
 //   x = s sum_{i < OZ_SLICES} k_i 2^(-8 i),   k_i integers with |k_i| <= 129,
 // and slice i is stored as the bf16 number k_i 2^(-8 i), which is exact (k_i has at most 8 significant
 // bits).  This is the error-free splitting of Ozaki, Ogita, Oishi and Rump (2012) with a fixed-point
-// grid per chunk.  Seven slices keep 55 bits below the chunk maximum; the products of two sliced values
-// with i + j = L are integers times 2^(-8 L) whose sums over 32 nodes stay below 2^22 units, so the
-// tensor core's FP32 accumulator holds each level exactly.
+// grid per window.  Seven slices keep 55 bits below the window maximum; the products of two sliced
+// values with i + j = L <= 3 (at most four per level) are integers times 2^(-8 L) whose sums over 128
+// nodes stay below 4 x 128 x 129^2 < 2^24 units, so the tensor core's FP32 accumulator holds each of
+// those levels exactly; levels 4 to 6 share one rounded accumulator.
 #pragma once
 
 #include <cuda_bf16.h>
