@@ -18,9 +18,9 @@
 // fifth, whose FP32 rounding over its 144 MMAs stays near 2^-48 of the window's largest term; levels
 // >= 7 are dropped (below 2^-53).  Per window the epilogue forms s_m s_n (L0 + L1 + L2 + L3 + T) with
 // the exact parts folded into double-float running sums (two TwoSums), so the result carries about
-// 2^-46 of the largest term.  With SL = 3 (levels 0-2, six products, three exact accumulators) the
-// result carries about 2^-22 of the largest term, the FP32 level, without the truncation bias of the
-// tensor core's FP32 accumulation.
+// 2^-46 of the largest term.  With SL = 3 (levels 0-2, six products, three exact accumulators) each
+// operand keeps 23 bits below its row's window maximum, and a window's sum errs by up to about 2^-20 of
+// its largest term: the FP32 level, without the truncation bias of the tensor core's FP32 accumulation.
 //
 // Pipeline per CTA (416 threads): warps 0-11 generate the Bw tiles (64-byte swizzled K-major rows) and
 // drain the accumulators; warp 12 issues the TMA loads of the table tiles (cp.async.bulk.tensor, 64-byte
