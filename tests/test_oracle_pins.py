@@ -367,3 +367,57 @@ def test_interaction_picture_mistakes_fail(schroedinger_case, mistake, monkeypat
         monkeypatch.setattr(O, "coupling_M", lambda bs, b, v, z: -_COUPLING(bs, b, v, z))
     P = O.probabilities(O.propagate(basis, b, v, zg))
     assert np.abs(P - ref).max() > 1e-4
+
+
+@pytest.fixture(scope="module")
+def schroedinger_two_centre():
+    # Two-centre p + H, tiny basis (target 1s, 2s, 2p; projectile 1s, 2p), v = 1.2. Without the energy
+    # phases the oracle's system reads i v S0 da/dz = (S0 diag(eps) + V0) a, with S0 and V0 the blocks of
+    # Eq. 1 at phase zero (K, Q rotated from the molecular frame; D_T, D_P; lower-left Q^+). Reference: that
+    # ODE in the form da/dz = -(i/v)(diag(eps) + S0^-1 V0) a, integrated by scipy's DOP853 at rtol 1e-11.
+    from scipy.integrate import solve_ivp
+    g = wi.radial_grid(1000)
+    T = _centre(1.0, [(1, 0), (2, 0), (2, 1)], g, eps=[-0.5, -0.125, -0.125])
+    P = _centre(1.0, [(1, 0), (2, 1)], g, eps=[-0.5, -0.125])
+    basis = wi.Basis(grid=g, T=T, P=P, quad=wi.make_quadrature(24, 24, 0.5), Z_T=1.0, Z_P=1.0)
+    b, v, z0, z1 = 1.0, 1.2, -6.0, 6.0
+    NT, N = T.N, basis.N
+    eps = np.concatenate([T.st_eps, P.st_eps])
+
+    def generator(z):
+        R = math.hypot(b, z)
+        th = math.acos(z / R)
+        Smol, Qmol = O.molecular_integrals(basis, b, v, z)
+        K, Q = O.rotate(T, P, Smol, th), O.rotate(T, P, Qmol, th)
+        S0 = np.eye(N, dtype=np.complex128)
+        S0[:NT, NT:] = K
+        S0[NT:, :NT] = K.conj().T
+        V0 = np.zeros((N, N), dtype=np.complex128)
+        V0[:NT, :NT] = O.direct_block(g, T, 1.0, R, z / R, other_at_minus_R=False)
+        V0[NT:, NT:] = O.direct_block(g, P, 1.0, R, z / R, other_at_minus_R=True)
+        V0[:NT, NT:] = Q
+        V0[NT:, :NT] = Q.conj().T
+        return (-1j / v) * (np.diag(eps) + np.linalg.solve(S0, V0))
+
+    a0 = np.zeros(N, dtype=np.complex128)
+    a0[0] = 1.0
+    sol = solve_ivp(lambda z, a: generator(z) @ a, (z0, z1), a0, method="DOP853", rtol=1e-11, atol=1e-13)
+    assert sol.status == 0
+    return basis, b, v, wi.uniform_zgrid(z0, z1, 0.04), np.abs(sol.y[:, -1]) ** 2
+
+
+def test_two_centre_interaction_picture_matches_schroedinger_picture(schroedinger_two_centre):
+    # |a|^2 = |c|^2: fixes the energy phases of K and Q (target-minus-projectile energies), the solve
+    # M = -(i/v) S^-1 H of Eq. 4 with phased S, and Algorithm 1 in the two-centre form
+    basis, b, v, zg, ref = schroedinger_two_centre
+    P = O.probabilities(O.propagate(basis, b, v, zg))
+    assert P[basis.T.N] > 0.1                    # capture into the projectile 1s is strong
+    assert np.abs(P - ref).max() < 1e-8
+
+
+def test_two_centre_phase_mistake_fails(schroedinger_two_centre, monkeypatch):
+    # the phases of the target-projectile blocks with the opposite sign (diagonal blocks unchanged)
+    basis, b, v, zg, ref = schroedinger_two_centre
+    monkeypatch.setattr(O, "phases", lambda er, ec, z, v: _PHASES(er, ec, z if er is ec else -z, v))
+    P = O.probabilities(O.propagate(basis, b, v, zg))
+    assert np.abs(P - ref).max() > 1e-2
