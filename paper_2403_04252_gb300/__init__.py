@@ -276,24 +276,14 @@ class Basis:
         """Amplitudes at the end of each path (``wpccc_propagate``); `c` (n_paths, N) complex128 on the
         device is advanced in place (default: Algorithm 1's initial state)."""
         import torch
-        b = np.atleast_1d(np.asarray(b, dtype=np.float64))
-        v = np.broadcast_to(np.asarray(v, dtype=np.float64), b.shape)
-        if isinstance(zgrids, np.ndarray) and zgrids.ndim == 1:
-            zgrids = [zgrids] * b.size
-        nz = np.array([len(zg) for zg in zgrids], dtype=np.int32)
-        zc = np.concatenate([np.asarray(zg, dtype=np.float64) for zg in zgrids])
+        keep = []
+        pd = _paths_desc(b, v, zgrids, keep)
         if c is None:
-            c = torch.zeros((b.size, self.N), dtype=torch.complex128, device=torch.device("cuda", self.device))
+            c = torch.zeros((pd.n_paths, self.N), dtype=torch.complex128, device=torch.device("cuda", self.device))
             c[:, 0] = 1.0
-        bb, bp = _arr(b, np.float64)
-        vv, vp = _arr(v, np.float64)
-        nn, np_ = _arr(nz, np.int32)
-        zz, zp = _arr(zc, np.float64)
-        pd = _PathsDesc(n_paths=int(b.size), b=bp, v=vp, n_z=np_, z=zp)
         _check(_lib.wpccc_propagate(self._h, C.byref(pd), int(precision_mode), int(batch_mode), _ptr(c),
                                     _stream(stream)), "wpccc_propagate")
         return c
-
 
     def propagate_adjoint(self, b, v, zgrids, g, checkpoint_every: int = 50, c=None, stream=None):
         """Observables P[p, o] = sum_i g[o, i] |c_i|^2 at the end of each path and their derivatives
