@@ -216,11 +216,20 @@ static void free_centre(CentreDev& c) {
     c = CentreDev();
 }
 
+static bool all_finite(const double* x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
 static wpccc_status check_centre(const wpccc_centre_desc& d, int Nr, bool all_m, const char* name) {
     std::string n(name);
     if (d.n_rad < 1 || !d.rad_l || !d.f) return fail(WPCCC_EINVAL, n + ": n_rad < 1 or null rad_l/f");
     if (d.n_states < 1 || !d.st_rad || !d.st_m || !d.st_eps)
         return fail(WPCCC_EINVAL, n + ": n_states < 1 or null state arrays");
+    if (!std::isfinite(d.Z)) return fail(WPCCC_EINVAL, n + ": non-finite charge");
+    if (!all_finite(d.f, (size_t)d.n_rad * Nr)) return fail(WPCCC_EINVAL, n + ": non-finite radial table");
+    if (!all_finite(d.st_eps, (size_t)d.n_states)) return fail(WPCCC_EINVAL, n + ": non-finite state energy");
     for (int a = 0; a < d.n_rad; ++a)
         if (d.rad_l[a] < 0 || d.rad_l[a] > WPCCC_LMAX)
             return fail(WPCCC_EINVAL, n + ": rad_l out of range 0..WPCCC_LMAX");
@@ -238,7 +247,6 @@ static wpccc_status check_centre(const wpccc_centre_desc& d, int Nr, bool all_m,
             for (int m = -d.rad_l[a]; m <= d.rad_l[a]; ++m)
                 if (!seen[(size_t)a * (2 * WPCCC_LMAX + 1) + m + WPCCC_LMAX])
                     return fail(WPCCC_EINVAL, n + ": two-centre mode needs every m of every radial function");
-    (void)Nr;
     return WPCCC_OK;
 }
 
@@ -339,6 +347,8 @@ extern "C" wpccc_status wpccc_basis_create(const wpccc_basis_desc* d, int device
     if (!(d->r[0] > 0.0)) return fail(WPCCC_EINVAL, "r[0] must be > 0");
     for (int i = 1; i < d->Nr; ++i)
         if (!(d->r[i] > d->r[i - 1])) return fail(WPCCC_EINVAL, "r must be strictly increasing");
+    if (!std::isfinite(d->r[d->Nr - 1]) || !all_finite(d->w, (size_t)d->Nr))
+        return fail(WPCCC_EINVAL, "non-finite r or w");
     const bool two = d->n_centres == 2;
     wpccc_status st = check_centre(d->T, d->Nr, two, "target");
     if (st != WPCCC_OK) return st;
@@ -346,7 +356,11 @@ extern "C" wpccc_status wpccc_basis_create(const wpccc_basis_desc* d, int device
         if ((st = check_centre(d->P, d->Nr, true, "projectile")) != WPCCC_OK) return st;
         if (d->Geta < 1 || d->Gtau < 1 || !d->s || !d->ws || !d->tau || !d->wtau)
             return fail(WPCCC_EINVAL, "two-centre mode needs the (eta, tau) quadrature");
-        if (!(d->gamma > 0.0)) return fail(WPCCC_EINVAL, "gamma must be > 0");
+        if (!(d->gamma > 0.0) || !std::isfinite(d->gamma)) return fail(WPCCC_EINVAL, "gamma must be finite and > 0");
+        if (!all_finite(d->s, (size_t)d->Geta) || !all_finite(d->ws, (size_t)d->Geta) ||
+            !all_finite(d->tau, (size_t)d->Gtau) || !all_finite(d->wtau, (size_t)d->Gtau) ||
+            !std::isfinite(d->mp_c) || !std::isfinite(d->mp_a) || !std::isfinite(d->mp_b))
+            return fail(WPCCC_EINVAL, "non-finite quadrature or model-potential parameter");
     }
     int N = d->T.n_states + (two ? d->P.n_states : 0);
     if (N > WPCCC_NMAX) return fail(WPCCC_EINVAL, "N exceeds WPCCC_NMAX");
@@ -554,6 +568,8 @@ extern "C" wpccc_status wpccc_basis_set_tangents(wpccc_basis B, int n_par, const
         return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: null pointer");
     for (int k = 0; k < 4 * n_par; ++k)
         if (!std::isfinite(dexplicit[k])) return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: non-finite dexplicit");
+    if (!all_finite(dfT, (size_t)n_par * B->T.n_rad * B->Nr) || !all_finite(dfP, (size_t)n_par * B->P.n_rad * B->Nr))
+        return fail(WPCCC_EINVAL, "wpccc_basis_set_tangents: non-finite radial derivative table");
     WPCCC_CUDA(cudaSetDevice(B->device));
     WPCCC_CUDA(cudaDeviceSynchronize());
     void* old[] = {B->tanT.df, B->tanT.dF, B->tanP.df, B->tanP.dF, B->deps};

@@ -92,3 +92,30 @@ def test_null_handles_are_argument_errors_without_gpu(lib):
         assert name.encode() in lib.wpccc_last_error() or b"null" in lib.wpccc_last_error(), name
     lib.wpccc_batch_destroy.argtypes = [P]
     assert lib.wpccc_batch_destroy(None) == 0
+
+
+def test_non_finite_inputs_are_argument_errors_without_gpu():
+    # corrupt tables are refused at basis creation, before any device work: a NaN radial value, an
+    # infinite state energy, a NaN quadrature weight
+    import numpy as np
+    import wpccc_inputs as wi
+    import paper_2403_04252_gb300 as w
+
+    def corrupt(kind):
+        b = wi.make_basis(1.0, 1.0, 2, 1, 1, 2.0, True, Nr=200, Geta=8, Gtau=8)
+        if kind == "f":
+            b.T.f = b.T.f.copy()
+            b.T.f[1, 50] = np.nan
+        elif kind == "eps":
+            b.P.st_eps = b.P.st_eps.copy()
+            b.P.st_eps[2] = np.inf
+        else:
+            b.quad.ws = b.quad.ws.copy()
+            b.quad.ws[3] = np.nan
+        return b
+
+    for kind, words in (("f", b"radial table"), ("eps", b"state energy"), ("quad", b"quadrature")):
+        with pytest.raises(w.WpcccError) as e:
+            w.Basis(corrupt(kind))
+        assert e.value.status == w.EINVAL, kind
+        assert words in w._lib.wpccc_last_error(), kind
