@@ -140,8 +140,9 @@ typedef struct {
  * the radial functions, energies and quadrature rules, and computes on the GPU the
  * radial multipole table F_{n'l'nl lambda}(r_i) of Eq. 7 at every grid radius and
  * the angular coefficients of Eq. 6.  Synchronous.  On success *out owns device
- * memory until wpccc_basis_destroy.  Errors: EINVAL (inconsistent description),
- * ENOMEM, ECUDA.
+ * memory until wpccc_basis_destroy.  Errors: EINVAL (inconsistent description, or a
+ * non-finite value in r, w, the radial tables, energies, charges, quadrature rules or
+ * model-potential parameters; checked on the host before any device work), ENOMEM, ECUDA.
  */
 WPCCC_API wpccc_status wpccc_basis_create(const wpccc_basis_desc* desc, int device, wpccc_basis* out);
 
