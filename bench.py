@@ -94,25 +94,29 @@ def _reasons(mask: int) -> list:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running. start() returns once
+    the first sample has arrived (or after 3 s), so that sampling is live when the timed region begins."""
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, cmd=None):
         self.index = index
+        self.cmd = cmd
         self.samples = []
         self.proc = None
         self.thread = None
+        self.first = threading.Event()
 
     def start(self):
         q = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active"
+        cmd = self.cmd or ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                           "--format=csv,noheader,nounits", "-lms", "100"]
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        self.first.wait(timeout=3.0)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -120,6 +124,7 @@ class ClockSampler:
             if len(parts) >= 4:
                 try:
                     self.samples.append((float(parts[0]), float(parts[1]), float(parts[2]), int(parts[3], 16)))
+                    self.first.set()
                 except ValueError:
                     pass
 
