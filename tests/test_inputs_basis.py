@@ -112,3 +112,30 @@ def test_geometric_zgrid_of_section_two():
     assert np.all(np.diff(z) > 0) and np.array_equal(z[:500], -z[:500:-1])
     assert z[501] == pytest.approx(1e-3 * 1e5 ** (1 / 500), rel=1e-14)
     assert z[-1] == pytest.approx(100.0, rel=1e-14) and z[502] / z[501] == pytest.approx(z[-1] / z[-2], rel=1e-12)
+
+
+def test_observable_and_cross_section_weights():
+    # capture = every bound projectile state, 2p excitation = the target's 2p states (all m)
+    b = wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=300, Geta=8, Gtau=8)
+    g = wi.observable_weights(b)
+    T, P = b.T, b.P
+    assert g.shape == (2, b.N) and set(np.unique(g)) <= {0.0, 1.0}
+    assert g[0, :T.N].sum() == 0 and g[0, T.N:].sum() == 2 + 3          # projectile 1s, 2s, 2p(m = -1, 0, 1)
+    assert g[1, T.N:].sum() == 0 and g[1, :T.N].sum() == 3              # target 2p(m = -1, 0, 1)
+    assert np.all(T.st_l[g[1, :T.N] == 1] == 1)
+    # sigma = 2 pi int b P(b) db: exact for P linear in b on [0, b_max] by the trapezoid rule with b = 0
+    bs = np.linspace(0.5, 6.0, 12)
+    wts = wi.cross_section_weights(bs)
+    assert np.isclose(wts @ np.ones_like(bs), np.pi * bs[-1] ** 2)   # P = 1: pi b_max^2 (b P linear)
+    # and b P(b) = 0 at the added node b = 0: for P = b the rule's error is the trapezoid's on b^2
+    h = np.diff(np.concatenate([[0.0], bs]))
+    assert np.isclose(wts @ bs, 2.0 * np.pi * (bs[-1] ** 3 / 3.0 + np.sum(h ** 3) / 6.0))
+
+
+def test_model_potential_parameters_are_seeded_within_five_percent():
+    a0, b0 = wi.li_parameters(0)
+    assert (a0, b0) == wi.li_parameters(0)
+    for seed in range(20):
+        a, b = wi.li_parameters(seed)
+        assert abs(a / 3.0 - 1.0) < 0.05 and abs(b / 1.5 - 1.0) < 0.05
+    assert wi.li_parameters(1) != (a0, b0)
