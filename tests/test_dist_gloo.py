@@ -88,3 +88,12 @@ def test_single_process_fallbacks():
     # trapezoid rule is exact for P = const on the linear b P(b): 2 pi * b_max^2 / 2
     b = np.linspace(0.5, 4.0, 8)
     assert np.isclose(D.cross_sections(b, np.ones(8))[0], np.pi * 4.0 ** 2)
+
+
+def test_cross_sections_match_the_input_generator_weights():
+    # the package's cross-section rule and the workload generator's per-path weights are the same rule
+    import wpccc_inputs as wi
+    D = _dist_module()
+    b = np.linspace(0.2, 12.0, 32)
+    P = _fake_observables(b)
+    assert np.allclose(D.cross_sections(b, P), wi.cross_section_weights(b) @ P, rtol=1e-14, atol=0)
