@@ -119,3 +119,18 @@ def test_non_finite_inputs_are_argument_errors_without_gpu():
             w.Basis(corrupt(kind))
         assert e.value.status == w.EINVAL, kind
         assert words in w._lib.wpccc_last_error(), kind
+
+
+def test_binding_constants_match_header():
+    # every status code and #define the binding mirrors has the header's value
+    import paper_2403_04252_gb300 as w
+    src = open(os.path.join(ROOT, "include", "wpccc.h")).read()
+    enum = {k: int(v) for k, v in re.findall(r"\bWPCCC_([A-Z]+)\s*=\s*(\d+)", src)}
+    for name in ("OK", "EINVAL", "ENOMEM", "ESINGULAR", "ENONFINITE", "ECUDA", "EUNSUPPORTED"):
+        assert getattr(w, name) == enum[name], name
+    defines = {k: v for k, v in re.findall(r"#define WPCCC_(\w+)\s+(\S.*)", src)}
+    for name in ("LMAX", "NMAX", "MAX_PARAMS", "MAX_REFINE", "SOLVE_STAGE", "SOLVE_MATRIX", "SOLVE_SCHUR",
+                 "RK4_AUTO", "RK4_SHARED", "RK4_GLOBAL"):
+        assert getattr(w, name) == int(defines[name]), name
+    assert w.NOALLOC_SCRATCH_BYTES == 64 << 20 and "64 << 20" in defines["NOALLOC_SCRATCH_BYTES"]
+    assert len(w.PROF_CATEGORIES) == int(defines["PROF_N"])
