@@ -172,6 +172,19 @@ WPCCC_API wpccc_status wpccc_matrix_elements(wpccc_basis basis, double b, double
                                    void* S, void* H, void* stream);
 
 /*
+ * wpccc_matrix_elements with the element arithmetic of a reduced-precision form, to measure its element
+ * error against the FP64 elements (the paper has no counterpart):
+ *   precision_mode 0 FP64 (= wpccc_matrix_elements), 1 the Eq. 9 contraction on the FP32 pipe,
+ *   3 the Eq. 9 contraction on the tensor cores at FP32 level, 4 the same to FP64 accuracy (see
+ *   wpccc_propagate).  S and H are returned in FP64.
+ * Errors: as wpccc_matrix_elements; EUNSUPPORTED for other modes, one-centre bases or model-potential
+ * targets in modes 1, 3 and 4.
+ */
+WPCCC_API wpccc_status wpccc_matrix_elements_precision(wpccc_basis basis, double b, double v, int nz,
+                                                       const double* z, void* S, void* H, int precision_mode,
+                                                       void* stream);
+
+/*
  * wpccc_matrix_elements without any device allocation.  The paper has no
  * counterpart: this is for callers that cannot let the library allocate device
  * memory inside a call, e.g. a host framework that reserved the device memory up
@@ -186,25 +199,16 @@ WPCCC_API wpccc_status wpccc_matrix_elements(wpccc_basis basis, double b, double
  * calls whose GPU work overlaps (other streams, other threads, other bases) race
  * and corrupt each other's results; serialise them.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Positions are
- * processed in groups that fit the array, and the call waits for each group on
- * `stream`.  Errors: EINVAL (as wpccc_matrix_elements, or a basis whose single
- * position needs more scratch than the array holds; the message states both
- * sizes), ECUDA.  The basis itself must have been created beforehand.
+ * current and keeps it for the life of the process, so a cudaDeviceReset (or any
+ * other end of the device's primary context) invalidates the library for that
+ * device.  Positions are processed in groups that fit the array (at most 65535 per
+ * group), and the call waits for each group with cudaStreamSynchronize(stream):
+ * the call blocks, and it must not be issued while `stream` (or, for the legacy
+ * default stream, any stream) is being captured into a CUDA graph.  Errors: EINVAL
+ * (as wpccc_matrix_elements, or a basis whose single position needs more scratch
+ * than the array holds; the message states both sizes), ECUDA.  The basis itself
+ * must have been created beforehand.
  */
-/*
- * wpccc_matrix_elements with the element arithmetic of a reduced-precision form, to measure its element
- * error against the FP64 elements (the paper has no counterpart):
- *   precision_mode 0 FP64 (= wpccc_matrix_elements), 1 the Eq. 9 contraction on the FP32 pipe,
- *   3 the Eq. 9 contraction on the tensor cores at FP32 level, 4 the same to FP64 accuracy (see
- *   wpccc_propagate).  S and H are returned in FP64.
- * Errors: as wpccc_matrix_elements; EUNSUPPORTED for other modes, one-centre bases or model-potential
- * targets in modes 1, 3 and 4.
- */
-WPCCC_API wpccc_status wpccc_matrix_elements_precision(wpccc_basis basis, double b, double v, int nz,
-                                                       const double* z, void* S, void* H, int precision_mode,
-                                                       void* stream);
-
 #define WPCCC_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 WPCCC_API wpccc_status wpccc_matrix_elements_noalloc(wpccc_basis basis, double b, double v, int nz,
                                                      const double* z, void* S, void* H, void* stream);

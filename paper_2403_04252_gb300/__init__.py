@@ -132,6 +132,36 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _check_matrices(S, H, nz: int, N: int, device: int, where: str) -> None:
+    """Refuses, before any launch, output tensors the kernels would write past or misread: both must be
+    complex128, contiguous, on the basis' CUDA device and hold at least nz * N * N elements."""
+    for name, t in (("S", S), ("H", H)):
+        if t is None:
+            raise ValueError(f"{where}: {name} is required")
+        if str(t.dtype) != "torch.complex128":
+            raise ValueError(f"{where}: {name} must be complex128, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{where}: {name} must be contiguous")
+        if t.numel() < nz * N * N:
+            raise ValueError(f"{where}: {name} holds {t.numel()} elements, {nz} positions of N = {N} need "
+                             f"{nz * N * N}")
+        if t.device.type != "cuda" or t.device.index != device:
+            raise ValueError(f"{where}: {name} is on {t.device}, the basis is on cuda:{device}")
+
+
+def _check_amplitudes(c, n_paths: int, N: int, device: int, where: str) -> None:
+    """Refuses an amplitude tensor the kernels would misread: complex128, contiguous, on the basis' device,
+    at least n_paths * N elements."""
+    if str(c.dtype) != "torch.complex128":
+        raise ValueError(f"{where}: c must be complex128, got {c.dtype}")
+    if not c.is_contiguous():
+        raise ValueError(f"{where}: c must be contiguous")
+    if c.numel() < n_paths * N:
+        raise ValueError(f"{where}: c holds {c.numel()} elements, {n_paths} paths of N = {N} need {n_paths * N}")
+    if c.device.type != "cuda" or c.device.index != device:
+        raise ValueError(f"{where}: c is on {c.device}, the basis is on cuda:{device}")
+
+
 def natural(t):
     """(batch, row, column) view of column-major matrix storage."""
     return t.transpose(-1, -2)
@@ -244,6 +274,7 @@ class Basis:
             S = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
         if H is None:
             H = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
+        _check_matrices(S, H, z.size, self.N, self.device, "matrix_elements")
         _check(_lib.wpccc_matrix_elements(self._h, float(b), float(v), int(z.size), zp, _ptr(S), _ptr(H),
                                           _stream(stream)), "wpccc_matrix_elements")
         return S, H
@@ -259,6 +290,7 @@ class Basis:
             S = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
         if H is None:
             H = torch.empty((z.size, self.N, self.N), dtype=torch.complex128, device=dev)
+        _check_matrices(S, H, z.size, self.N, self.device, "matrix_elements_precision")
         _check(_lib.wpccc_matrix_elements_precision(self._h, float(b), float(v), int(z.size), zp, _ptr(S), _ptr(H),
                                                     int(precision_mode), _stream(stream)),
                "wpccc_matrix_elements_precision")
@@ -268,6 +300,7 @@ class Basis:
         """Same as matrix_elements into caller-owned S, H, but the library allocates no device memory:
         its scratch is a fixed 64 MiB array shared by every call on the device (serialise calls)."""
         z, zp = _arr(np.atleast_1d(z), np.float64)
+        _check_matrices(S, H, z.size, self.N, self.device, "matrix_elements_noalloc")
         _check(_lib.wpccc_matrix_elements_noalloc(self._h, float(b), float(v), int(z.size), zp, _ptr(S), _ptr(H),
                                                   _stream(stream)), "wpccc_matrix_elements_noalloc")
         return S, H
@@ -281,6 +314,7 @@ class Basis:
         if c is None:
             c = torch.zeros((pd.n_paths, self.N), dtype=torch.complex128, device=torch.device("cuda", self.device))
             c[:, 0] = 1.0
+        _check_amplitudes(c, pd.n_paths, self.N, self.device, "propagate")
         _check(_lib.wpccc_propagate(self._h, C.byref(pd), int(precision_mode), int(batch_mode), _ptr(c),
                                     _stream(stream)), "wpccc_propagate")
         return c
@@ -297,6 +331,7 @@ class Basis:
         if c is None:
             c = torch.zeros((n_paths, self.N), dtype=torch.complex128, device=dev)
             c[:, 0] = 1.0
+        _check_amplitudes(c, n_paths, self.N, self.device, "propagate_adjoint")
         g, gp = _arr(np.atleast_2d(g), np.float64)
         if g.ndim != 2 or g.shape[1] != self.N:
             raise ValueError(f"observable weights must have shape (n_obs, {self.N})")
@@ -329,6 +364,10 @@ class Batch:
     def __init__(self, sets, c, precision_mode: int = 0, autotune: bool = True):
         keep = []
         n = len(sets)
+        if len(c) != n:
+            raise ValueError(f"Batch: {n} sets but {len(c)} amplitude tensors")
+        for (g, b, _, _), t in zip(sets, c):
+            _check_amplitudes(t, int(np.atleast_1d(b).size), g.N, g.device, "Batch")
         descs = (_PathsDesc * n)(*[_paths_desc(b, v, zg, keep) for (_, b, v, zg) in sets])
         handles = (C.c_void_p * n)(*[g._h.value for (g, _, _, _) in sets])
         cptrs = (C.c_void_p * n)(*[t.data_ptr() for t in c])

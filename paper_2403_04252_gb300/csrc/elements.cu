@@ -1488,7 +1488,8 @@ static wpccc_status matrix_elements_prec(wpccc_basis B, double b, double v, int 
     const ElemScratch L = elem_scratch_layout(B);
     // evaluations per launch bounded by the workspace limit
     size_t per = L.bytes_per_eval + sizeof(EvalDesc);
-    int chunk = (int)std::min<size_t>((size_t)nz, std::max<size_t>(1, (B->ws_limit - 256) / per));
+    int chunk = (int)std::min<size_t>({(size_t)nz, (size_t)MAX_EVALS_PER_LAUNCH,
+                                       std::max<size_t>(1, (B->ws_limit - 256) / per)});
     size_t need = (size_t)chunk * L.bytes_per_eval + 256 + (size_t)chunk * sizeof(EvalDesc);
     wpccc_status s = ensure_workspace(B, need);
     if (s != WPCCC_OK) return s;

@@ -7,6 +7,7 @@
 // runs the same element kernels as wpccc_matrix_elements with its scratch memory
 // (node tables, molecular-frame blocks, the position list) in the fixed array
 // below, which every GPU that loads this library holds until the process exits.
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -23,7 +24,9 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static std::mutex g_noalloc_mutex;
 static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device, looked up once per device and kept for the
+// life of the process: a cudaDeviceReset (a new primary context) leaves the kept address stale, so the
+// library does not support calls on a device after it has been reset.
 static wpccc_status noalloc_scratch(int device, void** out) {
     if (device < 0 || device >= NOALLOC_MAX_DEVICES)
         return fail(WPCCC_EINVAL, "wpccc_matrix_elements_noalloc: device index beyond 63");
@@ -48,24 +51,21 @@ extern "C" wpccc_status wpccc_matrix_elements_noalloc(wpccc_basis B, double b, d
     if (nz < 1) return fail(WPCCC_EINVAL, "wpccc_matrix_elements_noalloc: nz < 1");
     if (!(b > 0.0) || !(v > 0.0)) return fail(WPCCC_EINVAL, "wpccc_matrix_elements_noalloc: b and v must be > 0");
     const ElemScratch L = elem_scratch_layout(B);
-    // one position needs its element scratch plus its entry of the position list (both 256-aligned)
-    const size_t list_slot = 256;
-    const size_t per = L.bytes_per_eval + sizeof(EvalDesc);
-    if (L.bytes_per_eval + list_slot > NOALLOC_SCRATCH_BYTES)
+    // one position needs its element scratch plus its entry of the position list (the list is rounded up
+    // to 256 bytes, so 256 bytes cover that rounding and any list of up to 256 / sizeof(EvalDesc) entries)
+    if (L.bytes_per_eval + 256 > NOALLOC_SCRATCH_BYTES)
         return fail(WPCCC_EINVAL, "wpccc_matrix_elements_noalloc: one position of this basis needs " +
-                                      std::to_string(L.bytes_per_eval + list_slot) +
+                                      std::to_string(L.bytes_per_eval + 256) +
                                       " bytes of scratch, more than the fixed " +
                                       std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes");
     WPCCC_CUDA(cudaSetDevice(B->device));
     void* base = nullptr;
     wpccc_status s = noalloc_scratch(B->device, &base);
     if (s != WPCCC_OK) return s;
-    // positions per launch: the list (rounded up to 256 bytes) and the scratch must fit
-    int chunk = nz;
-    while (chunk > 1 &&
-           ((chunk * sizeof(EvalDesc) + 255) / 256) * 256 + (size_t)chunk * L.bytes_per_eval > NOALLOC_SCRATCH_BYTES)
-        --chunk;
-    (void)per;
+    // positions per launch: the list (rounded up to 256 bytes) and the scratch fit the array, and the element
+    // kernels take one grid row per position (at most 65535)
+    const int chunk = (int)std::min<size_t>(
+        {(size_t)nz, (size_t)MAX_EVALS_PER_LAUNCH, (NOALLOC_SCRATCH_BYTES - 256) / (L.bytes_per_eval + sizeof(EvalDesc))});
     char* wsb = static_cast<char*>(base);
     EvalDesc* dev_ev = reinterpret_cast<EvalDesc*>(wsb);
     void* scratch = wsb + ((chunk * sizeof(EvalDesc) + 255) / 256) * 256;

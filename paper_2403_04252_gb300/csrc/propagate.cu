@@ -390,9 +390,14 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
               (P.mixed ? align256((size_t)np * mat * sizeof(float2)) : 0) + align256((size_t)np * N * sizeof(int)) +
               align256((size_t)zoff[np] * sizeof(double)) + align256((size_t)total_evals * sizeof(EvalDesc)) +
               align256((size_t)np * P.max_steps * sizeof(PathChunk)) + 16 * 256;
+    // a chunk evaluates at most 2C + 1 positions per path in one launch of each element kernel
+    if (3LL * np > MAX_EVALS_PER_LAUNCH)
+        return fail(WPCCC_EINVAL, "wpccc_propagate: more than " + std::to_string(MAX_EVALS_PER_LAUNCH / 3) +
+                                      " paths in one call");
+    const int C_launch = (int)((MAX_EVALS_PER_LAUNCH / np - 1) / 2);
     int C;
     if (C_request > 0) {
-        C = std::min(C_request, P.max_steps);
+        C = std::min({C_request, P.max_steps, C_launch});
     } else {
         // Two chunks are in flight (the RK4 sweep of one overlaps the assembly of the next), so each
         // buffer set gets half the budget.  Aim for at least four chunks per call, each with enough
@@ -404,7 +409,8 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
         const long long cap_steps = std::max<long long>(1, (cap_evals - np) / (2LL * np));
         const long long fill_steps = std::max<long long>(1, (2LL * dev_sms / np + 1) / 2);
         long long want = std::max<long long>((P.max_steps + 3) / 4, fill_steps);
-        C = (int)std::max<long long>(1, std::min<long long>({(long long)P.max_steps, cap_steps, want}));
+        C = (int)std::max<long long>(1, std::min<long long>({(long long)P.max_steps, cap_steps, want,
+                                                              (long long)C_launch}));
     }
     P.C = C;
     P.n_chunks = (P.max_steps + C - 1) / C;

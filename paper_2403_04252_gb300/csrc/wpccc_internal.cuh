@@ -144,6 +144,9 @@ struct wpccc_basis_s {
 namespace wpccc {
 
 // one projectile position to evaluate
+// The element kernels take one grid row (gridDim.y) per position, so one launch holds at most this many.
+constexpr int MAX_EVALS_PER_LAUNCH = 65535;
+
 struct EvalDesc {
     double b, v, z;
     int path;
