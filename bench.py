@@ -60,15 +60,18 @@ BATCH_FORMS = ((0, 2, "fp64"), (4, 2, "fp64-tensor-core"), (5, 4, "fp64-tc-refin
 SOLVE_MODES = {"stage": lambda w: w.SOLVE_STAGE, "matrix": lambda w: w.SOLVE_MATRIX, "schur": lambda w: w.SOLVE_SCHUR}
 
 
-def _measured_bf16() -> float:
+def _measured_peak(key: str, fallback: float) -> float:
+    """A peak from MEASURED_PEAKS.json (measured on the GB300s), else the stated fallback figure."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["bf16_tflops"])
-    except (OSError, KeyError, ValueError):
-        return 1900.0   # fallback figure for a GB300 when the measured file is absent
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError, TypeError):
+        return fallback
 
 
-BF16_MEASURED_TFLOPS = _measured_bf16()
+BF16_MEASURED_TFLOPS = _measured_peak("bf16_tflops", 1900.0)               # burst: a kernel timed alone
+BF16_SUSTAINED_TFLOPS = _measured_peak("bf16_tflops_sustained", 1700.0)    # a kernel timed inside a long step
+HBM_MEASURED_GBS = _measured_peak("hbm_gbs", 6800.0)
 CONFIG_DESC_C6 = ("two-centre bare C6+ on H (Z_T=1, Z_P=6): hydrogenic n<=6 + 20 Coulomb wave-packet bins per "
                   "l<=5 (k<=4) on each centre, all m, N_T=N_P=811, N=1622; 128x48 (eta,tau) nodes; Nr=2000 to "
                   "100 a.u.; v=2; 16 b uniform in [0.5,15]; the paper's geometric z-grid, z_min=1e-3, "
@@ -198,7 +201,7 @@ def run_reference(args) -> None:
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def run_batch(args) -> None:
+def run_batch(args) -> dict:
     """Batched form: six speeds (bases of different size), 64 paths each, uneven step counts (the
     same z extent at h = 0.1 v/1.5), captured into one CUDA graph with autotuned chunk schedules.
     Timed against the same sets propagated by separate wpccc_propagate calls (plain FP64 form)."""
@@ -339,26 +342,35 @@ def run_batch(args) -> None:
     e2e_s = time.perf_counter() - t0
     h2d = sum(t.numel() * 16 for t in c_host)
     d2h = sum(t.numel() * 8 for t in P_host)
-    # roofline of the dominant kernel (from the profiled separate calls: the same kernels)
-    dom = max(prof, key=lambda k: prof[k][0])
-    flops = {"mol_gemm": 0.0, "solve": 0.0}
-    tc64 = mode in (4, 5)
+    # roofline of every kernel category (from the profiled separate calls: the same kernels), the work
+    # summed over the six bases; the dominant category (largest device time) is the line's `roofline`
+    work = {}
+    cat_meta = {}
     for (g, b, v, seg), (vv, basis, _) in zip(sets, sets_in):
         evals = args.steps * b.size * (2 * (seg.size - 1) + 1)
         n_half = int(sum(1 for m in basis.P.st_m if m >= 0))
-        flops["mol_gemm"] += (28.0 if tc64 else 1.0) * 8.0 * basis.T.N * n_half * basis.quad.G * evals
-        if args.solve_mode == "schur":
-            flops["solve"] += (4.0 * basis.P.N ** 2 * basis.T.N + (4.0 / 3.0) * basis.P.N ** 3) * evals
-        else:
-            flops["solve"] += (8.0 / 3.0) * basis.N ** 3 * evals
-    dom_f = dom if dom in flops else "mol_gemm"
-    achieved = flops[dom_f] / (prof[dom_f][0] / 1e3) / 1e12
-    refined = mode == 5
-    dom_peak = (BF16_MEASURED_TFLOPS if (dom_f == "mol_gemm" and tc64)
-                else FP32_PEAK_TFLOPS if (dom_f == "solve" and refined) else FP64_PEAK_TFLOPS)
-    dom_kernel = {"mol_gemm": "k_mol_tc64" if tc64 else "k_mol_gemm<double>",
-                  "solve": ("k_schur_factor<float>" if args.solve_mode == "schur" else "k_lu_factor_f32") if refined
-                  else ("k_schur_factor<double>" if args.solve_mode == "schur" else "k_lu_solve")}[dom_f]
+        cats = _category_rooflines(basis, mode, args.solve_mode, basis.N, n_half)
+        cats["rk4"] = (_rk4_flops_per_step(mode, args.solve_mode, basis.N, basis.T.N, basis.P.N),
+                       ("alu", FP64_PEAK_TFLOPS, "TFLOP/s"), "k_rk4")
+        for k, (per_unit, meta, name) in cats.items():
+            units = args.steps * b.size * (seg.size - 1) if k == "rk4" else evals
+            work[k] = work.get(k, 0.0) + per_unit * units
+            cat_meta[k] = (meta, name)
+
+    def roof_b(key: str) -> dict:
+        k_ms, k_n = prof[key]
+        (bound, peak, unit), name = cat_meta[key]
+        ach = work[key] / (k_ms / 1e3) / (1e9 if unit == "GB/s" else 1e12)
+        return {"bound": bound, "kernel": name, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": None, "peak_source": _peak_source(bound, peak), "launch_ms_avg": k_ms / max(k_n, 1)}
+
+    timed = {k: prof[k][0] for k in work if k in prof and prof[k][1] > 0}
+    dom = max(timed, key=lambda k: timed[k])
+    roofline_b = roof_b(dom)
+    roofline_b["by_kernel"] = {k: {kk: vv for kk, vv in roof_b(k).items()
+                                   if kk in ("kernel", "bound", "achieved", "peak", "unit", "frac")}
+                               | {"ms": timed[k], "share": timed[k] / sum(timed.values())} for k in timed}
+    roofline_b["timing"] = "kernel times from the same sets' separate, profiled wpccc_propagate calls"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -380,16 +392,7 @@ def run_batch(args) -> None:
                                           "speedup": ms_seq / ms},
             "autotune": {"chunk_steps": [int(x) for x in chunk_steps],
                          "ms_per_rk4_step": [float(x) for x in tuned], "create_s": t_create},
-            "roofline": {"bound": "tensor" if dom_peak == BF16_MEASURED_TFLOPS else "alu", "kernel": dom_kernel,
-                         "achieved": achieved, "peak": dom_peak, "unit": "TFLOP/s",
-                         "frac": achieved / dom_peak, "traffic": None,
-                         "peak_source": ("measured bf16 dense tensor peak (MEASURED_PEAKS.json) against the "
-                                         "contraction's algorithmic flops times its 28 slice products")
-                         if dom_peak == BF16_MEASURED_TFLOPS else
-                         "FP32 pipe from unit counts and clocks (152 SMs x 128 FFMA/clk x 2.07 GHz)"
-                         if dom_peak == FP32_PEAK_TFLOPS else
-                         "FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
-                         "kernel time from the same sets' separate, profiled calls"},
+            "roofline": roofline_b,
             "kernel_ms_separate_calls": {k: v_[0] for k, v_ in prof.items()},
             "forms": {n: ({"value": f["value"], "ms_per_step": f["ms"] / args.steps, "create_s": f["create_s"],
                            "max_abs_prob_error_vs_fp64": f["err"],
@@ -405,13 +408,10 @@ def run_batch(args) -> None:
             "gpu_launches": int(sum(n for _, n in prof.values())), "clocks": clocks}
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    if rank == 0:
-        print(json.dumps(line))
     batch.close()
     for g, _, _, _ in sets:
         g.close()
-    if dist:
-        dist.destroy_process_group()
+    return line
 
 
 def oracle_gradient_rate(basis, paths, gw, n_steps: int, path_index: int = 8) -> dict:
@@ -690,52 +690,89 @@ def run_grad(args) -> None:
         dist.destroy_process_group()
 
 
-def main() -> None:
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all of the workload)")
-    ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
-    ap.add_argument("--solve-mode", default="auto", choices=["auto", "stage", "matrix", "schur"],
-                    help="S^-1 per RK4 stage through the Schur complement's Cholesky factor (schur), from pivoted LU "
-                         "factors (stage), or as X = S^-1 H (matrix); auto = schur (the Cholesky factor needs a "
-                         "positive-definite S, i.e. the workloads' converged (eta, tau) rules)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v",
-                                                             "pLi_2c_grad", "p_H_1c_n10l10"],
-                    help="p_H_2c_n4l3: two-centre p + H (N = 380, 32 paths); C6_H_2c_n6l5: bare C6+ on H "
-                         "(N = 1622, 16 paths); p_H_2c_batch6v: p + H at six speeds, N = 316..572, 64 paths "
-                         "each, all in one graph launch (batched form); pLi_2c_grad: p + Li-like model-potential "
-                         "target (N = 379, 32 paths), observables and their gradient by the adjoint "
-                         "(differentiation form)")
-    ap.add_argument("--checkpoint-every", type=int, default=25, help="pLi_2c_grad: RK4 steps per checkpoint")
-    ap.add_argument("--no-fd-check", action="store_true", help="pLi_2c_grad: skip the central-difference sample")
-    ap.add_argument("--workspace-gb", type=float, default=0.0, help="0: 16 GB (p + H) or 96 GB (C6+ on H)")
-    ap.add_argument("--precision", default="auto",
-                    choices=["auto", "fp64", "mixed", "mixed-fp64-elements", "mixed-tensor-core", "fp64-tensor-core",
-                             "mixed-fp64-tc-elements", "fp64-tc-refined"],
-                    help="auto: time plain FP64 and the reduced-precision forms, report the fastest form whose "
-                         "probabilities stay within 1e-6 of the FP64 form on the same steps")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
-    if args.solve_mode == "auto":
-        args.solve_mode = "schur"
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.workload == "p_H_2c_batch6v":
-        run_batch(args)
-        return
-    if args.workload == "pLi_2c_grad":
-        run_grad(args)
-        return
-    if args.workload == "p_H_1c_n10l10":
-        run_one_centre_large(args)
-        return
+# algorithmic bytes or flops per position of each kernel category, and the peak each is measured against
+def _category_rooflines(basis, mode: int, solve_mode: str, N: int, n_half: int) -> dict:
+    """Per position (evaluation of S and H at one z): the work each category of kernels must do, as the
+    method defines it, with the bound and peak that apply.  Contraction: K and Q over the full N_T x N_P
+    block, 4 real flops per node each (8 N_T N_P G; the q -> -q reflection lets the kernels form only the
+    n_half projectile columns with q >= 0, and the tensor-core forms issue 6 or 28 bf16 slice products per
+    algorithmic product: neither changes the algorithmic count).  Factorisation: the Schur complement's
+    lower triangle and its Cholesky factor (4 N_P^2 N_T + 4/3 N_P^3), or LU (8/3 N^3).  Node tables and
+    rotation/direct blocks are bound by memory: the bytes they must write (node tables of the layout the
+    form uses; S and H)."""
+    NT, NP_, G = basis.T.N, basis.P.N, basis.quad.G
+    mixed = mode in (1, 2, 3, 5)
+    tc = mode in (3, 4, 5)
+    slices = 3 if mode == 3 else 7
+    nradT, nradP = basis.T.n_rad, basis.P.n_rad
+    lT = int(max(basis.T.rad_l)) if nradT else 0
+    lP = int(max(basis.P.rad_l)) if nradP else 0
+    nlqT, nlqP = (lT + 1) * (lT + 2) // 2, (lP + 1) * (lP + 2) // 2
+    dmax = lT + lP
+    if tc:
+        node_bytes = slices * 2 * NT * G * 2 + (n_half + 2 * (dmax + 1)) * G * 8
+    elif mode == 1:
+        node_bytes = (NT + n_half) * G * 4 + 2 * (dmax + 1) * G * 8
+    else:
+        node_bytes = (nradT + nradP + nlqT + nlqP) * G * 8 + 2 * (dmax + 1) * G * 16
+    if solve_mode == "schur":
+        f_solve = 4.0 * NP_ * NP_ * NT + (4.0 / 3.0) * NP_ ** 3
+    else:
+        f_solve = (8.0 / 3.0 + (8.0 if (solve_mode == "matrix" and not mixed) else 0.0)) * N ** 3
+    mol_name = {1: "k_mol_gemm_f32q", 3: "k_mol_tc64<3>", 4: "k_mol_tc64<7>", 5: "k_mol_tc64<7>"}.get(
+        mode, "k_mol_gemm<double>")
+    solve_name = (("k_schur_factor<float>" if solve_mode == "schur" else "k_lu_factor_f32") if mixed
+                  else ("k_schur_factor<double>" if solve_mode == "schur" else "k_lu_solve"))
+    mol_peak = (("tensor", BF16_SUSTAINED_TFLOPS, "TFLOP/s") if tc else
+                ("alu", FP32_PEAK_TFLOPS, "TFLOP/s") if mode == 1 else ("alu", FP64_PEAK_TFLOPS, "TFLOP/s"))
+    return {
+        "node_tables": (float(node_bytes), ("hbm", HBM_MEASURED_GBS, "GB/s"),
+                        "k_node_tables<float>" if (tc or mode == 1) else "k_node_tables<double>"),
+        "mol_gemm": (8.0 * NT * NP_ * G, mol_peak, mol_name),
+        "rotate_direct": (float(2 * 16 * N * N + 2 * 16 * NT * n_half), ("hbm", HBM_MEASURED_GBS, "GB/s"),
+                          "k_rotate+k_direct"),
+        "solve": (f_solve, ("alu", FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS, "TFLOP/s"), solve_name),
+    }
 
+
+def _peak_source(bound: str, peak: float) -> str:
+    if bound == "hbm":
+        return "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    if bound == "tensor":
+        return ("measured sustained bf16 dense tensor peak (MEASURED_PEAKS.json bf16_tflops_sustained; the kernel "
+                "is timed inside the step) against the method's algorithmic flops, not the bf16 slice products "
+                "the kernel issues")
+    if peak == FP32_PEAK_TFLOPS:
+        return ("FP32 pipe from unit counts and clocks (152 SMs x 128 FFMA/clk x 2.07 GHz); "
+                f"measured FFMA microbenchmark {FP32_FFMA_MEASURED_TFLOPS} TFLOP/s")
+    return ("FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
+            f"measured DFMA microbenchmark {FP64_DFMA_MEASURED_TFLOPS} TFLOP/s")
+
+
+def _rk4_flops_per_step(mode: int, solve_mode: str, N: int, NT: int, NP_: int) -> float:
+    """RK4 per path-step (FP64): 4 applications of M; matrix form X y, stage form H y + two triangles,
+    Schur form H y, K^+ t_T, K x_P and two triangles of N_P; refined forms H y, two preconditioner solves
+    and one residual S x (off-diagonal blocks)."""
+    mixed = mode in (1, 2, 3, 5)
+    schur = solve_mode == "schur"
+    if mixed:
+        solve_once = (16.0 * NT * NP_ + 8.0 * NP_ * NP_) if schur else 8.0 * N * N
+        return 4.0 * (8.0 * N * N + 2.0 * solve_once + 16.0 * NT * NP_)
+    if schur:
+        return 4.0 * (8.0 * N * N + 16.0 * NT * NP_ + 8.0 * NP_ * NP_)
+    return {"matrix": 32.0, "stage": 64.0}[solve_mode] * N * N
+
+
+# DRAM bytes per position of a kernel on a workload, measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum over a capture of whole launches, divided by the positions): only kernels whose code
+# is unchanged since the capture are listed (the others report traffic null)
+MEASURED_TRAFFIC_PER_POSITION = {}
+
+
+def run_fixed_speed(args, sub: bool = False) -> dict:
+    """One fixed-speed workload (p + H, or C6+ on H): every precision form timed on the same consecutive
+    segments of all paths; the headline is the fastest form within 1e-6 of the plain FP64 form both on the
+    timed segments and, for p + H, over whole paths of a subset of impact parameters."""
     import torch
     import wpccc_inputs as wi
 
@@ -745,20 +782,21 @@ def main() -> None:
     dist = None
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    c6 = args.workload == "C6_H_2c_n6l5"
 
     basis, paths = wi.config_inputs(args.workload)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(basis, paths, 40 if args.workload == WORKLOAD else 2,
-                              path_index=min(16, paths.n_paths // 2))
+        cpu = cpu_oracle_rate(basis, paths, 40 if not c6 else 1, path_index=min(16, paths.n_paths // 2))
 
     import paper_2403_04252_gb300 as w
     g = w.Basis(basis, device=local)
-    ws_gb = args.workspace_gb or (16.0 if args.workload == WORKLOAD else 96.0)
+    ws_gb = args.workspace_gb or (16.0 if not c6 else 96.0)
     g.set_workspace_limit(int(ws_gb * (1 << 30)))
     g.set_solve_mode(SOLVE_MODES[args.solve_mode](w))
     n_paths = paths.n_paths if args.paths <= 0 else min(args.paths, paths.n_paths)
@@ -836,8 +874,6 @@ def main() -> None:
                 forms[prec] = {"prec": prec, "unsupported": str(exc)}
                 continue
             forms[prec]["err"] = float(np.abs(forms[prec]["P"] - forms[0]["P"]).max())
-        ok = [p for p in forms if p == 0 or forms[p].get("err", 1.0) <= 1e-6]
-        head = max(ok, key=lambda p: forms[p]["value"])
     else:
         head = {v_: k for k, v_ in names.items()}[args.precision]
         forms[head] = measure(head)
@@ -845,6 +881,32 @@ def main() -> None:
             ref = measure(0)
             forms[head]["err"] = float(np.abs(forms[head]["P"] - ref["P"]).max())
             forms[0] = ref
+
+    # whole paths (untimed) of a stated subset of impact parameters: every form against the plain FP64 form
+    whole = None
+    if args.whole_path_paths > 0 and not c6 and world == 1:
+        k = min(args.whole_path_paths, n_paths)
+        idx = np.unique(np.linspace(0, n_paths - 1, k).round().astype(int))
+        P_ref = None
+        whole = {"paths": idx.tolist(), "b": [float(x) for x in b[idx]], "rk4_steps_per_path": int(n_total),
+                 "forms": {}}
+        for p in sorted(forms):
+            if "unsupported" in forms[p]:
+                continue
+            prec = 5 if p == 6 else p
+            g.set_refine_iters(4 if p == 6 else 2)
+            P = w.probabilities(g.propagate(b[idx], v[idx], zg, precision_mode=prec)).cpu().numpy()
+            g.set_refine_iters(2)
+            if p == 0:
+                P_ref = P
+            e = float(np.abs(P - P_ref).max())
+            forms[p]["whole_err"] = e
+            whole["forms"][names[p]] = {
+                "max_abs_prob_error_vs_fp64": e,
+                "meets_fp64_bar": bool(np.all(np.abs(P - P_ref) <= 1e-10 * np.maximum(P_ref, 1e-4)))}
+    if args.precision == "auto":
+        ok = [p for p in forms if p == 0 or (forms[p].get("err", 1.0) <= 1e-6 and forms[p].get("whole_err", 0.0) <= 1e-6)]
+        head = max(ok, key=lambda p: forms[p]["value"])
     H = forms[head]
     prec, ms, prof, clocks, value = H["prec"], H["ms"], H["prof"], H["clocks"], H["value"]
     mode = 5 if prec == 6 else prec          # the library's precision mode of the headline form
@@ -870,80 +932,52 @@ def main() -> None:
     h2d = c_host.numel() * 16 + seg_bytes
     d2h = P_host.numel() * 8
 
-    # ---- roofline of the dominant kernel of the headline form
+    # ---- roofline: every kernel category of the headline form against its bound; the dominant one
+    # (largest device time) is the line's `roofline`
     NT, NP_, G = basis.T.N, basis.P.N, basis.quad.G
     n_half = int(sum(1 for m in basis.P.st_m if m >= 0))
     evals = args.steps * n_paths * (2 * STEP + 1)
-    # Eq. 9 contraction, two integrals (K and Q; the lower-left block is Q^+), per z: projectile columns
-    # with q >= 0 (the reflection gives the rest): 4 real flops per node per integral
-    flops_mol = 8.0 * NT * n_half * G
-    # LU, plus N right-hand sides in the paper's form; the stage form's triangular solves run in the RK4 kernel.
-    # Schur form (every two-centre form): the lower triangle of K^+ K (4 N_P^2 N_T) and the Cholesky of
-    # I - K^+ K (4/3 N_P^3), in FP64 (forms 0, 4) or FP32 (the refined forms)
-    mixed_form = mode in (1, 2, 3, 5)
-    schur = args.solve_mode == "schur"
-    if schur:
-        flops_solve = 4.0 * NP_ * NP_ * NT + (4.0 / 3.0) * NP_ ** 3
-    else:
-        flops_solve = (8.0 / 3.0 + (8.0 if (args.solve_mode == "matrix" and not mixed_form) else 0.0)) * N ** 3
-    # RK4 per path-step (FP64): 4 applications of M; matrix form X y, stage form H y + two triangles,
-    # Schur form H y, K^+ t_T, K x_P and two triangles of N_P; refined forms H y, two preconditioner
-    # solves and one residual S x (off-diagonal blocks)
-    if mixed_form:
-        solve_once = (16.0 * NT * NP_ + 8.0 * NP_ * NP_) if schur else 8.0 * N * N
-        rk4_flops = 4.0 * (8.0 * N * N + 2.0 * solve_once + 16.0 * NT * NP_)
-    elif schur:
-        rk4_flops = 4.0 * (8.0 * N * N + 16.0 * NT * NP_ + 8.0 * NP_ * NP_)
-    else:
-        rk4_flops = {"matrix": 32.0, "stage": 64.0}[args.solve_mode] * N * N
-    # the tensor-core contractions issue 6 (three slices) or 28 (seven slices) bf16 slice products per
-    # algorithmic product
-    mol_work = {3: 6.0, 4: 28.0, 5: 28.0}.get(mode, 1.0)
-    mol_peak = {1: FP32_PEAK_TFLOPS, 3: BF16_MEASURED_TFLOPS, 4: BF16_MEASURED_TFLOPS,
-                5: BF16_MEASURED_TFLOPS}.get(mode, FP64_PEAK_TFLOPS)
-    solve_name = (("k_schur_factor<float>" if schur else "k_lu_factor_f32") if mixed_form
-                  else ("k_schur_factor<double>" if schur else "k_lu_solve"))
-    mol_name = {1: "k_mol_gemm_f32q", 3: "k_mol_tc64<3>", 4: "k_mol_tc64<7>", 5: "k_mol_tc64<7>"}.get(
-        mode, "k_mol_gemm<double>")
-    cand = {"mol_gemm": (mol_work * flops_mol * evals, mol_peak, mol_name),
-            "solve": (flops_solve * evals, FP32_PEAK_TFLOPS if mixed_form else FP64_PEAK_TFLOPS, solve_name),
-            "rk4": (rk4_flops * n_paths * STEP * args.steps, FP64_PEAK_TFLOPS, "k_rk4")}
+    cats = _category_rooflines(basis, mode, args.solve_mode, N, n_half)
+    cats["rk4"] = (_rk4_flops_per_step(mode, args.solve_mode, N, NT, NP_), ("alu", FP64_PEAK_TFLOPS, "TFLOP/s"),
+                   "k_rk4")
+    issued = {3: 6.0, 4: 28.0, 5: 28.0}.get(mode)
 
     def roof(key: str) -> dict:
         k_ms, k_launches = prof[key]
-        k_flops, k_peak, k_name = cand[key]
-        ach = k_flops / (k_ms / 1e3) / 1e12
-        # DRAM bytes per position of the tensor-core contractions on this workload (ncu,
-        # dram__bytes_read.sum + dram__bytes_write.sum over 33 positions), scaled to the launch's positions
-        per_pos = {"k_mol_tc64<3>": 8.35e6, "k_mol_tc64<7>": 15.94e6}.get(k_name) if args.workload == WORKLOAD else None
-        return {"bound": "tensor" if k_peak == BF16_MEASURED_TFLOPS else "alu", "kernel": k_name,
-                "achieved": ach, "peak": k_peak, "unit": "TFLOP/s", "frac": ach / k_peak,
-                "traffic": per_pos * evals / max(k_launches, 1) if per_pos else None,
-                "peak_source": ("measured bf16 dense tensor peak (MEASURED_PEAKS.json, burst) against the "
-                                f"contraction's algorithmic flops times its {int(mol_work)} slice products")
-                if k_peak == BF16_MEASURED_TFLOPS else
-                ("FP32 pipe from unit counts and clocks (152 SMs x 128 FFMA/clk x 2.07 GHz); "
-                 f"measured FFMA microbenchmark {FP32_FFMA_MEASURED_TFLOPS} TFLOP/s")
-                if k_peak == FP32_PEAK_TFLOPS else
-                ("FP64 pipe from unit counts and clocks (152 SMs x 2 DFMA/clk x 2.07 GHz); "
-                 f"measured DFMA microbenchmark {FP64_DFMA_MEASURED_TFLOPS} TFLOP/s"),
-                "launch_ms_avg": k_ms / max(k_launches, 1),
-                "flop_per_launch": k_flops / max(k_launches, 1)}
+        per_unit, (bound, peak, unit), k_name = cats[key]
+        units = n_paths * STEP * args.steps if key == "rk4" else evals
+        work = per_unit * units
+        ach = work / (k_ms / 1e3) / (1e9 if unit == "GB/s" else 1e12)
+        per_pos = MEASURED_TRAFFIC_PER_POSITION.get((args.workload, k_name))
+        r = {"bound": bound, "kernel": k_name, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+             "traffic": per_pos * evals / max(k_launches, 1) if (per_pos and key != "rk4") else None,
+             "peak_source": _peak_source(bound, peak), "launch_ms_avg": k_ms / max(k_launches, 1),
+             ("bytes_per_launch" if unit == "GB/s" else "flop_per_launch"): work / max(k_launches, 1),
+             "work_per_unit": per_unit, "unit_of_work": "path-step" if key == "rk4" else "position"}
+        if key == "mol_gemm" and issued:
+            r["issued_bf16_tflops"] = issued * 8.0 * NT * n_half * G * evals / (k_ms / 1e3) / 1e12
+            r["issued_note"] = (f"bf16 slice products issued ({int(issued)} per algorithmic product, q >= 0 "
+                                "columns only)")
+        return r
 
-    # the dominant kernel is taken on the assembly stream, which bounds the step (the RK4 sweep overlaps
-    # it on its own stream and is reported beside it)
-    dom = max(("mol_gemm", "solve"), key=lambda k: prof[k][0] if k in prof else 0.0)
+    timed = {k: prof[k][0] for k in cats if k in prof and prof[k][1] > 0}
+    dom = max(timed, key=lambda k: timed[k])
     roofline = roof(dom)
-    roofline["overlapped_rk4"] = roof("rk4")
-    total_flops = (flops_mol + flops_solve) * evals + rk4_flops * n_paths * STEP * args.steps
+    roofline["by_kernel"] = {k: {kk: vv for kk, vv in roof(k).items() if kk in ("kernel", "bound", "achieved",
+                                                                                   "peak", "unit", "frac",
+                                                                                   "launch_ms_avg")}
+                             | {"ms": timed[k], "share": timed[k] / sum(timed.values())} for k in timed}
+    roofline["streams"] = ("RK4 sweeps run on a second stream, overlapping the next chunk's element kernels and "
+                           "factorisation on the caller's stream; shares are of the summed kernel time")
+    total_flops = (cats["mol_gemm"][0] + cats["solve"][0]) * evals + cats["rk4"][0] * n_paths * STEP * args.steps
     launches = int(sum(n for _, n in prof.values()))
     form_desc = {0: "plain FP64, all paths batched; S^-1 applied "
                     + {"stage": "per RK4 stage from LU factors",
                        "schur": "per RK4 stage through the Cholesky factor of the Schur complement I - K^+ K",
                        "matrix": "as X = S^-1 H with N right-hand sides (the paper's ZGESV form)"}[args.solve_mode],
-                 1: "mixed precision: Eq. 9 contraction and LU on the FP32 pipe (FP64 running sums), FP64 "
+                 1: "mixed precision: Eq. 9 contraction and the factors of S on the FP32 pipe, FP64 "
                     "node tables, refinement and RK4; all paths batched",
-                 2: "mixed precision with FP64 elements: LU on the FP32 pipe, FP64 refinement and RK4",
+                 2: "mixed precision with FP64 elements: factors of S on the FP32 pipe, FP64 refinement and RK4",
                  3: "mixed precision, tensor-core contraction: Eq. 9 on tcgen05 (fixed-point bf16 slices, exact "
                     "main accumulation), FP32 factors of S, FP64 refinement and RK4; all paths batched",
                  4: "FP64-accurate: Eq. 9 contraction emulated on tcgen05 (seven bf16 slices per operand, 28 "
@@ -954,10 +988,11 @@ def main() -> None:
                     "preconditioner of four FP64 refinement sweeps per RK4 stage, FP64 RK4"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 3: "bf16-slices+f32+f64", 4: "bf16-slices(fp64-accurate)+f64",
-                                                  5: "bf16-slices(fp64-accurate)+f32+f64",
-                                                  6: "bf16-slices(fp64-accurate)+f32+f64"}.get(prec, "f32+f64"), "data": "synthetic",
-            "config": {"workload": CONFIG_DESC if args.workload == WORKLOAD else CONFIG_DESC_C6, "paths": n_paths,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f64", 3: "bf16-slices+f32+f64", 4: "bf16-slices(fp64-accurate)+f64",
+                      5: "bf16-slices(fp64-accurate)+f32+f64",
+                      6: "bf16-slices(fp64-accurate)+f32+f64"}.get(prec, "f32+f64"), "data": "synthetic",
+            "config": {"workload": CONFIG_DESC if not c6 else CONFIG_DESC_C6, "paths": n_paths,
                        "form": form_desc[prec],
                        "bench_step": f"{STEP} RK4 steps of each of the {n_paths} paths per rank, consecutive "
                                      "segments centred on z = 0",
@@ -965,6 +1000,8 @@ def main() -> None:
                              f"{2 * 16 * N * N * n_paths * (2 * STEP + 1) / 1e9:.1f} GB"},
             "forms": {names[p]: ({"value": f["value"], "ms_per_step": f["ms"] / args.steps,
                                   "max_abs_prob_error_vs_fp64": f.get("err", 0.0),
+                                  **({"whole_path_max_abs_prob_error_vs_fp64": f["whole_err"]}
+                                     if "whole_err" in f else {}),
                                   "kernel_ms": {k: v_[0] for k, v_ in f["prof"].items()}}
                                  if "unsupported" not in f else {"unsupported": f["unsupported"]})
                       for p, f in forms.items()},
@@ -978,7 +1015,9 @@ def main() -> None:
                    for p in (0, 4, 6) if p in forms and "unsupported" not in forms[p]}},
             "prob_error": {"max_abs": H.get("err", 0.0), "bound": 1e-6,
                            "against": "the plain FP64 form on the same steps (itself within 1e-10 of the oracle)",
-                           "rk4_steps_per_path": (args.warmup + args.steps) * STEP},
+                           "rk4_steps_per_path": (args.warmup + args.steps) * STEP,
+                           **({"whole_path_max_abs": H.get("whole_err", 0.0)} if whole else {})},
+            "whole_path_check": whole,
             "roofline": roofline,
             "algorithmic_tflops_whole_step": total_flops / (ms / 1e3) / 1e12,
             "matrix_elements_per_s": world * evals * (NT * NT + NP_ * NP_ + 3 * NT * NP_) / (ms / 1e3),
@@ -988,11 +1027,96 @@ def main() -> None:
             "gpu_launches": launches, "clocks": clocks}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    g.close()
+    return line
+
+
+_SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "forms", "speedup_vs_plain_fp64",
+             "fp64_accurate_forms", "prob_error", "whole_path_check", "roofline", "e2e", "cpu_baseline", "clocks",
+             "kernel_ms", "kernel_ms_separate_calls", "batched_vs_separate_calls", "autotune", "gpu_launches")
+
+
+def _sub_entry(line: dict) -> dict:
+    return {k: line[k] for k in _SUB_KEYS if k in line}
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", type=int, default=0, help="use only the first P paths (0: all of the workload)")
+    ap.add_argument("--rk4-per-step", type=int, default=STEP_RK4)
+    ap.add_argument("--solve-mode", default="auto", choices=["auto", "stage", "matrix", "schur"],
+                    help="S^-1 per RK4 stage through the Schur complement's Cholesky factor (schur), from pivoted LU "
+                         "factors (stage), or as X = S^-1 H (matrix); auto = schur (the Cholesky factor needs a "
+                         "positive-definite S, i.e. the workloads' converged (eta, tau) rules)")
+    ap.add_argument("--workload", default=None, choices=["p_H_2c_n4l3", "C6_H_2c_n6l5", "p_H_2c_batch6v",
+                                                         "pLi_2c_grad", "p_H_1c_n10l10"],
+                    help="run one workload only.  Default: the p + H headline (p_H_2c_n4l3: two-centre p + H, "
+                         "N = 380, 32 paths) with the batched velocity scan (p_H_2c_batch6v: six speeds, "
+                         "N = 316..572, 64 paths each, one graph launch) and the precision workload "
+                         "(C6_H_2c_n6l5: bare C6+ on H, N = 1622, 16 paths) carried in `workloads`; "
+                         "pLi_2c_grad: p + Li-like model-potential target (N = 379, 32 paths), observables and "
+                         "their gradient by the adjoint; p_H_1c_n10l10: one-centre p + H at l <= 10 (N = 4257)")
+    ap.add_argument("--no-sub-workloads", action="store_true",
+                    help="default run: skip the velocity-scan and C6+ entries")
+    ap.add_argument("--whole-path-paths", type=int, default=4,
+                    help="p + H: impact parameters (evenly spread, the smallest included) whose whole 1000-step "
+                         "paths every form runs untimed, against the plain FP64 form; 0 skips the check")
+    ap.add_argument("--checkpoint-every", type=int, default=25, help="pLi_2c_grad: RK4 steps per checkpoint")
+    ap.add_argument("--no-fd-check", action="store_true", help="pLi_2c_grad: skip the central-difference sample")
+    ap.add_argument("--workspace-gb", type=float, default=0.0, help="0: 16 GB (p + H) or 96 GB (C6+ on H)")
+    ap.add_argument("--precision", default="auto",
+                    choices=["auto", "fp64", "mixed", "mixed-fp64-elements", "mixed-tensor-core", "fp64-tensor-core",
+                             "mixed-fp64-tc-elements", "fp64-tc-refined"],
+                    help="auto: time plain FP64 and the reduced-precision forms, report the fastest form whose "
+                         "probabilities stay within 1e-6 of the FP64 form on the same steps")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.solve_mode == "auto":
+        args.solve_mode = "schur"
+    if args.impl == "reference":
+        args.workload = args.workload or WORKLOAD
+        run_reference(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "p_H_2c_batch6v":
+        line = run_batch(args)
+    elif args.workload == "pLi_2c_grad":
+        run_grad(args)
+        return
+    elif args.workload == "p_H_1c_n10l10":
+        run_one_centre_large(args)
+        return
+    elif args.workload is not None:
+        line = run_fixed_speed(args)
+    else:
+        args.workload = WORKLOAD
+        line = run_fixed_speed(args)
+        if world == 1 and not args.no_sub_workloads:
+            # the batched and precision workloads of the metric, each with its own forms, errors, roofline,
+            # end-to-end rate and CPU baseline; a few bench steps each, so the whole run stays within minutes
+            import copy
+            sub = {}
+            a = copy.copy(args)
+            a.workload, a.steps, a.warmup, a.rk4_per_step = "p_H_2c_batch6v", min(args.steps, 3), 3, STEP_RK4
+            sub["p_H_2c_batch6v"] = _sub_entry(run_batch(a))
+            a = copy.copy(args)
+            a.workload, a.steps, a.warmup, a.rk4_per_step = "C6_H_2c_n6l5", min(args.steps, 3), 3, 4
+            a.whole_path_paths = 0
+            sub["C6_H_2c_n6l5"] = _sub_entry(run_fixed_speed(a, sub=True))
+            line["workloads"] = sub
     if rank == 0:
         print(json.dumps(line))
-    g.close()
-    if dist:
-        dist.destroy_process_group()
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -57,7 +57,11 @@ typedef enum {
     WPCCC_ESINGULAR = 3,   /* a linear system had an exactly zero pivot (ZGESV info > 0) */
     WPCCC_ENONFINITE = 4,  /* amplitudes became NaN or infinite during propagation */
     WPCCC_ECUDA = 5,       /* a CUDA runtime call or kernel launch failed */
-    WPCCC_EUNSUPPORTED = 6 /* a mode this build does not provide */
+    WPCCC_EUNSUPPORTED = 6, /* a mode this build does not provide */
+    WPCCC_ETIMEOUT = 7,    /* a bounded wait inside a tensor-core kernel gave up (see wpccc_basis_set_wait_limit);
+                              the kernel returned cleanly and the device stays usable */
+    WPCCC_ENOCONV = 8      /* the FP64 iterative refinement of a reduced-precision form did not converge (see
+                              wpccc_basis_set_refine_tolerance); the amplitudes are returned but not trusted */
 } wpccc_status;
 
 /* Largest orbital angular momentum a basis may hold, and largest system size.  Beyond about 2840 states
@@ -264,7 +268,8 @@ WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv
  * itself (kept with the basis for reuse) and checks the pivots and the
  * amplitudes at the end.
  * Errors: EINVAL, EUNSUPPORTED, ENOMEM, ESINGULAR (some S had a zero pivot),
- * ENONFINITE (amplitudes became non-finite), ECUDA.
+ * ENONFINITE (amplitudes became non-finite), ENOCONV (a refined mode's refinement did not converge, see
+ * wpccc_basis_set_refine_tolerance), ETIMEOUT (a tensor-core wait gave up), ECUDA.
  */
 WPCCC_API wpccc_status wpccc_propagate(wpccc_basis basis, const wpccc_paths* paths, int precision_mode,
                              int batch_mode, void* c, void* stream);
@@ -304,6 +309,48 @@ WPCCC_API wpccc_status wpccc_batch_destroy(wpccc_batch batch);
 WPCCC_API wpccc_status wpccc_probabilities(int n_paths, int N, const void* c, double* P, void* stream);
 
 /*
+ * Observables at the end of the paths (Sec. II: the amplitudes at z_max give the transition
+ * probabilities; capture sums the projectile's bound states, excitation a level's states):
+ *   P[p][o] = sum_i g[o][i] |c[p][i]|^2.
+ *   g  device [n_obs][N] real weights;  c  device [n_paths][N] complex128;  P  device [n_paths][n_obs].
+ * Errors: EINVAL (n_paths < 0, N < 1, n_obs outside 1..65535, null pointers), ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_observables(int n_paths, int N, int n_obs, const double* g, const void* c, double* P,
+                                         void* stream);
+
+/*
+ * Cross sections sigma_o = 2 pi int_0^inf b P_o(b) db (Sec. II: the probabilities of all impact parameters
+ * give the cross sections) by the trapezoid rule on the nodes 0, b[0], ..., b[n_b - 1] (b P(b) = 0 at b = 0):
+ * sigma_o = sum_j 2 pi b_j w_j P[j][o], w_j = (b_{j+1} - b_{j-1}) / 2 with b_{-1} = 0 and, for the last node,
+ * (b_{n-1} - b_{n-2}) / 2.
+ *   b      host [n_b] impact parameters, finite, > 0, strictly increasing (1 <= n_b <= 2048)
+ *   P      device [n_b][n_obs] observables of those paths;  sigma  device [n_obs]
+ * Errors: EINVAL (sizes, unsorted or non-positive b, null pointers), ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_cross_sections(int n_b, const double* b, int n_obs, const double* P, double* sigma,
+                                            void* stream);
+
+/*
+ * Norms of the amplitudes at one position per path: out[p][0] = c_p^+ S(z_p) c_p and out[p][1] = c_p^+ c_p,
+ * with S of Eq. 1 assembled at (b[p], v[p], z[p]) by the FP64 element kernels.  In the two-centre basis the
+ * states are not orthogonal, so the probability the amplitudes carry is c^+ S c; with the lower-left block
+ * of H taken as Q^+ (Eq. 1 as printed) the equations give d(c^+ S c)/dz = c^+ (dS/dz) c, so it is not an
+ * invariant of the two-centre propagation (in one-centre mode S = I and both norms are c^+ c).
+ *   b, v, z  host [n_paths];  c  device [n_paths][N] complex128;  out  device [n_paths][2] double
+ * Blocks until done; allocates S and H for the positions (freed before it returns) and uses the basis
+ * workspace.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_overlap_norms(wpccc_basis basis, int n_paths, const double* b, const double* v,
+                                           const double* z, const void* c, double* out, void* stream);
+
+/*
+ * The basis' states in state order (every target state, then every projectile state): qn[i] = (centre:
+ * 0 target, 1 projectile; radial function index on that centre; l; m) and eps[i] its energy (host arrays
+ * [N][4] and [N]; either may be NULL).  Errors: EINVAL (null basis), ECUDA.
+ */
+WPCCC_API wpccc_status wpccc_basis_states(wpccc_basis basis, int* qn, double* eps);
+
+/*
  * How wpccc_propagate applies S^{-1} (two-centre mode).  Both give M(z) c up to rounding.
  *   WPCCC_SOLVE_STAGE  (default) LU-factorise S(z) once per position; at every RK4
  *                      stage form H(z) y and solve S(z) k = H(z) y with the factors
@@ -330,6 +377,27 @@ WPCCC_API wpccc_status wpccc_basis_set_solve_mode(wpccc_basis basis, int mode);
  */
 #define WPCCC_MAX_REFINE 8
 WPCCC_API wpccc_status wpccc_basis_set_refine_iters(wpccc_basis basis, int iters);
+
+/*
+ * Convergence check of the refined precision modes (1, 2, 3, 5; the paper solves in FP64 only, no
+ * counterpart): at every RK4 stage the last refinement sweep's correction dx is compared with the solution,
+ * and wpccc_propagate returns WPCCC_ENOCONV if max|dx| > tol max|x| on any stage of any path (the sweeps
+ * contract the error by a factor rho per sweep, so the error left after the last one is about rho max|dx|:
+ * tol = 1e-3 bounds it near 1e-6 relative whenever rho < 1e-3, while a refinement that stalls or diverges,
+ * rho >= 1, leaves max|dx| ~ max|x|).  Needs at least two sweeps (wpccc_basis_set_refine_iters).  tol <= 0
+ * switches the check off.  Default 1e-3.  Errors: EINVAL (null basis, non-finite tol).
+ */
+WPCCC_API wpccc_status wpccc_basis_set_refine_tolerance(wpccc_basis basis, double tol);
+
+/*
+ * Iteration limit of every mbarrier wait in the tensor-core kernels (precision modes 3-5): a wait that has
+ * polled `polls` times gives up, the CTA records the failure, lets the copies and tensor-core operations it
+ * has in flight complete, frees its tensor memory and returns; the call then reports WPCCC_ETIMEOUT and the
+ * device stays usable.  Default 2^20 polls (far longer than any wait of a healthy launch).  A small limit
+ * makes the waits run out on purpose, to exercise that path.  Errors: EINVAL (null basis, polls < 1).
+ */
+#define WPCCC_DEFAULT_WAIT_POLLS (1L << 20)
+WPCCC_API wpccc_status wpccc_basis_set_wait_limit(wpccc_basis basis, long polls);
 
 /*
  * Where the RK4 sweep of Algorithm 1 keeps its vectors.

@@ -27,8 +27,10 @@ if not os.path.exists(LIB_PATH):
 
 _lib = C.CDLL(LIB_PATH)
 
-OK, EINVAL, ENOMEM, ESINGULAR, ENONFINITE, ECUDA, EUNSUPPORTED = range(7)
-_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENONFINITE", 5: "ECUDA", 6: "EUNSUPPORTED"}
+OK, EINVAL, ENOMEM, ESINGULAR, ENONFINITE, ECUDA, EUNSUPPORTED, ETIMEOUT, ENOCONV = range(9)
+_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENONFINITE", 5: "ECUDA", 6: "EUNSUPPORTED",
+          7: "ETIMEOUT", 8: "ENOCONV"}
+DEFAULT_WAIT_POLLS = 1 << 20
 LMAX = 10
 NMAX = 8192
 
@@ -81,13 +83,21 @@ _lib.wpccc_matrix_elements_precision.argtypes = [C.c_void_p, C.c_double, C.c_dou
 _lib.wpccc_basis_set_tangents.argtypes = [C.c_void_p, C.c_int, _pd, _pd, _pd, _pd, _pd]
 _lib.wpccc_propagate_adjoint.argtypes = [C.c_void_p, C.POINTER(_PathsDesc), C.c_int, _pd, C.c_int, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.wpccc_observables.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.wpccc_cross_sections.argtypes = [C.c_int, _pd, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.wpccc_overlap_norms.argtypes = [C.c_void_p, C.c_int, _pd, _pd, _pd, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.wpccc_basis_states.argtypes = [C.c_void_p, _pi, _pd]
+_lib.wpccc_basis_set_refine_tolerance.argtypes = [C.c_void_p, C.c_double]
+_lib.wpccc_basis_set_wait_limit.argtypes = [C.c_void_p, C.c_long]
 _lib.wpccc_last_error.restype = C.c_char_p
 for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
            "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
            "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode",
            "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
            "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
-           "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters", "wpccc_basis_set_rk4_layout"):
+           "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters", "wpccc_basis_set_rk4_layout",
+           "wpccc_observables", "wpccc_cross_sections", "wpccc_overlap_norms", "wpccc_basis_states",
+           "wpccc_basis_set_refine_tolerance", "wpccc_basis_set_wait_limit"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
@@ -95,7 +105,9 @@ EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wp
             "wpccc_profile_enable", "wpccc_profile_read", "wpccc_basis_set_solve_mode", "wpccc_last_error",
             "wpccc_matrix_elements_noalloc", "wpccc_batch_create", "wpccc_batch_launch", "wpccc_batch_status",
             "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
-            "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters", "wpccc_basis_set_rk4_layout")
+            "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters", "wpccc_basis_set_rk4_layout",
+            "wpccc_observables", "wpccc_cross_sections", "wpccc_overlap_norms", "wpccc_basis_states",
+            "wpccc_basis_set_refine_tolerance", "wpccc_basis_set_wait_limit")
 MAX_PARAMS = 4
 RK4_AUTO, RK4_SHARED, RK4_GLOBAL = 0, 1, 2
 MAX_REFINE = 8
@@ -254,6 +266,15 @@ class Basis:
         """FP64 refinement sweeps per RK4 stage of the refined precision modes (1, 2, 3, 5); default 2."""
         _check(_lib.wpccc_basis_set_refine_iters(self._h, int(iters)), "wpccc_basis_set_refine_iters")
 
+    def set_refine_tolerance(self, tol: float) -> None:
+        """Largest last refinement correction relative to the solution before wpccc_propagate reports
+        ENOCONV (refined precision modes; default 1e-3, <= 0 switches the check off)."""
+        _check(_lib.wpccc_basis_set_refine_tolerance(self._h, float(tol)), "wpccc_basis_set_refine_tolerance")
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls of every mbarrier wait in the tensor-core kernels before it gives up (ETIMEOUT); default 2^20."""
+        _check(_lib.wpccc_basis_set_wait_limit(self._h, int(polls)), "wpccc_basis_set_wait_limit")
+
     def profile_enable(self, on: bool = True) -> None:
         """Reset the per-kernel counters; with on=True time every launch with CUDA events."""
         _check(_lib.wpccc_profile_enable(self._h, int(bool(on))), "wpccc_profile_enable")
@@ -264,6 +285,29 @@ class Basis:
         n = (C.c_longlong * len(PROF_CATEGORIES))()
         _check(_lib.wpccc_profile_read(self._h, ms, n), "wpccc_profile_read")
         return {k: (ms[i], n[i]) for i, k in enumerate(PROF_CATEGORIES)}
+
+    def states(self):
+        """(qn, eps): qn[i] = (centre 0/1, radial index, l, m) and eps[i] of every state (``wpccc_basis_states``)."""
+        qn = np.zeros((self.N, 4), dtype=np.int32)
+        eps = np.zeros(self.N, dtype=np.float64)
+        _check(_lib.wpccc_basis_states(self._h, qn.ctypes.data_as(_pi), eps.ctypes.data_as(_pd)),
+               "wpccc_basis_states")
+        return qn, eps
+
+    def overlap_norms(self, b, v, z, c, stream=None):
+        """(c^+ S c, c^+ c) of every path's amplitudes at its position (b[p], v[p], z[p]) as a device tensor
+        (n_paths, 2) (``wpccc_overlap_norms``)."""
+        import torch
+        b = np.atleast_1d(np.asarray(b, dtype=np.float64))
+        n = b.size
+        v, vp = _arr(np.broadcast_to(np.asarray(v, dtype=np.float64), b.shape), np.float64)
+        z, zp = _arr(np.broadcast_to(np.asarray(z, dtype=np.float64), b.shape), np.float64)
+        b, bp = _arr(b, np.float64)
+        _check_amplitudes(c, n, self.N, self.device, "overlap_norms")
+        out = torch.empty((n, 2), dtype=torch.float64, device=c.device)
+        _check(_lib.wpccc_overlap_norms(self._h, n, bp, vp, zp, _ptr(c), _ptr(out), _stream(stream)),
+               "wpccc_overlap_norms")
+        return out
 
     def matrix_elements(self, b: float, v: float, z, S=None, H=None, stream=None):
         """S, H at the positions z (column-major storage tensors of shape (nz, N, N))."""
@@ -425,6 +469,38 @@ def probabilities(c, stream=None):
     return P
 
 
+def observables_of(c, g, stream=None):
+    """P[p, o] = sum_i g[o, i] |c[p, i]|^2 for a (n_paths, N) complex128 device tensor c and weights g
+    (n_obs, N) (``wpccc_observables``)."""
+    import torch
+    n_paths, N = c.shape
+    gt = torch.as_tensor(np.atleast_2d(np.asarray(g, dtype=np.float64)), device=c.device).contiguous()
+    if gt.shape[1] != N:
+        raise ValueError(f"observable weights must have shape (n_obs, {N})")
+    n_obs = int(gt.shape[0])
+    P = torch.empty((n_paths, n_obs), dtype=torch.float64, device=c.device)
+    _check(_lib.wpccc_observables(int(n_paths), int(N), n_obs, _ptr(gt), _ptr(c), _ptr(P), _stream(stream)),
+           "wpccc_observables")
+    return P
+
+
+def cross_sections(b, P, stream=None):
+    """sigma_o = 2 pi int b P_o(b) db by the trapezoid rule on the (increasing) impact parameters b and the
+    node b = 0, for P (n_b, n_obs) (a device tensor, or a host array copied to the current device)
+    (``wpccc_cross_sections``); returns a device tensor (n_obs,)."""
+    import torch
+    b, bp = _arr(np.atleast_1d(b), np.float64)
+    Pt = torch.as_tensor(P, dtype=torch.float64)
+    if Pt.device.type != "cuda":
+        Pt = Pt.cuda()
+    Pt = Pt.reshape(b.size, -1).contiguous()
+    n_obs = int(Pt.shape[1])
+    sigma = torch.empty((n_obs,), dtype=torch.float64, device=Pt.device)
+    _check(_lib.wpccc_cross_sections(int(b.size), bp, n_obs, _ptr(Pt), _ptr(sigma), _stream(stream)),
+           "wpccc_cross_sections")
+    return sigma
+
+
 def _observables_function():
     import torch
 
@@ -445,8 +521,7 @@ def _observables_function():
                     ctx.save_for_backward(J)
                 else:
                     c = gb.propagate(b, v, zgrids)
-                    gw = torch.as_tensor(np.atleast_2d(g), dtype=torch.float64, device=c.device)
-                    P = probabilities(c) @ gw.T
+                    P = observables_of(c, g)
             finally:
                 gb.close()
             ctx.theta_device = theta.device

@@ -508,6 +508,20 @@ extern "C" wpccc_status wpccc_basis_set_refine_iters(wpccc_basis B, int iters) {
     return WPCCC_OK;
 }
 
+extern "C" wpccc_status wpccc_basis_set_refine_tolerance(wpccc_basis B, double tol) {
+    if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_refine_tolerance: null basis");
+    if (!std::isfinite(tol)) return fail(WPCCC_EINVAL, "wpccc_basis_set_refine_tolerance: non-finite tolerance");
+    B->refine_tol = tol;
+    return WPCCC_OK;
+}
+
+extern "C" wpccc_status wpccc_basis_set_wait_limit(wpccc_basis B, long polls) {
+    if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_wait_limit: null basis");
+    if (polls < 1) return fail(WPCCC_EINVAL, "wpccc_basis_set_wait_limit: polls must be >= 1");
+    B->wait_polls = polls;
+    return WPCCC_OK;
+}
+
 extern "C" wpccc_status wpccc_basis_set_workspace_limit(wpccc_basis B, size_t bytes) {
     if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_workspace_limit: null basis");
     if (bytes < ((size_t)64 << 20)) return fail(WPCCC_EINVAL, "workspace limit below 64 MiB");

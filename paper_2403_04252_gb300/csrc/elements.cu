@@ -17,6 +17,7 @@
 //   k_direct_sr    (model-potential target only) the short-range part of the target
 //                  potential between projectile states, on the (eta, tau) rule, added to D_P
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -60,13 +61,15 @@ __device__ inline void bessel_j_orders(int dmax, double x, double* J) {
     if (x >= (double)dmax) {
         J[0] = j0v;
         if (dmax >= 1) J[1] = j1v;
-        for (int n = 1; n < dmax; ++n) J[n + 1] = (2.0 * n / x) * J[n] - J[n - 1];
+        const double ix2 = 2.0 / x;
+        for (int n = 1; n < dmax; ++n) J[n + 1] = (n * ix2) * J[n] - J[n - 1];
         return;
     }
     const int M = dmax + 26 + (int)x;
+    const double ix2 = 2.0 / x;
     double fn1 = 0.0, fn = 1.0;   // f_{n+1}, f_n
     for (int n = M; n >= 1; --n) {
-        const double fm = (2.0 * n / x) * fn - fn1;   // f_{n-1}
+        const double fm = (n * ix2) * fn - fn1;   // f_{n-1}
         fn1 = fn;
         fn = fm;
         if (n - 1 <= dmax) J[n - 1] = fm;
@@ -102,14 +105,46 @@ struct NodeArgs {
     const int* tc_row;          // [2 N_T]: row of each target state in the slice planes, then its tile's size
     int tc_rows;
     size_t t6_ap_off, t6_w_off, t6_sc_off;
+    // sqrt((2l+1)/2 (l-q)!/(l+q)!) at l(l+1)/2 + q, and 1/k for k = 0..WPCCC_LMAX (entry 0 unused): the
+    // Legendre recurrence's constants, formed once on the host instead of per node
+    double th_nrm[(WPCCC_LMAX + 1) * (WPCCC_LMAX + 2) / 2];
+    double inv_int[WPCCC_LMAX + 1];
 };
+
+// Radial functions of the tensor-core layout's target rows processed per shared-memory batch.
+constexpr int TC_NA = 16;
+
+// Normalised Legendre functions Theta_lq(c) = sqrt((2l+1)/2 (l-q)!/(l+q)!) P_l^q(c) (Condon-Shortley phase)
+// for 0 <= q <= l <= lmax, by the upward recurrence in l at fixed q, handed to put(l (l+1)/2 + q, value).
+template <typename F>
+__device__ inline void theta_lq(double c, int lmax, const NodeArgs& A, F put) {
+    const double sq = sqrt((1.0 - c) * (1.0 + c));
+    double pmm = 1.0;   // P_q^q, built up from P_0^0 = 1
+    for (int q = 0; q <= lmax; ++q) {
+        if (q > 0) pmm *= -(2.0 * q - 1.0) * sq;
+        double pa = 0.0, pb = pmm;   // P_{l-2}^q, P_{l-1}^q
+        for (int l = q; l <= lmax; ++l) {
+            double pl;
+            if (l == q) pl = pmm;
+            else if (l == q + 1) pl = c * (2.0 * q + 1.0) * pmm;
+            else pl = (c * (2.0 * l - 1.0) * pb - (l + q - 1.0) * pa) * A.inv_int[l - q];
+            if (l > q) {
+                pa = pb;
+                pb = pl;
+            }
+            const int t = l * (l + 1) / 2 + q;
+            put(t, A.th_nrm[t] * pl);
+        }
+    }
+}
 
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 
 // The per-node factors are computed in FP64; T = double keeps them in FP64, T = float (mixed-precision
-// form) stores them rounded to FP32 for the FP32 contraction.
+// form) stores them rounded to FP32 for the FP32 contraction.  In the tensor-core layout a block is one
+// 128-node scaling window and needs dynamic shared memory (see node_tables_smem).
 template <typename T>
 __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc* __restrict__ ev) {
     using T2 = typename Vec2<T>::type;
@@ -145,163 +180,137 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
     double LT[5], LP[5];
     const bool inT = stencil5_fast(A.r, A.inv_den, A.Nr, rT, sT, LT);
     const bool inP = stencil5_fast(A.r, A.inv_den, A.Nr, rP, sP, LP);
-    // Theta_lq(c) = sqrt((2l+1)/2 (l-q)!/(l+q)!) P_l^q(c), index l(l+1)/2 + q
-    double thv[2][(WPCCC_LMAX + 1) * (WPCCC_LMAX + 2) / 2];
-    for (int cen = 0; cen < 2; ++cen) {
-        const double c = cen == 0 ? cT : cP;
-        const int lmax = cen == 0 ? A.lmaxT : A.lmaxP;
-        const double sq = sqrt((1.0 - c) * (1.0 + c));
-        double pmm = 1.0;   // P_q^q, built up from P_0^0 = 1
-        for (int q = 0; q <= lmax; ++q) {
-            if (q > 0) pmm *= -(2.0 * q - 1.0) * sq;
-            double pa = 0.0, pb = pmm;   // P_{l-2}^q, P_{l-1}^q
-            for (int l = q; l <= lmax; ++l) {
-                double pl;
-                if (l == q) pl = pmm;
-                else if (l == q + 1) pl = c * (2.0 * q + 1.0) * pmm;
-                else pl = (c * (2.0 * l - 1.0) * pb - (l + q - 1.0) * pa) / (double)(l - q);
-                if (l > q) {
-                    pa = pb;
-                    pb = pl;
-                }
-                const double nrm = sqrt((2.0 * l + 1.0) * 0.5 * dfact(l - q) / dfact(l + q));
-                thv[cen][l * (l + 1) / 2 + q] = nrm * pl;
-            }
-        }
-    }
+    auto interp = [&](const double* f, int a, bool in, int st, const double* Lw) {
+        if (!in) return 0.0;
+        const double* fa = f + (size_t)a * A.Nr + st;
+        return Lw[0] * fa[0] + Lw[1] * fa[1] + Lw[2] * fa[2] + Lw[3] * fa[3] + Lw[4] * fa[4];
+    };
     if (sizeof(T) == 8) {
-        for (int a = 0; a < A.nradT; ++a) {
-            double val = 0.0;
-            if (inT) {
-                const double* fa = A.fT + (size_t)a * A.Nr + sT;
-                val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
-            }
-            oT[(size_t)a * A.G + g] = (T)val;
-        }
-        for (int a = 0; a < A.nradP; ++a) {
-            double val = 0.0;
-            if (inP) {
-                const double* fa = A.fP + (size_t)a * A.Nr + sP;
-                val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
-            }
-            oP[(size_t)a * A.G + g] = (T)val;
-        }
-        for (int t = 0; t < A.nlqT; ++t) thT[(size_t)t * A.G + g] = (T)thv[0][t];
-        for (int t = 0; t < A.nlqP; ++t) thP[(size_t)t * A.G + g] = (T)thv[1][t];
+        for (int a = 0; a < A.nradT; ++a) oT[(size_t)a * A.G + g] = (T)interp(A.fT, a, inT, sT, LT);
+        for (int a = 0; a < A.nradP; ++a) oP[(size_t)a * A.G + g] = (T)interp(A.fP, a, inP, sP, LP);
+        // Theta_lq(c) = sqrt((2l+1)/2 (l-q)!/(l+q)!) P_l^q(c), index l(l+1)/2 + q
+        theta_lq(cT, A.lmaxT, A, [&](int q, double val) { thT[(size_t)q * A.G + g] = (T)val; });
+        theta_lq(cP, A.lmaxP, A, [&](int q, double val) { thP[(size_t)q * A.G + g] = (T)val; });
     } else if (A.tc) {
         // tensor-core layout: A_T r_T and A_T r_T V_T per target state (rows of the row tiles), each as
-        // tc_slices bf16 slices against a power-of-two scale per 128-node window (this block: the node
-        // count is a multiple of 128 in this layout); the products are formed in double-float arithmetic
-        // from FP64 factors split once per node
-        __shared__ float s_wm[2][4][2];   // per-warp row maxima, double-buffered across states
-        const double rTV = A.mp_c == 0.0 ? -A.Z_T : -A.Z_T + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT);
-        const float2 frT = df_split(rT), frTV = df_split(rTV);   // r_T and r_T V_T(r_T)
-        float2 fth[(WPCCC_LMAX + 1) * (WPCCC_LMAX + 2) / 2];
-        for (int q = 0; q < (A.lmaxT + 1) * (A.lmaxT + 2) / 2; ++q) fth[q] = df_split(thv[0][q]);
-        __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(base);
-        float* sc = reinterpret_cast<float*>(base) + A.t6_sc_off + (size_t)(g >> 7) * A.tc_rows;
-        const size_t split = (size_t)A.tc_rows * A.G;
-        const int wid = threadIdx.x >> 5, lid = threadIdx.x & 31;
-        auto put7 = [&](size_t row, float2 x, float mx) {
-            const int sh = oz_shift(mx);
-            __nv_bfloat16 q[OZ_SLICES];
-            const size_t o = row * A.G + g;
-            if (A.tc_slices == 3) {
-                oz_slices<3>(x.x, x.y, sh, q);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) sp[i * split + o] = q[i];
-            } else {
-                oz_slices<OZ_SLICES>(x.x, x.y, sh, q);
-#pragma unroll
-                for (int i = 0; i < OZ_SLICES; ++i) sp[i * split + o] = q[i];
-            }
-            if (threadIdx.x == 0) sc[row] = ldexpf(1.f, -sh);
-        };
-        int par = 0;
-        for (int a = 0; a < A.nradT; ++a) {
-            double val = 0.0;
-            if (inT) {
-                const double* fa = A.fT + (size_t)a * A.Nr + sT;
-                val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
-            }
-            const float2 fv = df_split(val);
-            const int l = A.radT_l[a];
-            for (int m = -l; m <= l; ++m) {
-                const int i = A.stT_index[a * (2 * WPCCC_LMAX + 1) + m + WPCCC_LMAX];
-                const int am = m < 0 ? -m : m;
-                float2 t = df_mul(fv, fth[l * (l + 1) / 2 + am]);
-                if (m < 0 && (am & 1)) t = make_float2(-t.x, -t.y);
-                const float2 x1 = df_mul(t, frT), x2 = df_mul(t, frTV);
-                // the two rows' maxima over the block's 128 nodes: warp shuffles, then the four warps
-                float m1 = fabsf(x1.x), m2 = fabsf(x2.x);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-                    m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-                }
-                if (lid == 0) {
-                    s_wm[par][wid][0] = m1;
-                    s_wm[par][wid][1] = m2;
-                }
-                __syncthreads();
-                m1 = fmaxf(fmaxf(s_wm[par][0][0], s_wm[par][1][0]), fmaxf(s_wm[par][2][0], s_wm[par][3][0]));
-                m2 = fmaxf(fmaxf(s_wm[par][0][1], s_wm[par][1][1]), fmaxf(s_wm[par][2][1], s_wm[par][3][1]));
-                par ^= 1;
-                const int row = A.tc_row[i];
-                const int tsz = A.tc_row[A.N_T + i];
-                put7((size_t)row, x1, m1);
-                put7((size_t)(row + tsz), x2, m2);
-            }
-        }
+        // tc_slices bf16 slices against a power-of-two scale per 128-node window (this block); the
+        // products are formed in double-float arithmetic from FP64 factors split once per node.
+        // Shared memory: th [nlq][128] (this thread's column only while it builds A_P from the projectile's
+        // Theta, then the target's Theta for every warp), r [2][128] (r_T, r_T V_T), f [TC_NA][128]
+        // (a batch of target radial functions at the window's nodes).
+        extern __shared__ float2 s_tc[];
+        const int nlq = A.nlqT > A.nlqP ? A.nlqT : A.nlqP;
+        float2* s_th = s_tc;
+        float2* s_r = s_th + (size_t)nlq * 128;
+        float2* s_f = s_r + 2 * 128;
+        const int tx = threadIdx.x, wid = tx >> 5, lid = tx & 31;
         // A_P per half column as double-floats
+        theta_lq(cP, A.lmaxP, A, [&](int q, double val) { s_th[q * 128 + tx] = df_split(val); });
         float2* aP = reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.t6_ap_off);
         for (int b2 = 0; b2 < A.nradP; ++b2) {
-            double val = 0.0;
-            if (inP) {
-                const double* fa = A.fP + (size_t)b2 * A.Nr + sP;
-                val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
-            }
-            const float2 fv = df_split(val);
+            const float2 fv = df_split(interp(A.fP, b2, inP, sP, LP));
             const int l = A.radP_l[b2];
             for (int q = 0; q <= l; ++q) {
                 const int j = A.half_of[b2 * (WPCCC_LMAX + 1) + q];
-                aP[(size_t)j * A.G + g] = df_mul(fv, df_split(thv[1][l * (l + 1) / 2 + q]));
+                aP[(size_t)j * A.G + g] = df_mul(fv, s_th[(l * (l + 1) / 2 + q) * 128 + tx]);
+            }
+        }
+        theta_lq(cT, A.lmaxT, A, [&](int q, double val) { s_th[q * 128 + tx] = df_split(val); });
+        const double rTV = A.mp_c == 0.0 ? -A.Z_T : -A.Z_T + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT);
+        s_r[tx] = df_split(rT);
+        s_r[128 + tx] = df_split(rTV);
+        __nv_bfloat16* sp = reinterpret_cast<__nv_bfloat16*>(base);
+        float* sc = reinterpret_cast<float*>(base) + A.t6_sc_off + (size_t)blockIdx.x * A.tc_rows;
+        const size_t split = (size_t)A.tc_rows * A.G;
+        const int g0 = blockIdx.x * 128;
+        // one row of the slice planes at the window's 128 nodes: lane holds nodes lid + 32 j
+        auto put_row = [&](size_t row, const float2* xv, float mx) {
+            const int sh = oz_shift(mx);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                __nv_bfloat16 q[OZ_SLICES];
+                const size_t o = row * A.G + g0 + lid + 32 * j;
+                if (A.tc_slices == 3) {
+                    oz_slices<3>(xv[j].x, xv[j].y, sh, q);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) sp[i * split + o] = q[i];
+                } else {
+                    oz_slices<OZ_SLICES>(xv[j].x, xv[j].y, sh, q);
+#pragma unroll
+                    for (int i = 0; i < OZ_SLICES; ++i) sp[i * split + o] = q[i];
+                }
+            }
+            if (lid == 0) sc[row] = ldexpf(1.f, -sh);
+        };
+        for (int a0 = 0; a0 < A.nradT; a0 += TC_NA) {
+            const int na = A.nradT - a0 < TC_NA ? A.nradT - a0 : TC_NA;
+            __syncthreads();   // the previous batch's rows are written (and, first time, Theta_T and r are in)
+            for (int j = 0; j < na; ++j) s_f[j * 128 + tx] = df_split(interp(A.fT, a0 + j, inT, sT, LT));
+            __syncthreads();
+            // the batch's states, one per warp in turn: (radial function, m) pairs in order
+            int pair = 0;
+            for (int j = 0; j < na; ++j) {
+                const int a = a0 + j, l = A.radT_l[a];
+                for (int m = -l; m <= l; ++m, ++pair) {
+                    if ((pair & 3) != wid) continue;
+                    const int i = A.stT_index[a * (2 * WPCCC_LMAX + 1) + m + WPCCC_LMAX];
+                    const int am = m < 0 ? -m : m;
+                    const bool neg = m < 0 && (am & 1);
+                    const float2* th = s_th + (l * (l + 1) / 2 + am) * 128;
+                    float2 x1[4], x2[4];
+                    float m1 = 0.f, m2 = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int n = lid + 32 * jj;
+                        float2 tv = df_mul(s_f[j * 128 + n], th[n]);
+                        if (neg) tv = make_float2(-tv.x, -tv.y);
+                        x1[jj] = df_mul(tv, s_r[n]);
+                        x2[jj] = df_mul(tv, s_r[128 + n]);
+                        m1 = fmaxf(m1, fabsf(x1[jj].x));
+                        m2 = fmaxf(m2, fabsf(x2[jj].x));
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+                        m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                    }
+                    const int row = A.tc_row[i];
+                    const int tsz = A.tc_row[A.N_T + i];
+                    put_row((size_t)row, x1, m1);
+                    put_row((size_t)(row + tsz), x2, m2);
+                }
             }
         }
     } else {
         // per state: A_T[i][g] = f_a(r_T) Theta_{l|m|}(c_T) (-1)^m [m < 0], A_P[j][g] = f_b(r_P) Theta_{lq}(c_P)
+        double thv[(WPCCC_LMAX + 1) * (WPCCC_LMAX + 2) / 2];
         T* aT = base;
         T* aP = aT + (size_t)A.N_T * A.G;
+        theta_lq(cT, A.lmaxT, A, [&](int q, double val) { thv[q] = val; });
         for (int a = 0; a < A.nradT; ++a) {
-            double val = 0.0;
-            if (inT) {
-                const double* fa = A.fT + (size_t)a * A.Nr + sT;
-                val = LT[0] * fa[0] + LT[1] * fa[1] + LT[2] * fa[2] + LT[3] * fa[3] + LT[4] * fa[4];
-            }
+            const double val = interp(A.fT, a, inT, sT, LT);
             const int l = A.radT_l[a];
             for (int m = -l; m <= l; ++m) {
                 const int i = A.stT_index[a * (2 * WPCCC_LMAX + 1) + m + WPCCC_LMAX];
                 const int am = m < 0 ? -m : m;
                 const double sg = (m < 0 && (am & 1)) ? -1.0 : 1.0;
-                aT[(size_t)i * A.G + g] = (T)(val * thv[0][l * (l + 1) / 2 + am] * sg);
+                aT[(size_t)i * A.G + g] = (T)(val * thv[l * (l + 1) / 2 + am] * sg);
             }
         }
+        theta_lq(cP, A.lmaxP, A, [&](int q, double val) { thv[q] = val; });
         for (int b2 = 0; b2 < A.nradP; ++b2) {
-            double val = 0.0;
-            if (inP) {
-                const double* fa = A.fP + (size_t)b2 * A.Nr + sP;
-                val = LP[0] * fa[0] + LP[1] * fa[1] + LP[2] * fa[2] + LP[3] * fa[3] + LP[4] * fa[4];
-            }
+            const double val = interp(A.fP, b2, inP, sP, LP);
             const int l = A.radP_l[b2];
             for (int q = 0; q <= l; ++q) {
                 const int j = A.half_of[b2 * (WPCCC_LMAX + 1) + q];
-                aP[(size_t)j * A.G + g] = (T)(val * thv[1][l * (l + 1) / 2 + q]);
+                aP[(size_t)j * A.G + g] = (T)(val * thv[l * (l + 1) / 2 + q]);
             }
         }
     }
     // node weights for the two integrands, d = |q - q'| = 0..dmax; Q carries the target potential
-    const double uQ = A.mp_c == 0.0 ? -A.Z_T / rT
-                                    : -A.Z_T / rT + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT) / rT;
+    const double irT = 1.0 / rT;
+    const double uQ = A.mp_c == 0.0 ? -A.Z_T * irT
+                                    : (-A.Z_T + (-A.mp_c * exp(-A.mp_a * rT)) * (1.0 + A.mp_b * rT)) * irT;
     const size_t stride = (size_t)(A.dmax + 1) * A.G;
     double Jd[BESSEL_MAX + 1];
     bessel_j_orders(A.dmax, x, Jd);
@@ -317,22 +326,29 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         }
         const double2 w0 = make_double2(J * re, J * im);
         const size_t o = (size_t)d * A.G + g;
-        T2 a, bq;
-        a.x = (T)w0.x;
-        a.y = (T)w0.y;
-        bq.x = (T)(w0.x * uQ);
-        bq.y = (T)(w0.y * uQ);
         if (sizeof(T) == 4 && A.tc) {
             // tensor-core layout: W_K / r_T as double-floats, [d][re, im][G] (r_T and the transfer
             // potential sit in the slice planes)
             float2* w6 = reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.t6_w_off);
-            w6[((size_t)d * 2) * A.G + g] = df_split(w0.x / rT);
-            w6[((size_t)d * 2 + 1) * A.G + g] = df_split(w0.y / rT);
+            w6[((size_t)d * 2) * A.G + g] = df_split(w0.x * irT);
+            w6[((size_t)d * 2 + 1) * A.G + g] = df_split(w0.y * irT);
         } else {
+            T2 a, bq;
+            a.x = (T)w0.x;
+            a.y = (T)w0.y;
+            bq.x = (T)(w0.x * uQ);
+            bq.y = (T)(w0.y * uQ);
             W[o] = a;
             W[stride + o] = bq;
         }
     }
+}
+
+// Dynamic shared memory of k_node_tables: the tensor-core layout's per-window tables, else none.
+static size_t node_tables_smem(const wpccc_basis_s* B, bool tc) {
+    if (!tc) return 0;
+    const int nlq = std::max(B->nlq_T, B->nlq_P);
+    return (size_t)(nlq + 2 + TC_NA) * 128 * sizeof(float2);
 }
 
 // ---------------------------------------------------------------------------
@@ -1243,10 +1259,26 @@ static wpccc_status launch_tables(wpccc_basis_s* B, const EvalDesc* evals, int n
     na.t6_ap_off = L.t6_ap_off;
     na.t6_w_off = L.t6_w_off;
     na.t6_sc_off = L.t6_sc_off;
+    for (int l = 0; l <= WPCCC_LMAX; ++l) {
+        na.inv_int[l] = l > 0 ? 1.0 / l : 0.0;
+        for (int q = 0; q <= l; ++q) {
+            double num = 1.0, den = 1.0;   // (l-q)!, (l+q)!
+            for (int k = 2; k <= l - q; ++k) num *= k;
+            for (int k = 2; k <= l + q; ++k) den *= k;
+            na.th_nrm[l * (l + 1) / 2 + q] = std::sqrt((2.0 * l + 1.0) * 0.5 * num / den);
+        }
+    }
     if (na.tc && !B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
+    if (na.tc && B->G % 128 != 0) return fail(WPCCC_EUNSUPPORTED, "the tensor-core layout needs a multiple of 128 nodes");
+    const size_t nsm = node_tables_smem(B, na.tc);
     cudaEvent_t e0 = B->prof.begin(PROF_NODES, st);
-    if (precision == 0) k_node_tables<double><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
-    else k_node_tables<float><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
+    if (precision == 0) {
+        k_node_tables<double><<<dim3((B->G + 127) / 128, nev), 128, 0, st>>>(na, evals);
+    } else {
+        if (nsm > 48 * 1024)
+            WPCCC_CUDA(cudaFuncSetAttribute(k_node_tables<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm));
+        k_node_tables<float><<<dim3((B->G + 127) / 128, nev), 128, nsm, st>>>(na, evals);
+    }
     WPCCC_CHECK_LAUNCH("k_node_tables");
     B->prof.end(PROF_NODES, st, e0);
     return WPCCC_OK;
@@ -1513,7 +1545,7 @@ static wpccc_status matrix_elements_prec(wpccc_basis B, double b, double v, int 
         WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
             WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
-            return fail(WPCCC_ECUDA, "a wait of the tensor-core contraction timed out (stage " + std::to_string(e) + ")");
+            return fail(WPCCC_ETIMEOUT, "a wait of the tensor-core contraction timed out (stage " + std::to_string(e) + ")");
         }
     }
     return WPCCC_OK;

@@ -40,31 +40,39 @@
 namespace wpccc {
 
 constexpr int T6_M = 128;                              // table rows per CTA (MMA M)
-constexpr int T6_N = 48;                               // generated rows per CTA (MMA N)
 constexpr int T6_K = 32;                               // nodes per chunk: one 64-byte bf16 row
 constexpr int T6_WIN = 4;                              // chunks per scaling window (128 nodes)
-// accumulators: SL = 7: levels 0, 1, 2, 3 (exact) and >= 4; SL = 3: levels 0, 1, 2 (exact)
+// Per slice count: accumulators (SL = 7: levels 0, 1, 2, 3 exact and >= 4; SL = 3: levels 0, 1, 2 exact)
+// and generated rows per CTA (MMA N), so that two buffers of accumulators fill the 512 TMEM columns
+// (2 x 5 x 48 = 2 x 3 x 80 = 480); eight producer threads per generated row.
 template <int SL> struct Tc64Cfg {
     static constexpr int ACC = SL == 7 ? 5 : SL;
+    static constexpr int N = SL == 7 ? 48 : 64;
+    static constexpr int PE_WARPS = N / 4;                       // producer / epilogue warps
+    static constexpr int THREADS = (PE_WARPS + 1) * 32;
+    static constexpr int BUF_COLS = ACC * N;                    // column offset of the second buffer
+    static constexpr int B_TILE = N * 64;                       // bytes of one slice of the generated tile
+    static constexpr int TSTAGE_BYTES = SL * T6_M * 64;         // a multiple of 1024
+    static constexpr int GSTAGE_BYTES = SL * N * 64;            // a multiple of 1024
+    static constexpr int SC_FLOATS = T6_M + N;                  // per scale slot: table rows, generated rows
+    static constexpr int COLS_PER_WARP = N / (PE_WARPS / 4);    // 16 columns per epilogue warp
+    static_assert(PE_WARPS * 32 == N * 8, "eight producer threads (4 nodes each) per generated row");
+    static_assert(2 * BUF_COLS <= 512, "two buffers of accumulators fit the TMEM allocation");
+    static_assert(TSTAGE_BYTES % 1024 == 0 && GSTAGE_BYTES % 1024 == 0, "1024-byte aligned stages");
 };
-constexpr int T6_ACC_MAX = 5;
 constexpr int T6_TSTAGES = 3;                          // table tiles in flight (TMA ring)
 constexpr int T6_GSTAGES = 2;                          // generated tiles (producer ring)
 constexpr int T6_SC_SLOTS = 2;                         // scale ring, one slot per window (see the drain)
-constexpr int T6_PE_WARPS = 12;                        // producer / epilogue warps
-constexpr int T6_THREADS = (T6_PE_WARPS + 1) * 32;
-constexpr int T6_TMEM_COLS = 512;                      // 2 buffers x 5 accumulators x 48 columns = 480
-constexpr int T6_BUF_COLS = T6_ACC_MAX * T6_N;          // column offset of the second buffer
+constexpr int T6_TMEM_COLS = 512;
 constexpr int T6_A_TILE = T6_M * 64;                   // bytes of one slice of the table tile
-constexpr int T6_B_TILE = T6_N * 64;                   // bytes of one slice of the generated tile
-constexpr int T6_TSTAGE_BYTES = OZ_SLICES * T6_A_TILE;          // 56 KB (room for seven slices), a multiple of 1024
-constexpr int T6_GSTAGE_BYTES = OZ_SLICES * T6_B_TILE;          // 21 KB, a multiple of 1024
-constexpr int T6_BOXES = T6_M / 32;                             // table box heights 32, 64, 96, 128 rows
-constexpr int T6_SC_FLOATS = T6_M + T6_N;              // per slot: table row scales, generated row scales
-constexpr int T6_COLS_PER_WARP = T6_N / (T6_PE_WARPS / 4);   // 16 columns per epilogue warp
+constexpr int T6_BOXES = T6_M / 32;                    // table box heights 32, 64, 96, 128 rows
 
-static_assert(T6_PE_WARPS * 32 == T6_N * 8, "eight producer threads (4 nodes each) per generated row");
-static_assert(2 * T6_BUF_COLS <= T6_TMEM_COLS, "two buffers of accumulators fit the TMEM allocation");
+template <int SL>
+static size_t tc64_smem_bytes() {
+    using CF = Tc64Cfg<SL>;
+    return 1024 + (size_t)T6_TSTAGES * CF::TSTAGE_BYTES + (size_t)T6_GSTAGES * CF::GSTAGE_BYTES +
+           sizeof(float) * T6_SC_SLOTS * CF::SC_FLOATS + 8 * (2 * T6_TSTAGES + 2 * T6_GSTAGES + 4);
+}
 
 // Tensor maps of the slice planes with box heights 32, 64, 96 and 128 rows: a row tile loads only the
 // 32-row multiple that covers its rows (rows past its end are loaded from the next tile, or left stale,
@@ -84,11 +92,21 @@ struct Tc64Args {
     size_t sc_off_f, ap_off_f, w_off_f;
     double* mol;           // [nev][2][N_T][n_half] complex, written as (re, im) doubles
     int* err;
+    long wait_limit;       // polls of an mbarrier wait before it gives up
 };
 
 template <int SL>
-__global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constant__ Tc64Maps maps, Tc64Args A) {
-    constexpr int T6_ACC = Tc64Cfg<SL>::ACC;
+__global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS) k_mol_tc64(const __grid_constant__ Tc64Maps maps, Tc64Args A) {
+    using CF = Tc64Cfg<SL>;
+    constexpr int T6_ACC = CF::ACC;
+    constexpr int T6_N = CF::N;
+    constexpr int T6_PE_WARPS = CF::PE_WARPS;
+    constexpr int T6_BUF_COLS = CF::BUF_COLS;
+    constexpr int T6_B_TILE = CF::B_TILE;
+    constexpr int T6_TSTAGE_BYTES = CF::TSTAGE_BYTES;
+    constexpr int T6_GSTAGE_BYTES = CF::GSTAGE_BYTES;
+    constexpr int T6_SC_FLOATS = CF::SC_FLOATS;
+    constexpr int T6_COLS_PER_WARP = CF::COLS_PER_WARP;
     extern __shared__ __align__(1024) unsigned char t6_smem_raw[];
     unsigned char* sm = t6_smem_raw + ((1024 - (smem_u32(t6_smem_raw) & 1023)) & 1023);
     unsigned char* gsm = sm + T6_TSTAGES * T6_TSTAGE_BYTES;                        // generated tiles
@@ -150,11 +168,12 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
             int issued = 0;
             for (; issued < T6_TSTAGES && issued < nk; ++issued) issue_tma(issued);
             bool ok = true;
+            int last_mma = -1;   // the last chunk whose MMAs were issued (their completion commits to tempty)
             for (int k = 0; k < nk && ok; ++k) {
                 const int s = k % T6_TSTAGES, s2 = k % T6_GSTAGES, w = k / T6_WIN, b = w & 1;
-                ok = mbar_wait(tfull0 + 8 * s, (k / T6_TSTAGES) & 1, abort_flag, A.err, 11);
-                if (ok) ok = mbar_wait(gfull0 + 8 * s2, (k / T6_GSTAGES) & 1, abort_flag, A.err, 16);
-                if (ok && k % T6_WIN == 0 && w >= 2) ok = mbar_wait(acce0 + 8 * b, ((w - 2) >> 1) & 1, abort_flag, A.err, 12);
+                ok = mbar_wait(tfull0 + 8 * s, (k / T6_TSTAGES) & 1, abort_flag, A.err, 11, A.wait_limit);
+                if (ok) ok = mbar_wait(gfull0 + 8 * s2, (k / T6_GSTAGES) & 1, abort_flag, A.err, 16, A.wait_limit);
+                if (ok && k % T6_WIN == 0 && w >= 2) ok = mbar_wait(acce0 + 8 * b, ((w - 2) >> 1) & 1, abort_flag, A.err, 12, A.wait_limit);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(sm + s * T6_TSTAGE_BYTES), b0 = smem_u32(gsm + s2 * T6_GSTAGE_BYTES);
@@ -180,11 +199,12 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
                 }
                 tc_commit(tempty0 + 8 * s);
                 tc_commit(gempty0 + 8 * s2);
+                last_mma = k;
                 if (k % T6_WIN == T6_WIN - 1) tc_commit(accf0 + 8 * b);
                 if (k >= 1 && issued < nk) {
                     // refill the table slot of the previous chunk (for chunk k + 2) once its MMAs have completed
                     const int kp = k - 1, sp = kp % T6_TSTAGES;
-                    ok = mbar_wait(tempty0 + 8 * sp, (kp / T6_TSTAGES) & 1, abort_flag, A.err, 13);
+                    ok = mbar_wait(tempty0 + 8 * sp, (kp / T6_TSTAGES) & 1, abort_flag, A.err, 13, A.wait_limit);
                     if (ok) issue_tma(issued++);
                 }
             }
@@ -194,6 +214,14 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
                     const int s = k % T6_TSTAGES;
                     for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(tfull0 + 8 * s, (k / T6_TSTAGES) & 1); ++it) {
                     }
+                }
+            }
+            // the MMAs issued complete before the tensor memory is released (they finish in order: the last
+            // chunk's commit covers them all); on the normal path the epilogue has waited for them already,
+            // on a give-up path nobody else does
+            if (last_mma >= 0) {
+                const int s = last_mma % T6_TSTAGES;
+                for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(tempty0 + 8 * s, (last_mma / T6_TSTAGES) & 1); ++it) {
                 }
             }
         }
@@ -225,7 +253,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
         // drain of window j: its accumulators with the window's scales
         auto drain = [&](int j) {
             const int b = j & 1;
-            ok = ok && mbar_wait(accf0 + 8 * b, (j >> 1) & 1, abort_flag, A.err, 14);
+            ok = ok && mbar_wait(accf0 + 8 * b, (j >> 1) & 1, abort_flag, A.err, 14, A.wait_limit);
             if (!ok) return;
             tc_fence_after();
             if (live) {
@@ -290,7 +318,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) k_mol_tc64(const __grid_constan
             for (int cc = 0; cc < T6_WIN; ++cc) {
                 const int k = w * T6_WIN + cc, s = k % T6_GSTAGES;
                 if (k >= T6_GSTAGES)
-                    ok = ok && mbar_wait(gempty0 + 8 * s, ((k - T6_GSTAGES) / T6_GSTAGES) & 1, abort_flag, A.err, 15);
+                    ok = ok && mbar_wait(gempty0 + 8 * s, ((k - T6_GSTAGES) / T6_GSTAGES) & 1, abort_flag, A.err, 15, A.wait_limit);
                 if (!ok) break;
                 unsigned char* bt = gsm + s * T6_GSTAGE_BYTES;
                 __nv_bfloat16 q[4][SL];
@@ -355,7 +383,7 @@ wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double
     a.N_T = B->N_T;
     a.n_half = B->n_half;
     a.nchunks = B->G / T6_K;
-    a.n_ntiles = (2 * B->n_half + T6_N - 1) / T6_N;
+    a.n_ntiles = 0;   // per slice count, below
     a.tc_rows = L.tc_rows;
     a.qg_max = B->qg_max;
     a.qg_off = B->qg_off;
@@ -369,15 +397,19 @@ wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double
     a.w_off_f = L.t6_w_off;
     a.mol = reinterpret_cast<double*>(mol);
     a.err = err;
-    const size_t smem = 1024 + (size_t)T6_TSTAGES * T6_TSTAGE_BYTES + (size_t)T6_GSTAGES * T6_GSTAGE_BYTES +
-                        sizeof(float) * T6_SC_SLOTS * T6_SC_FLOATS + 8 * (2 * T6_TSTAGES + 2 * T6_GSTAGES + 4);
-    const dim3 grid(a.n_ntiles * B->n_qgroups, nev);
+    a.wait_limit = B->wait_polls;
     if (slices == OZ_SLICES) {
+        using CF = Tc64Cfg<OZ_SLICES>;
+        a.n_ntiles = (2 * B->n_half + CF::N - 1) / CF::N;
+        const size_t smem = tc64_smem_bytes<OZ_SLICES>();
         WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<OZ_SLICES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_mol_tc64<OZ_SLICES><<<grid, T6_THREADS, smem, st>>>(maps, a);
+        k_mol_tc64<OZ_SLICES><<<dim3(a.n_ntiles * B->n_qgroups, nev), CF::THREADS, smem, st>>>(maps, a);
     } else {
+        using CF = Tc64Cfg<3>;
+        a.n_ntiles = (2 * B->n_half + CF::N - 1) / CF::N;
+        const size_t smem = tc64_smem_bytes<3>();
         WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_mol_tc64<3><<<grid, T6_THREADS, smem, st>>>(maps, a);
+        k_mol_tc64<3><<<dim3(a.n_ntiles * B->n_qgroups, nev), CF::THREADS, smem, st>>>(maps, a);
     }
     WPCCC_CHECK_LAUNCH("k_mol_tc64");
     return WPCCC_OK;

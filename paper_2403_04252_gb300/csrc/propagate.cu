@@ -26,12 +26,12 @@ struct PathChunk {
     double v;
 };
 
-enum : int { FLAG_SINGULAR = 1, FLAG_NONFINITE = 2 };
 
 struct RkArgs {
     int N;
     int N_T;                // target states (two-centre: S = [[I, K], [K^+, I]])
     int iters;              // refinement iterations (mixed-precision form)
+    double tol;             // convergence tolerance of the refinement's last sweep (<= 0: unchecked)
     const float2* LU32;     // chunk: FP32 factors per evaluation (mixed forms: LU, or K and the Schur factor)
     float2* carryLU32;      // per path (mixed form)
     const double2* H;       // chunk: H (one-centre, or X = S^{-1} H in matrix mode) per evaluation
@@ -114,10 +114,10 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
             apply_LU(m.S, m.piv, m.H, N, v, in, out, t, static_cast<double2*>(blk));
         } else if (MODE == RK_MIXED_SCHUR) {
             apply_schur_mixed(m.S, m.L32, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds, us32,
-                              static_cast<float2*>(blk));
+                              static_cast<float2*>(blk), A.tol, A.flags);
         } else {
             apply_LU_mixed(m.S, m.L32, m.piv, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds,
-                           static_cast<float2*>(blk));
+                           static_cast<float2*>(blk), A.tol, A.flags);
         }
     };
     PosMats Mz;
@@ -366,7 +366,8 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     P.stage = P.two && !P.mixed && B->solve_mode != WPCCC_SOLVE_MATRIX;
     P.schur = P.two && B->solve_mode == WPCCC_SOLVE_SCHUR;
     P.mode = P.mixed ? (P.schur ? RK_MIXED_SCHUR : RK_MIXED) : (P.schur ? RK_SCHUR : (P.stage ? RK_STAGE : RK_MATRIX));
-    const bool fits = rk_smem_bytes(P.mode, N) <= (size_t)227 * 1024;
+    // 227 KB per block, less the kernels' static shared memory (the refinement check's reduction)
+    const bool fits = rk_smem_bytes(P.mode, N) + 1024 <= (size_t)227 * 1024;
     if (P.two && B->rk4_layout == WPCCC_RK4_GLOBAL)
         return fail(WPCCC_EUNSUPPORTED, "wpccc_propagate: the global-memory RK4 layout is one-centre only");
     P.wide = !P.two && (B->rk4_layout == WPCCC_RK4_GLOBAL || (B->rk4_layout == WPCCC_RK4_AUTO && !fits));
@@ -536,6 +537,7 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     ra.N = N;
     ra.N_T = B->N_T;
     ra.iters = B->refine_iters;
+    ra.tol = B->refine_tol;
     ra.carryH = P.d_carry;
     ra.carryLU = P.d_carryLU;
     ra.carryPiv = P.d_carryPiv;
@@ -611,6 +613,9 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
 static wpccc_status flags_status(int flags) {
     if (flags & FLAG_SINGULAR) return fail(WPCCC_ESINGULAR, "an overlap matrix had a zero pivot");
     if (flags & FLAG_NONFINITE) return fail(WPCCC_ENONFINITE, "amplitudes became non-finite");
+    if (flags & FLAG_NOCONV)
+        return fail(WPCCC_ENOCONV, "the FP64 refinement of a reduced-precision solve did not converge (last "
+                                   "correction above the tolerance relative to the solution)");
     return WPCCC_OK;
 }
 
@@ -651,7 +656,7 @@ wpccc_status propagate_internal(wpccc_basis_s* B, const wpccc_paths* paths, int 
         WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
             WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
-            return fail(WPCCC_ECUDA, "wpccc_propagate: a wait of the tensor-core contraction timed out (stage " +
+            return fail(WPCCC_ETIMEOUT, "wpccc_propagate: a wait of the tensor-core contraction timed out (stage " +
                                          std::to_string(e) + ")");
         }
     }
@@ -927,7 +932,7 @@ extern "C" wpccc_status wpccc_batch_status(wpccc_batch X, void* stream) {
             WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
             if (e) {
                 WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
-                return fail(WPCCC_ECUDA, "wpccc_batch_status: a wait of the tensor-core contraction timed out");
+                return fail(WPCCC_ETIMEOUT, "wpccc_batch_status: a wait of the tensor-core contraction timed out");
             }
         }
     }

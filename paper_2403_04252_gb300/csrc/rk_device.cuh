@@ -9,6 +9,33 @@ namespace wpccc {
 
 constexpr int RK_THREADS = 512;
 
+// Status bits the RK4 kernels raise in the propagation's flag word.
+enum : int { FLAG_SINGULAR = 1, FLAG_NONFINITE = 2, FLAG_NOCONV = 4 };
+
+// Convergence test of a refinement's last sweep: max|dx| <= tol max|x| over the block's vector, else
+// FLAG_NOCONV (dmax, xmax: this thread's maxima).  Called by all threads; ends with a block barrier.
+static __device__ void refine_check(double dmax, double xmax, double tol, int* flags) {
+    __shared__ double red[2][RK_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = dmax;
+        red[1][threadIdx.x >> 5] = xmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && flags) {
+        double d = 0.0, x = 0.0;
+        for (int i = 0; i < RK_THREADS / 32; ++i) {
+            d = fmax(d, red[0][i]);
+            x = fmax(x, red[1][i]);
+        }
+        if (!(d <= tol * x)) atomicOr(flags, FLAG_NOCONV);
+    }
+    __syncthreads();
+}
+
 // t <- S^{-1} t in place from the factors P S = L U (LAPACK layout, pivots 1-based);
 // C2 = double2 (FP64 factors) or float2 (FP32 factors of the mixed-precision form).
 // Blocked by 32 rows: each 32 x 32 diagonal block is staged in shared memory (blk) and solved by
@@ -163,12 +190,13 @@ static __device__ void apply_LU(const double2* __restrict__ LU, const int* __res
 }
 
 // Mixed-precision form: k = -(i/v) x with S x = H y solved by FP64 iterative refinement
-// preconditioned by FP32 factors: x_0 = 0, r = H y - S x_n (FP64), x_{n+1} = x_n + (LU_32)^{-1} r.
+// preconditioned by FP32 factors: x_0 = 0, r = H y - S x_n (FP64), x_{n+1} = x_n + (LU_32)^{-1} r; the
+// last sweep's correction is checked against the solution (refine_check) when tol > 0.
 // Shared scratch: b, x, r (double2) and d (float2), N each.
 static __device__ void apply_LU_mixed(const double2* __restrict__ S64, const float2* __restrict__ LU32,
                                const int* __restrict__ piv, const double2* __restrict__ Hm, int N, int N_T, double v,
                                int iters, const double2* y, double2* k, double2* b, double2* x, double2* r,
-                               float2* d, float2* blk) {
+                               float2* d, float2* blk, double tol = 0.0, int* flags = nullptr) {
     matvec(Hm, N, y, b);
     for (int it = 0; it < iters; ++it) {
         const double2* rr = b;
@@ -179,11 +207,15 @@ static __device__ void apply_LU_mixed(const double2* __restrict__ S64, const flo
         for (int i = threadIdx.x; i < N; i += RK_THREADS) d[i] = make_float2((float)rr[i].x, (float)rr[i].y);
         __syncthreads();
         lu_solve_inplace<float2>(LU32, piv, N, d, blk);
+        double dm = 0.0, xm = 0.0;
         for (int i = threadIdx.x; i < N; i += RK_THREADS) {
             const double2 dx = make_double2((double)d[i].x, (double)d[i].y);
             x[i] = it == 0 ? dx : make_double2(x[i].x + dx.x, x[i].y + dx.y);
+            dm = fmax(dm, fmax(fabs(dx.x), fabs(dx.y)));
+            xm = fmax(xm, fmax(fabs(x[i].x), fabs(x[i].y)));
         }
         __syncthreads();
+        if (it > 0 && it == iters - 1 && tol > 0.0) refine_check(dm, xm, tol, flags);
     }
     for (int i = threadIdx.x; i < N; i += RK_THREADS) k[i] = make_double2(x[i].y / v, -x[i].x / v);
     __syncthreads();
@@ -362,7 +394,7 @@ static __device__ void apply_schur(const double2* __restrict__ S, const double2*
 static __device__ void apply_schur_mixed(const double2* __restrict__ S64, const float2* __restrict__ D32,
                                          const double2* __restrict__ Hm, int N, int N_T, double v, int iters,
                                          const double2* y, double2* k, double2* b, double2* x, double2* r, float2* d,
-                                         float2* u, float2* blk) {
+                                         float2* u, float2* blk, double tol = 0.0, int* flags = nullptr) {
     matvec(Hm, N, y, b);
     for (int it = 0; it < iters; ++it) {
         const double2* rr = b;
@@ -373,11 +405,15 @@ static __device__ void apply_schur_mixed(const double2* __restrict__ S64, const 
         for (int i = threadIdx.x; i < N; i += RK_THREADS) d[i] = make_float2((float)rr[i].x, (float)rr[i].y);
         __syncthreads();
         schur_solve_inplace<float2>(D32, N, N_T, d, u, blk);
+        double dm = 0.0, xm = 0.0;
         for (int i = threadIdx.x; i < N; i += RK_THREADS) {
             const double2 dx = make_double2((double)d[i].x, (double)d[i].y);
             x[i] = it == 0 ? dx : make_double2(x[i].x + dx.x, x[i].y + dx.y);
+            dm = fmax(dm, fmax(fabs(dx.x), fabs(dx.y)));
+            xm = fmax(xm, fmax(fabs(x[i].x), fabs(x[i].y)));
         }
         __syncthreads();
+        if (it > 0 && it == iters - 1 && tol > 0.0) refine_check(dm, xm, tol, flags);
     }
     for (int i = threadIdx.x; i < N; i += RK_THREADS) k[i] = make_double2(x[i].y / v, -x[i].x / v);
     __syncthreads();

@@ -11,7 +11,7 @@
 
 namespace wpccc {
 
-constexpr long TC_WAIT_LIMIT = 1L << 20;   // polls of an mbarrier before a wait gives up
+constexpr long TC_WAIT_LIMIT = 1L << 20;   // polls of an mbarrier before a give-up path's own wait ends
 
 static __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -35,9 +35,10 @@ static __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false when the CTA has given up (another role timed out, or this wait did).
-static __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err, int code) {
-    for (long it = 0; it < TC_WAIT_LIMIT; ++it) {
+// Bounded wait (`limit` polls): false when the CTA has given up (another role timed out, or this wait did).
+static __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err, int code,
+                                 long limit) {
+    for (long it = 0; it < limit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
     }

@@ -124,6 +124,8 @@ struct wpccc_basis_s {
     double* deps = nullptr;                  // [n_par][N]: d eps_i / d theta_p per state
     wpccc::CentreTan tanT, tanP;
     int refine_iters = 2;       // FP64 refinement iterations of the mixed-precision form
+    double refine_tol = 1e-3;   // largest last correction / solution of a refinement (<= 0: not checked)
+    long wait_polls = 1L << 20; // polls of an mbarrier before a tensor-core kernel's wait gives up
     // tensor-core contraction (precision mode 3): node tables carry the split operand tables
     bool tc_layout = false;
     int n_qgroups = 0;          // row tiles: target states of one q', at most 56 per tile

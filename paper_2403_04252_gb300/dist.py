@@ -3,14 +3,15 @@
 Every straight-line path is independent (the paper runs one MPI rank per impact parameter), so the data
 path has no collective at all: each rank propagates its own paths with the library.  The only
 collectives are host-side: the maximum of the per-rank timings (a benchmark reports the slowest rank)
-and the gather of per-path observables to rank 0, which forms the cross sections.  They go through
+and the gather of per-path observables to rank 0, which forms the cross sections with the library's
+wpccc_cross_sections (paper_2403_04252_gb300.cross_sections).  They go through
 torch.distributed, so the same code runs on NCCL (one GPU per rank) and on gloo (CPU tests).
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["shard_impact_parameters", "max_over_ranks", "gather_paths", "cross_sections"]
+__all__ = ["shard_impact_parameters", "max_over_ranks", "gather_paths"]
 
 
 def shard_impact_parameters(b0: float, b1: float, per_rank: int, rank: int, world: int) -> np.ndarray:
@@ -61,16 +62,3 @@ def gather_paths(b: np.ndarray, values: np.ndarray, device=None):
     rows = np.concatenate([bufs[k].cpu().numpy()[:counts[k]] for k in range(world)])
     order = np.argsort(rows[:, 0], kind="stable")
     return rows[order, 0], rows[order, 1:]
-
-
-def cross_sections(b: np.ndarray, P: np.ndarray) -> np.ndarray:
-    """sigma_o = 2 pi int_0^inf b P_o(b) db by the trapezoid rule on the (sorted) impact parameters
-    plus b = 0, where b P(b) = 0.  P: [n_b][n_obs]."""
-    b = np.asarray(b, dtype=np.float64)
-    P = np.asarray(P, dtype=np.float64).reshape(b.size, -1)
-    nodes = np.concatenate([[0.0], b])
-    w = np.zeros(nodes.size)
-    d = np.diff(nodes)
-    w[:-1] += 0.5 * d
-    w[1:] += 0.5 * d
-    return 2.0 * np.pi * (w[1:] * b) @ P

@@ -126,7 +126,8 @@ def test_binding_constants_match_header():
     import paper_2403_04252_gb300 as w
     src = open(os.path.join(ROOT, "include", "wpccc.h")).read()
     enum = {k: int(v) for k, v in re.findall(r"\bWPCCC_([A-Z]+)\s*=\s*(\d+)", src)}
-    for name in ("OK", "EINVAL", "ENOMEM", "ESINGULAR", "ENONFINITE", "ECUDA", "EUNSUPPORTED"):
+    for name in ("OK", "EINVAL", "ENOMEM", "ESINGULAR", "ENONFINITE", "ECUDA", "EUNSUPPORTED", "ETIMEOUT",
+                 "ENOCONV"):
         assert getattr(w, name) == enum[name], name
     defines = {k: v for k, v in re.findall(r"#define WPCCC_(\w+)\s+(\S.*)", src)}
     for name in ("LMAX", "NMAX", "MAX_PARAMS", "MAX_REFINE", "SOLVE_STAGE", "SOLVE_MATRIX", "SOLVE_SCHUR",
@@ -134,3 +135,4 @@ def test_binding_constants_match_header():
         assert getattr(w, name) == int(defines[name]), name
     assert w.NOALLOC_SCRATCH_BYTES == 64 << 20 and "64 << 20" in defines["NOALLOC_SCRATCH_BYTES"]
     assert len(w.PROF_CATEGORIES) == int(defines["PROF_N"])
+    assert w.DEFAULT_WAIT_POLLS == 1 << 20 and "1L << 20" in defines["DEFAULT_WAIT_POLLS"]

@@ -421,3 +421,51 @@ def test_two_centre_phase_mistake_fails(schroedinger_two_centre, monkeypatch):
     monkeypatch.setattr(O, "phases", lambda er, ec, z, v: _PHASES(er, ec, z if er is ec else -z, v))
     P = O.probabilities(O.propagate(basis, b, v, zg))
     assert np.abs(P - ref).max() > 1e-2
+
+
+def test_parallel_oracle_driver_equals_the_serial_oracle():
+    # the pool only reorders independent M(z) evaluations: the amplitudes are bit-identical
+    import oracle_parallel as OP
+    basis = wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=16, Gtau=12)
+    zg = wi.uniform_zgrid(-3.0, 3.0, 0.25)
+    c1 = OP.propagate(basis, 0.7, 1.2, zg, workers=3, block=7)
+    c0 = O.propagate(basis, 0.7, 1.2, zg)
+    assert np.array_equal(c1, c0)
+
+
+def _overlap_balance(basis, b, v, zg, Mfun):
+    """(change of c^+ S c over the path, Simpson integral of c^+ (dS/dz) c) for the amplitudes that
+    oracle.rk4_path produces step by step with the given M(z)."""
+    c = O.initial_state(basis)
+    cs, norms = [c], [np.real(c.conj() @ O.assemble(basis, b, v, zg[0])[0] @ c)]
+    for k in range(1, zg.size):
+        c = O.rk4_path(Mfun, zg[k - 1:k + 1], c)
+        cs.append(c)
+        norms.append(np.real(c.conj() @ O.assemble(basis, b, v, zg[k])[0] @ c))
+    dz = 1e-4
+    f = np.array([np.real(ck.conj() @ ((O.assemble(basis, b, v, z + dz)[0] - O.assemble(basis, b, v, z - dz)[0])
+                                       / (2 * dz)) @ ck) for ck, z in zip(cs, zg)])
+    h = zg[1] - zg[0]
+    simpson = h / 3 * (f[0] + f[-1] + 4 * f[1:-1:2].sum() + 2 * f[2:-1:2].sum())
+    return norms[-1] - norms[0], simpson
+
+
+def test_overlap_norm_obeys_its_balance_law():
+    # i v S dc/dz = H c with Hermitian H and S (Eq. 1 with the lower-left block Q^+) gives
+    # d(c^+ S c)/dz = c^+ (dS/dz) c: the two-centre propagation moves c^+ S c exactly by that integral
+    # (it is not conserved: dS/dz != 0).  Planted mistake: the lower-left block Q^T (H not Hermitian)
+    basis = wi.make_basis(1.0, 1.0, 2, 1, 2, 2.0, True, Nr=600, Geta=16, Gtau=12)
+    b, v = 0.7, 1.2
+    zg = wi.uniform_zgrid(-2.0, 2.0, 0.02)
+    drift, integral = _overlap_balance(basis, b, v, zg, lambda z: O.coupling_M(basis, b, v, z))
+    assert abs(drift) > 1e-3
+    assert abs(drift - integral) < 1e-8
+
+    def M_transposed(z):
+        S, H = O.assemble(basis, b, v, z)
+        NT = basis.T.N
+        H = H.copy()
+        H[NT:, :NT] = H[:NT, NT:].T
+        return (-1j / v) * np.linalg.solve(S, H)
+    drift_m, integral_m = _overlap_balance(basis, b, v, zg, M_transposed)
+    assert abs(drift_m - integral_m) > 1e-4

@@ -35,7 +35,7 @@ from scipy.interpolate import CubicSpline
 __all__ = [
     "RadialGrid", "Centre", "Basis", "Quadrature", "Paths",
     "radial_grid", "hydrogenic_radial", "coulomb_bins", "make_centre",
-    "make_basis", "make_quadrature", "uniform_zgrid", "geometric_zgrid",
+    "make_basis", "make_quadrature", "uniform_zgrid", "geometric_zgrid", "piecewise_zgrid",
     "make_paths", "CONFIGS", "config_inputs", "CentreTangent", "box_centre", "li_model_potential",
     "li_basis", "li_parameters", "observable_weights", "cross_section_weights", "li_inputs",
 ]
@@ -488,6 +488,26 @@ def geometric_zgrid(zmin: float = 1e-3, zmax: float = 100.0, nz: int = 500) -> n
     return np.concatenate([-pos[::-1], [0.0], pos])
 
 
+# Segments of the C6+ + H z-grid: (end of the |z| range, largest step in it).  The step bound in each
+# range is 2 / omega_max at the range's start, where omega_max = max |lambda(H, S)| / v of the workload's
+# basis at its smallest impact parameter b = 0.5 (FP64 oracle: 984 at |z| = 0.3, 514 at 2, 123 at 4,
+# 40 at 6, 13.4 at 8, 2.6 at 12, 0.22 at 50); RK4 is stable on the imaginary axis for h omega < 2.83.
+C6_ZGRID_SEGMENTS = ((2.0, 2.0e-3), (4.0, 3.9e-3), (6.0, 0.016), (8.0, 0.05), (12.0, 0.15), (50.0, 0.5))
+
+
+def piecewise_zgrid(segments) -> np.ndarray:
+    """Symmetric z-grid, uniform within each |z| range: segments = ((z_1, h_1), (z_2, h_2), ...) cover
+    [0, z_1], [z_1, z_2], ... with ceil((z_k - z_{k-1}) / h_k) equal steps each, mirrored to z < 0."""
+    pos = [0.0]
+    z0 = 0.0
+    for z1, h in segments:
+        n = int(math.ceil((z1 - z0) / h - 1e-9))
+        pos.extend(z0 + (z1 - z0) * np.arange(1, n + 1, dtype=np.float64) / n)
+        z0 = z1
+    pos = np.asarray(pos)
+    return np.concatenate([-pos[:0:-1], pos])
+
+
 @dataclass
 class Paths:
     b: np.ndarray                     # [n_paths]
@@ -519,13 +539,14 @@ CONFIGS = {
     # two-centre p + H with electron capture
     "p_H_2c_n4l3": dict(Z_T=1.0, Z_P=1.0, nmax=4, lmax=3, nbins=10, kmax=3.0, two_centre=True,
                         v=1.5, b=(0.2, 12.0, 32), z=(-50.0, 50.0, 0.1)),
-    # two-centre bare C6+ on H (projectile charge 6), the mixed-precision workload; on the paper's
-    # geometric z-grid (Sec. II: dense near closest approach, where the C6+ couplings need h << 0.1)
-    # 128 eta nodes: the compact C5+ orbitals and the k <= 4 packets need them for a positive-definite S
-    # (sigma_max(K) at b = 0.5, z = 0: 1.56 with 48 nodes, 1.28 with 72, 1.06 with 96, 0.99847 with 128,
-    # 0.99846 with 160 x 64)
+    # two-centre bare C6+ on H (projectile charge 6), the mixed-precision workload.  128 eta nodes: the
+    # compact C5+ orbitals and the k <= 4 packets need them for a positive-definite S (sigma_max(K) at
+    # b = 0.5, z = 0: 1.56 with 48 nodes, 1.28 with 72, 1.06 with 96, 0.99847 with 128, 0.99846 with
+    # 160 x 64).  z-grid: steps bounded by the basis' stiffness (C6_ZGRID_SEGMENTS, 3562 RK4 steps); the
+    # paper's geometric grid of Sec. II takes steps of 0.022 |z|, which RK4 cannot follow where
+    # omega_max ~ 1e3 (0.1 < |z| < 6 at b = 0.5: the amplitudes overflow)
     "C6_H_2c_n6l5": dict(Z_T=1.0, Z_P=6.0, nmax=6, lmax=5, nbins=20, kmax=4.0, two_centre=True,
-                         v=2.0, b=(0.5, 15.0, 16), z=("geometric", 1e-3, 50.0, 500), Geta=128, Gtau=48),
+                         v=2.0, b=(0.5, 15.0, 16), z=("piecewise", C6_ZGRID_SEGMENTS), Geta=128, Gtau=48),
 }
 
 
@@ -562,6 +583,8 @@ def config_inputs(name: str, **over):
     b0, b1, nb = c["b"]
     if c["z"][0] == "geometric":
         zgrid = geometric_zgrid(*c["z"][1:])
+    elif c["z"][0] == "piecewise":
+        zgrid = piecewise_zgrid(c["z"][1])
     else:
         zgrid = uniform_zgrid(*c["z"])
     paths = make_paths(np.linspace(b0, b1, nb), c["v"], zgrid)
