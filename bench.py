@@ -55,7 +55,8 @@ FP32_FFMA_MEASURED_TFLOPS = 69.9
 
 
 # forms of the batched bench: (precision mode, refinement sweeps, name)
-BATCH_FORMS = ((0, 2, "fp64"), (4, 2, "fp64-tensor-core"), (5, 4, "fp64-tc-refined"), (5, 2, "mixed-fp64-tc-elements"))
+BATCH_FORMS = ((0, 2, "fp64"), (4, 2, "fp64-tensor-core"), (5, 4, "fp64-tc-refined"), (5, 2, "mixed-fp64-tc-elements"),
+               (3, 2, "mixed-tensor-core"))
 
 SOLVE_MODES = {"stage": lambda w: w.SOLVE_STAGE, "matrix": lambda w: w.SOLVE_MATRIX, "schur": lambda w: w.SOLVE_SCHUR}
 
@@ -353,8 +354,8 @@ def run_batch(args) -> dict:
         cats["rk4"] = (_rk4_flops_per_step(mode, args.solve_mode, basis.N, basis.T.N, basis.P.N),
                        ("alu", FP64_PEAK_TFLOPS, "TFLOP/s"), "k_rk4")
         for k, (per_unit, meta, name) in cats.items():
-            units = args.steps * b.size * (seg.size - 1) if k == "rk4" else evals
-            work[k] = work.get(k, 0.0) + per_unit * units
+            n_units = args.steps * b.size * (seg.size - 1) if k == "rk4" else evals
+            work[k] = work.get(k, 0.0) + per_unit * n_units
             cat_meta[k] = (meta, name)
 
     def roof_b(key: str) -> dict:
@@ -374,7 +375,8 @@ def run_batch(args) -> dict:
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {0: "f64", 4: "bf16-slices(fp64-accurate)+f64"}.get(mode, "bf16-slices(fp64-accurate)+f32+f64"),
+            "dtype": {0: "f64", 4: "bf16-slices(fp64-accurate)+f64", 3: "bf16x4-slices+f32+f64"}.get(
+                mode, "bf16-slices(fp64-accurate)+f32+f64"),
             "data": "synthetic",
             "config": {"workload": "batched form: two-centre p+H at v in {0.5,0.8,1.2,2,3,4}, pseudostates per "
                                    "l = round(8+8(v-0.5)/3.5) = 8..16 (k<=3), hydrogenic n<=4, l<=3, all m, "
@@ -695,7 +697,7 @@ def _category_rooflines(basis, mode: int, solve_mode: str, N: int, n_half: int) 
     """Per position (evaluation of S and H at one z): the work each category of kernels must do, as the
     method defines it, with the bound and peak that apply.  Contraction: K and Q over the full N_T x N_P
     block, 4 real flops per node each (8 N_T N_P G; the q -> -q reflection lets the kernels form only the
-    n_half projectile columns with q >= 0, and the tensor-core forms issue 6 or 28 bf16 slice products per
+    n_half projectile columns with q >= 0, and the tensor-core forms issue 10 or 28 bf16 slice products per
     algorithmic product: neither changes the algorithmic count).  Factorisation: the Schur complement's
     lower triangle and its Cholesky factor (4 N_P^2 N_T + 4/3 N_P^3), or LU (8/3 N^3).  Node tables and
     rotation/direct blocks are bound by memory: the bytes they must write (node tables of the layout the
@@ -940,7 +942,7 @@ def run_fixed_speed(args, sub: bool = False) -> dict:
     cats = _category_rooflines(basis, mode, args.solve_mode, N, n_half)
     cats["rk4"] = (_rk4_flops_per_step(mode, args.solve_mode, N, NT, NP_), ("alu", FP64_PEAK_TFLOPS, "TFLOP/s"),
                    "k_rk4")
-    issued = {3: 6.0, 4: 28.0, 5: 28.0}.get(mode)
+    issued = {3: 10.0, 4: 28.0, 5: 28.0}.get(mode)
 
     def roof(key: str) -> dict:
         k_ms, k_launches = prof[key]
@@ -978,8 +980,9 @@ def run_fixed_speed(args, sub: bool = False) -> dict:
                  1: "mixed precision: Eq. 9 contraction and the factors of S on the FP32 pipe, FP64 "
                     "node tables, refinement and RK4; all paths batched",
                  2: "mixed precision with FP64 elements: factors of S on the FP32 pipe, FP64 refinement and RK4",
-                 3: "mixed precision, tensor-core contraction: Eq. 9 on tcgen05 (fixed-point bf16 slices, exact "
-                    "main accumulation), FP32 factors of S, FP64 refinement and RK4; all paths batched",
+                 3: "mixed precision, tensor-core contraction: Eq. 9 on tcgen05 (four fixed-point bf16 slices, ten "
+                    "slice products into exact FP32 accumulators), FP32 factors of S, FP64 refinement and RK4; all "
+                    "paths batched",
                  4: "FP64-accurate: Eq. 9 contraction emulated on tcgen05 (seven bf16 slices per operand, 28 "
                     "slice products, exact level accumulators, double-float sums), FP64 solve and RK4",
                  5: "mixed precision with FP64-accurate tensor-core elements: FP32 factors of S, FP64 refinement "
@@ -989,7 +992,7 @@ def run_fixed_speed(args, sub: bool = False) -> dict:
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {0: "f64", 3: "bf16-slices+f32+f64", 4: "bf16-slices(fp64-accurate)+f64",
+            "dtype": {0: "f64", 3: "bf16x4-slices+f32+f64", 4: "bf16-slices(fp64-accurate)+f64",
                       5: "bf16-slices(fp64-accurate)+f32+f64",
                       6: "bf16-slices(fp64-accurate)+f32+f64"}.get(prec, "f32+f64"), "data": "synthetic",
             "config": {"workload": CONFIG_DESC if not c6 else CONFIG_DESC_C6, "paths": n_paths,

@@ -179,7 +179,7 @@ WPCCC_API wpccc_status wpccc_matrix_elements(wpccc_basis basis, double b, double
  * wpccc_matrix_elements with the element arithmetic of a reduced-precision form, to measure its element
  * error against the FP64 elements (the paper has no counterpart):
  *   precision_mode 0 FP64 (= wpccc_matrix_elements), 1 the Eq. 9 contraction on the FP32 pipe,
- *   3 the Eq. 9 contraction on the tensor cores at FP32 level, 4 the same to FP64 accuracy (see
+ *   3 the Eq. 9 contraction on the tensor cores with four slices, 4 the same to FP64 accuracy (see
  *   wpccc_propagate).  S and H are returned in FP64.
  * Errors: as wpccc_matrix_elements; EUNSUPPORTED for other modes, one-centre bases or model-potential
  * targets in modes 1, 3 and 4.
@@ -250,17 +250,17 @@ WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv
  *     2  mixed with FP64 elements: as 1 but the contraction stays in FP64 (for
  *        ill-conditioned S, where FP32 element errors get amplified by cond(S));
  *     3  as 1 with the Eq. 9 contraction on the 5th-generation tensor cores: tcgen05.mma
- *        (kind::f16) on three bf16 fixed-point slices of both operands per 128-node window
- *        (six slice products into three exact FP32 accumulators, FP32-level result), drained
- *        per window into double-float sums; table tiles staged by TMA;
+ *        (kind::f16) on four bf16 fixed-point slices of both operands per 128-node window
+ *        (ten slice products into four exact FP32 accumulators, about 2^-28 of each window's
+ *        largest term), drained per window into double-float sums; table tiles staged by TMA;
  *     4  the FP64 form (solve and RK4 as mode 0) with the Eq. 9 contraction emulated to FP64
  *        accuracy on the tensor cores: seven bf16 slices of both operands in fixed point per
  *        128-node window (error-free splitting, Ozaki et al.), 28 slice products into five FP32
  *        accumulators of which four are exact, drained into double-float sums; element errors
  *        about 2^-47 of the largest quadrature term;
  *     5  as 2 (FP32 factors and FP64 refinement) with the elements of mode 4;
- *     modes 3-5 need no model potential and a node count that is a multiple of 32 (mode 3) or
- *     128 (modes 4 and 5: fixed-point scales per 128-node window); in one-centre mode all modes
+ *     modes 3-5 need no model potential and a node count that is a multiple of 128 (fixed-point
+ *     scales per 128-node window); in one-centre mode all modes
  *     are the FP64 form (no contraction, no solve).
  *   batch_mode 0 = all paths batched together in chunks of RK4 steps (the only
  *   batch mode of this build).
@@ -367,6 +367,26 @@ WPCCC_API wpccc_status wpccc_basis_states(wpccc_basis basis, int* qn, double* ep
 #define WPCCC_SOLVE_MATRIX 1
 #define WPCCC_SOLVE_SCHUR 2
 WPCCC_API wpccc_status wpccc_basis_set_solve_mode(wpccc_basis basis, int mode);
+
+/*
+ * How the refined precision modes with WPCCC_SOLVE_SCHUR form their FP32 preconditioner's trailing matrix
+ * I - K^+ K (the rank-N_T update that eliminates the identity block of S, the bulk of the factorisation):
+ *   WPCCC_SCHUR_UPDATE_TENSOR      on the tcgen05 tensor cores as a real GEMM over the target index, both
+ *                                  operands in four fixed-point bf16 slices per 128-wide window with exact
+ *                                  FP32 level accumulators (about 2^-28 of each window's largest term), then
+ *                                  the Cholesky factor on the CUDA cores;
+ *   WPCCC_SCHUR_UPDATE_CUDA_CORES  update and Cholesky factor in FP32 on the CUDA cores, one block per
+ *                                  position;
+ *   WPCCC_SCHUR_UPDATE_AUTO        (default) tensor cores when N_P >= 256, else CUDA cores (below that the
+ *                                  three launches of the tensor-core route cost more than they save).
+ * Both are preconditioners of the same FP64 refinement; the tensor-core one is the more accurate (its
+ * update carries no FP32 rounding), so the refinement converges faster.  Errors: EINVAL (null basis,
+ * unknown mode).  The paper has no counterpart.
+ */
+#define WPCCC_SCHUR_UPDATE_AUTO 0
+#define WPCCC_SCHUR_UPDATE_TENSOR 1
+#define WPCCC_SCHUR_UPDATE_CUDA_CORES 2
+WPCCC_API wpccc_status wpccc_basis_set_schur_update(wpccc_basis basis, int mode);
 
 /*
  * Sweeps of FP64 iterative refinement per RK4 stage in the refined precision modes (1, 2, 3, 5):

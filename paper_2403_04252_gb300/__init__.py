@@ -89,6 +89,7 @@ _lib.wpccc_overlap_norms.argtypes = [C.c_void_p, C.c_int, _pd, _pd, _pd, C.c_voi
 _lib.wpccc_basis_states.argtypes = [C.c_void_p, _pi, _pd]
 _lib.wpccc_basis_set_refine_tolerance.argtypes = [C.c_void_p, C.c_double]
 _lib.wpccc_basis_set_wait_limit.argtypes = [C.c_void_p, C.c_long]
+_lib.wpccc_basis_set_schur_update.argtypes = [C.c_void_p, C.c_int]
 _lib.wpccc_last_error.restype = C.c_char_p
 for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
            "wpccc_solve", "wpccc_propagate", "wpccc_probabilities", "wpccc_basis_set_workspace_limit",
@@ -97,7 +98,7 @@ for _f in ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpc
            "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
            "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters", "wpccc_basis_set_rk4_layout",
            "wpccc_observables", "wpccc_cross_sections", "wpccc_overlap_norms", "wpccc_basis_states",
-           "wpccc_basis_set_refine_tolerance", "wpccc_basis_set_wait_limit"):
+           "wpccc_basis_set_refine_tolerance", "wpccc_basis_set_wait_limit", "wpccc_basis_set_schur_update"):
     getattr(_lib, _f).restype = C.c_int
 
 EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wpccc_matrix_elements",
@@ -107,8 +108,9 @@ EXPORTED = ("wpccc_basis_create", "wpccc_basis_destroy", "wpccc_basis_info", "wp
             "wpccc_batch_info", "wpccc_batch_destroy", "wpccc_basis_set_tangents", "wpccc_propagate_adjoint",
             "wpccc_matrix_elements_precision", "wpccc_basis_set_refine_iters", "wpccc_basis_set_rk4_layout",
             "wpccc_observables", "wpccc_cross_sections", "wpccc_overlap_norms", "wpccc_basis_states",
-            "wpccc_basis_set_refine_tolerance", "wpccc_basis_set_wait_limit")
+            "wpccc_basis_set_refine_tolerance", "wpccc_basis_set_wait_limit", "wpccc_basis_set_schur_update")
 MAX_PARAMS = 4
+SCHUR_UPDATE_AUTO, SCHUR_UPDATE_TENSOR, SCHUR_UPDATE_CUDA_CORES = 0, 1, 2
 RK4_AUTO, RK4_SHARED, RK4_GLOBAL = 0, 1, 2
 MAX_REFINE = 8
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -270,6 +272,11 @@ class Basis:
         """Largest last refinement correction relative to the solution before wpccc_propagate reports
         ENOCONV (refined precision modes; default 1e-3, <= 0 switches the check off)."""
         _check(_lib.wpccc_basis_set_refine_tolerance(self._h, float(tol)), "wpccc_basis_set_refine_tolerance")
+
+    def set_schur_update(self, mode: int) -> None:
+        """SCHUR_UPDATE_AUTO (default), _TENSOR or _CUDA_CORES: where the refined Schur forms' FP32
+        preconditioner forms I - K^+ K (``wpccc_basis_set_schur_update``)."""
+        _check(_lib.wpccc_basis_set_schur_update(self._h, int(mode)), "wpccc_basis_set_schur_update")
 
     def set_wait_limit(self, polls: int) -> None:
         """Polls of every mbarrier wait in the tensor-core kernels before it gives up (ETIMEOUT); default 2^20."""

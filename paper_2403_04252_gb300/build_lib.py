@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwpccc.so")
-SOURCES = ["basis.cu", "elements.cu", "solve.cu", "propagate.cu", "noalloc.cu", "adjoint.cu", "mol_tc.cu", "mol_tc64.cu", "schur.cu", "observables.cu"]
+SOURCES = ["basis.cu", "elements.cu", "solve.cu", "propagate.cu", "noalloc.cu", "adjoint.cu", "mol_tc.cu", "mol_tc64.cu", "schur.cu", "schur_tc.cu", "observables.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

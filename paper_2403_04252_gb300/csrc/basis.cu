@@ -323,7 +323,7 @@ static void free_basis(wpccc_basis_s* B) {
     free_centre(B->T);
     free_centre(B->P);
     void* tptrs[] = {B->tanT.df, B->tanT.dF, B->tanP.df, B->tanP.dF, B->deps, B->tc_row, B->qg_off, B->qg_rows,
-                     B->tc_err, B->tc_halfq};
+                     B->tc_err, B->tc_halfq, B->su_tiles};
     for (void* p : tptrs)
         if (p) cudaFree(p);
     void* ptrs[] = {B->r, B->w, B->inv_den, B->s, B->ws, B->tau, B->wtau, B->half_state, B->half_of, B->qtile_q,
@@ -505,6 +505,14 @@ extern "C" wpccc_status wpccc_basis_set_refine_iters(wpccc_basis B, int iters) {
     if (iters < 1 || iters > WPCCC_MAX_REFINE)
         return fail(WPCCC_EINVAL, "wpccc_basis_set_refine_iters: iterations must be 1 to " + std::to_string(WPCCC_MAX_REFINE));
     B->refine_iters = iters;
+    return WPCCC_OK;
+}
+
+extern "C" wpccc_status wpccc_basis_set_schur_update(wpccc_basis B, int mode) {
+    if (!B) return fail(WPCCC_EINVAL, "wpccc_basis_set_schur_update: null basis");
+    if (mode != WPCCC_SCHUR_UPDATE_AUTO && mode != WPCCC_SCHUR_UPDATE_TENSOR && mode != WPCCC_SCHUR_UPDATE_CUDA_CORES)
+        return fail(WPCCC_EINVAL, "wpccc_basis_set_schur_update: unknown mode");
+    B->schur_update = mode;
     return WPCCC_OK;
 }
 

@@ -99,7 +99,8 @@ struct NodeArgs {
     int N_T, n_half;
     const int *stT_index, *half_of, *radT_l, *radP_l;
     // tensor-core layout (T = float, precision modes 3-5): bf16 slice planes of A_T r_T and A_T r_T V_T
-    // (tc_slices of them: 3 at FP32 level, 7 for FP64 accuracy) with scales per 128-node window, and
+    // (tc_slices of them: OZ_FAST_SLICES for the reduced-precision form, 7 for FP64 accuracy) with scales per
+    // 128-node window, and
     // A_P and W_K / r_T as double-floats
     int tc, tc_slices;
     const int* tc_row;          // [2 N_T]: row of each target state in the slice planes, then its tile's size
@@ -230,10 +231,10 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
             for (int j = 0; j < 4; ++j) {
                 __nv_bfloat16 q[OZ_SLICES];
                 const size_t o = row * A.G + g0 + lid + 32 * j;
-                if (A.tc_slices == 3) {
-                    oz_slices<3>(xv[j].x, xv[j].y, sh, q);
+                if (A.tc_slices == OZ_FAST_SLICES) {
+                    oz_slices<OZ_FAST_SLICES>(xv[j].x, xv[j].y, sh, q);
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) sp[i * split + o] = q[i];
+                    for (int i = 0; i < OZ_FAST_SLICES; ++i) sp[i * split + o] = q[i];
                 } else {
                     oz_slices<OZ_SLICES>(xv[j].x, xv[j].y, sh, q);
 #pragma unroll
@@ -902,9 +903,8 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
         T[t] = make_double2(re, im);
     }
     __syncwarp();
-    // K[x][m_a][m_b] = sum_q' d^{la}_{m_a q'} T[x][q'][m_b], energy phases, S and H entries
-    double2* S = A.S + (size_t)e * A.mat;
-    double2* H = A.H + (size_t)e * A.mat;
+    // K[x][m_a][m_b] = sum_q' d^{la}_{m_a q'} T[x][q'][m_b] with the energy phases, into X (free again)
+    const double2* phs = reinterpret_cast<const double2*>(etd + A.ph_off);
     for (int t = lane; t < blk; t += 32) {
         const int mi = t / nbq, mb = t % nbq;
         const double* dr = da + mi * na;
@@ -919,16 +919,30 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
         }
         const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
         const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
-        const double2* phs = reinterpret_cast<const double2*>(etd + A.ph_off);
         const double2 ph = cmul(phs[i], cconj(phs[A.N_T + j]));
-        const double2 K = cmul(make_double2(acc[0], acc[1]), ph);
-        const double2 Q = cmul(make_double2(acc[2], acc[3]), ph);
+        X[t] = cmul(make_double2(acc[0], acc[1]), ph);          // K
+        X[blk + t] = cmul(make_double2(acc[2], acc[3]), ph);    // Q
+    }
+    __syncwarp();
+    // S and H entries: the upper blocks with the target index fastest (consecutive rows of a column), the
+    // lower blocks with the projectile index fastest, so that both writes run along memory
+    double2* S = A.S + (size_t)e * A.mat;
+    double2* H = A.H + (size_t)e * A.mat;
+    for (int t = lane; t < blk; t += 32) {
+        const int mi = t % na, mb = t / na;
+        const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
+        const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
         const size_t up = (size_t)i + (size_t)(A.N_T + j) * A.N;     // row i, column N_T + j
+        S[up] = X[mi * nbq + mb];
+        H[up] = X[blk + mi * nbq + mb];
+    }
+    for (int t = lane; t < blk; t += 32) {
+        const int mi = t / nbq, mb = t % nbq;
+        const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
+        const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
         const size_t lo = (size_t)(A.N_T + j) + (size_t)i * A.N;     // row N_T + j, column i
-        S[up] = K;
-        S[lo] = cconj(K);
-        H[up] = Q;
-        H[lo] = cconj(Q);     // Eq. 1: the lower-left block of H is Q^+
+        S[lo] = cconj(X[t]);
+        H[lo] = cconj(X[blk + t]);     // Eq. 1: the lower-left block of H is Q^+
     }
 }
 
@@ -994,7 +1008,8 @@ __global__ void __launch_bounds__(256) k_direct(DirArgs A0, DirArgs A1, const Ev
     const double* et = A.et + (size_t)e * A.et_doubles;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)A.Nc * A.Nc) return;
-    const int i = (int)(idx / A.Nc), j = (int)(idx % A.Nc);
+    // consecutive threads take consecutive rows of a column: the writes run along column-major memory
+    const int i = (int)(idx % A.Nc), j = (int)(idx / A.Nc);
     const int ra = A.st_rad[i], rb = A.st_rad[j];
     const double* cp = et + A.cp_off + ((size_t)A.st_lm[i] * A.LM + A.st_lm[j]) * A.nlam;
     const int* foff = A.Foff + ((size_t)ra * A.n_rad + rb) * A.nlam;
@@ -1253,7 +1268,7 @@ static wpccc_status launch_tables(wpccc_basis_s* B, const EvalDesc* evals, int n
     na.radT_l = B->T.rad_l;
     na.radP_l = B->P.rad_l;
     na.tc = precision == 3 || precision == 4;
-    na.tc_slices = precision == 3 ? 3 : OZ_SLICES;
+    na.tc_slices = precision == 3 ? OZ_FAST_SLICES : OZ_SLICES;
     na.tc_row = B->tc_row;
     na.tc_rows = L.tc_rows;
     na.t6_ap_off = L.t6_ap_off;
@@ -1332,7 +1347,8 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
                                             (int)gsm));
             k_mol_gemm<double><<<dim3(n_row_tiles * ga.n_col_tiles, nev), 256, gsm, st>>>(ga);
         } else if (precision == 3 || precision == 4) {
-            wpccc_status ms = launch_mol_tc64(B, nev, node, mol, B->tc_err, st, precision == 3 ? 3 : OZ_SLICES);
+            wpccc_status ms = launch_mol_tc64(B, nev, node, mol, B->tc_err, st,
+                                               precision == 3 ? OZ_FAST_SLICES : OZ_SLICES);
             if (ms != WPCCC_OK) return ms;
         } else {
             Gemm32Args g32;

@@ -72,11 +72,17 @@ wpccc_status tc_prepare(wpccc_basis_s* B) {
     if ((s = up(&B->qg_off, qg)) != WPCCC_OK) return s;
     if ((s = up(&B->qg_rows, rows)) != WPCCC_OK) return s;
     if ((s = up(&B->tc_halfq, halfq)) != WPCCC_OK) return s;
-    WPCCC_CUDA(cudaMalloc((void**)&B->tc_err, sizeof(int)));
-    WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
+    if ((s = ensure_tc_err(B)) != WPCCC_OK) return s;
     B->n_qgroups = ntl;
     B->qg_max = qmax;
     B->tc_layout = true;
+    return WPCCC_OK;
+}
+
+wpccc_status ensure_tc_err(wpccc_basis_s* B) {
+    if (B->tc_err) return WPCCC_OK;
+    WPCCC_CUDA(cudaMalloc((void**)&B->tc_err, sizeof(int)));
+    WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
     return WPCCC_OK;
 }
 

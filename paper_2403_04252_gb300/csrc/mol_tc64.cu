@@ -1,5 +1,5 @@
 // Eq. 9 contraction on the 5th-generation tensor cores: to FP64 accuracy with seven slices per operand
-// (precision modes 4 and 5), at FP32 level with three (precision mode 3).
+// (precision modes 4 and 5), and with four (precision mode 3, the reduced-precision form).
 //
 // The two-centre integrals of one row tile (target states of one molecular-frame projection q') are
 //   X_K[i][c] = sum_g (A_T r_T)[i][g] Bw[c][g],   X_Q[i][c] = sum_g (A_T r_T V_T)[i][g] Bw[c][g],
@@ -18,9 +18,9 @@
 // fifth, whose FP32 rounding over its 144 MMAs stays near 2^-48 of the window's largest term; levels
 // >= 7 are dropped (below 2^-53).  Per window the epilogue forms s_m s_n (L0 + L1 + L2 + L3 + T) with
 // the exact parts folded into double-float running sums (two TwoSums), so the result carries about
-// 2^-46 of the largest term.  With SL = 3 (levels 0-2, six products, three exact accumulators) each
-// operand keeps 23 bits below its row's window maximum, and a window's sum errs by up to about 2^-20 of
-// its largest term: the FP32 level, without the truncation bias of the tensor core's FP32 accumulation.
+// 2^-46 of the largest term.  With SL = 4 (levels 0-3, ten products, four exact accumulators, no tail) each
+// operand keeps 31 bits below its row's window maximum, and a window's sum errs by up to about 2^-28 of its
+// largest term, without the truncation bias of the tensor core's FP32 accumulation.
 //
 // Pipeline per CTA (416 threads): warps 0-11 generate the Bw tiles (64-byte swizzled K-major rows) and
 // drain the accumulators; warp 12 issues the TMA loads of the table tiles (cp.async.bulk.tensor, 64-byte
@@ -42,12 +42,12 @@ namespace wpccc {
 constexpr int T6_M = 128;                              // table rows per CTA (MMA M)
 constexpr int T6_K = 32;                               // nodes per chunk: one 64-byte bf16 row
 constexpr int T6_WIN = 4;                              // chunks per scaling window (128 nodes)
-// Per slice count: accumulators (SL = 7: levels 0, 1, 2, 3 exact and >= 4; SL = 3: levels 0, 1, 2 exact)
-// and generated rows per CTA (MMA N), so that two buffers of accumulators fill the 512 TMEM columns
-// (2 x 5 x 48 = 2 x 3 x 80 = 480); eight producer threads per generated row.
+// Per slice count: accumulators (SL = 7: levels 0, 1, 2, 3 exact and >= 4; SL = 4: levels 0-3, all exact)
+// and generated rows per CTA (MMA N), two buffers of accumulators within the 512 TMEM columns
+// (2 x 5 x 48 = 480, 2 x 4 x 48 = 384); eight producer threads per generated row.
 template <int SL> struct Tc64Cfg {
     static constexpr int ACC = SL == 7 ? 5 : SL;
-    static constexpr int N = SL == 7 ? 48 : 64;
+    static constexpr int N = 48;
     static constexpr int PE_WARPS = N / 4;                       // producer / epilogue warps
     static constexpr int THREADS = (PE_WARPS + 1) * 32;
     static constexpr int BUF_COLS = ACC * N;                    // column offset of the second buffer
@@ -96,7 +96,7 @@ struct Tc64Args {
 };
 
 template <int SL>
-__global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS) k_mol_tc64(const __grid_constant__ Tc64Maps maps, Tc64Args A) {
+__global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __grid_constant__ Tc64Maps maps, Tc64Args A) {
     using CF = Tc64Cfg<SL>;
     constexpr int T6_ACC = CF::ACC;
     constexpr int T6_N = CF::N;
@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS) k_mol_tc64(const __grid_
                         const float l1h = rintf(v[1][u]);
                         const float xa = __fadd_rn(v[0][u], l1h);
                         const float xb = __fadd_rn(__fsub_rn(v[1][u], l1h), v[2][u]);
-                        const float xc = T6_ACC > 3 ? __fadd_rn(v[T6_ACC > 3 ? 3 : 0][u], v[T6_ACC - 1][u]) : 0.f;
+                        const float xc = T6_ACC == 5 ? __fadd_rn(v[3][u], v[T6_ACC - 1][u])
+                                         : T6_ACC == 4 ? v[T6_ACC - 1][u] : 0.f;
                         float r1, r2;
                         hi[k] = two_sum(hi[k], xa * sc, r1);
                         hi[k] = two_sum(hi[k], xb * sc, r2);
@@ -361,7 +362,8 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS) k_mol_tc64(const __grid_
 
 wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st,
                              int slices) {
-    if (slices != 3 && slices != OZ_SLICES) return fail(WPCCC_EINVAL, "tensor-core contraction: 3 or 7 slices");
+    if (slices != OZ_FAST_SLICES && slices != OZ_SLICES)
+        return fail(WPCCC_EINVAL, "tensor-core contraction: 4 or 7 slices");
     if (!B->tc_layout) return fail(WPCCC_EINVAL, "tensor-core layout not prepared");
     if (B->G % (T6_K * T6_WIN) != 0) return fail(WPCCC_EUNSUPPORTED, "the node count must be a multiple of 128");
     const ElemScratch L = elem_scratch_layout(B);
@@ -405,11 +407,12 @@ wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double
         WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<OZ_SLICES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_mol_tc64<OZ_SLICES><<<dim3(a.n_ntiles * B->n_qgroups, nev), CF::THREADS, smem, st>>>(maps, a);
     } else {
-        using CF = Tc64Cfg<3>;
+        using CF = Tc64Cfg<OZ_FAST_SLICES>;
         a.n_ntiles = (2 * B->n_half + CF::N - 1) / CF::N;
-        const size_t smem = tc64_smem_bytes<3>();
-        WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_mol_tc64<3><<<dim3(a.n_ntiles * B->n_qgroups, nev), CF::THREADS, smem, st>>>(maps, a);
+        const size_t smem = tc64_smem_bytes<OZ_FAST_SLICES>();
+        WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<OZ_FAST_SLICES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+        k_mol_tc64<OZ_FAST_SLICES><<<dim3(a.n_ntiles * B->n_qgroups, nev), CF::THREADS, smem, st>>>(maps, a);
     }
     WPCCC_CHECK_LAUNCH("k_mol_tc64");
     return WPCCC_OK;

@@ -20,6 +20,7 @@
 namespace wpccc {
 
 constexpr int OZ_SLICES = 7;   // slices of the FP64-accurate form (the most any layout holds)
+constexpr int OZ_FAST_SLICES = 4;   // slices of the reduced-precision tensor-core form (precision mode 3)
 
 // hi + lo = x to about 2^-48 relative (hi = x rounded to FP32, lo = the rest rounded to FP32).
 static __device__ __forceinline__ float2 df_split(double x) {
@@ -61,7 +62,8 @@ static __device__ __forceinline__ int oz_shift(float mx) {
 // afterwards p and k are integers below 2^24).  Only p + e may round, which can move k by one where
 // the remainder is near a half unit; the next remainder then stays within (0.5 + 2^-17) 256 of zero,
 // so |k_i| <= 129.
-// NS slices: 7 for FP64 accuracy, 3 for FP32 level (about 23 bits below the window's largest value).
+// NS slices: 7 for FP64 accuracy, 4 for the reduced-precision form (about 31 bits below the window's largest
+// value).
 template <int NS>
 static __device__ __forceinline__ void oz_slices(float h, float l, int sh, __nv_bfloat16 out[NS]) {
     float p = ldexpf(h, sh), e = ldexpf(l, sh), w = 1.f;

@@ -303,6 +303,7 @@ struct PropPlan {
     int np = 0, N = 0, mode = RK_MATRIX, elem_precision = 0, C = 1, n_chunks = 0, max_chunk_evals = 0;
     int max_steps = 0;
     bool two = false, mixed = false, stage = false, schur = false;
+    bool schur_tc = false;   // mixed Schur forms: the trailing update I - K^+ K on the tensor cores
     bool wide = false;       // one-centre RK4 with the vectors in global memory (k_rk4_wide)
     size_t per_eval = 0, fixed = 0;
     std::vector<double> z;
@@ -365,6 +366,13 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
                        : (precision_mode == 4 || precision_mode == 5) ? 4 : 0;
     P.stage = P.two && !P.mixed && B->solve_mode != WPCCC_SOLVE_MATRIX;
     P.schur = P.two && B->solve_mode == WPCCC_SOLVE_SCHUR;
+    const bool want_tc = B->schur_update == WPCCC_SCHUR_UPDATE_TENSOR ||
+                         (B->schur_update == WPCCC_SCHUR_UPDATE_AUTO && B->N_P >= 256);
+    P.schur_tc = P.mixed && P.schur && want_tc && schur_tc_applicable(B, elem_scratch_layout(B).bytes_per_eval);
+    if (P.schur_tc) {
+        wpccc_status ts = schur_tc_prepare(B);
+        if (ts != WPCCC_OK) return ts;
+    }
     P.mode = P.mixed ? (P.schur ? RK_MIXED_SCHUR : RK_MIXED) : (P.schur ? RK_SCHUR : (P.stage ? RK_STAGE : RK_MATRIX));
     // 227 KB per block, less the kernels' static shared memory (the refinement check's reduction)
     const bool fits = rk_smem_bytes(P.mode, N) + 1024 <= (size_t)227 * 1024;
@@ -564,7 +572,9 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
         if (s != WPCCC_OK) return s;
         if (P.two) {
             cudaEvent_t e0 = B->prof.begin(PROF_SOLVE, st);
-            if (P.mixed && P.schur) s = launch_schur_factor_f32(N, B->N_T, nev, bS, bL, bI, st);
+            if (P.mixed && P.schur && P.schur_tc)
+                s = launch_schur_factor_f32_tc(B, nev, bS, bL, bI, P.d_scr, elem_scratch_layout(B).bytes_per_eval, st);
+            else if (P.mixed && P.schur) s = launch_schur_factor_f32(N, B->N_T, nev, bS, bL, bI, st);
             else if (P.mixed) s = launch_factor_f32(N, nev, bS, bL, bP, bI, st);
             else if (P.schur) s = launch_schur_factor(N, B->N_T, nev, bS, bI, st);
             else s = launch_solve(N, nev, bS, P.stage ? nullptr : bH, bP, bI, st);
@@ -651,12 +661,12 @@ wpccc_status propagate_internal(wpccc_basis_s* B, const wpccc_paths* paths, int 
     int flags = 0;
     WPCCC_CUDA(cudaMemcpyAsync(&flags, P.d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     WPCCC_CUDA(cudaStreamSynchronize(st));
-    if (P.elem_precision == 3 || P.elem_precision == 4) {
+    if (B->tc_err) {
         int e = 0;
         WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
             WPCCC_CUDA(cudaMemset(B->tc_err, 0, sizeof(int)));
-            return fail(WPCCC_ETIMEOUT, "wpccc_propagate: a wait of the tensor-core contraction timed out (stage " +
+            return fail(WPCCC_ETIMEOUT, "wpccc_propagate: a wait of a tensor-core kernel timed out (stage " +
                                          std::to_string(e) + ")");
         }
     }
@@ -927,7 +937,7 @@ extern "C" wpccc_status wpccc_batch_status(wpccc_batch X, void* stream) {
     WPCCC_CUDA(cudaStreamSynchronize(st));
     for (int k = 0; k < X->n_sets; ++k) {
         wpccc_basis_s* B = X->plans[k].B;
-        if ((X->plans[k].elem_precision == 3 || X->plans[k].elem_precision == 4) && B && B->tc_err) {
+        if (B && B->tc_err) {
             int e = 0;
             WPCCC_CUDA(cudaMemcpy(&e, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
             if (e) {

@@ -91,10 +91,12 @@ __device__ void cta_update_lower(typename SchurC<R>::type* __restrict__ C, int l
 // One system per block.  R = double: D is S itself (FP64, in place).  R = float (preconditioner of the
 // mixed-precision form): D is a separate FP32 N x N buffer that receives K rounded to FP32 in its
 // target-projectile block and the FP32 Cholesky factor in its projectile block; S is only read.
+// given = true: D already holds K in FP32 and the trailing matrix I - K^+ K in the projectile block's
+// lower triangle (formed on the tensor cores, schur_tc.cu); only the Cholesky factor is computed.
 template <typename R>
 __global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, const double2* Sall,
                                                              typename SchurC<R>::type* __restrict__ Dall,
-                                                             int* __restrict__ info_all) {
+                                                             int* __restrict__ info_all, bool given) {
     using C2 = typename SchurC<R>::type;
     extern __shared__ __align__(16) unsigned char sc_smem_raw[];
     C2* sA = reinterpret_cast<C2*>(sc_smem_raw);   // SC_TM * SC_NB
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, con
     C2* C = D + N_T + (size_t)N_T * N;           // projectile block, leading dimension N
     const C2* K = D + (size_t)N_T * N;           // K[i][j] = D[i][N_T + j], i < N_T
     if (tid == 0) s_info = 0;
-    if (sizeof(R) == 4) {
+    if (sizeof(R) == 4 && !given) {
         // K to FP32, identity into the lower triangle of the projectile block
         const double2* S = Sall + (size_t)sys * mat;
         for (size_t q = tid; q < (size_t)N_T * NP; q += SC_THREADS) {
@@ -123,13 +125,14 @@ __global__ void __launch_bounds__(SC_THREADS) k_schur_factor(int N, int N_T, con
         __syncthreads();
     }
     // C = I - K^+ K on the lower triangle (the block holds I already)
-    cta_update_lower<R>(
-        C, N, NP, N_T,
-        [&](int i, int kk) {   // (K^+)[i][kk] = conj(K[kk][i])
-            const C2 a = K[(size_t)kk + (size_t)i * N];
-            return C2{a.x, -a.y};
-        },
-        [&](int kk, int j) { return K[(size_t)kk + (size_t)j * N]; }, sA, sB);
+    if (!given)
+        cta_update_lower<R>(
+            C, N, NP, N_T,
+            [&](int i, int kk) {   // (K^+)[i][kk] = conj(K[kk][i])
+                const C2 a = K[(size_t)kk + (size_t)i * N];
+                return C2{a.x, -a.y};
+            },
+            [&](int kk, int j) { return K[(size_t)kk + (size_t)j * N]; }, sA, sB);
     __syncthreads();
     // blocked right-looking Cholesky of C, lower
     for (int k0 = 0; k0 < NP; k0 += SC_NB) {
@@ -189,7 +192,7 @@ wpccc_status launch_schur_factor(int N, int N_T, int batch, double2* S, int* inf
     if (batch == 0) return WPCCC_OK;
     const int smem = (int)(sizeof(double2) * (SC_TM * SC_NB + SC_NB * SC_TN));   // 48 KB: needs the opt-in
     WPCCC_CUDA(cudaFuncSetAttribute(k_schur_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_schur_factor<double><<<batch, SC_THREADS, smem, st>>>(N, N_T, S, S, info);
+    k_schur_factor<double><<<batch, SC_THREADS, smem, st>>>(N, N_T, S, S, info, false);
     WPCCC_CHECK_LAUNCH("k_schur_factor<double>");
     return WPCCC_OK;
 }
@@ -198,8 +201,16 @@ wpccc_status launch_schur_factor_f32(int N, int N_T, int batch, const double2* S
                                      cudaStream_t st) {
     if (batch == 0) return WPCCC_OK;
     const int smem = (int)(sizeof(float2) * (SC_TM * SC_NB + SC_NB * SC_TN));
-    k_schur_factor<float><<<batch, SC_THREADS, smem, st>>>(N, N_T, S, D, info);
+    k_schur_factor<float><<<batch, SC_THREADS, smem, st>>>(N, N_T, S, D, info, false);
     WPCCC_CHECK_LAUNCH("k_schur_factor<float>");
+    return WPCCC_OK;
+}
+
+wpccc_status launch_schur_cholesky_f32(int N, int N_T, int batch, float2* D, int* info, cudaStream_t st) {
+    if (batch == 0) return WPCCC_OK;
+    const int smem = (int)(sizeof(float2) * (SC_TM * SC_NB + SC_NB * SC_TN));
+    k_schur_factor<float><<<batch, SC_THREADS, smem, st>>>(N, N_T, nullptr, D, info, true);
+    WPCCC_CHECK_LAUNCH("k_schur_factor<float> (Cholesky of the given trailing matrix)");
     return WPCCC_OK;
 }
 

@@ -131,6 +131,10 @@ struct wpccc_basis_s {
     int n_qgroups = 0;          // row tiles: target states of one q', at most 56 per tile
     int* tc_row = nullptr;      // [2 N_T]: row of each target state in a split table, then its group's size
     int* tc_err = nullptr;      // device flag: a wait of the tensor-core pipeline gave up
+    // tensor-core Schur update (schur_tc.cu): (A tile, B tile) pairs for N_P = su_np
+    int* su_tiles = nullptr;
+    int su_np = 0, su_ntiles = 0;
+    int schur_update = WPCCC_SCHUR_UPDATE_AUTO;   // where the mixed Schur forms form I - K^+ K
     int* tc_halfq = nullptr;    // [n_half]: q of each half column
     int* qg_off = nullptr;      // [n_qgroups + 1]: first split-table row of each tile (2 x cumulative size),
                                 // then [n_qgroups]: the tile's q'
@@ -213,6 +217,18 @@ wpccc_status launch_schur_factor(int N, int N_T, int batch, double2* S, int* inf
 // of the mixed-precision forms' refinement.
 wpccc_status launch_schur_factor_f32(int N, int N_T, int batch, const double2* S, float2* D, int* info,
                                      cudaStream_t st);
+
+// The Cholesky factor of a trailing matrix I - K^+ K already in D's projectile block (K in FP32 in D).
+wpccc_status launch_schur_cholesky_f32(int N, int N_T, int batch, float2* D, int* info, cudaStream_t st);
+// The FP32 preconditioner of the mixed Schur forms with the rank-N_T update I - K^+ K on the tensor cores
+// (schur_tc.cu); `scratch` holds at least `scratch_per_eval` bytes per evaluation.
+bool schur_tc_applicable(const wpccc_basis_s* B, size_t scratch_per_eval);
+// Its tile list and timeout flag, made on the host before any launch (and before a graph capture).
+wpccc_status schur_tc_prepare(wpccc_basis_s* B);
+wpccc_status launch_schur_factor_f32_tc(wpccc_basis_s* B, int nev, const double2* S, float2* D, int* info,
+                                        void* scratch, size_t scratch_per_eval, cudaStream_t st);
+// Allocates the device flag of the tensor-core kernels' bounded waits, if the basis has none yet.
+wpccc_status ensure_tc_err(wpccc_basis_s* B);
 
 // Queue the batched solve of S X = H (results in place).
 wpccc_status launch_solve(int N, int batch, double2* S, double2* H, int* ipiv, int* info,

@@ -131,7 +131,8 @@ def test_binding_constants_match_header():
         assert getattr(w, name) == enum[name], name
     defines = {k: v for k, v in re.findall(r"#define WPCCC_(\w+)\s+(\S.*)", src)}
     for name in ("LMAX", "NMAX", "MAX_PARAMS", "MAX_REFINE", "SOLVE_STAGE", "SOLVE_MATRIX", "SOLVE_SCHUR",
-                 "RK4_AUTO", "RK4_SHARED", "RK4_GLOBAL"):
+                 "RK4_AUTO", "RK4_SHARED", "RK4_GLOBAL", "SCHUR_UPDATE_AUTO", "SCHUR_UPDATE_TENSOR",
+                 "SCHUR_UPDATE_CUDA_CORES"):
         assert getattr(w, name) == int(defines[name]), name
     assert w.NOALLOC_SCRATCH_BYTES == 64 << 20 and "64 << 20" in defines["NOALLOC_SCRATCH_BYTES"]
     assert len(w.PROF_CATEGORIES) == int(defines["PROF_N"])

@@ -13,8 +13,9 @@ grid per 128-node window; the CUDA kernels are not involved):
   frac(L1) + L2 exact in FP32, L3 + tail rounded, the window terms folded into a double-float running sum
   by two TwoSums) ends within 2^-42 of the largest term of the exact sum (observed 2^-43.8 to 2^-48);
 * with three slices (levels 0-2, six products, all exact) the window's dot product errs by less than
-  2^-25 of (128 nodes x the largest term), observed up to 2^-27.5: the FP32 level of precision mode 3
-  (each operand keeps 23 bits below its row's window maximum).
+  2^-25 of (128 nodes x the largest term), observed up to 2^-27.5: the FP32 level (each operand keeps
+  23 bits below its row's window maximum);
+* with four slices (levels 0-3, ten products, all exact: precision mode 3) by less than 2^-31.
 """
 from fractions import Fraction
 
@@ -110,6 +111,31 @@ def test_three_slices_give_the_fp32_level():
         worst = max(worst, err)
     # and no better than the truncation predicts: the dropped levels (i + j >= 3) are not accidentally kept
     assert worst > 2.0 ** -32
+
+
+def test_four_slices_give_the_reduced_precision_level():
+    # precision mode 3: four slices, levels 0-3 (ten products), every level exact in FP32; the dropped
+    # levels (i + j >= 4) leave about 2^-32 of (128 nodes x the largest term)
+    rng = np.random.default_rng(17)
+    worst = 0.0
+    for _ in range(50):
+        xa, ha, la, sa = _window(rng)
+        xb, hb, lb, sb = _window(rng)
+        A = [k.astype(np.float64) * 2.0 ** (-8 * i) for i, k in enumerate(_slices(ha, la, sa, 4))]
+        Bs = [k.astype(np.float64) * 2.0 ** (-8 * j) for j, k in enumerate(_slices(hb, lb, sb, 4))]
+        levels = [sum(np.dot(A[i], Bs[L - i]) for i in range(L + 1)) for L in range(4)]
+        for L, v in enumerate(levels):
+            assert float(np.float32(v)) == v and abs(v * 2.0 ** (8 * L)) < 2.0 ** 24   # exact in FP32
+        # the kernel's epilogue terms: L0 + rint(L1) and frac(L1) + L2 exact in FP32, L3 as it is
+        l1h = np.rint(levels[1])
+        xa_, xb_ = levels[0] + l1h, (levels[1] - l1h) + levels[2]
+        assert float(np.float32(xa_)) == xa_ and float(np.float32(xb_)) == xb_
+        value = (xa_ + xb_ + levels[3]) * 2.0 ** (-sa - sb)
+        scale = float(np.abs(xa).max() * np.abs(xb).max() * NODES)
+        err = abs(value - float(np.dot(xa, xb))) / scale
+        assert err <= 2.0 ** -31
+        worst = max(worst, err)
+    assert worst > 2.0 ** -40
 
 
 def _two_sum(a, b):
