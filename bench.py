@@ -1110,7 +1110,7 @@ def main() -> None:
             a.workload, a.steps, a.warmup, a.rk4_per_step = "p_H_2c_batch6v", min(args.steps, 3), 3, STEP_RK4
             sub["p_H_2c_batch6v"] = _sub_entry(run_batch(a))
             a = copy.copy(args)
-            a.workload, a.steps, a.warmup, a.rk4_per_step = "C6_H_2c_n6l5", min(args.steps, 3), 3, 4
+            a.workload, a.steps, a.warmup, a.rk4_per_step = "C6_H_2c_n6l5", min(args.steps, 2), 3, STEP_RK4
             a.whole_path_paths = 0
             sub["C6_H_2c_n6l5"] = _sub_entry(run_fixed_speed(a, sub=True))
             line["workloads"] = sub

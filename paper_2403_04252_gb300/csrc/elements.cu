@@ -91,6 +91,7 @@ struct NodeArgs {
     double gamma, Z_T, Z_P;
     double mp_c, mp_a, mp_b;   // short-range part of a model-potential target (mp_c = 0: bare nucleus)
     const double *r, *fT, *fP, *s, *ws, *tau, *wtau;
+    const float2 *fT2, *fP2;   // the radial tables as double-floats (tensor-core layout)
     const double* inv_den;   // Lagrange denominators per stencil start
     double* node;            // per evaluation: [fT | fP | thT | thP | pad | W] (see elem_scratch_layout)
     size_t node_doubles;     // stride between evaluations, in doubles
@@ -200,6 +201,33 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         // Theta, then the target's Theta for every warp), r [2][128] (r_T, r_T V_T), f [TC_NA][128]
         // (a batch of target radial functions at the window's nodes).
         extern __shared__ float2 s_tc[];
+        // the 5-point interpolation in double-float arithmetic on the FP32 pipe (the FP64 pipe is two
+        // operations per clock per SM on this part): Lagrange weights split once per node, tables stored
+        // split; each term's product is exact in its high parts (FMA residual) and the sum a TwoSum chain
+        float2 LT2[5], LP2[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            LT2[k] = df_split(LT[k]);
+            LP2[k] = df_split(LP[k]);
+        }
+        auto interp2 = [&](const float2* f2, int a, bool in, int st, const float2* Lw) {
+            if (!in) return make_float2(0.f, 0.f);
+            const float2* fa = f2 + (size_t)a * A.Nr + st;
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const float2 v = fa[k];
+                const float p = Lw[k].x * v.x;
+                float e = fmaf(Lw[k].x, v.x, -p);
+                e = fmaf(Lw[k].x, v.y, e);
+                e = fmaf(Lw[k].y, v.x, e);
+                float r;
+                hi = two_sum(hi, p, r);
+                lo += r + e;
+            }
+            const float s = hi + lo;
+            return make_float2(s, lo - (s - hi));
+        };
         const int nlq = A.nlqT > A.nlqP ? A.nlqT : A.nlqP;
         float2* s_th = s_tc;
         float2* s_r = s_th + (size_t)nlq * 128;
@@ -209,7 +237,7 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         theta_lq(cP, A.lmaxP, A, [&](int q, double val) { s_th[q * 128 + tx] = df_split(val); });
         float2* aP = reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + A.t6_ap_off);
         for (int b2 = 0; b2 < A.nradP; ++b2) {
-            const float2 fv = df_split(interp(A.fP, b2, inP, sP, LP));
+            const float2 fv = interp2(A.fP2, b2, inP, sP, LP2);
             const int l = A.radP_l[b2];
             for (int q = 0; q <= l; ++q) {
                 const int j = A.half_of[b2 * (WPCCC_LMAX + 1) + q];
@@ -246,7 +274,7 @@ __global__ void __launch_bounds__(128) k_node_tables(NodeArgs A, const EvalDesc*
         for (int a0 = 0; a0 < A.nradT; a0 += TC_NA) {
             const int na = A.nradT - a0 < TC_NA ? A.nradT - a0 : TC_NA;
             __syncthreads();   // the previous batch's rows are written (and, first time, Theta_T and r are in)
-            for (int j = 0; j < na; ++j) s_f[j * 128 + tx] = df_split(interp(A.fT, a0 + j, inT, sT, LT));
+            for (int j = 0; j < na; ++j) s_f[j * 128 + tx] = interp2(A.fT2, a0 + j, inT, sT, LT2);
             __syncthreads();
             // the batch's states, one per warp in turn: (radial function, m) pairs in order
             int pair = 0;
@@ -877,17 +905,18 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
     for (int t = lane; t < NX * blk; t += 32) {
         const int x = t / blk, r = t % blk, qp = r / nbq - la, q = r % nbq - lb;
         int row, col;
-        double sg = 1.0;
+        bool neg = false;
         if (q >= 0) {
             row = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + qp + WPCCC_LMAX];
             col = A.half_of[rb * (WPCCC_LMAX + 1) + q];
         } else {
             row = A.stT_index[ra * (2 * WPCCC_LMAX + 1) - qp + WPCCC_LMAX];
             col = A.half_of[rb * (WPCCC_LMAX + 1) - q];
-            if ((qp + q) & 1) sg = -1.0;
+            neg = (qp + q) & 1;
         }
-        const double2 val = mol[(size_t)x * plane + (size_t)row * A.n_half + col];
-        X[t] = make_double2(sg * val.x, sg * val.y);
+        double2 val = mol[(size_t)x * plane + (size_t)row * A.n_half + col];
+        if (neg) val = make_double2(-val.x, -val.y);
+        X[t] = val;
     }
     __syncwarp();
     // T[x][q'][m_b] = sum_q d^{lb}_{m_b q} X[x][q'][q]
@@ -908,7 +937,7 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
     for (int t = lane; t < blk; t += 32) {
         const int mi = t / nbq, mb = t % nbq;
         const double* dr = da + mi * na;
-        double acc[4] = {0, 0, 0, 0};
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
         for (int qi = 0; qi < na; ++qi) {
             const double w = dr[qi];
             const double2 t0 = T[qi * nbq + mb], t1 = T[blk + qi * nbq + mb];
@@ -1253,6 +1282,8 @@ static wpccc_status launch_tables(wpccc_basis_s* B, const EvalDesc* evals, int n
     na.r = B->r;
     na.fT = B->T.f;
     na.fP = B->P.f;
+    na.fT2 = B->fT2;
+    na.fP2 = B->fP2;
     na.s = B->s;
     na.ws = B->ws;
     na.tau = B->tau;
@@ -1409,10 +1440,11 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         int rwarps = (int)std::min<size_t>(ROT_WARPS_MAX, ((size_t)200 * 1024 - dbytes) / per_warp);
         if (rwarps < 1) rwarps = 1;
         const size_t rsm = dbytes + (size_t)rwarps * per_warp;
-        WPCCC_CUDA(cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
         const int npairs = B->T.n_rad * B->P.n_rad;
+        const dim3 rgrid((unsigned)((npairs + rwarps - 1) / rwarps), nev);
         e0 = B->prof.begin(PROF_ROT_DIRECT, st);
-        k_rotate<<<dim3((unsigned)((npairs + rwarps - 1) / rwarps), nev), 32 * rwarps, rsm, st>>>(ra, evals);
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+        k_rotate<<<rgrid, 32 * rwarps, rsm, st>>>(ra, evals);
         WPCCC_CHECK_LAUNCH("k_rotate");
         B->prof.end(PROF_ROT_DIRECT, st, e0);
     }

@@ -13,6 +13,23 @@
 
 namespace wpccc {
 
+// The radial tables as double-floats, for the node tables' interpolation on the FP32 pipe.
+__global__ void k_split_table(long long n, const double* __restrict__ f, float2* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float h = __double2float_rn(f[i]);
+        out[i] = make_float2(h, __double2float_rn(f[i] - (double)h));
+    }
+}
+
+static wpccc_status split_table(const double* f, long long n, float2** out) {
+    WPCCC_CUDA(cudaMalloc((void**)out, n * sizeof(float2)));
+    k_split_table<<<(unsigned)((n + 255) / 256), 256>>>(n, f, *out);
+    WPCCC_CHECK_LAUNCH("k_split_table");
+    WPCCC_CUDA(cudaDeviceSynchronize());
+    return WPCCC_OK;
+}
+
 // target states per row tile: A_T r_T and A_T r_T V_T rows of at most 56 states (112 of the 128 rows)
 constexpr int TC_TILE_STATES = 56;
 
@@ -73,6 +90,8 @@ wpccc_status tc_prepare(wpccc_basis_s* B) {
     if ((s = up(&B->qg_rows, rows)) != WPCCC_OK) return s;
     if ((s = up(&B->tc_halfq, halfq)) != WPCCC_OK) return s;
     if ((s = ensure_tc_err(B)) != WPCCC_OK) return s;
+    if ((s = split_table(B->T.f, (long long)B->T.n_rad * B->Nr, &B->fT2)) != WPCCC_OK) return s;
+    if ((s = split_table(B->P.f, (long long)B->P.n_rad * B->Nr, &B->fP2)) != WPCCC_OK) return s;
     B->n_qgroups = ntl;
     B->qg_max = qmax;
     B->tc_layout = true;

@@ -66,7 +66,17 @@ static __device__ __forceinline__ int oz_shift(float mx) {
 // value).
 template <int NS>
 static __device__ __forceinline__ void oz_slices(float h, float l, int sh, __nv_bfloat16 out[NS]) {
-    float p = ldexpf(h, sh), e = ldexpf(l, sh), w = 1.f;
+    // scaling by 2^sh: one multiplication by the power of two where it is a normal float (as exact as
+    // ldexpf: a product with a power of two rounds only where it underflows, and both round the same way)
+    float p, e, w = 1.f;
+    if (sh >= -126 && sh <= 127) {
+        const float s2 = __int_as_float((sh + 127) << 23);
+        p = h * s2;
+        e = l * s2;
+    } else {
+        p = ldexpf(h, sh);
+        e = ldexpf(l, sh);
+    }
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         const float k = rintf(__fadd_rn(p, e));

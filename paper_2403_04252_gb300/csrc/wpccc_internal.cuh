@@ -136,6 +136,8 @@ struct wpccc_basis_s {
     int su_np = 0, su_ntiles = 0;
     int schur_update = WPCCC_SCHUR_UPDATE_AUTO;   // where the mixed Schur forms form I - K^+ K
     int* tc_halfq = nullptr;    // [n_half]: q of each half column
+    float2* fT2 = nullptr;      // [n_rad_T][Nr]: the target's radial tables as double-floats (hi, lo)
+    float2* fP2 = nullptr;      // the projectile's
     int* qg_off = nullptr;      // [n_qgroups + 1]: first split-table row of each tile (2 x cumulative size),
                                 // then [n_qgroups]: the tile's q'
     int* qg_rows = nullptr;     // [n_qgroups][max tile size]: target state of each row of a tile
