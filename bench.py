@@ -721,7 +721,7 @@ def _category_rooflines(basis, mode: int, solve_mode: str, N: int, n_half: int) 
         f_solve = 4.0 * NP_ * NP_ * NT + (4.0 / 3.0) * NP_ ** 3
     else:
         f_solve = (8.0 / 3.0 + (8.0 if (solve_mode == "matrix" and not mixed) else 0.0)) * N ** 3
-    mol_name = {1: "k_mol_gemm_f32q", 3: "k_mol_tc64<3>", 4: "k_mol_tc64<7>", 5: "k_mol_tc64<7>"}.get(
+    mol_name = {1: "k_mol_gemm_f32q", 3: "k_mol_tc64<4>", 4: "k_mol_tc64<7>", 5: "k_mol_tc64<7>"}.get(
         mode, "k_mol_gemm<double>")
     solve_name = (("k_schur_factor<float>" if solve_mode == "schur" else "k_lu_factor_f32") if mixed
                   else ("k_schur_factor<double>" if solve_mode == "schur" else "k_lu_solve"))
@@ -768,7 +768,11 @@ def _rk4_flops_per_step(mode: int, solve_mode: str, N: int, NT: int, NP_: int) -
 # DRAM bytes per position of a kernel on a workload, measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over a capture of whole launches, divided by the positions): only kernels whose code
 # is unchanged since the capture are listed (the others report traffic null)
-MEASURED_TRAFFIC_PER_POSITION = {}
+MEASURED_TRAFFIC_PER_POSITION = {
+    # ncu over 33 positions of the p + H workload, precision mode 3: (313.9 + 21.6) MB and (3.8 + 263.4) MB
+    ("p_H_2c_n4l3", "k_mol_tc64<4>"): 10.17e6,
+    ("p_H_2c_n4l3", "k_node_tables<float>"): 8.10e6,
+}
 
 
 def run_fixed_speed(args, sub: bool = False) -> dict:
