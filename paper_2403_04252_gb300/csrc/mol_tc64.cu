@@ -49,36 +49,52 @@ template <int SL> struct Tc64Cfg {
     static constexpr int ACC = SL == 7 ? 5 : SL;
     static constexpr int N = 48;
     static constexpr int PE_WARPS = N / 4;                       // producer / epilogue warps
-    static constexpr int THREADS = (PE_WARPS + 1) * 32;
+    static constexpr int MMA_WARP = PE_WARPS;                    // one thread issues the MMAs
+    static constexpr int TMA_WARP = PE_WARPS + 1;                // one thread issues the TMA loads
+    static constexpr int THREADS = (PE_WARPS + 2) * 32;
+    static constexpr int HALF = N / 2;                           // half columns of a CTA
+    // table tiles in flight: three with four slices, two with seven (shared memory)
+    static constexpr int TSTAGES = SL == 7 ? 2 : 3;
     static constexpr int BUF_COLS = ACC * N;                    // column offset of the second buffer
     static constexpr int B_TILE = N * 64;                       // bytes of one slice of the generated tile
     static constexpr int TSTAGE_BYTES = SL * T6_M * 64;         // a multiple of 1024
     static constexpr int GSTAGE_BYTES = SL * N * 64;            // a multiple of 1024
     static constexpr int SC_FLOATS = T6_M + N;                  // per scale slot: table rows, generated rows
     static constexpr int COLS_PER_WARP = N / (PE_WARPS / 4);    // 16 columns per epilogue warp
+    // generated tiles in flight: three with four slices (the drain of a window then overlaps two chunks'
+    // MMAs), two with seven (shared memory)
+    static constexpr int GSTAGES = SL == 7 ? 2 : 3;
+    static constexpr int DRAIN_AT = GSTAGES - 2;                 // chunk of the next window after which to drain
+    // scale slots, one per window: a thread may start window w + 1 (and write its slot) while another still
+    // drains window w - 1 when the drain comes after the next window's second chunk
+    static constexpr int SC_SLOTS = DRAIN_AT == 0 ? 2 : 3;
     static_assert(PE_WARPS * 32 == N * 8, "eight producer threads (4 nodes each) per generated row");
     static_assert(2 * BUF_COLS <= 512, "two buffers of accumulators fit the TMEM allocation");
     static_assert(TSTAGE_BYTES % 1024 == 0 && GSTAGE_BYTES % 1024 == 0, "1024-byte aligned stages");
 };
-constexpr int T6_TSTAGES = 3;                          // table tiles in flight (TMA ring)
-constexpr int T6_GSTAGES = 2;                          // generated tiles (producer ring)
-constexpr int T6_SC_SLOTS = 2;                         // scale ring, one slot per window (see the drain)
 constexpr int T6_TMEM_COLS = 512;
+constexpr int T6_WIN_BYTES = T6_WIN * T6_K * 8;        // one row of a window's double-floats (128 nodes)
 constexpr int T6_A_TILE = T6_M * 64;                   // bytes of one slice of the table tile
 constexpr int T6_BOXES = T6_M / 32;                    // table box heights 32, 64, 96, 128 rows
 
+// Dynamic shared memory: the table ring, the generated ring, one window of the generated operand's inputs
+// (A_P of the CTA's half columns, then hw rows of W / r_T), the scale slots and the mbarriers.
 template <int SL>
-static size_t tc64_smem_bytes() {
+static size_t tc64_smem_bytes(int hw) {
     using CF = Tc64Cfg<SL>;
-    return 1024 + (size_t)T6_TSTAGES * CF::TSTAGE_BYTES + (size_t)T6_GSTAGES * CF::GSTAGE_BYTES +
-           sizeof(float) * T6_SC_SLOTS * CF::SC_FLOATS + 8 * (2 * T6_TSTAGES + 2 * T6_GSTAGES + 4);
+    return 1024 + (size_t)CF::TSTAGES * CF::TSTAGE_BYTES + (size_t)CF::GSTAGES * CF::GSTAGE_BYTES +
+           (size_t)(CF::HALF + hw) * T6_WIN_BYTES + sizeof(float) * CF::SC_SLOTS * CF::SC_FLOATS +
+           8 * (2 * CF::TSTAGES + 2 * CF::GSTAGES + 6);
 }
 
 // Tensor maps of the slice planes with box heights 32, 64, 96 and 128 rows: a row tile loads only the
 // 32-row multiple that covers its rows (rows past its end are loaded from the next tile, or left stale,
 // and only feed accumulator lanes that are never read).
+// mA, mW: the double-float A_P rows and W / r_T rows of the node tables as FP32 tensors (x = float within a
+// row, y = row, z = evaluation) with boxes of one window (256 floats) by the CTA's half columns / hw rows.
 struct Tc64Maps {
     CUtensorMap m[T6_BOXES];
+    CUtensorMap mA, mW;
 };
 
 struct Tc64Args {
@@ -89,7 +105,8 @@ struct Tc64Args {
     const int* half_q;     // [n_half] q of each half column
     const char* node;      // node tables (FP64-accurate tensor-core layout) of the launch's evaluations
     size_t node_bytes;     // stride between evaluations
-    size_t sc_off_f, ap_off_f, w_off_f;
+    size_t sc_off_f;
+    int hw;                // W rows staged per window: 2 (l_P + 1), every d = |q - q'| one CTA can meet
     double* mol;           // [nev][2][N_T][n_half] complex, written as (re, im) doubles
     int* err;
     long wait_limit;       // polls of an mbarrier wait before it gives up
@@ -107,21 +124,29 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
     constexpr int T6_GSTAGE_BYTES = CF::GSTAGE_BYTES;
     constexpr int T6_SC_FLOATS = CF::SC_FLOATS;
     constexpr int T6_COLS_PER_WARP = CF::COLS_PER_WARP;
+    constexpr int T6_GSTAGES = CF::GSTAGES;
+    constexpr int T6_TSTAGES = CF::TSTAGES;
+    constexpr int T6_SC_SLOTS = CF::SC_SLOTS;
+    constexpr bool X2 = SL == OZ_FAST_SLICES;   // four slices: packed FP32x2 producer and drain
     extern __shared__ __align__(1024) unsigned char t6_smem_raw[];
     unsigned char* sm = t6_smem_raw + ((1024 - (smem_u32(t6_smem_raw) & 1023)) & 1023);
     unsigned char* gsm = sm + T6_TSTAGES * T6_TSTAGE_BYTES;                        // generated tiles
-    float* ring = reinterpret_cast<float*>(gsm + T6_GSTAGES * T6_GSTAGE_BYTES);  // [slot][T6_SC_FLOATS]
+    unsigned char* raw = gsm + T6_GSTAGES * T6_GSTAGE_BYTES;                     // A_P rows, then W rows
+    float* ring = reinterpret_cast<float*>(raw + (CF::HALF + A.hw) * T6_WIN_BYTES);  // [slot][T6_SC_FLOATS]
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + T6_SC_SLOTS * T6_SC_FLOATS);
     __shared__ uint32_t s_tmem;
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_dlo;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntile = blockIdx.x % A.n_ntiles, tile = blockIdx.x / A.n_ntiles, e = blockIdx.y;
     const int row0 = A.qg_off[tile], ns = (A.qg_off[tile + 1] - row0) / 2;   // states of the row tile
     const int qp = A.qg_q[tile];
     const int box = (2 * ns + 31) / 32;                  // table box height of this tile, in 32-row units
-    // tfull[3] (TMA), tempty[3], gfull[2] (producers), gempty[2], accf[2], acce[2]
+    // tfull[TSTAGES] (TMA), tempty[TSTAGES] (MMA commit), gfull[GSTAGES] (producers), gempty[GSTAGES] (MMA
+    // commit), accf[2] (MMA commit), acce[2] (drain), rawfull (TMA), rawempty (producers)
     const uint32_t tfull0 = smem_u32(bars), tempty0 = tfull0 + 8 * T6_TSTAGES, gfull0 = tempty0 + 8 * T6_TSTAGES,
-                   gempty0 = gfull0 + 8 * T6_GSTAGES, accf0 = gempty0 + 8 * T6_GSTAGES, acce0 = accf0 + 16;
+                   gempty0 = gfull0 + 8 * T6_GSTAGES, accf0 = gempty0 + 8 * T6_GSTAGES, acce0 = accf0 + 16,
+                   rawfull = acce0 + 16, rawempty = rawfull + 8;
+    const int c0 = ntile * CF::HALF;                     // first half column of this CTA
     if (tid == 0) {
         s_abort = 0;
         for (int s = 0; s < T6_TSTAGES; ++s) {
@@ -136,7 +161,19 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             mbar_init(accf0 + 8 * b, 1);
             mbar_init(acce0 + 8 * b, T6_PE_WARPS * 32);
         }
+        mbar_init(rawfull, 1);
+        mbar_init(rawempty, T6_PE_WARPS * 32);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) {
+        // the smallest d = |q_c - q'| over the CTA's half columns: the first W row the window loads hold
+        int dl = 1 << 20;
+        if (lane < CF::HALF && c0 + lane < A.n_half) {
+            dl = A.half_q[c0 + lane] - qp;
+            dl = dl < 0 ? -dl : dl;
+        }
+        for (int o = 16; o > 0; o >>= 1) dl = min(dl, __shfl_xor_sync(0xffffffffu, dl, o));
+        if (lane == 0) s_dlo = dl < (1 << 20) ? dl : 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
@@ -151,13 +188,16 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
     const char* nb = A.node + (size_t)e * A.node_bytes;
     const int nk = A.nchunks;
 
-    if (warp == T6_PE_WARPS) {
-        // ---- TMA and MMA issue (one thread)
+    if (warp == CF::TMA_WARP) {
+        // ---- TMA issue (one thread): the table tiles chunk by chunk into their ring, a slot refilled as soon as
+        // the MMAs that read it have completed; the generated operand's inputs window by window into the raw
+        // buffer, refilled as soon as every producer has read the previous window
         if (lane == 0) {
-            const uint32_t idesc = bf16_idesc_mn(T6_M, T6_N);
             const uint32_t tx = (uint32_t)(SL * box * 32 * 64);
+            const uint32_t rtx = (uint32_t)((CF::HALF + A.hw) * T6_WIN_BYTES);
             const CUtensorMap* tmap = &maps.m[box - 1];
-            auto issue_tma = [&](int k) {
+            const int dlo = s_dlo, nwin = nk / T6_WIN;
+            auto issue_table = [&](int k) {
                 const int s = k % T6_TSTAGES;
                 unsigned char* st = sm + s * T6_TSTAGE_BYTES;
                 const uint32_t bar = tfull0 + 8 * s;
@@ -165,8 +205,41 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                 for (int sp = 0; sp < SL; ++sp)
                     tma_load_3d(smem_u32(st + sp * T6_A_TILE), tmap, k * T6_K, sp * A.tc_rows + row0, e, bar);
             };
-            int issued = 0;
-            for (; issued < T6_TSTAGES && issued < nk; ++issued) issue_tma(issued);
+            auto issue_raw = [&](int w) {
+                mbar_arrive_tx(rawfull, rtx);
+                tma_load_3d(smem_u32(raw), &maps.mA, w * T6_WIN * T6_K * 2, c0, e, rawfull);
+                tma_load_3d(smem_u32(raw + CF::HALF * T6_WIN_BYTES), &maps.mW, w * T6_WIN * T6_K * 2, 2 * dlo, e, rawfull);
+            };
+            bool ok = true;
+            int issued = 0, issued_raw = 0;
+            if (nwin > 0) issue_raw(issued_raw++);
+            for (; issued < T6_TSTAGES && issued < nk; ++issued) issue_table(issued);
+            for (int k = 0; k < nk && ok; ++k) {
+                if (k % T6_WIN == 0 && issued_raw < nwin) {
+                    const int w = k / T6_WIN;   // window w read by every producer: load window w + 1
+                    ok = mbar_wait(rawempty, w & 1, abort_flag, A.err, 17, A.wait_limit);
+                    if (ok) issue_raw(issued_raw++);
+                }
+                if (ok && issued < nk) {
+                    ok = mbar_wait(tempty0 + 8 * (k % T6_TSTAGES), (k / T6_TSTAGES) & 1, abort_flag, A.err, 13, A.wait_limit);
+                    if (ok) issue_table(issued++);
+                }
+            }
+            // every copy issued has landed before the CTA exits: at once on the normal path (the consumers
+            // waited for them), bounded where a role gave up before reading its data
+            for (int k = issued > T6_TSTAGES ? issued - T6_TSTAGES : 0; k < issued; ++k) {
+                const int s = k % T6_TSTAGES;
+                for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(tfull0 + 8 * s, (k / T6_TSTAGES) & 1); ++it) {
+                }
+            }
+            if (issued_raw > 0)
+                for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(rawfull, (issued_raw - 1) & 1); ++it) {
+                }
+        }
+    } else if (warp == CF::MMA_WARP) {
+        // ---- MMA issue (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = bf16_idesc_mn(T6_M, T6_N);
             bool ok = true;
             int last_mma = -1;   // the last chunk whose MMAs were issued (their completion commits to tempty)
             for (int k = 0; k < nk && ok; ++k) {
@@ -201,20 +274,6 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                 tc_commit(gempty0 + 8 * s2);
                 last_mma = k;
                 if (k % T6_WIN == T6_WIN - 1) tc_commit(accf0 + 8 * b);
-                if (k >= 1 && issued < nk) {
-                    // refill the table slot of the previous chunk (for chunk k + 2) once its MMAs have completed
-                    const int kp = k - 1, sp = kp % T6_TSTAGES;
-                    ok = mbar_wait(tempty0 + 8 * sp, (kp / T6_TSTAGES) & 1, abort_flag, A.err, 13, A.wait_limit);
-                    if (ok) issue_tma(issued++);
-                }
-            }
-            if (!ok) {
-                // give the copies still in flight time to land before the CTA exits
-                for (int k = issued > T6_TSTAGES ? issued - T6_TSTAGES : 0; k < issued; ++k) {
-                    const int s = k % T6_TSTAGES;
-                    for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(tfull0 + 8 * s, (k / T6_TSTAGES) & 1); ++it) {
-                    }
-                }
             }
             // the MMAs issued complete before the tensor memory is released (they finish in order: the last
             // chunk's commit covers them all); on the normal path the epilogue has waited for them already,
@@ -230,24 +289,33 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
         const int n = tid >> 3, part = tid & 7;
         const int gr = ntile * T6_N + n, c = gr >> 1, ri = gr & 1;
         const bool valid = c < A.n_half;
-        int d = 0;
+        // this row's window inputs in the raw buffer: A_P row n / 2 (zero past the last half column), W row
+        // 2 (d - d_lo) + re/im
+        int lw = ri;
         if (valid) {
-            d = A.half_q[c] - qp;
+            int d = A.half_q[c] - qp;
             d = d < 0 ? -d : d;
+            lw = 2 * (d - s_dlo) + ri;
         }
+        const unsigned char* ap_s = raw + (n >> 1) * T6_WIN_BYTES + part * 32;
+        const unsigned char* wd_s = raw + (CF::HALF + lw) * T6_WIN_BYTES + part * 32;
         const float* nbf = reinterpret_cast<const float*>(nb);
-        const float2* ap = reinterpret_cast<const float2*>(nbf + A.ap_off_f) + (size_t)(valid ? c : 0) * A.G;
-        const float2* wd = reinterpret_cast<const float2*>(nbf + A.w_off_f) + ((size_t)d * 2 + ri) * A.G;
         const float* scT = nbf + A.sc_off_f;   // [chunk][tc_rows]
         // epilogue: accumulator lanes 32 qd .. 32 qd + 31 (table rows), 16 columns from col0
         const int qd = warp & 3, col0 = (warp >> 2) * T6_COLS_PER_WARP;
         const int lrow = qd * 32 + lane;
         const bool live = qd * 32 < 2 * ns;    // warps whose rows all lie past the tile skip the arithmetic
-        float hi[T6_COLS_PER_WARP], lo[T6_COLS_PER_WARP];
+        float hi[X2 ? 1 : T6_COLS_PER_WARP], lo[X2 ? 1 : T6_COLS_PER_WARP];
+        f32x2 hi2[X2 ? T6_COLS_PER_WARP / 2 : 1], lo2[X2 ? T6_COLS_PER_WARP / 2 : 1];
 #pragma unroll
-        for (int k = 0; k < T6_COLS_PER_WARP; ++k) {
+        for (int k = 0; k < (X2 ? 1 : T6_COLS_PER_WARP); ++k) {
             hi[k] = 0.f;
             lo[k] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < (X2 ? T6_COLS_PER_WARP / 2 : 1); ++k) {
+            hi2[k] = x2_pack(0.f, 0.f);
+            lo2[k] = x2_pack(0.f, 0.f);
         }
         bool ok = true;
         // drain of window j: its accumulators with the window's scales
@@ -256,6 +324,42 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             ok = ok && mbar_wait(accf0 + 8 * b, (j >> 1) & 1, abort_flag, A.err, 14, A.wait_limit);
             if (!ok) return;
             tc_fence_after();
+            if constexpr (X2) {
+                if (live) {
+                    const float* scl = ring + (j % T6_SC_SLOTS) * T6_SC_FLOATS;
+                    const float sa = scl[lrow];
+                    const f32x2 sa2 = x2_pack(sa, sa), CM = x2_pack(12582912.f, 12582912.f);
+                    const uint32_t base =
+                        tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * T6_BUF_COLS + col0);
+#pragma unroll
+                    for (int q = 0; q < T6_COLS_PER_WARP / 8; ++q) {
+                        float v[T6_ACC][8];
+#pragma unroll
+                        for (int lv = 0; lv < T6_ACC; ++lv) tmem_ld8(base + lv * T6_N + 8 * q, v[lv]);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                        for (int u = 0; u < 8; u += 2) {
+                            const int k = (8 * q + u) / 2;
+                            const float2 sn = *reinterpret_cast<const float2*>(scl + T6_M + col0 + 8 * q + u);
+                            const f32x2 sc = x2_mul(sa2, x2_pack(sn.x, sn.y));
+                            const f32x2 L0 = x2_pack(v[0][u], v[0][u + 1]), L1 = x2_pack(v[1][u], v[1][u + 1]),
+                                        L2 = x2_pack(v[2][u], v[2][u + 1]), L3 = x2_pack(v[3][u], v[3][u + 1]);
+                            // L0 + rint(L1) exact (into the TwoSum high part), frac(L1) + L2 exact, + L3
+                            // rounded once (below 2^8, its rounding under 2^-16 units: 2^-30 of one node's
+                            // largest product), into the low part
+                            const f32x2 l1h = x2_sub(x2_add(L1, CM), CM);
+                            const f32x2 xa = x2_add(L0, l1h);
+                            const f32x2 xbc = x2_add(x2_add(x2_sub(L1, l1h), L2), L3);
+                            f32x2 r1;
+                            hi2[k] = two_sum_x2(hi2[k], x2_mul(xa, sc), r1);
+                            lo2[k] = x2_fma(xbc, sc, x2_add(lo2[k], r1));
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(acce0 + 8 * b);
+                return;
+            }
             if (live) {
                 const float* scl = ring + (j % T6_SC_SLOTS) * T6_SC_FLOATS;
                 const float sa = scl[lrow];
@@ -272,15 +376,16 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                         const int k = 8 * q + u;
                         const float sc = sa * scl[T6_M + col0 + k];
                         // exact: L0 + round(L1) (integers below 2^22), frac(L1) + L2 (multiples of
-                        // 2^-16 below 2^7); rounded: L3 + T (below 1, its rounding under 2^-24)
+                        // 2^-16 below 2^7)
                         const float l1h = rintf(v[1][u]);
                         const float xa = __fadd_rn(v[0][u], l1h);
                         const float xb = __fadd_rn(__fsub_rn(v[1][u], l1h), v[2][u]);
-                        const float xc = T6_ACC == 5 ? __fadd_rn(v[3][u], v[T6_ACC - 1][u])
-                                         : T6_ACC == 4 ? v[T6_ACC - 1][u] : 0.f;
+                        // seven slices: frac(L1) + L2 exact into the high part as well; L3 + T rounded
+                        // (below 1, its rounding under 2^-24)
                         float r1, r2;
                         hi[k] = two_sum(hi[k], xa * sc, r1);
                         hi[k] = two_sum(hi[k], xb * sc, r2);
+                        const float xc = __fadd_rn(v[3][u], v[T6_ACC - 1][u]);
                         lo[k] = __fadd_rn(lo[k], __fadd_rn(__fadd_rn(r1, r2), xc * sc));
                     }
                 }
@@ -290,22 +395,88 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
         };
         const int nwin = nk / T6_WIN;
         const int trow = row0 + tid;
+        // the table rows' scales (rows past the table read as zero scale), loaded one window ahead of the
+        // window that stores them in its scale slot
+        const bool has_trow = tid < T6_M && trow < A.tc_rows;
+        float tsc = has_trow ? scT[trow] : 0.f;
+        if constexpr (X2) {
+        // four slices, two nodes per packed FP32x2 instruction: the products as unnormalised pairs p + e,
+        // sliced by rounding to each slice's grid
+        for (int w = 0; w < nwin && ok; ++w) {
+            f32x2 pw[T6_WIN * 2], ew[T6_WIN * 2];
+            float mx = 0.f;
+            ok = mbar_wait(rawfull, w & 1, abort_flag, A.err, 18, A.wait_limit);
+            if (!ok) break;
+#pragma unroll
+            for (int cc = 0; cc < T6_WIN; ++cc) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float4 wq = *reinterpret_cast<const float4*>(wd_s + cc * T6_K * 8 + h * 16);
+                    const float4 aq = *reinterpret_cast<const float4*>(ap_s + cc * T6_K * 8 + h * 16);
+                    const int j = 2 * cc + h;
+                    df_mul_pe_x2(x2_pack(wq.x, wq.z), x2_pack(wq.y, wq.w), x2_pack(aq.x, aq.z), x2_pack(aq.y, aq.w),
+                                 pw[j], ew[j]);
+                    float p0, p1;
+                    x2_unpack(pw[j], p0, p1);
+                    mx = fmaxf(mx, fmaxf(fabsf(p0), fabsf(p1)));
+                }
+            }
+            // this thread has read the window's inputs: its shared-memory reads ordered before the TMA
+            // (async proxy) writes of the next window, then the release to the TMA thread
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(rawempty);
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const int sh = min(oz_shift(mx), 127);
+            const float sc2 = __int_as_float((sh + 127) << 23);
+            const f32x2 s2 = x2_pack(sc2, sc2);
+            float* scl = ring + (w % T6_SC_SLOTS) * T6_SC_FLOATS;
+            if (part == 0) scl[T6_M + n] = ldexpf(1.f, -sh);
+            if (tid < T6_M) scl[tid] = tsc;
+            if (has_trow && w + 1 < nwin) tsc = scT[(size_t)(w + 1) * A.tc_rows + trow];
+#pragma unroll
+            for (int cc = 0; cc < T6_WIN; ++cc) {
+                const int k = w * T6_WIN + cc, s = k % T6_GSTAGES;
+                if (k >= T6_GSTAGES)
+                    ok = ok && mbar_wait(gempty0 + 8 * s, ((k - T6_GSTAGES) / T6_GSTAGES) & 1, abort_flag, A.err, 15, A.wait_limit);
+                if (!ok) break;
+                unsigned char* bt = gsm + s * T6_GSTAGE_BYTES;
+                f32x2 t0[4], t1[4];
+                oz_slices4_pe_x2(pw[2 * cc], ew[2 * cc], s2, t0);
+                oz_slices4_pe_x2(pw[2 * cc + 1], ew[2 * cc + 1], s2, t1);
+                const int off = n * 64 + (((part >> 1) ^ ((n >> 1) & 3)) << 4) + (part & 1) * 8;
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) {
+                    float a0, a1, b0, b1;
+                    x2_unpack(t0[sp], a0, a1);
+                    x2_unpack(t1[sp], b0, b1);
+                    *reinterpret_cast<uint2*>(bt + sp * T6_B_TILE + off) = make_uint2(bf16x2_exact(a0, a1), bf16x2_exact(b0, b1));
+                }
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(gfull0 + 8 * s);
+                if (cc == CF::DRAIN_AT && w >= 1) drain(w - 1);
+            }
+        }
+        } else {
         for (int w = 0; w < nwin && ok; ++w) {
             // this thread's 16 generated values of the window (four per chunk), their row maximum over the
             // window's 128 nodes (the row's eight threads), and the window's scales
             float2 xw[T6_WIN * 4];
             float mx = 0.f;
+            ok = mbar_wait(rawfull, w & 1, abort_flag, A.err, 18, A.wait_limit);
+            if (!ok) break;
 #pragma unroll
             for (int cc = 0; cc < T6_WIN; ++cc) {
-                const int g0 = (w * T6_WIN + cc) * T6_K + part * 4;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float4 wq = valid ? reinterpret_cast<const float4*>(wd + g0)[h] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 aq = valid ? reinterpret_cast<const float4*>(ap + g0)[h] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 wq = *reinterpret_cast<const float4*>(wd_s + cc * T6_K * 8 + h * 16);
+                    const float4 aq = *reinterpret_cast<const float4*>(ap_s + cc * T6_K * 8 + h * 16);
                     xw[4 * cc + 2 * h] = df_mul(make_float2(wq.x, wq.y), make_float2(aq.x, aq.y));
                     xw[4 * cc + 2 * h + 1] = df_mul(make_float2(wq.z, wq.w), make_float2(aq.z, aq.w));
                 }
             }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(rawempty);
 #pragma unroll
             for (int jj = 0; jj < T6_WIN * 4; ++jj) mx = fmaxf(mx, fabsf(xw[jj].x));
 #pragma unroll
@@ -313,8 +484,8 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             const int sh = oz_shift(mx);
             float* scl = ring + (w % T6_SC_SLOTS) * T6_SC_FLOATS;
             if (part == 0) scl[T6_M + n] = ldexpf(1.f, -sh);
-            // the table rows' scales of this window (rows past the table read as zero scale)
-            if (tid < T6_M) scl[tid] = trow < A.tc_rows ? scT[(size_t)w * A.tc_rows + trow] : 0.f;
+            if (tid < T6_M) scl[tid] = tsc;
+            if (has_trow && w + 1 < nwin) tsc = scT[(size_t)(w + 1) * A.tc_rows + trow];
 #pragma unroll
             for (int cc = 0; cc < T6_WIN; ++cc) {
                 const int k = w * T6_WIN + cc, s = k % T6_GSTAGES;
@@ -338,6 +509,7 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                 if (cc == 0 && w >= 1) drain(w - 1);
             }
         }
+        }
         if (ok) drain(nwin - 1);
         // results: row m of D is A_T row m of the tile (overlap K) or, from ns on, its A_T V_T row (Q)
         if (ok && live && lrow < 2 * ns) {
@@ -349,7 +521,16 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             for (int k = 0; k < T6_COLS_PER_WARP; ++k) {
                 const int go = ntile * T6_N + col0 + k, co = go >> 1, rio = go & 1;
                 if (co >= A.n_half) continue;
-                out[((size_t)x * plane + (size_t)i * A.n_half + co) * 2 + rio] = (double)hi[k] + (double)lo[k];
+                double val;
+                if constexpr (X2) {
+                    float h0, h1, l0, l1;
+                    x2_unpack(hi2[k / 2], h0, h1);
+                    x2_unpack(lo2[k / 2], l0, l1);
+                    val = (k & 1) ? (double)h1 + (double)l1 : (double)h0 + (double)l0;
+                } else {
+                    val = (double)hi[k] + (double)lo[k];
+                }
+                out[((size_t)x * plane + (size_t)i * A.n_half + co) * 2 + rio] = val;
             }
         }
     }
@@ -380,6 +561,29 @@ wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(WPCCC_ECUDA, "cuTensorMapEncodeTiled failed for the slice planes");
     }
+    // the generated operand's inputs as FP32 tensors (a double-float is two floats): A_P [n_half][2 G] and
+    // W / r_T [d][re, im][2 G] per evaluation; boxes of one window by 24 half columns / hw rows (rows past
+    // the tensor read as zero)
+    const int hw = 2 * (B->P.lmax + 1);
+    if (hw > 2 * (B->dmax + 1) || hw > 256) return fail(WPCCC_EINVAL, "tensor-core contraction: W rows");
+    {
+        const char* nodef = static_cast<const char*>(node);
+        const cuuint64_t fstr[2] = {(cuuint64_t)B->G * 2 * sizeof(float), (cuuint64_t)node_bytes};
+        const cuuint64_t dA[3] = {(cuuint64_t)B->G * 2, (cuuint64_t)B->n_half, (cuuint64_t)nev};
+        const cuuint64_t dW[3] = {(cuuint64_t)B->G * 2, (cuuint64_t)2 * (B->dmax + 1), (cuuint64_t)nev};
+        const cuuint32_t bA[3] = {(cuuint32_t)(T6_WIN * T6_K * 2), (cuuint32_t)(Tc64Cfg<OZ_FAST_SLICES>::HALF), 1};
+        const cuuint32_t bW[3] = {(cuuint32_t)(T6_WIN * T6_K * 2), (cuuint32_t)hw, 1};
+        CUresult r = encode_fn()(&maps.mA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                                 const_cast<char*>(nodef + L.t6_ap_off * sizeof(float)), dA, fstr, bA, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = encode_fn()(&maps.mW, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                            const_cast<char*>(nodef + L.t6_w_off * sizeof(float)), dW, fstr, bW, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(WPCCC_ECUDA, "cuTensorMapEncodeTiled failed for the node weights");
+    }
     Tc64Args a;
     a.G = B->G;
     a.N_T = B->N_T;
@@ -395,21 +599,20 @@ wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double
     a.node = static_cast<const char*>(node);
     a.node_bytes = node_bytes;
     a.sc_off_f = L.t6_sc_off;
-    a.ap_off_f = L.t6_ap_off;
-    a.w_off_f = L.t6_w_off;
+    a.hw = hw;
     a.mol = reinterpret_cast<double*>(mol);
     a.err = err;
     a.wait_limit = B->wait_polls;
     if (slices == OZ_SLICES) {
         using CF = Tc64Cfg<OZ_SLICES>;
         a.n_ntiles = (2 * B->n_half + CF::N - 1) / CF::N;
-        const size_t smem = tc64_smem_bytes<OZ_SLICES>();
+        const size_t smem = tc64_smem_bytes<OZ_SLICES>(hw);
         WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<OZ_SLICES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_mol_tc64<OZ_SLICES><<<dim3(a.n_ntiles * B->n_qgroups, nev), CF::THREADS, smem, st>>>(maps, a);
     } else {
         using CF = Tc64Cfg<OZ_FAST_SLICES>;
         a.n_ntiles = (2 * B->n_half + CF::N - 1) / CF::N;
-        const size_t smem = tc64_smem_bytes<OZ_FAST_SLICES>();
+        const size_t smem = tc64_smem_bytes<OZ_FAST_SLICES>(hw);
         WPCCC_CUDA(cudaFuncSetAttribute(k_mol_tc64<OZ_FAST_SLICES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
         k_mol_tc64<OZ_FAST_SLICES><<<dim3(a.n_ntiles * B->n_qgroups, nev), CF::THREADS, smem, st>>>(maps, a);

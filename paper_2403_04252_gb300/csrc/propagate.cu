@@ -31,6 +31,7 @@ struct RkArgs {
     int N;
     int N_T;                // target states (two-centre: S = [[I, K], [K^+, I]])
     int iters;              // refinement iterations (mixed-precision form)
+    int df_rhs;             // reduced-precision forms: H y in double-float arithmetic (matvec_df)
     double tol;             // convergence tolerance of the refinement's last sweep (<= 0: unchecked)
     const float2* LU32;     // chunk: FP32 factors per evaluation (mixed forms: LU, or K and the Schur factor)
     float2* carryLU32;      // per path (mixed form)
@@ -64,7 +65,7 @@ struct PosMats {
 //   RK_MIXED   S^{-1} applied by FP64 refinement on FP32 LU factors
 //   RK_MIXED_SCHUR  the same on the FP32 Schur factors
 template <int MODE>
-__global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
+__global__ void __launch_bounds__(RK_THREADS, 1) k_rk4(RkArgs A) {
     extern __shared__ double2 rk_smem[];
     const int N = A.N;
     double2* c = rk_smem;
@@ -114,10 +115,10 @@ __global__ void __launch_bounds__(RK_THREADS) k_rk4(RkArgs A) {
             apply_LU(m.S, m.piv, m.H, N, v, in, out, t, static_cast<double2*>(blk));
         } else if (MODE == RK_MIXED_SCHUR) {
             apply_schur_mixed(m.S, m.L32, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds, us32,
-                              static_cast<float2*>(blk), A.tol, A.flags);
+                              static_cast<float2*>(blk), A.tol, A.flags, A.df_rhs != 0);
         } else {
             apply_LU_mixed(m.S, m.L32, m.piv, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds,
-                           static_cast<float2*>(blk), A.tol, A.flags);
+                           static_cast<float2*>(blk), A.tol, A.flags, A.df_rhs != 0);
         }
     };
     PosMats Mz;
@@ -304,6 +305,7 @@ struct PropPlan {
     int max_steps = 0;
     bool two = false, mixed = false, stage = false, schur = false;
     bool schur_tc = false;   // mixed Schur forms: the trailing update I - K^+ K on the tensor cores
+    bool df_rhs = false;     // reduced-precision forms (1, 2, 3): H y on the FP32 pipe in double-float arithmetic
     bool wide = false;       // one-centre RK4 with the vectors in global memory (k_rk4_wide)
     size_t per_eval = 0, fixed = 0;
     std::vector<double> z;
@@ -361,6 +363,7 @@ static wpccc_status plan_build(wpccc_basis_s* B, const wpccc_paths* paths, int p
     // refinement; 3: as 1 with the contraction on the tensor cores (three bf16 slices); 4: FP64 form with
     // the contraction on the tensor cores to FP64 accuracy (seven slices); 5: as 2 with mode 4's elements
     P.mixed = P.two && precision_mode >= 1 && precision_mode != 4;
+    P.df_rhs = P.mixed && precision_mode != 5;
     P.elem_precision = !P.two ? 0
                        : (precision_mode == 1 || precision_mode == 3) ? precision_mode
                        : (precision_mode == 4 || precision_mode == 5) ? 4 : 0;
@@ -545,6 +548,7 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     ra.N = N;
     ra.N_T = B->N_T;
     ra.iters = B->refine_iters;
+    ra.df_rhs = P.df_rhs ? 1 : 0;
     ra.tol = B->refine_tol;
     ra.carryH = P.d_carry;
     ra.carryLU = P.d_carryLU;

@@ -3,6 +3,7 @@
 // Every helper is called by all RK_THREADS threads of a block and ends with a block barrier.
 #pragma once
 
+#include "ozaki.cuh"
 #include "wpccc_internal.cuh"
 
 namespace wpccc {
@@ -145,6 +146,7 @@ __device__ inline void matvec(const double2* __restrict__ M, int N, const double
     for (int i = threadIdx.x; i < N; i += RK_THREADS) {
         double re = 0.0, im = 0.0;
         const double2* row = M + i;
+#pragma unroll 4
         for (int j = 0; j < N; ++j) {
             const double2 a = row[(size_t)j * N];
             const double2 q = y[j];
@@ -158,6 +160,64 @@ __device__ inline void matvec(const double2* __restrict__ M, int N, const double
     __syncthreads();
 }
 
+// An FP64 value as a double-float (hi, lo), by integer operations on its bits (no FP64 arithmetic): hi is x
+// truncated to 24 significant bits, lo the next 23 bits (exact: the bits are taken, not rounded), so
+// |x - hi - lo| < 2^-46 |x|.  For 2^-126 <= |x| < 2^-80 lo is dropped (an absolute error below 2^-104), below
+// 2^-126 x reads as zero; infinities and NaNs go through the FP64 conversion and stay non-finite.
+static __device__ __forceinline__ float2 split_bits(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const uint32_t h = (uint32_t)(u >> 32), l = (uint32_t)u;
+    const uint32_t e = (h >> 20) & 0x7FFu, sg = h & 0x80000000u;
+    if (e - 897u > 253u) return make_float2(e < 897u ? 0.f : __double2float_rn(x), 0.f);
+    const float hi = __uint_as_float(sg | ((e - 896u) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
+    const uint32_t r = (l >> 6) & 0x7FFFFFu;   // mantissa bits 28..6, the value r 2^(e - 1069)
+    const float rf = __fsub_rn(__uint_as_float(0x4B000000u | r), 8388608.f);
+    const float lo = e >= 943u ? __fmul_rn(rf, __uint_as_float((e - 942u) << 23)) : 0.f;
+    return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sg));
+}
+
+// (s, c) += a b for double-floats a = (a.x, a.y) pairs, two real products at once (one per half of the
+// FP32x2 registers): the products' high parts join s by TwoSum, their residuals and the TwoSum errors
+// join c (the compensated dot product of Ogita, Rump and Oishi, with double-float operands).
+static __device__ __forceinline__ void dot2_acc_x2(f32x2& s, f32x2& c, f32x2 ah, f32x2 al, f32x2 bh, f32x2 bl) {
+    const f32x2 p = x2_mul(ah, bh);
+    f32x2 e = x2_fma(ah, bh, x2_neg(p));
+    e = x2_fma(ah, bl, e);
+    e = x2_fma(al, bh, e);
+    f32x2 t;
+    s = two_sum_x2(s, p, t);
+    c = x2_add(c, x2_add(t, e));
+}
+
+// out = M y like matvec, for the reduced-precision forms' right-hand side H y: M's FP64 entries and y taken
+// as double-floats (split_bits), the sums compensated on the FP32 pipe (dot2_acc_x2, the real and the
+// imaginary part in the two halves), about 2^-44 of sum_j |M_ij| |y_j|.  ys: scratch of N float4.
+__device__ inline void matvec_df(const double2* __restrict__ M, int N, const double2* y, double2* out, float4* ys) {
+    for (int j = threadIdx.x; j < N; j += RK_THREADS) {
+        const float2 a = split_bits(y[j].x), b = split_bits(y[j].y);
+        ys[j] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += RK_THREADS) {
+        f32x2 s = x2_pack(0.f, 0.f), c = x2_pack(0.f, 0.f);   // (re, im)
+        const double2* row = M + i;
+#pragma unroll 4
+        for (int j = 0; j < N; ++j) {
+            const double2 m = row[(size_t)j * N];
+            const float2 mr = split_bits(m.x), mi = split_bits(m.y);
+            const float4 q = ys[j];   // (Re y hi, Re y lo, Im y hi, Im y lo)
+            // re += mr yr - mi yi, im += mr yi + mi yr
+            dot2_acc_x2(s, c, x2_pack(mr.x, mr.x), x2_pack(mr.y, mr.y), x2_pack(q.x, q.z), x2_pack(q.y, q.w));
+            dot2_acc_x2(s, c, x2_pack(-mi.x, mi.x), x2_pack(-mi.y, mi.y), x2_pack(q.z, q.x), x2_pack(q.w, q.y));
+        }
+        float sr, si, cr, ci;
+        x2_unpack(s, sr, si);
+        x2_unpack(c, cr, ci);
+        out[i] = make_double2((double)sr + (double)cr, (double)si + (double)ci);
+    }
+    __syncthreads();
+}
+
 // out = b - S y for S = [[I, K], [K^+, I]] (two-centre overlap, FP64, column-major): only the
 // off-diagonal blocks are read, rows i < N_T against columns j >= N_T and the other way round.
 __device__ inline void residual_S(const double2* __restrict__ S, int N, int N_T, const double2* y, const double2* b,
@@ -166,6 +226,7 @@ __device__ inline void residual_S(const double2* __restrict__ S, int N, int N_T,
         double re = 0.0, im = 0.0;
         const int j0 = i < N_T ? N_T : 0, j1 = i < N_T ? N : N_T;
         const double2* row = S + i;
+#pragma unroll 4
         for (int j = j0; j < j1; ++j) {
             const double2 a = row[(size_t)j * N];
             const double2 q = y[j];
@@ -196,8 +257,9 @@ static __device__ void apply_LU(const double2* __restrict__ LU, const int* __res
 static __device__ void apply_LU_mixed(const double2* __restrict__ S64, const float2* __restrict__ LU32,
                                const int* __restrict__ piv, const double2* __restrict__ Hm, int N, int N_T, double v,
                                int iters, const double2* y, double2* k, double2* b, double2* x, double2* r,
-                               float2* d, float2* blk, double tol = 0.0, int* flags = nullptr) {
-    matvec(Hm, N, y, b);
+                               float2* d, float2* blk, double tol = 0.0, int* flags = nullptr, bool df_rhs = false) {
+    if (df_rhs) matvec_df(Hm, N, y, b, reinterpret_cast<float4*>(r));
+    else matvec(Hm, N, y, b);
     for (int it = 0; it < iters; ++it) {
         const double2* rr = b;
         if (it > 0) {
@@ -360,6 +422,7 @@ static __device__ void schur_solve_inplace(const C2* __restrict__ D, int N, int 
     chol_solve_inplace<C2>(D + N_T + (size_t)N_T * N, N, NP, u, blk);
     for (int i = threadIdx.x; i < N_T; i += RK_THREADS) {
         R re = 0, im = 0;
+#pragma unroll 4
         for (int j = 0; j < NP; ++j) {
             const C2 a = K[(size_t)i + (size_t)j * N];
             const C2 b = u[j];
@@ -394,8 +457,10 @@ static __device__ void apply_schur(const double2* __restrict__ S, const double2*
 static __device__ void apply_schur_mixed(const double2* __restrict__ S64, const float2* __restrict__ D32,
                                          const double2* __restrict__ Hm, int N, int N_T, double v, int iters,
                                          const double2* y, double2* k, double2* b, double2* x, double2* r, float2* d,
-                                         float2* u, float2* blk, double tol = 0.0, int* flags = nullptr) {
-    matvec(Hm, N, y, b);
+                                         float2* u, float2* blk, double tol = 0.0, int* flags = nullptr,
+                                         bool df_rhs = false) {
+    if (df_rhs) matvec_df(Hm, N, y, b, reinterpret_cast<float4*>(r));
+    else matvec(Hm, N, y, b);
     for (int it = 0; it < iters; ++it) {
         const double2* rr = b;
         if (it > 0) {

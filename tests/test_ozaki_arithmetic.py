@@ -176,3 +176,102 @@ def test_epilogue_fold_over_many_windows():
         exact = sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b))
         err = abs(float(Fraction(float(hi)) + Fraction(float(lo)) - exact))
         assert err <= 2.0 ** -42 * float(np.abs(a).max() * np.abs(b).max()), seed
+
+
+def _df(x):
+    h = x.astype(np.float32)
+    return h, (x - h.astype(np.float64)).astype(np.float32)
+
+
+def _mul_pe(ah, al, bh, bl):
+    """The generated operand's product as an unnormalised pair (p, e): p = fl(ah bh), e = the FMA residual
+    plus the cross terms, each FMA rounded once (float64 holds every intermediate exactly here)."""
+    f64 = np.float64
+    p = (ah * bh).astype(np.float32)
+    e = (ah.astype(f64) * bh.astype(f64) - p.astype(f64)).astype(np.float32)
+    e = (ah.astype(f64) * bl.astype(f64) + e.astype(f64)).astype(np.float32)
+    e = (al.astype(f64) * bh.astype(f64) + e.astype(f64)).astype(np.float32)
+    return p, e
+
+
+def _slices4_pe(p, e, sh):
+    """Four slices by rounding to each grid with the constants 1.5 2^23 u (u = 1, 2^-8, 2^-16, 2^-24)."""
+    f32, f64 = np.float32, np.float64
+    s = f32(2.0 ** sh)
+    C = [f32(1.5 * 2.0 ** 23), f32(1.5 * 2.0 ** 15), f32(1.5 * 2.0 ** 7), f32(0.75)]
+    ps = (p.astype(f64) * f64(s))                       # exact: a power-of-two scaling
+    t0 = (ps + f64(C[0])).astype(f32) - C[0]            # fma(p, s, C0) - C0
+    r0 = (ps - t0.astype(f64)).astype(f32)              # fma(p, s, -t0), exact
+    t1 = ((r0 + C[1]).astype(f32) - C[1]).astype(f32)
+    r1 = (r0 - t1).astype(f32)
+    s1 = (e.astype(f64) * f64(s) + r1.astype(f64)).astype(f32)   # fma(e, s, r1)
+    t2 = ((s1 + C[2]).astype(f32) - C[2]).astype(f32)
+    r2 = (s1 - t2).astype(f32)
+    t3 = ((r2 + C[3]).astype(f32) - C[3]).astype(f32)
+    return [t0.astype(f32), t1, t2, t3]
+
+
+def _gen_window(rng):
+    # a generated row: W (one node weight) times A_P (one projectile state), each a double-float
+    w = rng.standard_normal(NODES) * np.exp2(-rng.uniform(0.0, 20.0, NODES))
+    a = rng.standard_normal(NODES) * np.exp2(-rng.uniform(0.0, 20.0, NODES))
+    wh, wl = _df(w)
+    ah, al = _df(a)
+    p, e = _mul_pe(wh, wl, ah, al)
+    E = np.frexp(np.abs(p).max())[1]
+    return w * a, p, e, min(7 - E, 127)
+
+
+def test_generated_operand_slices_by_grid_rounding():
+    # the four-slice generated operand: p + e reconstructed to 2^-25 + 2^-33 of the window's scaled grid,
+    # every slice k 2^(-8 i) with |k| <= 130, an exact bf16 number
+    rng = np.random.default_rng(23)
+    for _ in range(100):
+        x, p, e, sh = _gen_window(rng)
+        assert np.all(np.abs(e.astype(np.float64)) <= 3.0 * 2.0 ** -24 * np.abs(p.astype(np.float64)) * (1 + 2.0 ** -20))
+        ts = _slices4_pe(p, e, sh)
+        pe = (p.astype(np.float64) + e.astype(np.float64)) * 2.0 ** sh
+        rec = sum(t.astype(np.float64) for t in ts)
+        assert np.abs(rec - pe).max() <= 2.0 ** -25 + 2.0 ** -33
+        assert np.all(np.abs(x * 2.0 ** sh - pe) <= 2.0 ** -44 * np.abs(x * 2.0 ** sh) + 2.0 ** -140)
+        for i, t in enumerate(ts):
+            k = t.astype(np.float64) * 2.0 ** (8 * i)
+            assert np.all(k == np.rint(k)) and np.abs(k).max() <= 130
+            assert _is_bf16(t)
+
+
+def test_four_slice_fold_with_generated_slices_over_many_windows():
+    # precision mode 3 end to end on the CPU: table slices by the exact rule, generated slices by grid
+    # rounding, every level sum exact in FP32, the epilogue's fold (L0 + rint(L1) into a TwoSum high part,
+    # frac(L1) + L2 + L3 rounded once into the low part) over the 18 windows of a 2304-node rule
+    f32 = np.float32
+    worst = 0.0
+    for seed in range(6):
+        rng = np.random.default_rng(200 + seed)
+        hi, lo = f32(0.0), f32(0.0)
+        xs, ys = [], []
+        for _ in range(2304 // NODES):
+            xa, ha, la, sa = _window(rng)
+            xb, p, e, sb = _gen_window(rng)
+            xs.append(xa)
+            ys.append((p.astype(np.float64) + e.astype(np.float64)))
+            A = [k.astype(np.float64) * 2.0 ** (-8 * i) for i, k in enumerate(_slices(ha, la, sa, 4))]
+            Bs = [t.astype(np.float64) for t in _slices4_pe(p, e, sb)]
+            lv = [sum(np.dot(A[i], Bs[L - i]) for i in range(L + 1)) for L in range(4)]
+            for L, v in enumerate(lv):
+                assert float(np.float32(v)) == v and abs(v * 2.0 ** (8 * L)) < 2.0 ** 24
+            L0, L1, L2, L3 = (f32(v) for v in lv)
+            sc = f32(2.0 ** (-sa - sb))
+            l1h = f32(np.rint(L1))
+            xa_ = f32(L0 + l1h)
+            xb_ = f32(f32(L1 - l1h) + L2)
+            assert float(xa_) == float(L0) + float(l1h) and float(xb_) == float(L1 - l1h) + float(L2)
+            hi, r1 = _two_sum(hi, f32(xa_ * sc))
+            lo = f32(np.float64(f32(xb_ + L3)) * np.float64(sc) + np.float64(f32(lo + r1)))
+        a, b = np.concatenate(xs), np.concatenate(ys)
+        exact = sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b))
+        err = abs(float(Fraction(float(hi)) + Fraction(float(lo)) - exact))
+        scale = float(np.abs(a).max() * np.abs(b).max())
+        assert err <= 2.0 ** -27 * scale, seed
+        worst = max(worst, err / scale)
+    assert worst > 2.0 ** -45   # the truncated levels are really dropped
