@@ -22,11 +22,13 @@
 // operand keeps 31 bits below its row's window maximum, and a window's sum errs by up to about 2^-28 of its
 // largest term, without the truncation bias of the tensor core's FP32 accumulation.
 //
-// Pipeline per CTA (416 threads): warps 0-11 generate the Bw tiles (64-byte swizzled K-major rows) and
-// drain the accumulators; warp 12 issues the TMA loads of the table tiles (cp.async.bulk.tensor, 64-byte
-// swizzle) and the tcgen05.mma instructions.  Three table tiles and two generated tiles in flight in
-// shared memory, a ring of scale slots (one per window), two TMEM buffers of five accumulators (one per
-// window), mbarriers between the roles; every wait is bounded and records a timeout in a device flag.
+// Pipeline per CTA: warps 0-11 generate the Bw tiles (64-byte swizzled K-major rows) from the window's
+// W and A_P, which warp 13 stages in shared memory by TMA one window ahead; warp 13 also streams the table
+// tiles (cp.async.bulk.tensor, 64-byte swizzle) into their ring; warp 12 issues the tcgen05.mma
+// instructions.  The accumulators (two TMEM buffers, one per window) are drained with seven slices by
+// the producer warps, with four slices by four drain warps (14-17) that keep the double-float running
+// sums in the spare TMEM columns.  Mbarriers between the roles; every wait is bounded and records a
+// timeout in a device flag.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -51,25 +53,34 @@ template <int SL> struct Tc64Cfg {
     static constexpr int PE_WARPS = N / 4;                       // producer / epilogue warps
     static constexpr int MMA_WARP = PE_WARPS;                    // one thread issues the MMAs
     static constexpr int TMA_WARP = PE_WARPS + 1;                // one thread issues the TMA loads
-    static constexpr int THREADS = (PE_WARPS + 2) * 32;
+    // four slices: four drain warps (one per TMEM lane quarter) fold the accumulators into double-float
+    // running sums held in the spare TMEM columns, so that the producers never wait for a drain; seven
+    // slices: the producers drain (their accumulators leave no spare columns)
+    static constexpr int DRAIN_WARPS = SL == 7 ? 0 : 4;
+    static constexpr int DRAIN0 = PE_WARPS + 2;                  // first drain warp
+    static constexpr int THREADS = (PE_WARPS + 2 + DRAIN_WARPS) * 32;
+    static constexpr int SUM_COL = 2 * SL * N;                   // TMEM column of the running sums (hi, then lo)
     static constexpr int HALF = N / 2;                           // half columns of a CTA
-    // table tiles in flight: three with four slices, two with seven (shared memory)
-    static constexpr int TSTAGES = SL == 7 ? 2 : 3;
+    // table tiles in flight: four with four slices, two with seven (shared memory)
+    static constexpr int TSTAGES = SL == 7 ? 2 : 4;
     static constexpr int BUF_COLS = ACC * N;                    // column offset of the second buffer
     static constexpr int B_TILE = N * 64;                       // bytes of one slice of the generated tile
     static constexpr int TSTAGE_BYTES = SL * T6_M * 64;         // a multiple of 1024
     static constexpr int GSTAGE_BYTES = SL * N * 64;            // a multiple of 1024
     static constexpr int SC_FLOATS = T6_M + N;                  // per scale slot: table rows, generated rows
     static constexpr int COLS_PER_WARP = N / (PE_WARPS / 4);    // 16 columns per epilogue warp
-    // generated tiles in flight: three with four slices (the drain of a window then overlaps two chunks'
-    // MMAs), two with seven (shared memory)
-    static constexpr int GSTAGES = SL == 7 ? 2 : 3;
-    static constexpr int DRAIN_AT = GSTAGES - 2;                 // chunk of the next window after which to drain
-    // scale slots, one per window: a thread may start window w + 1 (and write its slot) while another still
-    // drains window w - 1 when the drain comes after the next window's second chunk
-    static constexpr int SC_SLOTS = DRAIN_AT == 0 ? 2 : 3;
+    // generated tiles in flight: four with four slices (the producers run up to four chunks ahead of the
+    // MMAs); two with seven (shared memory; the producers drain window w - 1 after the first chunk of
+    // window w)
+    static constexpr int GSTAGES = SL == 7 ? 2 : 4;
+    // scale slots, one per window.  Seven slices: a thread may start window w + 1 only after every producer
+    // has drained window w - 1.  Four slices: while the drain warps fold window j, the MMAs may finish
+    // window j + 1 (window j + 2 needs the accumulators that drain frees) and the producers run four chunks
+    // further, into window j + 3, so four slots.
+    static constexpr int SC_SLOTS = SL == 7 ? 2 : 4;
     static_assert(PE_WARPS * 32 == N * 8, "eight producer threads (4 nodes each) per generated row");
     static_assert(2 * BUF_COLS <= 512, "two buffers of accumulators fit the TMEM allocation");
+    static_assert(DRAIN_WARPS == 0 || SUM_COL + 2 * N <= 512, "the running sums fit the spare TMEM columns");
     static_assert(TSTAGE_BYTES % 1024 == 0 && GSTAGE_BYTES % 1024 == 0, "1024-byte aligned stages");
 };
 constexpr int T6_TMEM_COLS = 512;
@@ -159,7 +170,7 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf0 + 8 * b, 1);
-            mbar_init(acce0 + 8 * b, T6_PE_WARPS * 32);
+            mbar_init(acce0 + 8 * b, (CF::DRAIN_WARPS > 0 ? CF::DRAIN_WARPS : T6_PE_WARPS) * 32);
         }
         mbar_init(rawfull, 1);
         mbar_init(rawempty, T6_PE_WARPS * 32);
@@ -190,8 +201,8 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
 
     if (warp == CF::TMA_WARP) {
         // ---- TMA issue (one thread): the table tiles chunk by chunk into their ring, a slot refilled as soon as
-        // the MMAs that read it have completed; the generated operand's inputs window by window into the raw
-        // buffer, refilled as soon as every producer has read the previous window
+        // the MMAs that read it have completed; the generated operand's inputs window by window into the
+        // staged-input buffer, refilled as soon as every producer has read the previous window
         if (lane == 0) {
             const uint32_t tx = (uint32_t)(SL * box * 32 * 64);
             const uint32_t rtx = (uint32_t)((CF::HALF + A.hw) * T6_WIN_BYTES);
@@ -214,15 +225,33 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             int issued = 0, issued_raw = 0;
             if (nwin > 0) issue_raw(issued_raw++);
             for (; issued < T6_TSTAGES && issued < nk; ++issued) issue_table(issued);
-            for (int k = 0; k < nk && ok; ++k) {
-                if (k % T6_WIN == 0 && issued_raw < nwin) {
-                    const int w = k / T6_WIN;   // window w read by every producer: load window w + 1
-                    ok = mbar_wait(rawempty, w & 1, abort_flag, A.err, 17, A.wait_limit);
-                    if (ok) issue_raw(issued_raw++);
+            // then whichever is free first: the staged-input buffer once every producer has read the previous
+            // window, a table slot once the MMAs of its previous chunk have completed (non-blocking tests, so
+            // that neither refill waits behind the other); a run of `wait_limit` idle polls gives up
+            long idle = 0;
+            while (ok && (issued < nk || issued_raw < nwin)) {
+                bool moved = false;
+                if (issued_raw < nwin && mbar_test(rawempty, (issued_raw - 1) & 1)) {
+                    issue_raw(issued_raw++);
+                    moved = true;
                 }
-                if (ok && issued < nk) {
-                    ok = mbar_wait(tempty0 + 8 * (k % T6_TSTAGES), (k / T6_TSTAGES) & 1, abort_flag, A.err, 13, A.wait_limit);
-                    if (ok) issue_table(issued++);
+                if (issued < nk) {
+                    const int kp = issued - T6_TSTAGES;
+                    if (mbar_test(tempty0 + 8 * (kp % T6_TSTAGES), (kp / T6_TSTAGES) & 1)) {
+                        issue_table(issued++);
+                        moved = true;
+                    }
+                }
+                if (moved) {
+                    idle = 0;
+                } else if (*abort_flag) {
+                    ok = false;
+                } else if (++idle >= A.wait_limit) {
+                    *abort_flag = 1;
+                    atomicExch(A.err, 13);
+                    ok = false;
+                } else {
+                    __nanosleep(32);   // leave the issue slots to the producers while nothing is free
                 }
             }
             // every copy issued has landed before the CTA exits: at once on the normal path (the consumers
@@ -256,6 +285,21 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                 // descriptors plus compile-time offsets (16-byte units; no carry out of the address field)
                 const uint64_t da = sw64_desc(a0), db = sw64_desc(b0);
                 const uint32_t fresh = k % T6_WIN == 0 ? 0u : 1u;
+                if constexpr (SL == OZ_FAST_SLICES) {
+                    // four slices: the generated tile's slices B_0..B_3 lie one after the other, so one MMA
+                    // per table slice A_i and K step forms A_i [B_0 .. B_{3-i}] (N = (4 - i) 48) into the
+                    // columns of levels i .. 3: product (i, j) lands on level i + j's accumulator.  Each table
+                    // slice is read once per K step (4 MMAs instead of 10); A_0 [B_0 .. B_3] opens a window.
+#pragma unroll
+                    for (int kk = 0; kk < T6_K / 16; ++kk) {
+#pragma unroll
+                        for (int i = 0; i < SL; ++i) {
+                            tc_mma(dbase + (uint32_t)(i * T6_N), da + (uint64_t)((i * T6_A_TILE + kk * 32) >> 4),
+                                   db + (uint64_t)((kk * 32) >> 4), bf16_idesc_mn(T6_M, (SL - i) * T6_N),
+                                   kk == 0 && i == 0 ? fresh : 1u);
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int L = SL - 1; L >= 0; --L) {
                     const int lv = L < T6_ACC - 1 ? L : T6_ACC - 1;
@@ -270,6 +314,7 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                         }
                     }
                 }
+                }
                 tc_commit(tempty0 + 8 * s);
                 tc_commit(gempty0 + 8 * s2);
                 last_mma = k;
@@ -283,6 +328,87 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                 for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(tempty0 + 8 * s, (last_mma / T6_TSTAGES) & 1); ++it) {
                 }
             }
+        }
+    } else if (CF::DRAIN_WARPS > 0 && warp >= CF::DRAIN0) {
+        // ---- drain warps (four slices): per window, the four level accumulators of this warp's 32 TMEM
+        // lanes (table rows) and 48 columns folded with the window's scales into the double-float running
+        // sums in TMEM columns SUM_COL (high parts) and SUM_COL + N (low parts), 8 columns at a time, two
+        // per packed FP32x2 instruction: L0 + rint(L1) exact into the TwoSum high part, frac(L1) + L2 + L3
+        // rounded once (below 2^8 units, its rounding under 2^-16 units: 2^-30 of one node's largest
+        // product) into the low part.  After the last window the sums go to the output.
+        const int qd = warp & 3, lrow = qd * 32 + lane;
+        const bool live = qd * 32 < 2 * ns;
+        const int nwin = nk / T6_WIN;
+        const uint32_t lb = tmem + ((uint32_t)(qd * 32) << 16);
+        const f32x2 CM = x2_pack(12582912.f, 12582912.f);
+        const size_t plane = (size_t)A.N_T * A.n_half;
+        double* out = A.mol + (size_t)e * 2 * plane * 2;
+        int xo = 0, io = 0;
+        if (lrow < 2 * ns) {
+            xo = lrow < ns ? 0 : 1;
+            io = A.qg_rows[tile * A.qg_max + (lrow < ns ? lrow : lrow - ns)];
+        }
+        bool ok = true;
+        for (int j = 0; j < nwin && ok; ++j) {
+            const int b = j & 1;
+            ok = mbar_wait(accf0 + 8 * b, (j >> 1) & 1, abort_flag, A.err, 14, A.wait_limit);
+            if (!ok) break;
+            tc_fence_after();
+            if (live) {
+                const float* scl = ring + (j % T6_SC_SLOTS) * T6_SC_FLOATS;
+                const float sa = scl[lrow];
+                const f32x2 sa2 = x2_pack(sa, sa);
+#pragma unroll 1
+                for (int g = 0; g < T6_N / 8; ++g) {
+                    float v[T6_ACC][8], hv[8], lv[8];
+#pragma unroll
+                    for (int a = 0; a < T6_ACC; ++a) tmem_ld8(lb + (uint32_t)(b * T6_BUF_COLS + a * T6_N + 8 * g), v[a]);
+                    if (j > 0) {
+                        tmem_ld8(lb + (uint32_t)(CF::SUM_COL + 8 * g), hv);
+                        tmem_ld8(lb + (uint32_t)(CF::SUM_COL + T6_N + 8 * g), lv);
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    if (j == 0) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            hv[u] = 0.f;
+                            lv[u] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        const float2 sn = *reinterpret_cast<const float2*>(scl + T6_M + 8 * g + u);
+                        const f32x2 sc = x2_mul(sa2, x2_pack(sn.x, sn.y));
+                        const f32x2 L0 = x2_pack(v[0][u], v[0][u + 1]), L1 = x2_pack(v[1][u], v[1][u + 1]),
+                                    L2 = x2_pack(v[2][u], v[2][u + 1]), L3 = x2_pack(v[3][u], v[3][u + 1]);
+                        const f32x2 l1h = x2_sub(x2_add(L1, CM), CM);
+                        const f32x2 xa = x2_add(L0, l1h);
+                        const f32x2 xbc = x2_add(x2_add(x2_sub(L1, l1h), L2), L3);
+                        f32x2 r1;
+                        const f32x2 hi2 = two_sum_x2(x2_pack(hv[u], hv[u + 1]), x2_mul(xa, sc), r1);
+                        const f32x2 lo2 = x2_fma(xbc, sc, x2_add(x2_pack(lv[u], lv[u + 1]), r1));
+                        x2_unpack(hi2, hv[u], hv[u + 1]);
+                        x2_unpack(lo2, lv[u], lv[u + 1]);
+                    }
+                    if (j + 1 < nwin) {
+                        tmem_st8(lb + (uint32_t)(CF::SUM_COL + 8 * g), hv);
+                        tmem_st8(lb + (uint32_t)(CF::SUM_COL + T6_N + 8 * g), lv);
+                    } else if (lrow < 2 * ns) {
+                        // results: row lrow of D is A_T row lrow of the tile (overlap K) or, from ns on, its
+                        // A_T V_T row (Q)
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int go = ntile * T6_N + 8 * g + u, co = go >> 1, rio = go & 1;
+                            if (co < A.n_half)
+                                out[((size_t)xo * plane + (size_t)io * A.n_half + co) * 2 + rio] =
+                                    (double)hv[u] + (double)lv[u];
+                        }
+                    }
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+            }
+            tc_fence_before();
+            mbar_arrive(acce0 + 8 * b);
         }
     } else {
         // ---- producers of the generated operand (eight threads per row, four nodes each), and the epilogue
@@ -305,17 +431,12 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
         const int qd = warp & 3, col0 = (warp >> 2) * T6_COLS_PER_WARP;
         const int lrow = qd * 32 + lane;
         const bool live = qd * 32 < 2 * ns;    // warps whose rows all lie past the tile skip the arithmetic
+        // seven slices: this thread's running sums (four slices: held in TMEM by the drain warps)
         float hi[X2 ? 1 : T6_COLS_PER_WARP], lo[X2 ? 1 : T6_COLS_PER_WARP];
-        f32x2 hi2[X2 ? T6_COLS_PER_WARP / 2 : 1], lo2[X2 ? T6_COLS_PER_WARP / 2 : 1];
 #pragma unroll
         for (int k = 0; k < (X2 ? 1 : T6_COLS_PER_WARP); ++k) {
             hi[k] = 0.f;
             lo[k] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < (X2 ? T6_COLS_PER_WARP / 2 : 1); ++k) {
-            hi2[k] = x2_pack(0.f, 0.f);
-            lo2[k] = x2_pack(0.f, 0.f);
         }
         bool ok = true;
         // drain of window j: its accumulators with the window's scales
@@ -324,42 +445,6 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             ok = ok && mbar_wait(accf0 + 8 * b, (j >> 1) & 1, abort_flag, A.err, 14, A.wait_limit);
             if (!ok) return;
             tc_fence_after();
-            if constexpr (X2) {
-                if (live) {
-                    const float* scl = ring + (j % T6_SC_SLOTS) * T6_SC_FLOATS;
-                    const float sa = scl[lrow];
-                    const f32x2 sa2 = x2_pack(sa, sa), CM = x2_pack(12582912.f, 12582912.f);
-                    const uint32_t base =
-                        tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * T6_BUF_COLS + col0);
-#pragma unroll
-                    for (int q = 0; q < T6_COLS_PER_WARP / 8; ++q) {
-                        float v[T6_ACC][8];
-#pragma unroll
-                        for (int lv = 0; lv < T6_ACC; ++lv) tmem_ld8(base + lv * T6_N + 8 * q, v[lv]);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-                        for (int u = 0; u < 8; u += 2) {
-                            const int k = (8 * q + u) / 2;
-                            const float2 sn = *reinterpret_cast<const float2*>(scl + T6_M + col0 + 8 * q + u);
-                            const f32x2 sc = x2_mul(sa2, x2_pack(sn.x, sn.y));
-                            const f32x2 L0 = x2_pack(v[0][u], v[0][u + 1]), L1 = x2_pack(v[1][u], v[1][u + 1]),
-                                        L2 = x2_pack(v[2][u], v[2][u + 1]), L3 = x2_pack(v[3][u], v[3][u + 1]);
-                            // L0 + rint(L1) exact (into the TwoSum high part), frac(L1) + L2 exact, + L3
-                            // rounded once (below 2^8, its rounding under 2^-16 units: 2^-30 of one node's
-                            // largest product), into the low part
-                            const f32x2 l1h = x2_sub(x2_add(L1, CM), CM);
-                            const f32x2 xa = x2_add(L0, l1h);
-                            const f32x2 xbc = x2_add(x2_add(x2_sub(L1, l1h), L2), L3);
-                            f32x2 r1;
-                            hi2[k] = two_sum_x2(hi2[k], x2_mul(xa, sc), r1);
-                            lo2[k] = x2_fma(xbc, sc, x2_add(lo2[k], r1));
-                        }
-                    }
-                }
-                tc_fence_before();
-                mbar_arrive(acce0 + 8 * b);
-                return;
-            }
             if (live) {
                 const float* scl = ring + (j % T6_SC_SLOTS) * T6_SC_FLOATS;
                 const float sa = scl[lrow];
@@ -454,7 +539,6 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                 }
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_arrive(gfull0 + 8 * s);
-                if (cc == CF::DRAIN_AT && w >= 1) drain(w - 1);
             }
         }
         } else {
@@ -510,6 +594,7 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             }
         }
         }
+        if constexpr (!X2) {
         if (ok) drain(nwin - 1);
         // results: row m of D is A_T row m of the tile (overlap K) or, from ns on, its A_T V_T row (Q)
         if (ok && live && lrow < 2 * ns) {
@@ -521,17 +606,9 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             for (int k = 0; k < T6_COLS_PER_WARP; ++k) {
                 const int go = ntile * T6_N + col0 + k, co = go >> 1, rio = go & 1;
                 if (co >= A.n_half) continue;
-                double val;
-                if constexpr (X2) {
-                    float h0, h1, l0, l1;
-                    x2_unpack(hi2[k / 2], h0, h1);
-                    x2_unpack(lo2[k / 2], l0, l1);
-                    val = (k & 1) ? (double)h1 + (double)l1 : (double)h0 + (double)l0;
-                } else {
-                    val = (double)hi[k] + (double)lo[k];
-                }
-                out[((size_t)x * plane + (size_t)i * A.n_half + co) * 2 + rio] = val;
+                out[((size_t)x * plane + (size_t)i * A.n_half + co) * 2 + rio] = (double)hi[k] + (double)lo[k];
             }
+        }
         }
     }
     __syncthreads();
