@@ -323,7 +323,7 @@ static void free_basis(wpccc_basis_s* B) {
     free_centre(B->T);
     free_centre(B->P);
     void* tptrs[] = {B->tanT.df, B->tanT.dF, B->tanP.df, B->tanP.dF, B->deps, B->tc_row, B->qg_off, B->qg_rows,
-                     B->tc_err, B->tc_halfq, B->su_tiles, B->fT2, B->fP2};
+                     B->tc_err, B->tc_halfq, B->su_tiles, B->fT2, B->fP2, B->rot_plan};
     for (void* p : tptrs)
         if (p) cudaFree(p);
     void* ptrs[] = {B->r, B->w, B->inv_den, B->s, B->ws, B->tau, B->wtau, B->half_state, B->half_of, B->qtile_q,
@@ -436,6 +436,7 @@ extern "C" wpccc_status wpccc_basis_create(const wpccc_basis_desc* d, int device
             return bail(st);
         if ((st = upload(&B->half_of, half_of.data(), half_of.size(), "upload half_of")) != WPCCC_OK)
             return bail(st);
+        if ((st = rotation_plan(B)) != WPCCC_OK) return bail(st);
     } else {
         B->P.Z = d->P.Z;
     }

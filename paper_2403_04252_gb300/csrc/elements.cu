@@ -871,13 +871,64 @@ struct RotArgs {
     const double2* mol;
     double2 *S, *H;
     size_t mat;   // N*N
+    const int* items;         // [n_items][4]: first pair, pairs, l_T, l_P
+    const int* pairs;         // [pairs][2]: target radial, projectile radial
+    int n_items;
 };
 
 constexpr int ROT_WARPS_MAX = 8;
+constexpr int ROT_LANE_CAP = 256;   // block entries one item may hold (more when a single pair has more)
 
-// One warp per (target radial a, projectile radial b): the (2l_a+1) x (2l_b+1) molecular-frame block
-// of each integral (q < 0 columns from the reflection) is rotated in two passes through shared
-// memory, T[q'][m_b] = sum_q d^{l_b}_{m_b q} X[q'][q], then K[m_a][m_b] = sum_q' d^{l_a}_{m_a q'} T[q'][m_b].
+// Work items of k_rotate: the radial pairs (a, b) grouped by (l_a, l_b), and per group the number P of
+// pairs one warp takes so that its P NX (2 l_a + 1)(2 l_b + 1) block entries fill the lanes best (the
+// passes run over all entries of the item, lane by lane).
+wpccc_status rotation_plan(wpccc_basis_s* B) {
+    std::vector<int> items, pairs;
+    int cap = 0;
+    for (int la = 0; la <= B->T.lmax; ++la)
+        for (int lb = 0; lb <= B->P.lmax; ++lb) {
+            std::vector<int> cls;
+            for (int ra = 0; ra < B->T.n_rad; ++ra)
+                if (B->T.h_rad_l[ra] == la)
+                    for (int rb = 0; rb < B->P.n_rad; ++rb)
+                        if (B->P.h_rad_l[rb] == lb) {
+                            cls.push_back(ra);
+                            cls.push_back(rb);
+                        }
+            const int np = (int)cls.size() / 2;
+            if (np == 0) continue;
+            const int E = NX * (2 * la + 1) * (2 * lb + 1);
+            int best = 1;
+            double bu = (double)E / (32.0 * ((E + 31) / 32));
+            for (int P = 2; P <= np && P * E <= std::max(ROT_LANE_CAP, E); ++P) {
+                const double u = (double)(P * E) / (32.0 * ((P * E + 31) / 32));
+                if (u > bu + 1e-12) {
+                    bu = u;
+                    best = P;
+                }
+            }
+            const int first = (int)pairs.size() / 2;
+            pairs.insert(pairs.end(), cls.begin(), cls.end());
+            for (int k = 0; k < np; k += best) {
+                const int cnt = std::min(best, np - k);
+                items.insert(items.end(), {first + k, cnt, la, lb});
+                cap = std::max(cap, cnt * E);
+            }
+        }
+    std::vector<int> plan(items);
+    plan.insert(plan.end(), pairs.begin(), pairs.end());
+    WPCCC_CUDA(cudaMalloc((void**)&B->rot_plan, plan.size() * sizeof(int)));
+    WPCCC_CUDA(cudaMemcpy(B->rot_plan, plan.data(), plan.size() * sizeof(int), cudaMemcpyHostToDevice));
+    B->n_rot_items = (int)items.size() / 4;
+    B->rot_cap = cap;
+    return WPCCC_OK;
+}
+
+// One warp per work item: P radial pairs (a, b) of one (l_a, l_b).  For each pair the (2l_a+1) x (2l_b+1)
+// molecular-frame block of each integral (q < 0 columns from the reflection) is rotated in two passes
+// through shared memory, T[q'][m_b] = sum_q d^{l_b}_{m_b q} X[q'][q], then K[m_a][m_b] =
+// sum_q' d^{l_a}_{m_a q'} T[q'][m_b] with the energy phases; every pass runs over the item's P NX blk
+// entries, lane by lane.
 __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const EvalDesc* __restrict__ ev) {
     extern __shared__ double sd[];     // Wigner d^l_{m q}(theta) for l <= lmax, then per-warp blocks
     const int e = blockIdx.y;
@@ -886,11 +937,12 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) sd[idx] = etd[idx];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pair = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (pair >= A.n_radT * A.n_radP) return;
-    const int ra = pair / A.n_radP, rb = pair % A.n_radP;
-    const int la = A.radT_l[ra], lb = A.radP_l[rb];
-    const int na = 2 * la + 1, nbq = 2 * lb + 1, blk = na * nbq;
+    const int item = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (item >= A.n_items) return;
+    const int p0 = A.items[4 * item], P = A.items[4 * item + 1], la = A.items[4 * item + 2],
+              lb = A.items[4 * item + 3];
+    const int* pr = A.pairs + 2 * p0;
+    const int na = 2 * la + 1, nbq = 2 * lb + 1, blk = na * nbq, E = NX * blk, PE = P * E;
     const int tot_pad = (total + 1) & ~1;
     double2* X = reinterpret_cast<double2*>(sd + tot_pad) + (size_t)warp * 2 * A.rot_block;
     double2* T = X + A.rot_block;
@@ -901,9 +953,10 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
     const double* db = sd + offb;
     const size_t plane = (size_t)A.N_T * A.n_half;
     const double2* mol = A.mol + (size_t)e * NX * plane;
-    // molecular block, X[x][q'][q] at x * blk + (q' + la) * nbq + (q + lb)
-    for (int t = lane; t < NX * blk; t += 32) {
-        const int x = t / blk, r = t % blk, qp = r / nbq - la, q = r % nbq - lb;
+    // molecular blocks, entry p E + x blk + (q' + la) nbq + (q + lb)
+    for (int t = lane; t < PE; t += 32) {
+        const int p = t / E, r0 = t - p * E, x = r0 / blk, r = r0 - x * blk, qp = r / nbq - la, q = r % nbq - lb;
+        const int ra = pr[2 * p], rb = pr[2 * p + 1];
         int row, col;
         bool neg = false;
         if (q >= 0) {
@@ -919,10 +972,10 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
         X[t] = val;
     }
     __syncwarp();
-    // T[x][q'][m_b] = sum_q d^{lb}_{m_b q} X[x][q'][q]
-    for (int t = lane; t < NX * blk; t += 32) {
-        const int x = t / blk, r = t % blk, qi = r / nbq, mb = r % nbq;
-        const double2* xr = X + x * blk + qi * nbq;
+    // T[p][x][q'][m_b] = sum_q d^{lb}_{m_b q} X[p][x][q'][q]
+    for (int t = lane; t < PE; t += 32) {
+        const int r = t % blk, qi = r / nbq, mb = r % nbq;
+        const double2* xr = X + (t - r) + qi * nbq;
         const double* dr = db + mb * nbq;
         double re = 0.0, im = 0.0;
         for (int q = 0; q < nbq; ++q) {
@@ -932,46 +985,47 @@ __global__ void __launch_bounds__(32 * ROT_WARPS_MAX) k_rotate(RotArgs A, const 
         T[t] = make_double2(re, im);
     }
     __syncwarp();
-    // K[x][m_a][m_b] = sum_q' d^{la}_{m_a q'} T[x][q'][m_b] with the energy phases, into X (free again)
+    // K, Q [p][x][m_a][m_b] = sum_q' d^{la}_{m_a q'} T[p][x][q'][m_b] with the energy phases, into X
     const double2* phs = reinterpret_cast<const double2*>(etd + A.ph_off);
-    for (int t = lane; t < blk; t += 32) {
-        const int mi = t / nbq, mb = t % nbq;
+    for (int t = lane; t < PE; t += 32) {
+        const int p = t / E, r = t % blk, mi = r / nbq, mb = r % nbq;
         const double* dr = da + mi * na;
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        const double2* tc = T + (t - r) + mb;
+        double re = 0.0, im = 0.0;
         for (int qi = 0; qi < na; ++qi) {
             const double w = dr[qi];
-            const double2 t0 = T[qi * nbq + mb], t1 = T[blk + qi * nbq + mb];
-            acc[0] = fma(w, t0.x, acc[0]);
-            acc[1] = fma(w, t0.y, acc[1]);
-            acc[2] = fma(w, t1.x, acc[2]);
-            acc[3] = fma(w, t1.y, acc[3]);
+            const double2 tv = tc[qi * nbq];
+            re = fma(w, tv.x, re);
+            im = fma(w, tv.y, im);
         }
+        const int ra = pr[2 * p], rb = pr[2 * p + 1];
         const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
         const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
         const double2 ph = cmul(phs[i], cconj(phs[A.N_T + j]));
-        X[t] = cmul(make_double2(acc[0], acc[1]), ph);          // K
-        X[blk + t] = cmul(make_double2(acc[2], acc[3]), ph);    // Q
+        X[t] = cmul(make_double2(re, im), ph);
     }
     __syncwarp();
     // S and H entries: the upper blocks with the target index fastest (consecutive rows of a column), the
     // lower blocks with the projectile index fastest, so that both writes run along memory
     double2* S = A.S + (size_t)e * A.mat;
     double2* H = A.H + (size_t)e * A.mat;
-    for (int t = lane; t < blk; t += 32) {
-        const int mi = t % na, mb = t / na;
+    for (int t = lane; t < P * blk; t += 32) {
+        const int p = t / blk, r = t - p * blk, mi = r % na, mb = r / na;
+        const int ra = pr[2 * p], rb = pr[2 * p + 1];
         const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
         const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
         const size_t up = (size_t)i + (size_t)(A.N_T + j) * A.N;     // row i, column N_T + j
-        S[up] = X[mi * nbq + mb];
-        H[up] = X[blk + mi * nbq + mb];
+        S[up] = X[p * E + mi * nbq + mb];
+        H[up] = X[p * E + blk + mi * nbq + mb];
     }
-    for (int t = lane; t < blk; t += 32) {
-        const int mi = t / nbq, mb = t % nbq;
+    for (int t = lane; t < P * blk; t += 32) {
+        const int p = t / blk, r = t - p * blk, mi = r / nbq, mb = r % nbq;
+        const int ra = pr[2 * p], rb = pr[2 * p + 1];
         const int i = A.stT_index[ra * (2 * WPCCC_LMAX + 1) + (mi - la) + WPCCC_LMAX];
         const int j = A.stP_index[rb * (2 * WPCCC_LMAX + 1) + (mb - lb) + WPCCC_LMAX];
         const size_t lo = (size_t)(A.N_T + j) + (size_t)i * A.N;     // row N_T + j, column i
-        S[lo] = cconj(X[t]);
-        H[lo] = cconj(X[blk + t]);     // Eq. 1: the lower-left block of H is Q^+
+        S[lo] = cconj(X[p * E + r]);
+        H[lo] = cconj(X[p * E + blk + r]);     // Eq. 1: the lower-left block of H is Q^+
     }
 }
 
@@ -1430,7 +1484,10 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         ra.mat = (size_t)B->N * B->N;
         int dtot = 0;
         for (int l = 0; l <= ra.lmax; ++l) dtot += (2 * l + 1) * (2 * l + 1);
-        ra.rot_block = NX * (2 * B->T.lmax + 1) * (2 * B->P.lmax + 1);
+        ra.rot_block = B->rot_cap;
+        ra.items = B->rot_plan;
+        ra.pairs = B->rot_plan + 4 * B->n_rot_items;
+        ra.n_items = B->n_rot_items;
         ra.dtot = L.dtot;
         ra.et = et;
         ra.et_doubles = L.et_doubles;
@@ -1440,8 +1497,7 @@ wpccc_status launch_elements(wpccc_basis_s* B, const EvalDesc* evals, int nev, d
         int rwarps = (int)std::min<size_t>(ROT_WARPS_MAX, ((size_t)200 * 1024 - dbytes) / per_warp);
         if (rwarps < 1) rwarps = 1;
         const size_t rsm = dbytes + (size_t)rwarps * per_warp;
-        const int npairs = B->T.n_rad * B->P.n_rad;
-        const dim3 rgrid((unsigned)((npairs + rwarps - 1) / rwarps), nev);
+        const dim3 rgrid((unsigned)((B->n_rot_items + rwarps - 1) / rwarps), nev);
         e0 = B->prof.begin(PROF_ROT_DIRECT, st);
         WPCCC_CUDA(cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
         k_rotate<<<rgrid, 32 * rwarps, rsm, st>>>(ra, evals);

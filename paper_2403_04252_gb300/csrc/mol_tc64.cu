@@ -423,8 +423,12 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             d = d < 0 ? -d : d;
             lw = 2 * (d - s_dlo) + ri;
         }
-        const unsigned char* ap_s = raw + (n >> 1) * T6_WIN_BYTES + part * 32;
-        const unsigned char* wd_s = raw + (CF::HALF + lw) * T6_WIN_BYTES + part * 32;
+        // seven slices: this thread's nodes 4 part .. 4 part + 3 of each chunk (32 bytes of each row); four
+        // slices: nodes 2 part, 2 part + 1 and 16 + 2 part, 17 + 2 part (16 bytes at part 16 and 128 + part 16),
+        // so that the eight threads of a row read 128 contiguous bytes per load, free of bank conflicts
+        const int pofs = X2 ? part * 16 : part * 32;
+        const unsigned char* ap_s = raw + (n >> 1) * T6_WIN_BYTES + pofs;
+        const unsigned char* wd_s = raw + (CF::HALF + lw) * T6_WIN_BYTES + pofs;
         const float* nbf = reinterpret_cast<const float*>(nb);
         const float* scT = nbf + A.sc_off_f;   // [chunk][tc_rows]
         // epilogue: accumulator lanes 32 qd .. 32 qd + 31 (table rows), 16 columns from col0
@@ -496,8 +500,8 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
             for (int cc = 0; cc < T6_WIN; ++cc) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float4 wq = *reinterpret_cast<const float4*>(wd_s + cc * T6_K * 8 + h * 16);
-                    const float4 aq = *reinterpret_cast<const float4*>(ap_s + cc * T6_K * 8 + h * 16);
+                    const float4 wq = *reinterpret_cast<const float4*>(wd_s + cc * T6_K * 8 + h * 128);
+                    const float4 aq = *reinterpret_cast<const float4*>(ap_s + cc * T6_K * 8 + h * 128);
                     const int j = 2 * cc + h;
                     df_mul_pe_x2(x2_pack(wq.x, wq.z), x2_pack(wq.y, wq.w), x2_pack(aq.x, aq.z), x2_pack(aq.y, aq.w),
                                  pw[j], ew[j]);
@@ -529,13 +533,19 @@ __global__ void __launch_bounds__(Tc64Cfg<SL>::THREADS, 1) k_mol_tc64(const __gr
                 f32x2 t0[4], t1[4];
                 oz_slices4_pe_x2(pw[2 * cc], ew[2 * cc], s2, t0);
                 oz_slices4_pe_x2(pw[2 * cc + 1], ew[2 * cc + 1], s2, t1);
-                const int off = n * 64 + (((part >> 1) ^ ((n >> 1) & 3)) << 4) + (part & 1) * 8;
+                // row n of each slice tile: 64 bytes, 16-byte chunk qq at (qq ^ ((n >> 1) & 3)); nodes 2 part, 2 part
+                // + 1 are bytes 4 part .. 4 part + 3 (chunk part >> 2), nodes 16 + 2 part, 17 + 2 part two
+                // chunks further
+                const int sw = (n >> 1) & 3, within = (part & 3) * 4;
+                const int off0 = n * 64 + (((part >> 2) ^ sw) << 4) + within;
+                const int off1 = n * 64 + (((2 + (part >> 2)) ^ sw) << 4) + within;
 #pragma unroll
                 for (int sp = 0; sp < 4; ++sp) {
                     float a0, a1, b0, b1;
                     x2_unpack(t0[sp], a0, a1);
                     x2_unpack(t1[sp], b0, b1);
-                    *reinterpret_cast<uint2*>(bt + sp * T6_B_TILE + off) = make_uint2(bf16x2_exact(a0, a1), bf16x2_exact(b0, b1));
+                    *reinterpret_cast<uint32_t*>(bt + sp * T6_B_TILE + off0) = bf16x2_exact(a0, a1);
+                    *reinterpret_cast<uint32_t*>(bt + sp * T6_B_TILE + off1) = bf16x2_exact(b0, b1);
                 }
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_arrive(gfull0 + 8 * s);

@@ -106,6 +106,10 @@ struct wpccc_basis_s {
     int n_half = 0;
     int* half_state = nullptr;  // [n_half] projectile state
     int* half_of = nullptr;     // [n_rad_P][WPCCC_LMAX+1]: half column of (radial, q>=0) or -1
+    // work items of the Eq. 8 rotation (k_rotate): radial pairs grouped by (l_T, l_P), several pairs per warp
+    int* rot_plan = nullptr;    // [n_rot_items][4] (first pair, pairs, l_T, l_P), then [pairs][2] (a, b)
+    int n_rot_items = 0;
+    int rot_cap = 0;            // largest block of one item: pairs x 2 (2 l_T + 1)(2 l_P + 1) entries
     // column tiles of the FP32 contraction: up to 16 half columns sharing one q
     int n_qtiles = 0;
     int* qtile_q = nullptr;     // [n_qtiles]
@@ -203,6 +207,7 @@ enum ProfCat { PROF_NODES = 0, PROF_MOL = 1, PROF_ROT_DIRECT = 2, PROF_SOLVE = 3
 // Tensor-core form of the Eq. 9 contraction (precision mode 3): from the node tables of the tensor-core
 // layout into the molecular-frame blocks, for `nev` evaluations.
 wpccc_status tc_prepare(wpccc_basis_s* B);
+wpccc_status rotation_plan(wpccc_basis_s* B);
 // The tensor-core contraction over the slice planes: slices = 7 to FP64 accuracy (precision modes 4, 5),
 // 3 at FP32 level (precision mode 3).
 wpccc_status launch_mol_tc64(wpccc_basis_s* B, int nev, const void* node, double2* mol, int* err, cudaStream_t st,
