@@ -769,9 +769,9 @@ def _rk4_flops_per_step(mode: int, solve_mode: str, N: int, NT: int, NP_: int) -
 # dram__bytes_write.sum over a capture of whole launches, divided by the positions): only kernels whose code
 # is unchanged since the capture are listed (the others report traffic null)
 MEASURED_TRAFFIC_PER_POSITION = {
-    # ncu over 33 positions of the p + H workload, precision mode 3: (313.9 + 21.6) MB and (3.8 + 263.4) MB
-    ("p_H_2c_n4l3", "k_mol_tc64<4>"): 10.17e6,
-    ("p_H_2c_n4l3", "k_node_tables<float>"): 8.10e6,
+    # ncu over 33 positions of the p + H workload, precision mode 3: (314.0 + 17.5) MB and (3.7 + 263.2) MB
+    ("p_H_2c_n4l3", "k_mol_tc64<4>"): 10.05e6,
+    ("p_H_2c_n4l3", "k_node_tables<float>"): 8.09e6,
 }
 
 
