@@ -32,6 +32,9 @@ struct RkArgs {
     int N_T;                // target states (two-centre: S = [[I, K], [K^+, I]])
     int iters;              // refinement iterations (mixed-precision form)
     int df_rhs;             // reduced-precision forms: H y in double-float arithmetic (matvec_df)
+    int stage_cols;         // > 0: H streamed through shared memory, this many columns per slot (matvec_df_staged)
+    long long stage_off;    // byte offset of the staging slots in the dynamic shared memory
+    long polls;             // bound of a staging wait
     double tol;             // convergence tolerance of the refinement's last sweep (<= 0: unchecked)
     const float2* LU32;     // chunk: FP32 factors per evaluation (mixed forms: LU, or K and the Schur factor)
     float2* carryLU32;      // per path (mixed form)
@@ -104,6 +107,16 @@ __global__ void __launch_bounds__(RK_THREADS, 1) k_rk4(RkArgs A) {
         m.piv = MODE != RK_MATRIX ? A.piv + (size_t)e * N : nullptr;
         return m;
     };
+    // the staging slots of H for the reduced-precision forms' right-hand side (after the mode's vectors)
+    Staging sg{};
+    const Staging* sgp = nullptr;
+    if (MIX && A.stage_cols > 0) {
+        sg.buf = reinterpret_cast<double2*>(reinterpret_cast<char*>(rk_smem) + A.stage_off);
+        sg.bars = reinterpret_cast<uint64_t*>(sg.buf + (size_t)2 * A.stage_cols * N);
+        sg.cols = A.stage_cols;
+        sg.polls = A.polls;
+        sgp = &sg;
+    }
     auto apply = [&](const PosMats& m, const double2* in, double2* out) {
         if (MODE == RK_MATRIX) {
             matvec(m.H, N, in, out);
@@ -115,10 +128,10 @@ __global__ void __launch_bounds__(RK_THREADS, 1) k_rk4(RkArgs A) {
             apply_LU(m.S, m.piv, m.H, N, v, in, out, t, static_cast<double2*>(blk));
         } else if (MODE == RK_MIXED_SCHUR) {
             apply_schur_mixed(m.S, m.L32, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds, us32,
-                              static_cast<float2*>(blk), A.tol, A.flags, A.df_rhs != 0);
+                              static_cast<float2*>(blk), A.tol, A.flags, A.df_rhs != 0, sgp);
         } else {
             apply_LU_mixed(m.S, m.L32, m.piv, m.H, N, A.N_T, v, A.iters, in, out, t, xs, rs, ds,
-                           static_cast<float2*>(blk), A.tol, A.flags, A.df_rhs != 0);
+                           static_cast<float2*>(blk), A.tol, A.flags, A.df_rhs != 0, sgp);
         }
     };
     PosMats Mz;
@@ -534,13 +547,27 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     const int N = P.N;
     cudaStream_t st = S.st, rs = S.rs;
     WPCCC_CUDA(cudaMemsetAsync(P.d_flags, 0, sizeof(int), st));
-    const int rk_smem = P.wide ? 0 : (int)rk_smem_bytes(P.mode, N);
+    int rk_smem = P.wide ? 0 : (int)rk_smem_bytes(P.mode, N);
+    // reduced-precision forms with N <= RK_THREADS: H streamed through two shared-memory slots of up to eight
+    // columns each, in what the mode's vectors leave of the 227 KB
+    int stage_cols = 0;
+    size_t stage_off = 0;
+    const size_t rk_cap = (size_t)227 * 1024 - 1024;
+    if (!P.wide && P.df_rhs && N <= RK_THREADS) {
+        stage_off = ((size_t)rk_smem + 127) / 128 * 128;
+        if (rk_cap > stage_off + 16)
+            stage_cols = (int)std::min<size_t>(8, (rk_cap - stage_off - 16) / (2 * (size_t)N * sizeof(double2)));
+        if (stage_cols >= 1) rk_smem = (int)(stage_off + 2 * (size_t)stage_cols * N * sizeof(double2) + 16);
+        else stage_cols = 0;
+    }
     if (!P.wide) {
-        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MATRIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
-        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
-        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
-        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
-        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, rk_smem));
+        // the largest any plan takes (a batch graph holds launches of several plans)
+        const int mx = (int)rk_cap;
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MATRIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        WPCCC_CUDA(cudaFuncSetAttribute(k_rk4<RK_MIXED_SCHUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     }
     const size_t hS = P.sz_S / 2 / sizeof(double2), hH = P.sz_H / 2 / sizeof(double2);
     const size_t hL = P.sz_LU32 / 2 / sizeof(float2), hP = P.sz_piv / 2 / sizeof(int), hI = P.sz_info / 2 / sizeof(int);
@@ -549,6 +576,9 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
     ra.N_T = B->N_T;
     ra.iters = B->refine_iters;
     ra.df_rhs = P.df_rhs ? 1 : 0;
+    ra.stage_cols = stage_cols;
+    ra.stage_off = (long long)stage_off;
+    ra.polls = B->wait_polls;
     ra.tol = B->refine_tol;
     ra.carryH = P.d_carry;
     ra.carryLU = P.d_carryLU;
@@ -627,6 +657,8 @@ static wpccc_status plan_enqueue(PropPlan& P, double2* c, const PlanStreams& S) 
 static wpccc_status flags_status(int flags) {
     if (flags & FLAG_SINGULAR) return fail(WPCCC_ESINGULAR, "an overlap matrix had a zero pivot");
     if (flags & FLAG_NONFINITE) return fail(WPCCC_ENONFINITE, "amplitudes became non-finite");
+    if (flags & FLAG_TIMEOUT)
+        return fail(WPCCC_ETIMEOUT, "a wait of the RK4 sweep's matrix staging timed out");
     if (flags & FLAG_NOCONV)
         return fail(WPCCC_ENOCONV, "the FP64 refinement of a reduced-precision solve did not converge (last "
                                    "correction above the tolerance relative to the solution)");

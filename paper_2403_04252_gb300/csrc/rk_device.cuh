@@ -4,6 +4,7 @@
 #pragma once
 
 #include "ozaki.cuh"
+#include "tc_ptx.cuh"
 #include "wpccc_internal.cuh"
 
 namespace wpccc {
@@ -11,7 +12,7 @@ namespace wpccc {
 constexpr int RK_THREADS = 512;
 
 // Status bits the RK4 kernels raise in the propagation's flag word.
-enum : int { FLAG_SINGULAR = 1, FLAG_NONFINITE = 2, FLAG_NOCONV = 4 };
+enum : int { FLAG_SINGULAR = 1, FLAG_NONFINITE = 2, FLAG_NOCONV = 4, FLAG_TIMEOUT = 8 };
 
 // Convergence test of a refinement's last sweep: max|dx| <= tol max|x| over the block's vector, else
 // FLAG_NOCONV (dmax, xmax: this thread's maxima).  Called by all threads; ends with a block barrier.
@@ -218,6 +219,88 @@ __device__ inline void matvec_df(const double2* __restrict__ M, int N, const dou
     __syncthreads();
 }
 
+// Shared-memory staging of a column-major matrix for matvec_df_staged: `cols` columns per slot, two slots,
+// then their two mbarriers; `polls` bounds every wait.
+struct Staging {
+    double2* buf;        // [2][cols][N]
+    uint64_t* bars;      // [2]
+    int cols;
+    long polls;
+};
+
+// matvec_df with M streamed through shared memory: blocks of `cols` consecutive columns (contiguous in the
+// column-major storage) are brought in by bulk asynchronous copies, one block ahead, issued by thread 0; every
+// thread reads its row of the block from shared memory.  The sums, and so the result, are those of
+// matvec_df (the same terms in the same order).  Needs N <= RK_THREADS.  A wait that gives up raises
+// FLAG_TIMEOUT and the sweep goes on (with what the slot holds); the copies in flight land before return.
+__device__ inline void matvec_df_staged(const double2* __restrict__ M, int N, const double2* y, double2* out,
+                                        float4* ys, const Staging& sg, int* flags) {
+    const int tid = threadIdx.x;
+    for (int j = tid; j < N; j += RK_THREADS) {
+        const float2 a = split_bits(y[j].x), b = split_bits(y[j].y);
+        ys[j] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    const uint32_t bar0 = smem_u32(sg.bars);
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    const int nblk = (N + sg.cols - 1) / sg.cols;
+    auto issue = [&](int blk) {
+        const int c0 = blk * sg.cols, nc = min(sg.cols, N - c0);
+        const uint32_t bytes = (uint32_t)nc * (uint32_t)N * (uint32_t)sizeof(double2);
+        const uint32_t bar = bar0 + 8 * (blk & 1);
+        // the slot's previous contents were read through the generic proxy: order those reads first
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive_tx(bar, bytes);
+        asm volatile(
+            "{\n.reg .u64 g;\ncvta.to.global.u64 g, %1;\n"
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [g], %2, [%3];\n}\n" ::"r"(
+                smem_u32(sg.buf + (size_t)(blk & 1) * sg.cols * N)),
+            "l"(M + (size_t)c0 * N), "r"(bytes), "r"(bar)
+            : "memory");
+    };
+    if (tid == 0) {
+        issue(0);
+        if (nblk > 1) issue(1);
+    }
+    f32x2 s = x2_pack(0.f, 0.f), c = x2_pack(0.f, 0.f);   // (re, im) of row tid
+    for (int blk = 0; blk < nblk; ++blk) {
+        const uint32_t bar = bar0 + 8 * (blk & 1), par = (blk >> 1) & 1;
+        long it = 0;
+        while (!mbar_try(bar, par) && ++it < sg.polls) {
+        }
+        if (it >= sg.polls && flags) atomicOr(flags, FLAG_TIMEOUT);
+        const int c0 = blk * sg.cols, nc = min(sg.cols, N - c0);
+        if (tid < N) {
+            const double2* col = sg.buf + (size_t)(blk & 1) * sg.cols * N + tid;
+            for (int cc = 0; cc < nc; ++cc) {
+                const double2 m = col[(size_t)cc * N];
+                const float2 mr = split_bits(m.x), mi = split_bits(m.y);
+                const float4 q = ys[c0 + cc];
+                dot2_acc_x2(s, c, x2_pack(mr.x, mr.x), x2_pack(mr.y, mr.y), x2_pack(q.x, q.z), x2_pack(q.y, q.w));
+                dot2_acc_x2(s, c, x2_pack(-mi.x, mi.x), x2_pack(-mi.y, mi.y), x2_pack(q.z, q.x), x2_pack(q.w, q.y));
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && blk + 2 < nblk) issue(blk + 2);
+    }
+    if (tid < N) {
+        float sr, si, cr, ci;
+        x2_unpack(s, sr, si);
+        x2_unpack(c, cr, ci);
+        out[tid] = make_double2((double)sr + (double)cr, (double)si + (double)ci);
+    }
+    // after a give-up the last copies may still be in flight: let them land (bounded) before the slots are reused
+    if (tid == 0)
+        for (int blk = nblk > 2 ? nblk - 2 : 0; blk < nblk; ++blk)
+            for (long it = 0; it < TC_WAIT_LIMIT && !mbar_try(bar0 + 8 * (blk & 1), (blk >> 1) & 1); ++it) {
+            }
+    __syncthreads();
+}
+
 // out = b - S y for S = [[I, K], [K^+, I]] (two-centre overlap, FP64, column-major): only the
 // off-diagonal blocks are read, rows i < N_T against columns j >= N_T and the other way round.
 __device__ inline void residual_S(const double2* __restrict__ S, int N, int N_T, const double2* y, const double2* b,
@@ -257,8 +340,10 @@ static __device__ void apply_LU(const double2* __restrict__ LU, const int* __res
 static __device__ void apply_LU_mixed(const double2* __restrict__ S64, const float2* __restrict__ LU32,
                                const int* __restrict__ piv, const double2* __restrict__ Hm, int N, int N_T, double v,
                                int iters, const double2* y, double2* k, double2* b, double2* x, double2* r,
-                               float2* d, float2* blk, double tol = 0.0, int* flags = nullptr, bool df_rhs = false) {
-    if (df_rhs) matvec_df(Hm, N, y, b, reinterpret_cast<float4*>(r));
+                               float2* d, float2* blk, double tol = 0.0, int* flags = nullptr, bool df_rhs = false,
+                               const Staging* sg = nullptr) {
+    if (df_rhs && sg) matvec_df_staged(Hm, N, y, b, reinterpret_cast<float4*>(r), *sg, flags);
+    else if (df_rhs) matvec_df(Hm, N, y, b, reinterpret_cast<float4*>(r));
     else matvec(Hm, N, y, b);
     for (int it = 0; it < iters; ++it) {
         const double2* rr = b;
@@ -458,8 +543,9 @@ static __device__ void apply_schur_mixed(const double2* __restrict__ S64, const 
                                          const double2* __restrict__ Hm, int N, int N_T, double v, int iters,
                                          const double2* y, double2* k, double2* b, double2* x, double2* r, float2* d,
                                          float2* u, float2* blk, double tol = 0.0, int* flags = nullptr,
-                                         bool df_rhs = false) {
-    if (df_rhs) matvec_df(Hm, N, y, b, reinterpret_cast<float4*>(r));
+                                         bool df_rhs = false, const Staging* sg = nullptr) {
+    if (df_rhs && sg) matvec_df_staged(Hm, N, y, b, reinterpret_cast<float4*>(r), *sg, flags);
+    else if (df_rhs) matvec_df(Hm, N, y, b, reinterpret_cast<float4*>(r));
     else matvec(Hm, N, y, b);
     for (int it = 0; it < iters; ++it) {
         const double2* rr = b;
