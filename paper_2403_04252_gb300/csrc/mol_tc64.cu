@@ -59,7 +59,7 @@ template <int SL> struct Tc64Cfg {
     static constexpr int DRAIN_WARPS = SL == 7 ? 0 : 4;
     static constexpr int DRAIN0 = PE_WARPS + 2;                  // first drain warp
     static constexpr int THREADS = (PE_WARPS + 2 + DRAIN_WARPS) * 32;
-    static constexpr int SUM_COL = 2 * SL * N;                   // TMEM column of the running sums (hi, then lo)
+    static constexpr int SUM_COL = 2 * ACC * N;                  // TMEM column of the running sums (hi, then lo)
     static constexpr int HALF = N / 2;                           // half columns of a CTA
     // table tiles in flight: four with four slices, two with seven (shared memory)
     static constexpr int TSTAGES = SL == 7 ? 2 : 4;
