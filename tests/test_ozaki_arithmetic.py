@@ -15,7 +15,11 @@ grid per 128-node window; the CUDA kernels are not involved):
 * with three slices (levels 0-2, six products, all exact) the window's dot product errs by less than
   2^-25 of (128 nodes x the largest term), observed up to 2^-27.5: the FP32 level (each operand keeps
   23 bits below its row's window maximum);
-* with four slices (levels 0-3, ten products, all exact: precision mode 3) by less than 2^-31.
+* with four slices (levels 0-3, ten products, all exact: precision mode 3) by less than 2^-31;
+* the four-slice generated operand sliced by grid rounding (from the unnormalised product pair) and the
+  drain's fold with frac(L1) + L2 + L3 rounded once keep that level over a 2304-node rule;
+* the wide MMAs A_i [B_0 .. B_{3-i}] written at accumulator column 48 i land every product on its level,
+  and the four-slice producer's stores fill the 64-byte-swizzled K-major generated tile exactly once.
 """
 from fractions import Fraction
 
@@ -275,3 +279,40 @@ def test_four_slice_fold_with_generated_slices_over_many_windows():
         assert err <= 2.0 ** -27 * scale, seed
         worst = max(worst, err / scale)
     assert worst > 2.0 ** -45   # the truncated levels are really dropped
+
+
+def test_wide_level_mmas_land_each_product_on_its_level():
+    # The four-slice contraction issues, per table slice A_i and K step, one MMA A_i [B_0 .. B_{3-i}] into
+    # accumulator columns 48 i .. 191 (the generated slices lie one after the other).  Emulated with exact
+    # integer arithmetic: column block L then holds sum_{i + j = L} A_i B_j^T, the level sums.
+    rng = np.random.default_rng(31)
+    M, N, K = 8, 48, 16
+    A = [rng.integers(-129, 130, (M, K)) for _ in range(4)]
+    B = [rng.integers(-130, 131, (N, K)) for _ in range(4)]
+    D = np.zeros((M, 4 * N), dtype=np.int64)
+    for i in range(4):
+        Bcat = np.concatenate(B[:4 - i])                 # rows of B_0 .. B_{3-i}: N (4 - i) rows
+        D[:, N * i:N * 4] += A[i] @ Bcat.T
+    for L in range(4):
+        want = sum(A[i] @ B[L - i].T for i in range(L + 1))
+        assert np.array_equal(D[:, N * L:N * (L + 1)], want)
+
+
+def test_generated_tile_store_layout_of_the_four_slice_producer():
+    # Each producer thread (row n, part p) stores nodes 2p, 2p + 1 and 16 + 2p, 17 + 2p of a 32-node chunk as
+    # two 4-byte words at n 64 + ((p >> 2) ^ s) 16 + 4 (p & 3) and n 64 + ((2 + (p >> 2)) ^ s) 16 + 4 (p & 3),
+    # s = (n >> 1) & 3.  Every byte of the 48-row tile is written once, and node m of row n lands where the
+    # 64-byte-swizzled K-major layout the MMA reads puts it: 16-byte chunk (2m / 16) ^ s, byte 2m % 16.
+    owner = {}
+    for n in range(48):
+        s = (n >> 1) & 3
+        for p in range(8):
+            for h, nodes in ((0, (2 * p, 2 * p + 1)), (1, (16 + 2 * p, 17 + 2 * p))):
+                base = n * 64 + (((h * 2 + (p >> 2)) ^ s) << 4) + 4 * (p & 3)
+                for k, m in enumerate(nodes):
+                    for byte in (base + 2 * k, base + 2 * k + 1):
+                        assert byte not in owner
+                        owner[byte] = (n, m)
+                    want = n * 64 + ((((2 * m) // 16) ^ s) << 4) + (2 * m) % 16
+                    assert base + 2 * k == want
+    assert sorted(owner) == list(range(48 * 64))
