@@ -58,7 +58,7 @@ typedef enum {
     WPCCC_ENONFINITE = 4,  /* amplitudes became NaN or infinite during propagation */
     WPCCC_ECUDA = 5,       /* a CUDA runtime call or kernel launch failed */
     WPCCC_EUNSUPPORTED = 6, /* a mode this build does not provide */
-    WPCCC_ETIMEOUT = 7,    /* a bounded wait inside a tensor-core kernel gave up (see wpccc_basis_set_wait_limit);
+    WPCCC_ETIMEOUT = 7,    /* a bounded wait inside a kernel gave up (see wpccc_basis_set_wait_limit);
                               the kernel returned cleanly and the device stays usable */
     WPCCC_ENOCONV = 8      /* the FP64 iterative refinement of a reduced-precision form did not converge (see
                               wpccc_basis_set_refine_tolerance); the amplitudes are returned but not trusted */
@@ -269,7 +269,7 @@ WPCCC_API wpccc_status wpccc_solve(int N, int batch, void* S, void* H, int* ipiv
  * amplitudes at the end.
  * Errors: EINVAL, EUNSUPPORTED, ENOMEM, ESINGULAR (some S had a zero pivot),
  * ENONFINITE (amplitudes became non-finite), ENOCONV (a refined mode's refinement did not converge, see
- * wpccc_basis_set_refine_tolerance), ETIMEOUT (a tensor-core wait gave up), ECUDA.
+ * wpccc_basis_set_refine_tolerance), ETIMEOUT (a bounded wait of a kernel gave up), ECUDA.
  */
 WPCCC_API wpccc_status wpccc_propagate(wpccc_basis basis, const wpccc_paths* paths, int precision_mode,
                              int batch_mode, void* c, void* stream);
@@ -410,11 +410,15 @@ WPCCC_API wpccc_status wpccc_basis_set_refine_iters(wpccc_basis basis, int iters
 WPCCC_API wpccc_status wpccc_basis_set_refine_tolerance(wpccc_basis basis, double tol);
 
 /*
- * Iteration limit of every mbarrier wait in the tensor-core kernels (precision modes 3-5): a wait that has
- * polled `polls` times gives up, the CTA records the failure, lets the copies and tensor-core operations it
- * has in flight complete, frees its tensor memory and returns; the call then reports WPCCC_ETIMEOUT and the
- * device stays usable.  Default 2^20 polls (far longer than any wait of a healthy launch).  A small limit
- * makes the waits run out on purpose, to exercise that path.  Errors: EINVAL (null basis, polls < 1).
+ * Iteration limit of every mbarrier wait in device code: the tensor-core kernels' waits (precision modes 3-5;
+ * the contraction's TMA thread counts polls in which neither of its buffers came free) and the RK4 sweep's
+ * waits for the bulk copies that stage H in shared memory (precision modes 1-3, N <= 512).  A tensor-core
+ * CTA whose wait has polled `polls` times gives up, records the failure, lets the copies and tensor-core
+ * operations it has in flight complete, frees its tensor memory and returns; an RK4 block records the
+ * failure and goes on in step with its other threads, its copies landing before it returns.  The call then
+ * reports WPCCC_ETIMEOUT and the device stays usable.  Default 2^20 polls (far longer than any wait of a
+ * healthy launch).  A small limit makes the waits run out on purpose, to exercise that path.
+ * Errors: EINVAL (null basis, polls < 1).
  */
 #define WPCCC_DEFAULT_WAIT_POLLS (1L << 20)
 WPCCC_API wpccc_status wpccc_basis_set_wait_limit(wpccc_basis basis, long polls);
